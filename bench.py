@@ -1,0 +1,359 @@
+"""Benchmark: half-space Spectral Ewald evaluation on GB300 (arXiv 1802.07844).
+
+One step = one full evaluation through the C ABI (hse_eval): input check,
+cell-list binning and sort, real-space sum, spreading, forward FFTs, k-space
+scaling, inverse FFTs and gather, for the workload
+  stokeslet + rotlet, N = 1M sources = targets, x, y uniform in [0,1),
+  z ~ Exponential(mean 0.05) truncated to (0,1], N(0,1) forces and torques,
+  FP64 path at relative RMS tolerance 1e-10 (plan set-up is not timed, Sec. 7).
+
+Prints one JSON line.  ``value`` is whole-job Mtargets/s with inputs resident
+on the device; ``e2e`` repeats the measurement with host inputs copied in and
+velocities copied out inside the timed region.  ``--impl reference`` times the
+FP64 CPU direct-sum oracle on a bounded target sample of the same workload.
+Multi-GPU: independent replicas (one per rank), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import KERNEL_S, KERNEL_W, problem  # noqa: E402
+
+WORKLOAD = dict(
+    name="hs_stokeslet_rotlet_n1m_nearwall",
+    mask=KERNEL_S | KERNEL_W, n=1_000_000, dist="near_wall", index=2, tol=1e-10,
+    # parameters checked against the FP64 oracle on a target sample (tests/test_gpu_parity.py)
+    xi=90.0, rc=0.0572, P=18, M=304,
+)
+METRIC = "Mtargets/s, N=1M stokeslet @1e-10 FP64 vs 1e-5 mixed; serve p50/p99 ms"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Algorithmic FP64 work per real-space pair (stokeslet + rotlet), counted from the
+# written formulas of the pair evaluation, with erfc, exp and the reciprocal
+# square root charged 60 flops together.
+FLOPS_FREE_PAIR = 57 + 60
+FLOPS_IMAGE_PAIR = 125 + 60
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "power_w_max": float(max(power)) if power else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- CPU oracle
+def time_oracle(pr, mask, budget_s: float, start_targets: int = 16):
+    """Times the FP64 direct-sum oracle on a growing seeded sample of targets
+    until about ``budget_s`` seconds of work; returns (targets/s, sample, cores)."""
+    import oracle
+    n = pr.src.shape[1]
+    rng = np.random.default_rng(1802078440 + 99)
+    k = start_targets
+    t_used = 0.0
+    while True:
+        idx = np.sort(rng.choice(n, size=min(k, n), replace=False))
+        t0 = time.perf_counter()
+        oracle.direct(mask, pr.src, pr.strengths, pr.src[:, idx])
+        dt = time.perf_counter() - t0
+        t_used += dt
+        if dt > 0.25 * budget_s or k >= n or t_used > budget_s:
+            return len(idx) / dt, len(idx), dt
+        k = int(min(n, max(2 * k, k * 0.5 * budget_s / max(dt, 1e-3))))
+
+
+# ------------------------------------------------------------ main arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1802_07844_gb300 as pkg
+    from paper_1802_07844_gb300 import build
+    build.build_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    W = dict(WORKLOAD)
+    if args.n:
+        W["n"] = args.n
+    mask = W["mask"]
+    pr = problem(mask, W["n"], 1.0, W["dist"], W["index"], sub=rank)
+    if args.real_only:
+        return run_real_only(args, pkg, torch, dev, W, pr)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
+    plan.set_timing(True)
+    prm = plan.params
+    src = torch.from_numpy(pr.src).to(dev)
+    st = torch.from_numpy(pr.strengths).to(dev)
+    vel = torch.empty((3, W["n"]), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)  # 512 MB > L2
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.eval(src, st, out=vel)
+    torch.cuda.synchronize()
+    # exact pair counts of the real-space stage (untimed)
+    a, b = plan.neighbor_counts(src)
+    n_free, n_img = int(a.sum().item()), int(b.sum().item())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    stages = {k: [] for k in pkg.hse.STAGE_NAMES}
+    launches = 0
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.eval(src, st, out=vel)
+        ev[i][1].record(stream)
+        s = plan.stats()
+        launches += s["n_kernel_launches"]
+        for k, v in s["stage_ms"].items():
+            stages[k].append(v)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    ms_step = total_ms / args.steps
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_step_max = float(t.item())
+    value = W["n"] * world / (ms_step_max / 1e3) / 1e6
+
+    # end-to-end: pinned host inputs in, velocities out, inside the timed region
+    h_src = torch.from_numpy(pr.src).pin_memory()
+    h_st = torch.from_numpy(pr.strengths).pin_memory()
+    h_vel = torch.empty((3, W["n"]), dtype=torch.float64).pin_memory()
+    d_src = torch.empty_like(src)
+    d_st = torch.empty_like(st)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e_ms = 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        e0.record(stream)
+        d_src.copy_(h_src, non_blocking=True)
+        d_st.copy_(h_st, non_blocking=True)
+        plan.eval(d_src, d_st, out=vel)
+        h_vel.copy_(vel, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e_ms += e0.elapsed_time(e1)
+    e_ms /= e2e_steps
+    t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = W["n"] * world / (float(t.item()) / 1e3) / 1e6
+    h2d = h_src.numel() * 8 + h_st.numel() * 8
+    d2h = h_vel.numel() * 8
+
+    # roofline of the dominant kernel of this library
+    avg = {k: float(np.mean(v)) if v else 0.0 for k, v in stages.items()}
+    own = {k: avg[k] for k in ("real", "spread", "scale", "gather")}
+    dom = max(own, key=own.get)
+    P, Mt, nc = prm["P"], prm["Mt"], prm["n_fft_in"]
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if dom == "real":
+        work = n_free * FLOPS_FREE_PAIR + n_img * FLOPS_IMAGE_PAIR
+        roof = {"kernel": "k_real", "bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 units x clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "achieved": work / (avg["real"] / 1e3) / 1e12,
+                "work": {"free_pairs": n_free, "image_pairs": n_img, "flops_per_free_pair": FLOPS_FREE_PAIR,
+                         "flops_per_image_pair": FLOPS_IMAGE_PAIR}}
+    elif dom in ("spread", "gather"):
+        per = P ** 3 * (2 * nc + 2) if dom == "spread" else P ** 3 * 12
+        work = W["n"] * per
+        roof = {"kernel": "k_" + dom, "bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 units x clock", "achieved": work / (avg[dom] / 1e3) / 1e12}
+    else:
+        nh = (2 * Mt) * (2 * Mt) * (2 * Mt + 1)
+        byts = (nc + 6) * nh * 16 + nh * 8 * 2
+        roof = {"kernel": "k_scale", "bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs", "achieved": byts / (avg["scale"] / 1e3) / 1e9}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["stage_ms"] = {k: round(v, 3) for k, v in avg.items()}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["name"], "n_sources": W["n"], "n_targets": W["n"], "kernels": "stokeslet+rotlet",
+                   "distribution": "x,y ~ U[0,1), z ~ TruncExp(0.05) on (0,1]", "tol": W["tol"],
+                   "precision": "fp64", "xi": prm["xi"], "rc": prm["rc"], "P": P, "M": prm["M"], "Mt": Mt,
+                   "fft_in": nc, "fft_out": prm["n_fft_out"], "parallelism": f"replicas x{world}",
+                   "l2": "512 MB buffer written between timed steps"},
+        "e2e": {"value": e2e_value, "unit": "Mtargets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tps, k, dt = time_oracle(pr, mask, args.cpu_budget)
+        out["cpu_baseline"] = {"value": tps / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"{k} seeded targets of the same workload against all {W['n']} sources "
+                                         f"(FP64 direct half-space sum, OpenMP), {dt:.1f} s"}
+    plan.close()
+    return out
+
+
+def run_real_only(args, pkg, torch, dev, W, pr):
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0)
+    src = torch.from_numpy(pr.src).to(dev)
+    st = torch.from_numpy(pr.strengths).to(dev)
+    for _ in range(args.warmup):
+        plan.eval_parts(src, st, fourier=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.eval_parts(src, st, fourier=False)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    plan.close()
+    return {"profiling_run": "real-space half only", "n": W["n"], "ms_per_step": dt * 1e3}
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args):
+    W = dict(WORKLOAD)
+    if args.n:
+        W["n"] = args.n
+    mask = W["mask"]
+    pr = problem(mask, W["n"], 1.0, W["dist"], W["index"])
+    import oracle
+    oracle.build()
+    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    tps, k, _ = time_oracle(pr, mask, budget)  # sizes the per-step sample
+    rng = np.random.default_rng(1802078440 + 98)
+    for _ in range(args.warmup):
+        idx = np.sort(rng.choice(W["n"], size=k, replace=False))
+        oracle.direct(mask, pr.src, pr.strengths, pr.src[:, idx])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        idx = np.sort(rng.choice(W["n"], size=k, replace=False))
+        oracle.direct(mask, pr.src, pr.strengths, pr.src[:, idx])
+    dt = (time.perf_counter() - t0) / args.steps
+    value = k / dt / 1e6
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mtargets/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["name"], "n_sources": W["n"], "targets_per_step": k, "kernels": "stokeslet+rotlet",
+                   "tol": W["tol"], "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{k} seeded targets per step against all {W['n']} sources"},
+        "e2e": {"value": value, "unit": "Mtargets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=0, help="override the number of sources (smaller test runs)")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--real-only", action="store_true",
+                    help="profiling aid: plan without a grid, time only the real-space half")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * hse.h -- C ABI of the GB300 (sm_103a) half-space Spectral Ewald library.
+ *
+ * Computes, on one GPU, the sums of Stokes singularities above a no-slip wall
+ * at x3 = 0 in the image representation of Srinivasan & Tornberg (arXiv
+ * 1802.07844, Sec. 3, eq. v_sum_halfspace): for every target x
+ *
+ *   stokeslet  u += S(r) f - S(rt) f^I - x3 grad(phi_S) + e3 phi_S
+ *   stresslet  u += T(r)(g q) - T(rt)(g^I q^I) - x3 grad(phi_T) + e3 phi_T
+ *   rotlet     u += W(r) tau + W(rt) tau^I - x3 grad(phi_W) + e3 phi_W
+ *
+ * summed over all sources y (r = x - y, rt = x - y^I, y^I = (y1, y2, -y3)),
+ * with the Ewald split of Sec. 4 (real-space erfc-screened neighbour sum within
+ * r_c over sources and images, Sec. 5.1) and the Fourier-space Spectral Ewald
+ * part of Alg. 1 (Gaussian spreading, zero-padded FFT, scaling by the truncated
+ * kernels of Sec. 5.2, inverse FFT, Gaussian quadrature).
+ *
+ * Units: velocities are returned in "8 pi units", i.e. 8*pi times the physical
+ * velocity at unit viscosity, with S(r) f = f/r + r (r.f)/r^3,
+ * T(r)(g q) = -6 r (r.g)(r.q)/r^5 and W(r) tau = 2 tau x r / r^3.
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller, in
+ * component-major ("SoA") layout: an array "3 x n" holds x[0..n), y[n..2n),
+ * z[2n..3n).  The plan owns all of its own device memory (grids, tables,
+ * cell lists, cuFFT plans and work areas).  Calls are asynchronous on the
+ * given CUDA stream except where stated; no caller memory is touched after
+ * the stream work of a call completes.  A plan is not re-entrant: use one
+ * plan per concurrent stream.
+ *
+ * Errors: status codes only; no exceptions cross this ABI and nothing exits.
+ * hse_last_error() gives the text of the last failure of a plan.
+ */
+#ifndef HSE_H
+#define HSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hse_plan_s* hse_plan;
+
+typedef enum {
+  HSE_OK = 0,
+  HSE_ERR_INVALID = 1,     /* argument or input data out of the documented domain */
+  HSE_ERR_OOM = 2,         /* a device allocation failed                          */
+  HSE_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed         */
+  HSE_ERR_CUFFT = 4,       /* a cuFFT call failed                                 */
+  HSE_ERR_TIMEOUT = 5,     /* a bounded wait ran out                              */
+  HSE_ERR_UNSUPPORTED = 6  /* valid request this build does not support           */
+} hse_status;
+
+/* kernel bit mask; several bits may be combined, the sums are added */
+enum { HSE_STOKESLET = 1, HSE_STRESSLET = 2, HSE_ROTLET = 4 };
+/* arithmetic of the path: HSE_FP64 everywhere (for tolerances down to 1e-10),
+ * HSE_MIXED: FP32 real space, spreading, FFT and gather (tolerances >= 1e-6) */
+enum { HSE_FP64 = 0, HSE_MIXED = 1 };
+
+/* Parameters of a plan, as chosen or given (Alg. 1 notation). */
+typedef struct {
+  int kernel_mask;
+  int precision;
+  double box[3];     /* L1, L2, L3 of the source box [0,L1) x [0,L2) x (0,L3]    */
+  double L;          /* max(L1, L2, L3): side of the cubic Fourier domain         */
+  double xi;         /* Ewald parameter                                            */
+  double rc;         /* real-space cut-off radius                                  */
+  int P;             /* Gaussian support width in grid points (even)               */
+  int M;             /* basic grid size, h = L / M                                 */
+  int Mt;            /* extended grid size M + P; grid Mt x Mt x 2 Mt              */
+  double h;          /* grid spacing                                               */
+  double eta;        /* Gaussian shape parameter P xi^2 h^2 / (c^2 pi), c = 0.95  */
+  int ncell[3];      /* real-space cell list dimensions (cell side >= rc)          */
+  int n_fft_in;      /* number of forward FFTs per evaluation                      */
+  int n_fft_out;     /* number of inverse FFTs per evaluation (6)                  */
+  size_t grid_bytes; /* device bytes held by grids and tables                      */
+} hse_params;
+
+/*
+ * hse_plan_create -- choose parameters and build the Fourier-space machinery.
+ *   kernel_mask  HSE_STOKESLET | HSE_STRESSLET | HSE_ROTLET (non-zero).
+ *   box          host array {L1, L2, L3} > 0; sources must lie in
+ *                [0,L1) x [0,L2) x (0,L3], targets in [0,L1) x [0,L2) x [0,L3].
+ *   xi, rc, P    Ewald parameter, cut-off radius, support width; a value <= 0
+ *                is chosen from tol (tol must then be > 0).  P is rounded up
+ *                to an even number.
+ *   tol          target relative RMS error (Sec. 6 definition); used to pick
+ *                missing parameters and the grid size M (Tables 2-3 estimates).
+ *                With tol <= 0 all of xi, rc, P must be given and M is set
+ *                with hse_plan_set_grid before the first evaluation.
+ *   precision    HSE_FP64 or HSE_MIXED.
+ *   out          receives the plan (host pointer).
+ * Builds the truncated-kernel tables of Sec. 5.2 on the device (untimed
+ * set-up work, synchronous).  Errors: HSE_ERR_INVALID, HSE_ERR_OOM,
+ * HSE_ERR_CUDA, HSE_ERR_CUFFT.  On error *out is NULL.
+ */
+hse_status hse_plan_create(int kernel_mask, const double box[3], double xi, double rc, int P, double tol,
+                           int precision, hse_plan* out);
+
+/* Set the basic grid size M explicitly (h = L/M) and rebuild the grids and
+ * tables (synchronous).  HSE_ERR_INVALID if M < 4 or the Gaussian shape
+ * parameter eta falls outside (0, 1). */
+hse_status hse_plan_set_grid(hse_plan plan, int M);
+
+/* Copy the plan's parameters to *out (host). */
+hse_status hse_plan_get_params(hse_plan plan, hse_params* out);
+
+/*
+ * hse_eval -- velocities at the targets.
+ *   n_src      number of sources (>= 0).
+ *   src_xyz    device, 3 x n_src positions.
+ *   strengths  device, rows stacked in the kernel order of the mask:
+ *              stokeslet f (3 rows), stresslet g then q (6 rows), rotlet tau
+ *              (3 rows); each row has n_src entries.
+ *   n_tgt      number of targets; tgt_xyz == NULL means the targets are the
+ *              sources (then n_tgt must equal n_src) and the pair of a target
+ *              with its own source is excluded from the free-space term
+ *              (Sec. 2).  With explicit targets, pairs at exactly zero
+ *              separation are excluded in the same way.
+ *   vel        device, 3 x n_tgt, overwritten.
+ *   cuda_stream  cudaStream_t (NULL = legacy default stream).
+ * The input check (finite values inside the box, sources strictly above the
+ * wall) synchronises the stream once.  Errors: HSE_ERR_INVALID (bad input;
+ * vel is then unspecified), HSE_ERR_OOM, HSE_ERR_CUDA, HSE_ERR_CUFFT.
+ */
+hse_status hse_eval(hse_plan plan, int64_t n_src, const double* src_xyz, const double* strengths, int64_t n_tgt,
+                    const double* tgt_xyz, double* vel, void* cuda_stream);
+
+/*
+ * hse_eval_parts -- as hse_eval, but returns the two halves of the split
+ * separately (Sec. 4): u_real = real-space sum within r_c plus the stokeslet
+ * self term, u_fourier = Fourier-space part (Alg. 1).  Either output pointer
+ * may be NULL to skip that half; the real-space half alone needs no grid
+ * (a plan created with tol <= 0 and no hse_plan_set_grid).  Same arguments
+ * and errors as hse_eval.
+ */
+hse_status hse_eval_parts(hse_plan plan, int64_t n_src, const double* src_xyz, const double* strengths,
+                          int64_t n_tgt, const double* tgt_xyz, double* u_real, double* u_fourier,
+                          void* cuda_stream);
+
+/*
+ * hse_cell_list -- the real-space cell list of the plan's box (Sec. 5.1).
+ *   pos        device, 3 x n positions.
+ *   cell_id    device, n int32: cell of each point,
+ *              c_d = clamp(floor((x_d - 0) * (1/cell_d)), 0, ncell_d - 1),
+ *              id = (c_z ncell_y + c_y) ncell_x + c_x.
+ *   perm       device, n int32: point indices sorted by (cell id, index).
+ *   cell_start device, ncell_x ncell_y ncell_z + 1 int32: first position in
+ *              perm of each cell; the last entry is n.
+ * Integer results; identical to a sequential stable counting sort.
+ */
+hse_status hse_cell_list(hse_plan plan, int64_t n, const double* pos, int32_t* cell_id, int32_t* perm,
+                         int32_t* cell_start, void* cuda_stream);
+
+/*
+ * hse_neighbor_counts -- per target, the number of free-space pairs and of
+ * image pairs inside the cut-off (|d|^2 < r_c^2 with the squared distance
+ * formed as ((dx*dx) + (dy*dy)) + (dz*dz) in FP64 without contraction), the
+ * same decision the real-space sum takes.  tgt_xyz == NULL: targets are the
+ * sources and the self pair is not counted.  n_pairs, n_images: device,
+ * n_tgt int32 each.
+ */
+hse_status hse_neighbor_counts(hse_plan plan, int64_t n_src, const double* src_xyz, int64_t n_tgt,
+                               const double* tgt_xyz, int32_t* n_pairs, int32_t* n_images, void* cuda_stream);
+
+/*
+ * hse_spread_grids -- the spread grids of Alg. 1 step 5 on the Mt x Mt x 2 Mt
+ * grid (z fastest), in the component order: per kernel in the order S, T, W,
+ *   S: C1 (3), C2 = f3 (1), C3 = y3 f^I (3)
+ *   T: C1 = sym(g q) (6: xx xy xz yy yz zz), C2 = g.q (1), C3 = y3 sym(g^I q^I) (6)
+ *   W: C1 = tau (3), C2 = (-tau2, tau1) (2)
+ * C1 holds the sources and their images, C2/C3 the images only.  Grid point
+ * (i, j, k) sits at (-P h/2 + i h, -P h/2 + j h, -Mt h + k h).
+ * grids: device, n_comp x Mt x Mt x 2 Mt doubles; *n_comp receives the count
+ * (pass grids = NULL to query it).  Diagnostic entry point (slow path).
+ */
+hse_status hse_spread_grids(hse_plan plan, int64_t n_src, const double* src_xyz, const double* strengths,
+                            double* grids, int* n_comp, void* cuda_stream);
+
+/* Stages of one evaluation, in order (the phases of Sec. 7, Fig. 6). */
+enum {
+  HSE_STAGE_CHECK = 0,     /* input check (one stream synchronisation)        */
+  HSE_STAGE_CELLS = 1,     /* binning, stable sort, cell starts, sorted copy   */
+  HSE_STAGE_REAL = 2,      /* real-space neighbour sum and self term           */
+  HSE_STAGE_SPREAD = 3,    /* window factors, spreading, image mirror (step 5) */
+  HSE_STAGE_FFT = 4,       /* forward zero-padded FFTs (step 6)                */
+  HSE_STAGE_SCALE = 5,     /* k-space scaling (steps 7-8)                      */
+  HSE_STAGE_IFFT = 6,      /* inverse FFTs (step 9)                            */
+  HSE_STAGE_GATHER = 7,    /* quadrature at the targets (step 10)              */
+  HSE_N_STAGES = 8
+};
+
+typedef struct {
+  int n_kernel_launches;            /* kernels of this library launched by the last evaluation */
+  int n_fft_execs;                  /* cuFFT executions of the last evaluation                  */
+  int timing;                       /* 1 when stage_ms is valid                                 */
+  double stage_ms[HSE_N_STAGES];    /* device time of each stage (CUDA events on the stream)   */
+} hse_eval_stats;
+
+/* Enable (1) or disable (0) CUDA-event timing of the stages of hse_eval and
+ * hse_eval_parts.  Timing adds one event record per stage on the stream. */
+hse_status hse_plan_set_timing(hse_plan plan, int enable);
+
+/* Statistics of the last evaluation (synchronises on its last event when
+ * timing is on).  out: host pointer. */
+hse_status hse_get_eval_stats(hse_plan plan, hse_eval_stats* out);
+
+/* Release all device memory and cuFFT plans of the plan (synchronises). */
+hse_status hse_plan_destroy(hse_plan plan);
+
+/* Static text of a status code. */
+const char* hse_status_string(hse_status status);
+
+/* Text of the last failure of a plan (valid until the next call on the plan);
+ * "" when none.  A NULL plan gives the last failure of hse_plan_create. */
+const char* hse_last_error(hse_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSE_H */

@@ -1,0 +1,556 @@
+// hse_fourier.cu -- Fourier-space part of the half-space Spectral Ewald method
+// (Alg. 1, steps 5-10; Sec. 5.2).
+//
+//  prep    per source: support start (ix0, iy0, iz0), the 1-D Gaussian factors
+//          of the window (2 xi^2/(pi eta))^{3/2} exp(-2 xi^2 |x - z|^2 / eta)
+//          and the strength of every spread component;
+//  spread  owner-computes tiles: each thread owns one grid point and sums the
+//          windows of the cell-listed sources whose P^3 support covers it.
+//          Everything is accumulated at the SOURCE position: an image's window
+//          is the mirror (k -> 2 Mt - k) of its source's window, so
+//  mirror  forms C1 = A(k) +- A(2Mt - k) and the image-only corrections
+//          C(k) = A(2Mt - k) in place;
+//  FFT     zero-padded by 2 in every direction (cuFFT D2Z, in place);
+//  scale   per wave vector k: T1^ = K^_F C1^ + e3 phi^, T2^ = i k phi^ with
+//          phi^ = E H^R (Cs^ + i k.Cv^ + k.Ct^.k) (the merged harmonic
+//          corrections), stokeslet A^S = -(k^2 I - k k), stresslet A^T,
+//          rotlet A^W = -2 i eps k, tables including exp(-(1-eta)k^2/4xi^2);
+//  IFFT    cuFFT Z2D of the 6 fields T1, T2;
+//  gather  u_F(x) = h^3 sum over the P^3 support of W(x - x_j) (T1 - x3 T2).
+#include "hse_internal.cuh"
+
+namespace hse {
+
+// ----------------------------------------------------------------------- prep
+struct PrepArgs {
+  int64_t n;
+  const double* spos;
+  const double* sstr;
+  int rowS, rowT, rowW, mask;
+  int paper;  // component set: 0 product (merged corrections), 1 paper (C1/C2/C3 per kernel)
+  int P, Mt;
+  double h, ox, oz, alpha, pre;
+  int stride;
+  double* prep;
+  int4* supp;
+};
+
+__global__ void k_prep(PrepArgs a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = a.n;
+    double x = a.spos[i], y = a.spos[n + i], z = a.spos[2 * n + i];
+    int ix0 = support_start(x, a.ox, a.h, a.P, a.Mt);
+    int iy0 = support_start(y, a.ox, a.h, a.P, a.Mt);
+    int iz0 = support_start(z, a.oz, a.h, a.P, 2 * a.Mt);
+    a.supp[i] = make_int4(ix0, iy0, iz0, 0);
+    double* o = a.prep + i * (int64_t)a.stride;
+    for (int t = 0; t < a.P; ++t) {
+      double dx = a.ox + (ix0 + t) * a.h - x;
+      double dy = a.ox + (iy0 + t) * a.h - y;
+      double dz = a.oz + (iz0 + t) * a.h - z;
+      o[t] = a.pre * exp(-a.alpha * dx * dx);
+      o[a.P + t] = exp(-a.alpha * dy * dy);
+      o[2 * a.P + t] = exp(-a.alpha * dz * dz);
+    }
+    double* c = o + 3 * a.P;
+    int k = 0;
+    double f[3] = {0, 0, 0}, g[3] = {0, 0, 0}, q[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
+    if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) f[d] = a.sstr[(a.rowS + d) * n + i];
+    if (a.mask & HSE_STRESSLET)
+      for (int d = 0; d < 3; ++d) { g[d] = a.sstr[(a.rowT + d) * n + i]; q[d] = a.sstr[(a.rowT + 3 + d) * n + i]; }
+    if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) tau[d] = a.sstr[(a.rowW + d) * n + i];
+    const double hz = z;  // source height y3
+    double gI[3] = {g[0], g[1], -g[2]}, qI[3] = {q[0], q[1], -q[2]};
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+    double sgq[6], sgqI[6];
+    for (int m = 0; m < 6; ++m) {
+      sgq[m] = 0.5 * (g[ia[m]] * q[ib[m]] + g[ib[m]] * q[ia[m]]);
+      sgqI[m] = 0.5 * (gI[ia[m]] * qI[ib[m]] + gI[ib[m]] * qI[ia[m]]);
+    }
+    double gdq = g[0] * q[0] + g[1] * q[1] + g[2] * q[2];
+    if (!a.paper) {
+      if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) c[k++] = f[d];
+      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = sgq[m];
+      if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = tau[d];
+      if (a.mask & HSE_STOKESLET) c[k++] = -2.0 * f[2];
+      double cv[3] = {0, 0, 0};
+      if (a.mask & HSE_STOKESLET) { cv[0] += -2.0 * hz * f[0]; cv[1] += -2.0 * hz * f[1]; cv[2] += 2.0 * hz * f[2]; }
+      if (a.mask & HSE_STRESSLET) cv[2] += 4.0 * gdq;
+      if (a.mask & HSE_ROTLET) { cv[0] += -4.0 * tau[1]; cv[1] += 4.0 * tau[0]; }
+      for (int d = 0; d < 3; ++d) c[k++] = cv[d];
+      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = 4.0 * hz * sgqI[m];
+    } else {
+      if (a.mask & HSE_STOKESLET) {
+        for (int d = 0; d < 3; ++d) c[k++] = f[d];
+        c[k++] = f[2];
+        c[k++] = hz * f[0]; c[k++] = hz * f[1]; c[k++] = -hz * f[2];
+      }
+      if (a.mask & HSE_STRESSLET) {
+        for (int m = 0; m < 6; ++m) c[k++] = sgq[m];
+        c[k++] = gdq;
+        for (int m = 0; m < 6; ++m) c[k++] = hz * sgqI[m];
+      }
+      if (a.mask & HSE_ROTLET) {
+        for (int d = 0; d < 3; ++d) c[k++] = tau[d];
+        c[k++] = -tau[1]; c[k++] = tau[0];
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------- spread
+struct SpreadArgs {
+  const int4* supp;
+  const double* prep;
+  const int32_t* cstart;
+  int stride, P, Mt, z0, nz_tiles;
+  double h, ox, oz;
+  double inv_cell[3];
+  int ncell[3];
+  double* out;           // component c, point (i,j,k) at out + c*cs + i*xs + j*pitch + k
+  int64_t cs, xs, pitch;
+};
+
+constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
+  __shared__ int list[256];
+  __shared__ int wcount[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int bx0 = kTX * blockIdx.x, by0 = kTY * blockIdx.y, bz0 = a.z0 + kTZ * blockIdx.z;
+  const int sx = bx0 + 2 * (w & 1), sy = by0 + 4 * ((w >> 1) & 1), sz = bz0 + 4 * (w >> 2);
+  const int px = sx + (lane & 1), py = sy + ((lane >> 1) & 3), pz = sz + (lane >> 3);
+  const int P = a.P;
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  // positions whose support can reach this tile (one grid step of slack for clamping)
+  auto cell_range = [&](int lo_idx, int hi_idx, double o, int d, int& c0, int& c1) {
+    double lo = o + (lo_idx - P / 2 - 1) * a.h, hi = o + (hi_idx + P / 2 + 1) * a.h;
+    c0 = cell_coord(lo, a.inv_cell[d], a.ncell[d]);
+    c1 = cell_coord(hi, a.inv_cell[d], a.ncell[d]);
+  };
+  int cx0, cx1, cy0, cy1, cz0, cz1;
+  cell_range(bx0, bx0 + kTX - 1, a.ox, 0, cx0, cx1);
+  cell_range(by0, by0 + kTY - 1, a.ox, 1, cy0, cy1);
+  cell_range(bz0, bz0 + kTZ - 1, a.oz, 2, cz0, cz1);
+  const int nx = a.ncell[0], ny = a.ncell[1];
+  for (int cz = cz0; cz <= cz1; ++cz)
+    for (int cy = cy0; cy <= cy1; ++cy) {
+      int c0 = (cz * ny + cy) * nx + cx0;
+      int s0 = a.cstart[c0], s1 = a.cstart[c0 + (cx1 - cx0) + 1];
+      for (int base = s0; base < s1; base += 256) {
+        int j = base + tid;
+        bool hit = false;
+        if (j < s1) {
+          int4 s = a.supp[j];
+          hit = s.x <= bx0 + kTX - 1 && s.x + P - 1 >= bx0 && s.y <= by0 + kTY - 1 && s.y + P - 1 >= by0 &&
+                s.z <= bz0 + kTZ - 1 && s.z + P - 1 >= bz0;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcount[w] = __popc(m);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int ww = 0; ww < 8; ++ww) { off += ww < w ? wcount[ww] : 0; tot += wcount[ww]; }
+        if (hit) list[off + __popc(m & ((1u << lane) - 1))] = j;
+        __syncthreads();
+        for (int e = 0; e < tot; ++e) {
+          int jj = list[e];
+          int4 s = a.supp[jj];
+          bool warp_hit = s.x <= sx + 1 && s.x + P - 1 >= sx && s.y <= sy + 3 && s.y + P - 1 >= sy &&
+                          s.z <= sz + 3 && s.z + P - 1 >= sz;
+          if (!warp_hit) continue;
+          int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
+          if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
+            const double* o = a.prep + (int64_t)jj * a.stride;
+            double wv = o[dx] * o[P + dy] * o[2 * P + dz];
+            const double* cv = o + 3 * P;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] += wv * cv[c];
+          }
+        }
+        __syncthreads();
+      }
+    }
+  if (px < a.Mt && py < a.Mt && pz < 2 * a.Mt) {
+    double* dst = a.out + px * a.xs + py * a.pitch + pz;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) dst[c * a.cs] = acc[c];
+  }
+}
+
+template <int NC>
+static void launch_spread_t(const SpreadArgs& a, dim3 grid, cudaStream_t s) {
+  k_spread<NC><<<grid, 256, 0, s>>>(a);
+}
+
+static bool launch_spread(int nc, const SpreadArgs& a, dim3 grid, cudaStream_t s) {
+  switch (nc) {
+    case 5: launch_spread_t<5>(a, grid, s); return true;
+    case 6: launch_spread_t<6>(a, grid, s); return true;
+    case 7: launch_spread_t<7>(a, grid, s); return true;
+    case 10: launch_spread_t<10>(a, grid, s); return true;
+    case 12: launch_spread_t<12>(a, grid, s); return true;
+    case 13: launch_spread_t<13>(a, grid, s); return true;
+    case 15: launch_spread_t<15>(a, grid, s); return true;
+    case 18: launch_spread_t<18>(a, grid, s); return true;
+    case 19: launch_spread_t<19>(a, grid, s); return true;
+    case 20: launch_spread_t<20>(a, grid, s); return true;
+    case 22: launch_spread_t<22>(a, grid, s); return true;
+    case 25: launch_spread_t<25>(a, grid, s); return true;
+  }
+  return false;
+}
+
+// --------------------------------------------------------------------- mirror
+struct MirrorArgs {
+  double* buf;
+  int64_t cs, xs, pitch;
+  int Mt, nc;
+  int sign[kMaxComp];
+};
+
+__global__ void k_mirror(MirrorArgs a) {
+  const int Mt = a.Mt;
+  const int64_t per = (int64_t)Mt * Mt * (Mt + 1);
+  const int64_t total = per * a.nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(e / per);
+    int64_t r = e - c * per;
+    int k = (int)(r % (Mt + 1));
+    int64_t ij = r / (Mt + 1);
+    int j = (int)(ij % Mt), i = (int)(ij / Mt);
+    double* col = a.buf + c * a.cs + i * a.xs + j * a.pitch;
+    int kp = 2 * Mt - k;
+    double va = col[k];
+    double vb = kp < 2 * Mt ? col[kp] : 0.0;
+    int s = a.sign[c];
+    if (s != 0) {
+      col[k] = va + s * vb;
+      if (kp < 2 * Mt && kp != k) col[kp] = vb + s * va;
+    } else {
+      col[k] = vb;
+      if (kp < 2 * Mt && kp != k) col[kp] = va;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------- scale
+struct ScaleArgs {
+  double2* buf;           // complex view of the spectra
+  int64_t cstride;        // complex elements per buffer
+  int Mt, mask;
+  double h;
+  const double* tabB;
+  const double* tabH;
+  int iS, iT, iW, iCs, iCv, iCt;  // first component index of each group, -1 if absent
+};
+
+__device__ __forceinline__ double2 cmul_i(double2 z) { return make_double2(-z.y, z.x); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cscale(double s, double2 z) { return make_double2(s * z.x, s * z.y); }
+
+__global__ void k_scale(ScaleArgs a) {
+  const int Mt = a.Mt, Nx = 2 * Mt, Ny = 2 * Mt, Nzh = 2 * Mt + 1;
+  const int64_t nh = (int64_t)Nx * Ny * Nzh;
+  const double dkx = 2.0 * kPi / (Nx * a.h), dkz = 2.0 * kPi / (4.0 * Mt * a.h);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nh; e += (int64_t)gridDim.x * blockDim.x) {
+    int jz = (int)(e % Nzh);
+    int64_t t = e / Nzh;
+    int iy = (int)(t % Ny), ix = (int)(t / Ny);
+    double2 T1[3], T2[3];
+    if (ix == Mt || iy == Mt || jz == 2 * Mt) {  // Nyquist modes are dropped
+      for (int d = 0; d < 3; ++d) T1[d] = T2[d] = make_double2(0.0, 0.0);
+    } else {
+      int wx = ix <= Mt ? ix : ix - Nx, wy = iy <= Mt ? iy : iy - Ny;
+      double k[3] = {dkx * wx, dkx * wy, dkz * jz};
+      double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+      int64_t ti = ((int64_t)abs(wx) * (Mt + 1) + abs(wy)) * Nzh + jz;
+      double TH = a.tabH[ti];
+      double TB = a.tabB ? a.tabB[ti] : 0.0;
+      for (int d = 0; d < 3; ++d) T1[d] = make_double2(0.0, 0.0);
+      auto ld = [&](int c) { return a.buf[c * a.cstride + e]; };
+      if (a.iS >= 0) {  // -(k^2 I - k k) (1 + k^2/4xi^2) E B^R C1
+        double2 C[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
+        double2 kc = cadd(cadd(cscale(k[0], C[0]), cscale(k[1], C[1])), cscale(k[2], C[2]));
+        for (int d = 0; d < 3; ++d)
+          T1[d] = cadd(T1[d], cscale(-TB, cadd(cscale(k2, C[d]), cscale(-k[d], kc))));
+      }
+      if (a.iT >= 0) {  // -i (1 + k^2/4xi^2) E B^R [(k d + k d + k d) k^2 - 2 k k k] : C
+        double2 c6[6];
+        for (int m = 0; m < 6; ++m) c6[m] = ld(a.iT + m);
+        const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+        double2 Ck[3], tr = cadd(cadd(c6[0], c6[3]), c6[5]);
+        for (int j = 0; j < 3; ++j) {
+          Ck[j] = make_double2(0.0, 0.0);
+          for (int m = 0; m < 3; ++m) Ck[j] = cadd(Ck[j], cscale(k[m], c6[sidx[j][m]]));
+        }
+        double2 kCk = cadd(cadd(cscale(k[0], Ck[0]), cscale(k[1], Ck[1])), cscale(k[2], Ck[2]));
+        for (int j = 0; j < 3; ++j) {
+          double2 v = cadd(cscale(k2, cadd(cscale(2.0, Ck[j]), cscale(k[j], tr))), cscale(-2.0 * k[j], kCk));
+          T1[j] = cadd(T1[j], cscale(-TB, cmul_i(v)));
+        }
+      }
+      if (a.iW >= 0) {  // -2 i E H^R (C x k)
+        double2 C[3] = {ld(a.iW), ld(a.iW + 1), ld(a.iW + 2)};
+        double2 cr[3] = {cadd(cscale(k[2], C[1]), cscale(-k[1], C[2])), cadd(cscale(k[0], C[2]), cscale(-k[2], C[0])),
+                         cadd(cscale(k[1], C[0]), cscale(-k[0], C[1]))};
+        for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale(-2.0 * TH, cmul_i(cr[d])));
+      }
+      // merged harmonic corrections: phi^ = E H^R (Cs^ + i k.Cv^ + k.Ct^.k)
+      double2 ph = make_double2(0.0, 0.0);
+      if (a.iCs >= 0) ph = ld(a.iCs);
+      {
+        double2 v[3] = {ld(a.iCv), ld(a.iCv + 1), ld(a.iCv + 2)};
+        double2 kv = cadd(cadd(cscale(k[0], v[0]), cscale(k[1], v[1])), cscale(k[2], v[2]));
+        ph = cadd(ph, cmul_i(kv));
+      }
+      if (a.iCt >= 0) {
+        double2 c6[6];
+        for (int m = 0; m < 6; ++m) c6[m] = ld(a.iCt + m);
+        double2 kck = cadd(cadd(cscale(k[0] * k[0], c6[0]), cscale(k[1] * k[1], c6[3])), cscale(k[2] * k[2], c6[5]));
+        kck = cadd(kck, cscale(2.0 * k[0] * k[1], c6[1]));
+        kck = cadd(kck, cscale(2.0 * k[0] * k[2], c6[2]));
+        kck = cadd(kck, cscale(2.0 * k[1] * k[2], c6[4]));
+        ph = cadd(ph, kck);
+      }
+      ph = cscale(TH, ph);
+      T1[2] = cadd(T1[2], ph);
+      for (int d = 0; d < 3; ++d) T2[d] = cmul_i(cscale(k[d], ph));
+    }
+    for (int d = 0; d < 3; ++d) {
+      a.buf[d * a.cstride + e] = T1[d];
+      a.buf[(3 + d) * a.cstride + e] = T2[d];
+    }
+  }
+}
+
+// --------------------------------------------------------------------- gather
+struct GatherArgs {
+  int64_t n_tgt, n_src;
+  const double* tgt;      // explicit targets or null
+  const double* spos;     // sorted sources (targets = sources)
+  const int32_t* sorig;
+  const double* buf;      // fields T1x..T2z, buffer stride bs, real layout
+  int64_t bs, xs, pitch;
+  int P, Mt;
+  double h, ox, oz, alpha, pre, h3;
+  double* out;
+  int add;
+};
+
+constexpr int kGatherWarps = 4;
+
+__global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs a) {
+  __shared__ double wsm[kGatherWarps][3][kMaxP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* wx = wsm[wib][0];
+  double* wy = wsm[wib][1];
+  double* wz = wsm[wib][2];
+  const int P = a.P;
+  const int64_t nwarps = (int64_t)gridDim.x * kGatherWarps;
+  for (int64_t w = blockIdx.x * (int64_t)kGatherWarps + wib; w < a.n_tgt; w += nwarps) {
+    double x, y, z;
+    int64_t dst;
+    if (a.tgt) {
+      x = a.tgt[w]; y = a.tgt[a.n_tgt + w]; z = a.tgt[2 * a.n_tgt + w];
+      dst = w;
+    } else {
+      x = a.spos[w]; y = a.spos[a.n_src + w]; z = a.spos[2 * a.n_src + w];
+      dst = a.sorig[w];
+    }
+    int ix0 = support_start(x, a.ox, a.h, P, a.Mt);
+    int iy0 = support_start(y, a.ox, a.h, P, a.Mt);
+    int iz0 = support_start(z, a.oz, a.h, P, 2 * a.Mt);
+    __syncwarp();
+    if (lane < P) {
+      double dx = a.ox + (ix0 + lane) * a.h - x;
+      double dy = a.ox + (iy0 + lane) * a.h - y;
+      double dz = a.oz + (iz0 + lane) * a.h - z;
+      wx[lane] = a.pre * exp(-a.alpha * dx * dx);
+      wy[lane] = exp(-a.alpha * dy * dy);
+      wz[lane] = exp(-a.alpha * dz * dz);
+    }
+    __syncwarp();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = lane; q < P * P; q += 32) {
+      int jj = q / P, kk = q - jj * P;
+      double s[6] = {0, 0, 0, 0, 0, 0};
+      const double* col = a.buf + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
+      for (int ii = 0; ii < P; ++ii) {
+        double wv = wx[ii];
+        const double* pnt = col + (int64_t)ii * a.xs;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s[c] += wv * pnt[c * a.bs];
+      }
+      double wyz = wy[jj] * wz[kk];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += wyz * s[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (lane == 0) {
+      for (int d = 0; d < 3; ++d) {
+        double v = a.h3 * (acc[d] - z * acc[3 + d]);
+        double* o = a.out + d * a.n_tgt + dst;
+        *o = a.add ? *o + v : v;
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------------- drivers
+static int blocks_for(int64_t n, int t, int cap) {
+  int64_t b = (n + t - 1) / t;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+static PrepArgs prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
+  const hse_params& q = p->prm;
+  PrepArgs a;
+  a.n = n;
+  a.spos = p->ws.spos;
+  a.sstr = p->ws.sstr;
+  a.rowS = p->row_S; a.rowT = p->row_T; a.rowW = p->row_W;
+  a.mask = q.kernel_mask;
+  a.paper = paper;
+  a.P = q.P;
+  a.Mt = q.Mt;
+  a.h = q.h;
+  a.ox = -0.5 * q.P * q.h;
+  a.oz = -(double)q.Mt * q.h;
+  a.alpha = 2.0 * q.xi * q.xi / q.eta;
+  a.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
+  a.stride = 3 * q.P + ncomp;
+  a.prep = p->ws.prep;
+  a.supp = reinterpret_cast<int4*>(p->ws.supp);
+  return a;
+}
+
+static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int paper, double* out, int64_t cstride,
+                              int64_t xs, int64_t pitch, cudaStream_t s) {
+  const hse_params& q = p->prm;
+  PrepArgs pa = prep_args(p, n_src, paper, cs.n);
+  if (n_src > 0) {
+    k_prep<<<blocks_for(n_src, 128, 152 * 32), 128, 0, s>>>(pa);
+    ++p->n_launch;
+    HSE_CUDA(p, cudaGetLastError());
+  }
+  SpreadArgs a;
+  a.supp = pa.supp;
+  a.prep = pa.prep;
+  a.cstart = p->ws.cell_start;
+  a.stride = pa.stride;
+  a.P = q.P;
+  a.Mt = q.Mt;
+  a.z0 = p->zA0;
+  a.h = q.h;
+  a.ox = pa.ox;
+  a.oz = pa.oz;
+  for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = q.ncell[d]; }
+  a.out = out;
+  a.cs = cstride;
+  a.xs = xs;
+  a.pitch = pitch;
+  int nzr = 2 * q.Mt - p->zA0;
+  dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, (nzr + kTZ - 1) / kTZ);
+  if (!launch_spread(cs.n, a, grid, s)) return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
+  ++p->n_launch;
+  HSE_CUDA(p, cudaGetLastError());
+  MirrorArgs m;
+  m.buf = out;
+  m.cs = cstride;
+  m.xs = xs;
+  m.pitch = pitch;
+  m.Mt = q.Mt;
+  m.nc = cs.n;
+  for (int c = 0; c < cs.n; ++c) m.sign[c] = cs.mirror_sign[c];
+  int64_t tot = (int64_t)q.Mt * q.Mt * (q.Mt + 1) * cs.n;
+  k_mirror<<<blocks_for(tot, 256, 152 * 64), 256, 0, s>>>(m);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), "k_mirror");
+}
+
+hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStream_t s) {
+  const int Mt = p->prm.Mt;
+  CompSet cs = paper_components(p->prm.kernel_mask);
+  int64_t per = (int64_t)Mt * Mt * 2 * Mt;
+  HSE_CUDA(p, cudaMemsetAsync(grids, 0, sizeof(double) * per * cs.n, s));
+  return spread_into(p, n_src, cs, 1, grids, per, (int64_t)Mt * 2 * Mt, 2 * Mt, s);
+}
+
+hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
+                         cudaStream_t s) {
+  const hse_params& q = p->prm;
+  const GridDims& g = p->g;
+  const int nin = p->comps.n;
+  HSE_CUDA(p, cudaMemsetAsync(p->spec, 0, sizeof(double) * g.buf_doubles * nin, s));
+  HSE_TRY(spread_into(p, n_src, p->comps, 0, p->spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
+  stage_mark(p, HSE_STAGE_FFT, s);
+  // forward transforms of every component
+  if (cufftSetStream(p->fwd, s) != CUFFT_SUCCESS || cufftSetStream(p->inv, s) != CUFFT_SUCCESS)
+    return set_err(p, HSE_ERR_CUFFT, "cufftSetStream");
+  for (int c = 0; c < nin; ++c) {
+    double* b = p->spec + c * g.buf_doubles;
+    cufftResult r = cufftExecD2Z(p->fwd, b, reinterpret_cast<cufftDoubleComplex*>(b));
+    ++p->n_fft;
+    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "cufftExecD2Z: %d", (int)r);
+  }
+  ScaleArgs sa;
+  sa.buf = reinterpret_cast<double2*>(p->spec);
+  sa.cstride = g.nh;
+  sa.Mt = q.Mt;
+  sa.mask = q.kernel_mask;
+  sa.h = q.h;
+  sa.tabB = p->tabB;
+  sa.tabH = p->tabH;
+  int k = 0;
+  sa.iS = sa.iT = sa.iW = sa.iCs = sa.iCt = -1;
+  if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
+  if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
+  if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
+  if (q.kernel_mask & HSE_STOKESLET) { sa.iCs = k; k += 1; }
+  sa.iCv = k; k += 3;
+  if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  stage_mark(p, HSE_STAGE_SCALE, s);
+  k_scale<<<blocks_for(g.nh, 256, 152 * 32), 256, 0, s>>>(sa);
+  ++p->n_launch;
+  HSE_CUDA(p, cudaGetLastError());
+  stage_mark(p, HSE_STAGE_IFFT, s);
+  for (int c = 0; c < 6; ++c) {
+    double* b = p->spec + c * g.buf_doubles;
+    cufftResult r = cufftExecZ2D(p->inv, reinterpret_cast<cufftDoubleComplex*>(b), b);
+    ++p->n_fft;
+    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "cufftExecZ2D: %d", (int)r);
+  }
+  stage_mark(p, HSE_STAGE_GATHER, s);
+  if (n_tgt == 0) return HSE_OK;
+  GatherArgs ga;
+  ga.n_tgt = n_tgt;
+  ga.n_src = n_src;
+  ga.tgt = tgt;
+  ga.spos = p->ws.spos;
+  ga.sorig = p->ws.val_a;
+  ga.buf = p->spec;
+  ga.bs = g.buf_doubles;
+  ga.xs = (int64_t)g.Ny * g.pitch;
+  ga.pitch = g.pitch;
+  ga.P = q.P;
+  ga.Mt = q.Mt;
+  ga.h = q.h;
+  ga.ox = -0.5 * q.P * q.h;
+  ga.oz = -(double)q.Mt * q.h;
+  ga.alpha = 2.0 * q.xi * q.xi / q.eta;
+  ga.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
+  ga.h3 = q.h * q.h * q.h;
+  ga.out = out;
+  ga.add = add ? 1 : 0;
+  k_gather<<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), "k_gather");
+}
+
+}  // namespace hse

@@ -1,0 +1,147 @@
+// hse_internal.cuh -- plan structure and device helpers shared by the CUDA
+// translation units of the half-space Spectral Ewald library (arXiv 1802.07844).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hse.h"
+
+namespace hse {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.77245385090551602730;
+constexpr double kWindowC = 0.95;  // Alg. 1 step 4
+constexpr int kMaxP = 32;          // support width limit (one warp lane per point)
+constexpr int kMaxComp = 25;       // most spread components of any kernel combination
+
+// Layout of the FFT buffers: padded grid Nx x Ny x Nz = 2Mt x 2Mt x 4Mt, in-place
+// R2C: real rows of pitch 2 (Nz/2 + 1) doubles, complex rows of Nz/2 + 1.
+struct GridDims {
+  int Mt = 0;
+  int Nx = 0, Ny = 0, Nz = 0;
+  int64_t pitch = 0;        // doubles per real z-row
+  int64_t nh = 0;           // complex points per buffer
+  int64_t buf_doubles = 0;  // doubles per buffer
+};
+
+// Spread-component description: which FFT input each component feeds and how
+// its image half is formed from the source-located accumulation A:
+//   mirror_sign = +1/-1 : C(k) = A(k) + s A(2Mt - k)   (C1 type: source + image)
+//   mirror_sign =  0    : C(k) = A(2Mt - k)            (image-only corrections)
+struct CompSet {
+  int n = 0;
+  int mirror_sign[kMaxComp];
+};
+
+struct Workspace {
+  int64_t cap = 0;   // particles
+  int P = 0, ncomp = 0;
+  int32_t *key_a = nullptr, *key_b = nullptr, *val_a = nullptr, *val_b = nullptr;
+  int32_t* cell_start = nullptr;
+  int64_t cell_cap = 0;
+  int32_t* radix_hist = nullptr;
+  int64_t hist_cap = 0;
+  double* spos = nullptr;      // 3 x cap sorted source positions
+  double* sstr = nullptr;      // rows x cap sorted strengths
+  double* prep = nullptr;      // per sorted particle: 3P weights + ncomp strengths
+  int32_t* supp = nullptr;     // per sorted particle: ix0, iy0, iz0, pad
+  int* flag = nullptr;         // device error flag
+  int* flag_host = nullptr;    // pinned host mirror
+};
+
+}  // namespace hse
+
+struct hse_plan_s {
+  hse_params prm{};
+  std::string err;
+  bool grid_ready = false;
+  // derived
+  double inv_cell[3] = {0, 0, 0};
+  hse::GridDims g;
+  int zA0 = 0;      // lowest z index any source support can reach
+  hse::CompSet comps;
+  int n_rows = 0;   // strength rows
+  int row_S = -1, row_T = -1, row_W = -1;
+  // device grids
+  double* spec = nullptr;  // n_fft_in buffers
+  double* tabB = nullptr;  // s E B^R / Np on the octant (Mt+1)(Mt+1)(2Mt+1)
+  double* tabH = nullptr;  // E H^R / Np on the octant
+  cufftHandle fwd = 0, inv = 0;
+  bool have_fft = false;
+  void* fft_work = nullptr;
+  size_t fft_work_bytes = 0;
+  hse::Workspace ws;
+  // statistics of the last evaluation
+  bool timing = false;
+  cudaEvent_t ev[HSE_N_STAGES + 1] = {};
+  bool ev_recorded = false;
+  int n_launch = 0;
+  int n_fft = 0;
+};
+
+namespace hse {
+
+// ---------------------------------------------------------------- host utils
+hse_status set_err(hse_plan p, hse_status s, const char* fmt, ...);
+hse_status cuda_check(hse_plan p, cudaError_t e, const char* what);
+hse_status build_grids(hse_plan p);           // tables, buffers, cuFFT plans
+void free_grids(hse_plan p);
+hse_status ensure_workspace(hse_plan p, int64_t n);
+void free_workspace(hse_plan p);
+CompSet product_components(int mask);
+CompSet paper_components(int mask);
+
+// ----------------------------------------------------------- stage launchers
+hse_status launch_validate(hse_plan p, int64_t n, const double* pos, int is_src, cudaStream_t s);
+hse_status read_flag(hse_plan p, cudaStream_t s, const char* what);
+hse_status build_cell_list(hse_plan p, int64_t n, const double* pos, int32_t* cell_id_out, int32_t* perm_out,
+                           int32_t* start_out, cudaStream_t s);
+hse_status gather_sorted(hse_plan p, int64_t n, const double* pos, const double* str, cudaStream_t s);
+hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
+                      cudaStream_t s);
+hse_status neighbor_counts(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, int32_t* a, int32_t* b,
+                           cudaStream_t s);
+hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
+                         cudaStream_t s);
+hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStream_t s);
+
+inline void stage_mark(hse_plan p, int i, cudaStream_t s) {
+  if (p->timing) cudaEventRecord(p->ev[i], s);
+}
+
+// ------------------------------------------------------------- device utils
+__device__ __forceinline__ int cell_coord(double x, double inv, int n) {
+  double t = floor(__dmul_rn(x, inv));
+  if (t < 0.0) return 0;
+  if (t > (double)(n - 1)) return n - 1;
+  return (int)t;
+}
+
+__device__ __forceinline__ double dist2_exact(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// support start along one axis: clamp(floor((c - o) / h) - P/2 + 1, 0, n - P)
+__device__ __forceinline__ int support_start(double c, double o, double h, int P, int n) {
+  double t = floor(__ddiv_rn(__dsub_rn(c, o), h));
+  long long i0 = (long long)t - P / 2 + 1;
+  if (i0 < 0) i0 = 0;
+  if (i0 > n - P) i0 = n - P;
+  return (int)i0;
+}
+
+}  // namespace hse
+
+#define HSE_TRY(expr)                     \
+  do {                                    \
+    hse_status _st = (expr);              \
+    if (_st != HSE_OK) return _st;        \
+  } while (0)
+
+#define HSE_CUDA(p, expr) HSE_TRY(hse::cuda_check((p), (expr), #expr))

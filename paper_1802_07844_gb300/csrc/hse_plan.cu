@@ -1,0 +1,475 @@
+// hse_plan.cu -- plan creation: parameter choice (Tables 2-3, Sec. 7 recipe),
+// grid geometry (Alg. 1 steps 2-4), the truncated-kernel tables of Sec. 5.2 and
+// the cuFFT plans of the zero-padded transforms (Alg. 1 steps 6 and 9).
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "hse_internal.cuh"
+
+namespace hse {
+
+static std::string g_create_error;
+
+hse_status set_err(hse_plan p, hse_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (p) p->err = buf; else g_create_error = buf;
+  return s;
+}
+
+hse_status cuda_check(hse_plan p, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HSE_OK;
+  hse_status s = (e == cudaErrorMemoryAllocation) ? HSE_ERR_OOM : HSE_ERR_CUDA;
+  cudaGetLastError();  // clear a non-sticky error
+  return set_err(p, s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static hse_status cufft_check(hse_plan p, cufftResult r, const char* what) {
+  if (r == CUFFT_SUCCESS) return HSE_OK;
+  hse_status s = (r == CUFFT_ALLOC_FAILED) ? HSE_ERR_OOM : HSE_ERR_CUFFT;
+  return set_err(p, s, "%s: cufft error %d", what, (int)r);
+}
+
+// ------------------------------------------------------------------------------
+// Spread components.  Product path: C1 per kernel with the mirror sign of its
+// image strength, and the wall corrections merged into one harmonic potential
+//   phi^ = E H^R (Cs^ + i k.Cv^ + k Ct^ k)
+// (stokeslet: Cs = -2 f3, Cv = -2 y3 f^I; stresslet: Cv_z = 4 g.q,
+//  Ct = 4 y3 sym(g^I q^I); rotlet: Cv_xy = 4 (-tau2, tau1)), all at images.
+// ------------------------------------------------------------------------------
+CompSet product_components(int mask) {
+  CompSet c;
+  auto add = [&](int s) { c.mirror_sign[c.n++] = s; };
+  if (mask & HSE_STOKESLET) { add(-1); add(-1); add(+1); }                   // -f^I  = (-f1,-f2,+f3)
+  if (mask & HSE_STRESSLET) { add(-1); add(-1); add(+1); add(-1); add(+1); add(-1); }  // -sym(g^I q^I)
+  if (mask & HSE_ROTLET) { add(+1); add(+1); add(-1); }                      // +tau^I
+  if (mask & HSE_STOKESLET) add(0);                                          // Cs
+  add(0); add(0); add(0);                                                    // Cv
+  if (mask & HSE_STRESSLET) for (int i = 0; i < 6; ++i) add(0);             // Ct
+  return c;
+}
+
+CompSet paper_components(int mask) {
+  CompSet c;
+  auto add = [&](int s) { c.mirror_sign[c.n++] = s; };
+  if (mask & HSE_STOKESLET) { add(-1); add(-1); add(+1); for (int i = 0; i < 4; ++i) add(0); }
+  if (mask & HSE_STRESSLET) {
+    add(-1); add(-1); add(+1); add(-1); add(+1); add(-1);
+    for (int i = 0; i < 7; ++i) add(0);
+  }
+  if (mask & HSE_ROTLET) { add(+1); add(+1); add(-1); add(0); add(0); }
+  return c;
+}
+
+// ------------------------------------------------------------------------------
+// Truncated kernels (Sec. 5.2): transforms of (1/r) 1{r<R} and r 1{r<R}.
+// B^R uses the corrected closed form 4 pi [(2 - R^2k^2) cos Rk + 2Rk sin Rk - 2]/k^4
+// and its Taylor series 4 pi R^4 sum (-1)^n (Rk)^2n / ((2n+1)! (2n+4)) for Rk < 1.
+// ------------------------------------------------------------------------------
+__device__ double trunc_H(double k, double R) {
+  double x = 0.5 * R * k;
+  double sinc = (x < 1e-8) ? 1.0 - x * x / 6.0 : sin(x) / x;
+  return 8.0 * kPi * 0.25 * R * R * sinc * sinc;
+}
+
+__device__ double trunc_B(double k, double R) {
+  double t = R * k;
+  if (t < 1.0) {
+    double t2 = t * t, term = 1.0, sum = 0.0;  // term = (-1)^n t^2n / (2n+1)!
+    for (int n = 0; n < 20; ++n) {
+      sum += term / (2.0 * n + 4.0);
+      term *= -t2 / ((2.0 * n + 2.0) * (2.0 * n + 3.0));
+    }
+    double R2 = R * R;
+    return 4.0 * kPi * R2 * R2 * sum;
+  }
+  double k2 = k * k;
+  return 4.0 * kPi * ((2.0 - t * t) * cos(t) + 2.0 * t * sin(t) - 2.0) / (k2 * k2);
+}
+
+// Pass 1 of the precomputation: for each fine-grid line (mx, my), sample K^R on
+// the k-grid refined by s_f (spacing 2 pi/(nf h) in x, y and 2 pi/(2 nf h) in z)
+// and synthesise the even cosine series along z at the padded box offsets
+// iz in [0, nout).  One block per line.
+__global__ void k_tab_pass1(int kind, int nf, int nfz, double h, double R, int nout, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  int nin = nfz / 2 + 1;
+  double* line = sm;           // nin
+  double* ctab = sm + nin;     // nfz entries: cos(2 pi t / nfz)
+  int mx = blockIdx.x, my = blockIdx.y;
+  int nh = nf / 2 + 1;
+  for (int t = threadIdx.x; t < nfz; t += blockDim.x) ctab[t] = cospi(2.0 * (double)t / (double)nfz);
+  double ax = (double)mx / nf, ay = (double)my / nf;
+  for (int m = threadIdx.x; m < nin; m += blockDim.x) {
+    double az = (double)m / nfz;
+    double k = 2.0 * kPi / h * sqrt(ax * ax + ay * ay + az * az);
+    double v = kind == 0 ? trunc_H(k, R) : trunc_B(k, R);
+    double w = (m == 0 || m == nin - 1) ? 1.0 : 2.0;
+    line[m] = w * v;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nout; j += blockDim.x) {
+    double acc = 0.0;
+    long long t = 0;
+    for (int m = 0; m < nin; ++m) {
+      acc += line[m] * ctab[t];
+      t += j;
+      if (t >= nfz) t -= nfz;
+    }
+    out[((size_t)mx * nh + my) * nout + j] = acc;
+  }
+}
+
+// Generic even cosine pass along one axis of in[n0][n1][n2]:
+//   out[.., j, ..] = scale sum_{i < nin} w_i in[.., i, ..] cos(2 pi i j / np),
+// w_i = 1 at i = 0 and i = nin - 1, else 2.  The other axes keep their size.
+__global__ void k_cos_pass(const double* __restrict__ in, double* __restrict__ out, int n0, int n1, int n2, int axis,
+                           int nout, int np, double scale) {
+  extern __shared__ double ctab[];
+  for (int t = threadIdx.x; t < np; t += blockDim.x) ctab[t] = cospi(2.0 * (double)t / (double)np);
+  __syncthreads();
+  int d[3] = {n0, n1, n2};
+  int nin = d[axis];
+  int o[3] = {n0, n1, n2};
+  o[axis] = nout;
+  int64_t total = (int64_t)o[0] * o[1] * o[2];
+  int64_t sin_[3] = {(int64_t)n1 * n2, n2, 1};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int c2 = (int)(e % o[2]);
+    int c1 = (int)((e / o[2]) % o[1]);
+    int c0 = (int)(e / ((int64_t)o[2] * o[1]));
+    int c[3] = {c0, c1, c2};
+    int j = c[axis];
+    c[axis] = 0;
+    const double* base = in + c[0] * sin_[0] + c[1] * sin_[1] + c[2];
+    int64_t st = sin_[axis];
+    double acc = 0.0;
+    long long t = 0;
+    for (int i = 0; i < nin; ++i) {
+      double w = (i == 0 || i == nin - 1) ? 1.0 : 2.0;
+      acc += w * base[i * st] * ctab[t];
+      t += j;
+      if (t >= np) t -= np;
+    }
+    out[e] = scale * acc;
+  }
+}
+
+// Final tables on the padded k-grid octant: fold the remaining Gaussian
+// exp(-(1 - eta) k^2 / 4 xi^2), the Hasimoto factor (1 + k^2/4xi^2) (B only)
+// and the 1/Np of the unnormalised inverse FFT.
+__global__ void k_tab_finish(double* __restrict__ tab, int Mt, double h, double xi, double eta, int with_s,
+                             double inv_np) {
+  int nx = Mt + 1, nz = 2 * Mt + 1;
+  int64_t total = (int64_t)nx * nx * nz;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int jz = (int)(e % nz);
+    int jy = (int)((e / nz) % nx);
+    int jx = (int)(e / ((int64_t)nz * nx));
+    double kx = 2.0 * kPi * jx / (2.0 * Mt * h);
+    double ky = 2.0 * kPi * jy / (2.0 * Mt * h);
+    double kz = 2.0 * kPi * jz / (4.0 * Mt * h);
+    double k2 = kx * kx + ky * ky + kz * kz;
+    double q = k2 / (4.0 * xi * xi);
+    double f = exp(-(1.0 - eta) * q) * inv_np;
+    if (with_s) f *= (1.0 + q);
+    tab[e] *= f;
+  }
+}
+
+static int grid_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// Builds one table (kind 0: H^R, 1: B^R) on the padded octant, Sec. 5.2:
+//  1. sample K^R on the k-grid refined by s_f (nf = s_f Mt even, s_f >= 1 + sqrt 6),
+//  2. inverse transform (even cosine synthesis) and truncate to the padded box,
+//  3. forward transform on the padded grid (even cosine analysis).
+static hse_status build_table(hse_plan p, int kind, double* tab) {
+  const int Mt = p->g.Mt;
+  const double h = p->prm.h;
+  const double R = std::sqrt(6.0) * Mt * h;  // diagonal of the Lt x Lt x 2Lt domain
+  int nf = (int)std::ceil((1.0 + std::sqrt(6.0)) * Mt);
+  if (nf % 2) ++nf;
+  const int nfz = 2 * nf;
+  const int nh = nf / 2 + 1;
+  const int ox = Mt + 1, oz = 2 * Mt + 1;  // octant of the padded box / k-grid
+  double *a = nullptr, *b = nullptr;
+  size_t na = (size_t)nh * nh * oz, nb = (size_t)nh * ox * oz;
+  HSE_CUDA(p, cudaMalloc(&a, na * sizeof(double)));
+  cudaError_t e = cudaMalloc(&b, nb * sizeof(double));
+  if (e != cudaSuccess) { cudaFree(a); return cuda_check(p, e, "cudaMalloc table scratch"); }
+  hse_status st = HSE_OK;
+  do {
+    size_t sm1 = sizeof(double) * (nfz / 2 + 1 + nfz);
+    cudaFuncSetAttribute(k_tab_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    k_tab_pass1<<<dim3(nh, nh), 256, sm1>>>(kind, nf, nfz, h, R, oz, a);             // a[mx][my][iz]
+    if ((st = cuda_check(p, cudaGetLastError(), "k_tab_pass1")) != HSE_OK) break;
+    auto pass = [&](const double* in, double* out, int n0, int n1, int n2, int axis, int nout, int np, double sc) {
+      int o[3] = {n0, n1, n2};
+      o[axis] = nout;
+      int64_t tot = (int64_t)o[0] * o[1] * o[2];
+      size_t smb = sizeof(double) * np;
+      cudaFuncSetAttribute(k_cos_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+      k_cos_pass<<<grid_blocks(tot, 256), 256, smb>>>(in, out, n0, n1, n2, axis, nout, np, sc);
+      return cuda_check(p, cudaGetLastError(), "k_cos_pass");
+    };
+    // synthesis along y then x; 1/(nf nf nfz) is the discrete inverse normalisation
+    if ((st = pass(a, b, nh, nh, oz, 1, ox, nf, 1.0)) != HSE_OK) break;                 // b[mx][iy][iz]
+    if ((st = pass(b, a, nh, ox, oz, 0, ox, nf, 1.0 / ((double)nf * nf * nfz))) != HSE_OK) break;  // a[ix][iy][iz]
+    // analysis on the padded grid (Nx = 2Mt, Nz = 4Mt): z, y, x
+    if ((st = pass(a, b, ox, ox, oz, 2, oz, 4 * Mt, 1.0)) != HSE_OK) break;
+    if ((st = pass(b, a, ox, ox, oz, 1, ox, 2 * Mt, 1.0)) != HSE_OK) break;
+    if ((st = pass(a, tab, ox, ox, oz, 0, ox, 2 * Mt, 1.0)) != HSE_OK) break;
+    double inv_np = 1.0 / ((double)p->g.Nx * p->g.Ny * p->g.Nz);
+    int64_t tot = (int64_t)ox * ox * oz;
+    k_tab_finish<<<grid_blocks(tot, 256), 256>>>(tab, Mt, h, p->prm.xi, p->prm.eta, kind == 1, inv_np);
+    if ((st = cuda_check(p, cudaGetLastError(), "k_tab_finish")) != HSE_OK) break;
+    st = cuda_check(p, cudaDeviceSynchronize(), "table precompute");
+  } while (0);
+  cudaFree(a);
+  cudaFree(b);
+  return st;
+}
+
+void free_grids(hse_plan p) {
+  if (p->have_fft) {
+    cufftDestroy(p->fwd);
+    cufftDestroy(p->inv);
+    p->have_fft = false;
+  }
+  cudaFree(p->fft_work);
+  cudaFree(p->spec);
+  cudaFree(p->tabB);
+  cudaFree(p->tabH);
+  p->fft_work = nullptr;
+  p->spec = p->tabB = p->tabH = nullptr;
+  p->grid_ready = false;
+}
+
+hse_status build_grids(hse_plan p) {
+  free_grids(p);
+  hse_params& q = p->prm;
+  q.h = q.L / q.M;
+  q.Mt = q.M + q.P;
+  q.eta = q.P * q.xi * q.xi * q.h * q.h / (kWindowC * kWindowC * kPi);
+  if (!(q.eta > 0.0 && q.eta < 1.0))
+    return set_err(p, HSE_ERR_INVALID, "eta = %g outside (0,1): increase M (M=%d, P=%d, xi=%g)", q.eta, q.M, q.P,
+                   q.xi);
+  GridDims& g = p->g;
+  g.Mt = q.Mt;
+  g.Nx = g.Ny = 2 * q.Mt;
+  g.Nz = 4 * q.Mt;
+  g.pitch = 2 * (g.Nz / 2 + 1);
+  g.nh = (int64_t)g.Nx * g.Ny * (g.Nz / 2 + 1);
+  g.buf_doubles = 2 * g.nh;
+  p->zA0 = q.Mt - q.P / 2 + 1;
+  p->comps = product_components(q.kernel_mask);
+  q.n_fft_in = p->comps.n;
+  q.n_fft_out = 6;
+  size_t tab_elems = (size_t)(q.Mt + 1) * (q.Mt + 1) * (2 * q.Mt + 1);
+  size_t spec_bytes = (size_t)g.buf_doubles * sizeof(double) * q.n_fft_in;
+  HSE_CUDA(p, cudaMalloc(&p->spec, spec_bytes));
+  HSE_CUDA(p, cudaMalloc(&p->tabH, tab_elems * sizeof(double)));
+  if (q.kernel_mask & (HSE_STOKESLET | HSE_STRESSLET)) HSE_CUDA(p, cudaMalloc(&p->tabB, tab_elems * sizeof(double)));
+  HSE_TRY(build_table(p, 0, p->tabH));
+  if (p->tabB) HSE_TRY(build_table(p, 1, p->tabB));
+  // cuFFT: one 3-D in-place transform per component, shared work area
+  long long n[3] = {g.Nx, g.Ny, g.Nz};
+  size_t wf = 0, wi = 0;
+  HSE_TRY(cufft_check(p, cufftCreate(&p->fwd), "cufftCreate"));
+  HSE_TRY(cufft_check(p, cufftCreate(&p->inv), "cufftCreate"));
+  p->have_fft = true;
+  cufftSetAutoAllocation(p->fwd, 0);
+  cufftSetAutoAllocation(p->inv, 0);
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fwd, 3, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_D2Z, 1, &wf),
+                      "cufftMakePlanMany64 D2Z"));
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->inv, 3, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_Z2D, 1, &wi),
+                      "cufftMakePlanMany64 Z2D"));
+  p->fft_work_bytes = wf > wi ? wf : wi;
+  if (p->fft_work_bytes) HSE_CUDA(p, cudaMalloc(&p->fft_work, p->fft_work_bytes));
+  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fwd, p->fft_work), "cufftSetWorkArea"));
+  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->inv, p->fft_work), "cufftSetWorkArea"));
+  q.grid_bytes = spec_bytes + tab_elems * sizeof(double) * (p->tabB ? 2 : 1) + p->fft_work_bytes;
+  p->grid_ready = true;
+  return HSE_OK;
+}
+
+// ------------------------------------------------------------------------------
+// Parameter choice from a relative RMS tolerance (Sec. 6-7).
+// The truncation estimates of Tables 2-3 (absolute RMS errors, with Q the sum
+// of squared strengths) are made relative with the RMS velocity model
+// |u|_rms ~ sqrt(4 pi Q)/L (uniform sources, stokeslet; the more singular
+// stresslet and rotlet fields are larger, so the rule is conservative there):
+//   real space  S: sqrt(rc/(pi L)) e^{-xi^2 rc^2}
+//               T: sqrt(28 xi^4 rc^3/(9 pi L)) e^{-xi^2 rc^2}
+//               W: sqrt(2/(3 pi L rc)) e^{-xi^2 rc^2}
+//   Fourier     S: R k^3 e^{-k^2/4xi^2} / (2 pi^1.5 xi^2)
+//               T: sqrt(7/6) R k^4 e^{-k^2/4xi^2} / (2 pi^1.5 xi^2)
+//               W: sqrt(2 xi^2/(3 pi^2 L k)) e^{-k^2/4xi^2}
+// with k = k_inf = pi/h and R = sqrt(6) L~.  Each part is held to tol/3; r_c
+// and k_inf are found by bisection, M = ceil(L k_inf / pi).  The support P is
+// the smallest even number with exp(-c^2 pi P/2) <= tol/20 (Gaussian
+// truncation, Alg. 1 step 4) and xi P h >= sqrt(ln(1/tol) + 4) (the extension
+// L~ = L + P h must hold the screened kernel, Sec. 5.2).
+// ------------------------------------------------------------------------------
+static double est_real(int mask, double xi, double rc, double L) {
+  double e = std::exp(-xi * xi * rc * rc), m = 0.0;
+  if (mask & HSE_STOKESLET) m = std::fmax(m, std::sqrt(rc / (kPi * L)));
+  if (mask & HSE_STRESSLET) m = std::fmax(m, std::sqrt(28.0 * std::pow(xi, 4) * std::pow(rc, 3) / (9.0 * kPi * L)));
+  if (mask & HSE_ROTLET) m = std::fmax(m, std::sqrt(2.0 / (3.0 * kPi * L * rc)));
+  return m * e;
+}
+
+static double est_fourier(int mask, double xi, double k, double L, double R) {
+  double e = std::exp(-k * k / (4.0 * xi * xi)), m = 0.0, d = 2.0 * std::pow(kPi, 1.5) * xi * xi;
+  if (mask & HSE_STOKESLET) m = std::fmax(m, R * k * k * k / d);
+  if (mask & HSE_STRESSLET) m = std::fmax(m, std::sqrt(7.0 / 6.0) * R * k * k * k * k / d);
+  if (mask & HSE_ROTLET) m = std::fmax(m, std::sqrt(2.0 * xi * xi / (3.0 * kPi * kPi * L * k)));
+  return m * e;
+}
+
+// smallest x in [lo, hi] with f(x) <= target, f decreasing there
+template <typename F>
+static double bisect_down(F f, double lo, double hi, double target) {
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (f(mid) <= target) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+static hse_status choose_params(hse_plan p, double xi, double rc, int P, double tol) {
+  hse_params& q = p->prm;
+  const int mask = q.kernel_mask;
+  const double L = q.L;
+  if (xi <= 0.0) {
+    if (tol <= 0.0 || rc <= 0.0) return set_err(p, HSE_ERR_INVALID, "xi <= 0 needs tol > 0 and rc > 0");
+    double t = bisect_down([&](double x) { return est_real(mask, x, rc, L); }, 0.1 / rc, 20.0 / rc, tol / 3.0);
+    xi = t;
+  }
+  if (rc <= 0.0) {
+    if (tol <= 0.0) return set_err(p, HSE_ERR_INVALID, "rc <= 0 needs tol > 0");
+    rc = bisect_down([&](double r) { return est_real(mask, xi, r, L); }, 1.0 / xi, 12.0 / xi, tol / 3.0);
+  }
+  q.xi = xi;
+  q.rc = rc;
+  int M = 0;
+  if (tol > 0.0) {
+    double R = std::sqrt(6.0) * 1.2 * L;  // L~ <= 1.2 L for the supports used here
+    double k = bisect_down([&](double kk) { return est_fourier(mask, xi, kk, L, R); }, 2.0 * xi, 30.0 * xi,
+                           tol / 3.0);
+    M = (int)std::ceil(L * k / kPi);
+    if (M < 4) M = 4;
+  }
+  if (P <= 0) {
+    if (tol <= 0.0) return set_err(p, HSE_ERR_INVALID, "P <= 0 needs tol > 0");
+    double h = M > 0 ? L / M : L / 16.0;
+    double p1 = 2.0 * std::log(20.0 / tol) / (kWindowC * kWindowC * kPi);
+    double p2 = std::sqrt(std::log(1.0 / tol) + 4.0) / (xi * h);
+    P = (int)std::ceil(p1 > p2 ? p1 : p2);
+  }
+  if (P % 2) ++P;
+  if (P < 4 || P > kMaxP) return set_err(p, HSE_ERR_INVALID, "P = %d outside [4, %d]", P, kMaxP);
+  q.P = P;
+  q.M = M;
+  return HSE_OK;
+}
+
+}  // namespace hse
+
+using namespace hse;
+
+extern "C" hse_status hse_plan_create(int kernel_mask, const double box[3], double xi, double rc, int P, double tol,
+                                      int precision, hse_plan* out) {
+  if (!out) return set_err(nullptr, HSE_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (kernel_mask <= 0 || kernel_mask > 7) return set_err(nullptr, HSE_ERR_INVALID, "kernel_mask %d", kernel_mask);
+  if (!box || !(box[0] > 0) || !(box[1] > 0) || !(box[2] > 0) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
+      !std::isfinite(box[2]))
+    return set_err(nullptr, HSE_ERR_INVALID, "box must be finite and positive");
+  if (precision != HSE_FP64 && precision != HSE_MIXED)
+    return set_err(nullptr, HSE_ERR_INVALID, "precision %d", precision);
+  if (precision == HSE_MIXED)
+    return set_err(nullptr, HSE_ERR_UNSUPPORTED, "HSE_MIXED is not available in this build");
+  if (!(tol < 1.0)) return set_err(nullptr, HSE_ERR_INVALID, "tol must be < 1");
+  hse_plan p = new (std::nothrow) hse_plan_s();
+  if (!p) return set_err(nullptr, HSE_ERR_OOM, "host allocation");
+  hse_params& q = p->prm;
+  q.kernel_mask = kernel_mask;
+  q.precision = precision;
+  for (int d = 0; d < 3; ++d) q.box[d] = box[d];
+  q.L = std::fmax(box[0], std::fmax(box[1], box[2]));
+  hse_status st = choose_params(p, xi, rc, P, tol);
+  if (st == HSE_OK) {
+    for (int d = 0; d < 3; ++d) {
+      double nc = std::floor(box[d] / q.rc);
+      if (nc < 1) nc = 1;
+      if (nc > 1024) nc = 1024;
+      q.ncell[d] = (int)nc;
+      p->inv_cell[d] = (double)q.ncell[d] / box[d];
+    }
+    p->n_rows = 0;
+    if (kernel_mask & HSE_STOKESLET) { p->row_S = p->n_rows; p->n_rows += 3; }
+    if (kernel_mask & HSE_STRESSLET) { p->row_T = p->n_rows; p->n_rows += 6; }
+    if (kernel_mask & HSE_ROTLET) { p->row_W = p->n_rows; p->n_rows += 3; }
+    if (q.M > 0) st = build_grids(p);
+  }
+  if (st != HSE_OK) {
+    g_create_error = p->err;
+    free_grids(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return HSE_OK;
+}
+
+extern "C" hse_status hse_plan_set_grid(hse_plan p, int M) {
+  if (!p) return HSE_ERR_INVALID;
+  if (M < 4) return set_err(p, HSE_ERR_INVALID, "M = %d < 4", M);
+  p->prm.M = M;
+  return build_grids(p);
+}
+
+extern "C" hse_status hse_plan_get_params(hse_plan p, hse_params* out) {
+  if (!p || !out) return HSE_ERR_INVALID;
+  *out = p->prm;
+  return HSE_OK;
+}
+
+extern "C" hse_status hse_plan_destroy(hse_plan p) {
+  if (!p) return HSE_ERR_INVALID;
+  cudaDeviceSynchronize();
+  if (p->timing)
+    for (int i = 0; i <= HSE_N_STAGES; ++i) cudaEventDestroy(p->ev[i]);
+  free_grids(p);
+  free_workspace(p);
+  delete p;
+  return HSE_OK;
+}
+
+extern "C" const char* hse_status_string(hse_status s) {
+  switch (s) {
+    case HSE_OK: return "HSE_OK";
+    case HSE_ERR_INVALID: return "HSE_ERR_INVALID";
+    case HSE_ERR_OOM: return "HSE_ERR_OOM";
+    case HSE_ERR_CUDA: return "HSE_ERR_CUDA";
+    case HSE_ERR_CUFFT: return "HSE_ERR_CUFFT";
+    case HSE_ERR_TIMEOUT: return "HSE_ERR_TIMEOUT";
+    case HSE_ERR_UNSUPPORTED: return "HSE_ERR_UNSUPPORTED";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* hse_last_error(hse_plan p) {
+  return p ? p->err.c_str() : g_create_error.c_str();
+}

@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in ``include/hse.h``.
+
+Every function here only marshals arguments to the CUDA library
+``libhse.so``; all of the computation runs in its kernels on the GPU.  The
+functions carry the C names.  ``Plan`` is a small convenience wrapper that
+takes torch CUDA tensors (component-major float64) and passes their device
+pointers and the current stream.  If the library cannot be loaded, importing
+the entry points raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HSE_OK, HSE_ERR_INVALID, HSE_ERR_OOM, HSE_ERR_CUDA, HSE_ERR_CUFFT, HSE_ERR_TIMEOUT, HSE_ERR_UNSUPPORTED = range(7)
+HSE_STOKESLET, HSE_STRESSLET, HSE_ROTLET = 1, 2, 4
+HSE_FP64, HSE_MIXED = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhse.so")
+
+
+class hse_params(ctypes.Structure):
+    _fields_ = [
+        ("kernel_mask", ctypes.c_int), ("precision", ctypes.c_int), ("box", ctypes.c_double * 3),
+        ("L", ctypes.c_double), ("xi", ctypes.c_double), ("rc", ctypes.c_double), ("P", ctypes.c_int),
+        ("M", ctypes.c_int), ("Mt", ctypes.c_int), ("h", ctypes.c_double), ("eta", ctypes.c_double),
+        ("ncell", ctypes.c_int * 3), ("n_fft_in", ctypes.c_int), ("n_fft_out", ctypes.c_int),
+        ("grid_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+HSE_N_STAGES = 8
+STAGE_NAMES = ("check", "cells", "real", "spread", "fft", "scale", "ifft", "gather")
+
+
+class hse_eval_stats(ctypes.Structure):
+    _fields_ = [("n_kernel_launches", ctypes.c_int), ("n_fft_execs", ctypes.c_int), ("timing", ctypes.c_int),
+                ("stage_ms", ctypes.c_double * HSE_N_STAGES)]
+
+
+class HseError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
+          "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
+          "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats")
+
+
+def load(path: str = LIB_PATH):
+    """Load libhse.so (raises OSError when it is absent: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library {path} is missing; build it with paper_1802_07844_gb300.build")
+    L = ctypes.CDLL(path)
+    vp, dp, i64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64
+    L.hse_plan_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
+    L.hse_plan_set_grid.argtypes = [vp, ctypes.c_int]
+    L.hse_plan_get_params.argtypes = [vp, ctypes.POINTER(hse_params)]
+    L.hse_eval.argtypes = [vp, i64, dp, dp, i64, dp, dp, vp]
+    L.hse_eval_parts.argtypes = [vp, i64, dp, dp, i64, dp, dp, dp, vp]
+    L.hse_cell_list.argtypes = [vp, i64, dp, dp, dp, dp, vp]
+    L.hse_neighbor_counts.argtypes = [vp, i64, dp, i64, dp, dp, dp, vp]
+    L.hse_spread_grids.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(ctypes.c_int), vp]
+    L.hse_plan_destroy.argtypes = [vp]
+    L.hse_plan_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hse_get_eval_stats.argtypes = [vp, ctypes.POINTER(hse_eval_stats)]
+    L.hse_status_string.argtypes = [ctypes.c_int]
+    L.hse_status_string.restype = ctypes.c_char_p
+    L.hse_last_error.argtypes = [vp]
+    L.hse_last_error.restype = ctypes.c_char_p
+    for n in _NAMES:
+        if getattr(L, n).restype is None and n not in ("hse_status_string", "hse_last_error"):
+            getattr(L, n).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_name(s: int) -> str:
+    return load().hse_status_string(int(s)).decode()
+
+
+def _check(status, plan=None):
+    if status != HSE_OK:
+        raise HseError(status, load().hse_last_error(plan).decode())
+
+
+# ---------------------------------------------------------------- C names
+def hse_plan_create(kernel_mask, box, xi, rc, P, tol, precision=HSE_FP64):
+    L = load()
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    out = ctypes.c_void_p()
+    _check(L.hse_plan_create(int(kernel_mask), b, float(xi), float(rc), int(P), float(tol), int(precision),
+                             ctypes.byref(out)))
+    return out
+
+
+def hse_plan_set_grid(plan, M):
+    _check(load().hse_plan_set_grid(plan, int(M)), plan)
+
+
+def hse_plan_get_params(plan) -> dict:
+    p = hse_params()
+    _check(load().hse_plan_get_params(plan, ctypes.byref(p)), plan)
+    return p.as_dict()
+
+
+def hse_eval(plan, n_src, src_ptr, str_ptr, n_tgt, tgt_ptr, vel_ptr, stream=0):
+    _check(load().hse_eval(plan, n_src, src_ptr, str_ptr, n_tgt, tgt_ptr, vel_ptr, stream), plan)
+
+
+def hse_eval_parts(plan, n_src, src_ptr, str_ptr, n_tgt, tgt_ptr, real_ptr, four_ptr, stream=0):
+    _check(load().hse_eval_parts(plan, n_src, src_ptr, str_ptr, n_tgt, tgt_ptr, real_ptr, four_ptr, stream), plan)
+
+
+def hse_cell_list(plan, n, pos_ptr, cell_ptr, perm_ptr, start_ptr, stream=0):
+    _check(load().hse_cell_list(plan, n, pos_ptr, cell_ptr, perm_ptr, start_ptr, stream), plan)
+
+
+def hse_neighbor_counts(plan, n_src, src_ptr, n_tgt, tgt_ptr, a_ptr, b_ptr, stream=0):
+    _check(load().hse_neighbor_counts(plan, n_src, src_ptr, n_tgt, tgt_ptr, a_ptr, b_ptr, stream), plan)
+
+
+def hse_spread_grids(plan, n_src, src_ptr, str_ptr, grids_ptr, stream=0) -> int:
+    n = ctypes.c_int()
+    _check(load().hse_spread_grids(plan, n_src, src_ptr, str_ptr, grids_ptr, ctypes.byref(n), stream), plan)
+    return n.value
+
+
+def hse_plan_destroy(plan):
+    _check(load().hse_plan_destroy(plan))
+
+
+def hse_plan_set_timing(plan, enable):
+    _check(load().hse_plan_set_timing(plan, int(bool(enable))), plan)
+
+
+def hse_get_eval_stats(plan) -> dict:
+    st = hse_eval_stats()
+    _check(load().hse_get_eval_stats(plan, ctypes.byref(st)), plan)
+    return {"n_kernel_launches": st.n_kernel_launches, "n_fft_execs": st.n_fft_execs, "timing": bool(st.timing),
+            "stage_ms": dict(zip(STAGE_NAMES, list(st.stage_ms)))}
+
+
+def hse_status_string(status) -> str:
+    return status_name(status)
+
+
+def hse_last_error(plan=None) -> str:
+    return load().hse_last_error(plan).decode()
+
+
+# ------------------------------------------------------ torch convenience
+class Plan:
+    """Owns an ``hse_plan``; methods take torch CUDA float64 tensors."""
+
+    def __init__(self, kernel_mask, box=(1.0, 1.0, 1.0), xi=0.0, rc=0.0, P=0, tol=0.0, precision=HSE_FP64, M=None):
+        self.handle = hse_plan_create(kernel_mask, box, xi, rc, P, tol, precision)
+        if M is not None:
+            hse_plan_set_grid(self.handle, M)
+        self.params = hse_plan_get_params(self.handle)
+
+    def set_grid(self, M):
+        hse_plan_set_grid(self.handle, M)
+        self.params = hse_plan_get_params(self.handle)
+
+    @staticmethod
+    def _ptr(t):
+        if t is None:
+            return None
+        import torch
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        return t.data_ptr()
+
+    @staticmethod
+    def _stream():
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def eval(self, src, strengths, tgt=None, out=None):
+        import torch
+        n_src = src.shape[1]
+        n_tgt = n_src if tgt is None else tgt.shape[1]
+        if out is None:
+            out = torch.empty((3, n_tgt), dtype=torch.float64, device=src.device)
+        hse_eval(self.handle, n_src, self._ptr(src), self._ptr(strengths), n_tgt, self._ptr(tgt), self._ptr(out),
+                 self._stream())
+        return out
+
+    def eval_parts(self, src, strengths, tgt=None, real=True, fourier=True):
+        import torch
+        n_src = src.shape[1]
+        n_tgt = n_src if tgt is None else tgt.shape[1]
+        ur = torch.empty((3, n_tgt), dtype=torch.float64, device=src.device) if real else None
+        uf = torch.empty((3, n_tgt), dtype=torch.float64, device=src.device) if fourier else None
+        hse_eval_parts(self.handle, n_src, self._ptr(src), self._ptr(strengths), n_tgt, self._ptr(tgt),
+                       None if ur is None else ur.data_ptr(), None if uf is None else uf.data_ptr(), self._stream())
+        return ur, uf
+
+    def cell_list(self, pos):
+        import torch
+        n = pos.shape[1]
+        nc = self.params["ncell"]
+        cid = torch.empty(n, dtype=torch.int32, device=pos.device)
+        perm = torch.empty(n, dtype=torch.int32, device=pos.device)
+        start = torch.empty(nc[0] * nc[1] * nc[2] + 1, dtype=torch.int32, device=pos.device)
+        hse_cell_list(self.handle, n, self._ptr(pos), cid.data_ptr(), perm.data_ptr(), start.data_ptr(),
+                      self._stream())
+        return cid, perm, start
+
+    def neighbor_counts(self, src, tgt=None):
+        import torch
+        n_src = src.shape[1]
+        n_tgt = n_src if tgt is None else tgt.shape[1]
+        a = torch.empty(n_tgt, dtype=torch.int32, device=src.device)
+        b = torch.empty(n_tgt, dtype=torch.int32, device=src.device)
+        hse_neighbor_counts(self.handle, n_src, self._ptr(src), n_tgt, self._ptr(tgt), a.data_ptr(), b.data_ptr(),
+                            self._stream())
+        return a, b
+
+    def spread_grids(self, src, strengths):
+        import torch
+        nc = hse_spread_grids(self.handle, 0, None, None, None, self._stream())
+        Mt = self.params["Mt"]
+        g = torch.empty((nc, Mt, Mt, 2 * Mt), dtype=torch.float64, device=src.device)
+        hse_spread_grids(self.handle, src.shape[1], self._ptr(src), self._ptr(strengths), g.data_ptr(),
+                         self._stream())
+        return g
+
+    def set_timing(self, enable=True):
+        hse_plan_set_timing(self.handle, enable)
+
+    def stats(self):
+        return hse_get_eval_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            hse_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
