@@ -206,6 +206,32 @@ hse_status hse_plan_set_timing(hse_plan plan, int enable);
  * timing is on).  out: host pointer. */
 hse_status hse_get_eval_stats(hse_plan plan, hse_eval_stats* out);
 
+/*
+ * hse_cell_list_noalloc -- the cell list of hse_cell_list (same cell ids,
+ * permutation and cell starts, bit for bit) without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not let a library call cudaMalloc/cudaFree -- applications whose framework
+ * or pool allocator owns the device heap, and loops where an allocation,
+ * which can synchronise the device, is not allowed.
+ *   n           number of points, 0 <= n <= HSE_NOALLOC_MAX_POINTS; larger n
+ *               is rejected with HSE_ERR_INVALID (see hse_last_error(NULL)).
+ *   pos         device, 3 x n positions.
+ *   box, ncell  host arrays: box side L_d > 0 and cells per side
+ *               1 <= ncell_d <= 1024; cell side L_d / ncell_d, cell of a point
+ *               clamp(floor(x_d * (ncell_d / L_d)), 0, ncell_d - 1) (non-finite
+ *               coordinates land in a boundary cell).
+ *   cell_id, perm  device, n int32 each; cell_start device, prod(ncell) + 1.
+ * Work arrays live in one fixed device array inside the library (3.3 MiB), resident on every GPU that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (no allocation), with the device current; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents: calls whose work can overlap on the GPU (different streams,
+ * threads or devices sharing a context) race -- serialise them.
+ */
+#define HSE_NOALLOC_MAX_POINTS 262144
+hse_status hse_cell_list_noalloc(int64_t n, const double* pos, const double box[3], const int ncell[3],
+                                 int32_t* cell_id, int32_t* perm, int32_t* cell_start, void* cuda_stream);
+
 /* Release all device memory and cuFFT plans of the plan (synchronises). */
 hse_status hse_plan_destroy(hse_plan plan);
 

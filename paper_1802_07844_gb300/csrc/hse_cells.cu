@@ -263,3 +263,47 @@ hse_status gather_sorted(hse_plan p, int64_t n, const double* pos, const double*
 }
 
 }  // namespace hse
+
+namespace hse {
+
+// Plan-free launcher of the cell-list kernels above on caller-provided work
+// arrays (used by the entry point that allocates nothing).  key_a/val_a hold
+// n entries each and receive the sorted cell ids / permutation; key_b/val_b
+// (n each) and hist (256 * ceil(n/2048)) are scratch.
+cudaError_t cell_list_on_buffers(int64_t n, const double* pos, const double inv_cell[3], const int ncell[3],
+                                 int32_t* key_a, int32_t* val_a, int32_t* key_b, int32_t* val_b, int32_t* hist,
+                                 int32_t* cell_id_out, int32_t* start_out, cudaStream_t s) {
+  int64_t ncells = (int64_t)ncell[0] * ncell[1] * ncell[2];
+  if (n == 0) return cudaMemsetAsync(start_out, 0, sizeof(int32_t) * (ncells + 1), s);
+  k_bin<<<nblocks(n, 256), 256, 0, s>>>(n, pos, inv_cell[0], inv_cell[1], inv_cell[2], ncell[0], ncell[1], ncell[2],
+                                         key_a, val_a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (cell_id_out) {
+    e = cudaMemcpyAsync(cell_id_out, key_a, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  int bits = 0;
+  while ((int64_t(1) << bits) < ncells) ++bits;
+  int passes = (bits + 7) / 8;
+  int64_t ntiles = (n + kTile - 1) / kTile;
+  int32_t *ka = key_a, *va = val_a, *kb = key_b, *vb = val_b;
+  for (int ps = 0; ps < passes; ++ps) {
+    k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ka, n, 8 * ps, ntiles, hist);
+    k_scan_excl<<<1, 1024, 0, s>>>(hist, 256 * ntiles);
+    k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ka, va, n, 8 * ps, ntiles, hist, kb, vb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int32_t* tk = ka; ka = kb; kb = tk;
+    int32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != key_a) {
+    e = cudaMemcpyAsync(key_a, ka, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(val_a, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_cell_start<<<nblocks(n + 1, 256), 256, 0, s>>>(key_a, n, ncells, start_out);
+  return cudaGetLastError();
+}
+
+}  // namespace hse

@@ -55,7 +55,7 @@ class HseError(RuntimeError):
 _lib = None
 _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
-          "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats")
+          "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats", "hse_cell_list_noalloc")
 
 
 def load(path: str = LIB_PATH):
@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH):
     L.hse_spread_grids.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(ctypes.c_int), vp]
     L.hse_plan_destroy.argtypes = [vp]
     L.hse_plan_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hse_cell_list_noalloc.argtypes = [i64, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), dp, dp,
+                                        dp, vp]
     L.hse_get_eval_stats.argtypes = [vp, ctypes.POINTER(hse_eval_stats)]
     L.hse_status_string.argtypes = [ctypes.c_int]
     L.hse_status_string.restype = ctypes.c_char_p
@@ -154,6 +156,17 @@ def hse_get_eval_stats(plan) -> dict:
     _check(load().hse_get_eval_stats(plan, ctypes.byref(st)), plan)
     return {"n_kernel_launches": st.n_kernel_launches, "n_fft_execs": st.n_fft_execs, "timing": bool(st.timing),
             "stage_ms": dict(zip(STAGE_NAMES, list(st.stage_ms)))}
+
+
+HSE_NOALLOC_MAX_POINTS = 262144
+
+
+def hse_cell_list_noalloc(n, pos_ptr, box, ncell, cell_ptr, perm_ptr, start_ptr, stream=0):
+    """Cell list without any device allocation (for callers whose allocator
+    owns the device heap or that may not allocate in their loop)."""
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    c = (ctypes.c_int * 3)(*[int(v) for v in ncell])
+    _check(load().hse_cell_list_noalloc(n, pos_ptr, b, c, cell_ptr, perm_ptr, start_ptr, stream))
 
 
 def hse_status_string(status) -> str:
