@@ -491,13 +491,16 @@ hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double*
   HSE_TRY(spread_into(p, n_src, p->comps, 0, p->spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
   stage_mark(p, HSE_STAGE_FFT, s);
   // forward transforms of every component
-  if (cufftSetStream(p->fwd, s) != CUFFT_SUCCESS || cufftSetStream(p->inv, s) != CUFFT_SUCCESS)
+  if (cufftSetStream(p->fwd2d, s) != CUFFT_SUCCESS || cufftSetStream(p->inv2d, s) != CUFFT_SUCCESS ||
+      cufftSetStream(p->fftx, s) != CUFFT_SUCCESS)
     return set_err(p, HSE_ERR_CUFFT, "cufftSetStream");
   for (int c = 0; c < nin; ++c) {
     double* b = p->spec + c * g.buf_doubles;
-    cufftResult r = cufftExecD2Z(p->fwd, b, reinterpret_cast<cufftDoubleComplex*>(b));
+    cufftDoubleComplex* z = reinterpret_cast<cufftDoubleComplex*>(b);
+    cufftResult r = cufftExecD2Z(p->fwd2d, b, z);
+    if (r == CUFFT_SUCCESS) r = cufftExecZ2Z(p->fftx, z, z, CUFFT_FORWARD);
     ++p->n_fft;
-    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "cufftExecD2Z: %d", (int)r);
+    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "forward FFT: %d", (int)r);
   }
   ScaleArgs sa;
   sa.buf = reinterpret_cast<double2*>(p->spec);
@@ -522,9 +525,11 @@ hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double*
   stage_mark(p, HSE_STAGE_IFFT, s);
   for (int c = 0; c < 6; ++c) {
     double* b = p->spec + c * g.buf_doubles;
-    cufftResult r = cufftExecZ2D(p->inv, reinterpret_cast<cufftDoubleComplex*>(b), b);
+    cufftDoubleComplex* z = reinterpret_cast<cufftDoubleComplex*>(b);
+    cufftResult r = cufftExecZ2Z(p->fftx, z, z, CUFFT_INVERSE);
+    if (r == CUFFT_SUCCESS) r = cufftExecZ2D(p->inv2d, z, b);
     ++p->n_fft;
-    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "cufftExecZ2D: %d", (int)r);
+    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "inverse FFT: %d", (int)r);
   }
   stage_mark(p, HSE_STAGE_GATHER, s);
   if (n_tgt == 0) return HSE_OK;

@@ -48,6 +48,7 @@ struct Workspace {
   int32_t* radix_hist = nullptr;
   int64_t hist_cap = 0;
   double* spos = nullptr;      // 3 x cap sorted source positions
+  float* spos32 = nullptr;     // the same rounded to FP32
   double* sstr = nullptr;      // rows x cap sorted strengths
   double* prep = nullptr;      // per sorted particle: 3P weights + ncomp strengths
   int32_t* supp = nullptr;     // per sorted particle: ix0, iy0, iz0, pad
@@ -72,7 +73,10 @@ struct hse_plan_s {
   double* spec = nullptr;  // n_fft_in buffers
   double* tabB = nullptr;  // s E B^R / Np on the octant (Mt+1)(Mt+1)(2Mt+1)
   double* tabH = nullptr;  // E H^R / Np on the octant
-  cufftHandle fwd = 0, inv = 0;
+  // zero-padded transforms split into a 2-D (y,z) transform over the Mt planes
+  // that hold data (fwd2d R2C / inv2d C2R) and a 1-D transform along x over
+  // all (y, kz) lines (fftx, Z2Z both directions)
+  cufftHandle fwd2d = 0, inv2d = 0, fftx = 0;
   bool have_fft = false;
   void* fft_work = nullptr;
   size_t fft_work_bytes = 0;

@@ -12,25 +12,46 @@
 // erfc; the last term of T^R carries r (not the unit vector), which is the
 // dimensionally consistent form.
 //
-// Work split: one warp per target.  Lanes test 32 candidates at a time with
-// the exact cut-off decision ((dx*dx + dy*dy) + dz*dz < r_c^2, no FMA) and the
-// passing ones are compacted into a per-warp queue; whenever 32 are queued,
-// every lane evaluates one pair, so the FP64 pipe always runs full warps.
+// Every radial coefficient follows from four numbers of the pair distance
+// rho (t = xi rho, c = 2 xi e^{-t^2}/sqrt(pi), E_r = erfc(t)/rho):
+//   a1 = (E_r + c)/rho^2,  g2 = (3 a1 + 2 xi^2 c)/rho^2,  g3 = -(5 g2 + 4 xi^4 c)/rho^2
+//   S^R: I (E_r - c) + r r a1          W^R: 2 a1 (tau x r)
+//   T^R: -2 g2 r(r.g)(r.q) + 2 xi^2 c (g(r.q) + q(r.g) + r(g.q))
+//   G_R: g0 = E_r, grad = -a1 r, grad grad = -a1 I + g2 r r, grad^3 with g2, g3.
+//
+// FP64 throughput (2 FMA/clk/SM on GB300) bounds this stage, so:
+//  * erfc(t) = exp(-t^2) erfcx(t), erfcx by degree-10 polynomials on intervals
+//    of width 1/4 (table from gen_special_tables.py), exp by Cody-Waite
+//    reduction and a degree-13 Taylor polynomial;
+//  * candidates are screened in FP32 with a proven error margin; only those
+//    within the margin of r_c take the exact FP64 test, so the accepted set
+//    equals the FP64 rule ((dx*dx + dy*dy) + dz*dz < r_c^2, no contraction);
+//  * with targets = sources each unordered pair is evaluated once (the radial
+//    part is shared by both directions: r -> -r for free pairs,
+//    rt -> (-rt1, -rt2, rt3) for image pairs); the partner's share is added
+//    with FP64 atomics.
+// Work split: one warp per target; passing candidates are compacted into a
+// per-warp queue and evaluated 32 at a time, so FP64 instructions run full warps.
 #include "hse_internal.cuh"
+#include "special_tables.inc"
 
 namespace hse {
+
+__device__ const double d_erfcx_coef[HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1)] = {HSE_ERFCX_COEFS};
 
 struct RealArgs {
   int64_t n_src, n_tgt;
   const double* spos;      // sorted sources, 3 x n_src
+  const float* spos32;     // the same in FP32 (candidate screening)
   const double* sstr;      // sorted strengths, rows x n_src
   const int32_t* sorig;    // sorted -> original source index
   const int32_t* cstart;   // cell starts
   const double* tgt;       // explicit targets (3 x n_tgt) or null (targets = sources)
   double* out;             // 3 x n_tgt in caller order
-  int add;                 // accumulate into out
+  int add;                 // accumulate into out (asymmetric kernel)
   int mask, rowS, rowT, rowW;
   double xi, rc2, rc;
+  float rc2_lo, rc2_hi;    // FP32 screening thresholds
   double inv_cell[3];
   int ncell[3];
 };
@@ -38,95 +59,137 @@ struct RealArgs {
 enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2 };
 constexpr int kWarpsPerBlock = 4;
 constexpr int kQueue = 64;
+constexpr int kTabN = HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1);
 
-// Contribution of one queued pair to the lane's accumulator.
-__device__ __forceinline__ void eval_pair(const RealArgs& a, const double* x, int j, int type, double* u) {
-  const int64_t n = a.n_src;
-  double y0 = a.spos[j], y1 = a.spos[n + j], y2 = a.spos[2 * n + j];
-  double f[3] = {0, 0, 0}, g[3] = {0, 0, 0}, q[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
-  if (a.mask & HSE_STOKESLET)
-    for (int i = 0; i < 3; ++i) f[i] = a.sstr[(a.rowS + i) * n + j];
-  if (a.mask & HSE_STRESSLET)
-    for (int i = 0; i < 3; ++i) { g[i] = a.sstr[(a.rowT + i) * n + j]; q[i] = a.sstr[(a.rowT + 3 + i) * n + j]; }
-  if (a.mask & HSE_ROTLET)
-    for (int i = 0; i < 3; ++i) tau[i] = a.sstr[(a.rowW + i) * n + j];
-  if (type == Q_SELF) {
-    double c = -4.0 * a.xi / kSqrtPi;
-    for (int i = 0; i < 3; ++i) u[i] += c * f[i];
-    return;
-  }
-  const double xi = a.xi;
-  double r[3] = {x[0] - y0, x[1] - y1, type == Q_IMAGE ? x[2] + y2 : x[2] - y2};
-  double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+// e^{-x} for 0 <= x (Cody-Waite: x log2 e = n + f, e^{-x} = 2^-n e^r)
+__device__ __forceinline__ double exp_neg(double x) {
+  if (x > 700.0) return 0.0;
+  const double magic = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low word
+  double y = -x;
+  double tn = fma(y, kLog2e, magic);
+  int n = __double2loint(tn);
+  double nd = tn - magic;
+  double r = fma(-nd, kLn2Head, y);
+  r = fma(-nd, kLn2Tail, r);
+  constexpr double C[14] = {HSE_EXP_TAYLOR_COEFS};
+  double p = C[13];
+#pragma unroll
+  for (int k = 12; k >= 0; --k) p = fma(p, r, C[k]);
+  double scale = __hiloint2double((n + 1023) << 20, 0);
+  return p * scale;
+}
+
+// erfcx(t) = e^{t^2} erfc(t) on [0, 12) from the interval table in shared memory
+__device__ __forceinline__ double erfcx_tab(double t, float tf, const double* tab) {
+  int k = (int)(tf * 4.0f);
+  k = k < 0 ? 0 : (k > HSE_ERFCX_NINT - 1 ? HSE_ERFCX_NINT - 1 : k);
+  const double* c = tab + k * (HSE_ERFCX_DEG + 1);
+  double u = fma(8.0, t, -(double)(2 * k + 1));
+  double p = c[HSE_ERFCX_DEG];
+#pragma unroll
+  for (int j = HSE_ERFCX_DEG - 1; j >= 0; --j) p = fma(p, u, c[j]);
+  return p;
+}
+
+struct Radial {
+  double er, c, a1, g2, g3;  // erfc(t)/rho, 2 xi e^{-t^2}/sqrt(pi), a1, g2, g3
+};
+
+__device__ __forceinline__ Radial radial(double s, float sf, double xi, const double* tab, bool need_g3) {
+  Radial R;
   double inv = rsqrt(s);
-  double rho = s * inv;
-  double t = xi * rho;
-  double ec = erfc(t);
-  double c = (2.0 / kSqrtPi) * xi * exp(-t * t);  // 2 xi e^{-t^2}/sqrt(pi)
-  double i1 = inv, i2 = inv * inv;
-  double ecr = ec * i1;
-  double a1 = (ecr + c) * i2;  // erfc/r^3 + 2 xi e/(sqrt(pi) r^2)
-  if (type == Q_FREE) {
-    if (a.mask & HSE_STOKESLET) {
-      double sa = ecr - c, sb = (c + ecr) * i2;
-      double rf = r[0] * f[0] + r[1] * f[1] + r[2] * f[2];
-      for (int i = 0; i < 3; ++i) u[i] += sa * f[i] + sb * r[i] * rf;
-    }
-    if (a.mask & HSE_STRESSLET) {
-      double ta = -2.0 * i2 * i2 * (3.0 * ecr + c * (3.0 + 2.0 * t * t));
-      double tb = 2.0 * xi * xi * c;
-      double rg = r[0] * g[0] + r[1] * g[1] + r[2] * g[2];
-      double rq = r[0] * q[0] + r[1] * q[1] + r[2] * q[2];
-      double gq = g[0] * q[0] + g[1] * q[1] + g[2] * q[2];
-      for (int i = 0; i < 3; ++i) u[i] += ta * r[i] * rg * rq + tb * (g[i] * rq + q[i] * rg + r[i] * gq);
-    }
-    if (a.mask & HSE_ROTLET) {
-      double wa = 2.0 * a1;
-      u[0] += wa * (tau[1] * r[2] - tau[2] * r[1]);
-      u[1] += wa * (tau[2] * r[0] - tau[0] * r[2]);
-      u[2] += wa * (tau[0] * r[1] - tau[1] * r[0]);
-    }
-    return;
+  double t = xi * s * inv;
+  double E = exp_neg(t * t);
+  double ec;
+  if (t < 0.25 * HSE_ERFCX_NINT) ec = E * erfcx_tab(t, (float)xi * sqrtf(sf), tab);
+  else ec = erfc(t);  // beyond the table: only reached when xi r_c > 12
+  double i2 = inv * inv;
+  R.c = (2.0 / kSqrtPi) * xi * E;
+  R.er = ec * inv;
+  R.a1 = (R.er + R.c) * i2;
+  R.g2 = i2 * fma(3.0, R.a1, 2.0 * xi * xi * R.c);
+  R.g3 = need_g3 ? -i2 * fma(5.0, R.g2, 4.0 * xi * xi * xi * xi * R.c) : 0.0;
+  return R;
+}
+
+struct Src {
+  double f[3], g[3], q[3], tau[3];
+};
+
+__device__ __forceinline__ void load_src(const RealArgs& a, int64_t j, Src& s) {
+  const int64_t n = a.n_src;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { s.f[i] = 0.0; s.g[i] = 0.0; s.q[i] = 0.0; s.tau[i] = 0.0; }
+  if (a.mask & HSE_STOKESLET)
+    for (int i = 0; i < 3; ++i) s.f[i] = a.sstr[(a.rowS + i) * n + j];
+  if (a.mask & HSE_STRESSLET)
+    for (int i = 0; i < 3; ++i) { s.g[i] = a.sstr[(a.rowT + i) * n + j]; s.q[i] = a.sstr[(a.rowT + 3 + i) * n + j]; }
+  if (a.mask & HSE_ROTLET)
+    for (int i = 0; i < 3; ++i) s.tau[i] = a.sstr[(a.rowW + i) * n + j];
+}
+
+// free-space contribution of source s at r = x - y (sign -1 gives the
+// contribution at the source's position from the target's strengths when the
+// roles are swapped: S is even in r, T and W odd)
+__device__ __forceinline__ void add_free(int mask, const Radial& R, const double* r, const Src& s, double xi,
+                                         double sgn_odd, double* u) {
+  if (mask & HSE_STOKESLET) {
+    double sa = R.er - R.c;
+    double rf = r[0] * s.f[0] + r[1] * s.f[1] + r[2] * s.f[2];
+    for (int i = 0; i < 3; ++i) u[i] += sa * s.f[i] + R.a1 * r[i] * rf;
   }
-  // image pair at rt = r, source height h
-  const double h = y2, x3 = x[2];
-  double g1 = -a1;
-  double g2 = 3.0 * ecr * i2 * i2 + c * (3.0 * i2 * i2 + 2.0 * xi * xi * i2);
+  if (mask & HSE_STRESSLET) {
+    double ta = -2.0 * R.g2, tb = 2.0 * xi * xi * R.c;
+    double rg = r[0] * s.g[0] + r[1] * s.g[1] + r[2] * s.g[2];
+    double rq = r[0] * s.q[0] + r[1] * s.q[1] + r[2] * s.q[2];
+    double gq = s.g[0] * s.q[0] + s.g[1] * s.q[1] + s.g[2] * s.q[2];
+    for (int i = 0; i < 3; ++i)
+      u[i] += sgn_odd * (ta * r[i] * rg * rq + tb * (s.g[i] * rq + s.q[i] * rg + r[i] * gq));
+  }
+  if (mask & HSE_ROTLET) {
+    double wa = sgn_odd * 2.0 * R.a1;
+    u[0] += wa * (s.tau[1] * r[2] - s.tau[2] * r[1]);
+    u[1] += wa * (s.tau[2] * r[0] - s.tau[0] * r[2]);
+    u[2] += wa * (s.tau[0] * r[1] - s.tau[1] * r[0]);
+  }
+}
+
+// image contribution at a target of height x3 from source s of height h,
+// rt = x - y^I
+__device__ __forceinline__ void add_image(int mask, const Radial& R, const double* r, double h, double x3,
+                                          const Src& s, double xi, double* u) {
+  const double g1 = -R.a1, g2 = R.g2;
   double phi = 0.0, gp[3] = {0.0, 0.0, 0.0};
-  if (a.mask & HSE_STOKESLET) {
-    double fI[3] = {f[0], f[1], -f[2]};
-    double sa = ecr - c, sb = (c + ecr) * i2;
+  if (mask & HSE_STOKESLET) {
+    double fI[3] = {s.f[0], s.f[1], -s.f[2]};
+    double sa = R.er - R.c;
     double rf = r[0] * fI[0] + r[1] * fI[1] + r[2] * fI[2];
-    for (int i = 0; i < 3; ++i) u[i] -= sa * fI[i] + sb * r[i] * rf;
-    double g0 = ecr;
-    phi += 2.0 * (-f[2] * g0 - h * g1 * rf);
-    for (int i = 0; i < 3; ++i) gp[i] += 2.0 * (-f[2] * g1 * r[i] - h * (g1 * fI[i] + g2 * r[i] * rf));
+    for (int i = 0; i < 3; ++i) u[i] -= sa * fI[i] + R.a1 * r[i] * rf;
+    phi += 2.0 * (-s.f[2] * R.er - h * g1 * rf);
+    for (int i = 0; i < 3; ++i) gp[i] += 2.0 * (-s.f[2] * g1 * r[i] - h * (g1 * fI[i] + g2 * r[i] * rf));
   }
-  if (a.mask & HSE_STRESSLET) {
-    double gI[3] = {g[0], g[1], -g[2]}, qI[3] = {q[0], q[1], -q[2]};
-    double ta = -2.0 * i2 * i2 * (3.0 * ecr + c * (3.0 + 2.0 * t * t));
-    double tb = 2.0 * xi * xi * c;
+  if (mask & HSE_STRESSLET) {
+    double gI[3] = {s.g[0], s.g[1], -s.g[2]}, qI[3] = {s.q[0], s.q[1], -s.q[2]};
+    double ta = -2.0 * R.g2, tb = 2.0 * xi * xi * R.c;
     double rg = r[0] * gI[0] + r[1] * gI[1] + r[2] * gI[2];
     double rq = r[0] * qI[0] + r[1] * qI[1] + r[2] * qI[2];
     double gq = gI[0] * qI[0] + gI[1] * qI[1] + gI[2] * qI[2];
     for (int i = 0; i < 3; ++i) u[i] -= ta * r[i] * rg * rq + tb * (gI[i] * rq + qI[i] * rg + r[i] * gq);
-    double g3 = -15.0 * ecr * i2 * i2 * i2 -
-                c * (15.0 * i2 * i2 * i2 + 10.0 * xi * xi * i2 * i2 + 4.0 * xi * xi * xi * xi * i2);
     // phi_T = 4 (gI.qI) d3G - 4 h gI.(grad grad G) qI
     phi += 4.0 * gq * g1 * r[2] - 4.0 * h * (g1 * gq + g2 * rg * rq);
     for (int i = 0; i < 3; ++i) {
       double d3i = g1 * (i == 2 ? 1.0 : 0.0) + g2 * r[2] * r[i];
-      double t3 = g2 * (gq * r[i] + gI[i] * rq + qI[i] * rg) + g3 * rg * rq * r[i];
+      double t3 = g2 * (gq * r[i] + gI[i] * rq + qI[i] * rg) + R.g3 * rg * rq * r[i];
       gp[i] += 4.0 * gq * d3i - 4.0 * h * t3;
     }
   }
-  if (a.mask & HSE_ROTLET) {
-    double tI[3] = {tau[0], tau[1], -tau[2]};
-    double wa = 2.0 * a1;
+  if (mask & HSE_ROTLET) {
+    double tI[3] = {s.tau[0], s.tau[1], -s.tau[2]};
+    double wa = 2.0 * R.a1;
     u[0] += wa * (tI[1] * r[2] - tI[2] * r[1]);
     u[1] += wa * (tI[2] * r[0] - tI[0] * r[2]);
     u[2] += wa * (tI[0] * r[1] - tI[1] * r[0]);
-    double v0 = -tau[1], v1 = tau[0];
+    double v0 = -s.tau[1], v1 = s.tau[0];
     double rv = r[0] * v0 + r[1] * v1;
     phi += 4.0 * g1 * rv;
     gp[0] += 4.0 * (g1 * v0 + g2 * r[0] * rv);
@@ -137,11 +200,13 @@ __device__ __forceinline__ void eval_pair(const RealArgs& a, const double* x, in
   u[2] += phi;
 }
 
-// Iterate the candidate cells of a target and call visit(j, type) for every
-// source passing the exact cut-off test (plus the self pair).
+// Candidate scan: cells around the target (free pairs) and the wall-layer
+// cells below its image (image pairs), 32 candidates per step, with the
+// FP32 screen and the exact FP64 decision for the rest.  j_min bounds the
+// sorted source index from below (half list of the symmetric kernel).
 template <typename Visit>
-__device__ __forceinline__ void for_candidates(const RealArgs& a, const double* x, int64_t own, int lane,
-                                               Visit&& visit) {
+__device__ __forceinline__ void for_candidates(const RealArgs& a, const double* x, const float* xf, int64_t own,
+                                               int lane, int free_min, int img_min, Visit&& visit) {
   int cx = cell_coord(x[0], a.inv_cell[0], a.ncell[0]);
   int cy = cell_coord(x[1], a.inv_cell[1], a.ncell[1]);
   int cz = cell_coord(x[2], a.inv_cell[2], a.ncell[2]);
@@ -153,28 +218,40 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
   for (int pass = 0; pass < 2; ++pass) {
     int z0 = pass == 0 ? (cz > 0 ? cz - 1 : 0) : 0;
     int z1 = pass == 0 ? (cz < nz - 1 ? cz + 1 : nz - 1) : czi_hi;
+    int jmin = pass == 0 ? free_min : img_min;
     for (int iz = z0; iz <= z1; ++iz)
       for (int iy = (cy > 0 ? cy - 1 : 0); iy <= (cy < ny - 1 ? cy + 1 : ny - 1); ++iy) {
         // x-neighbours are contiguous in the cell numbering
         int xa = cx > 0 ? cx - 1 : 0, xb = cx < nx - 1 ? cx + 1 : nx - 1;
         int c0 = (iz * ny + iy) * nx + xa;
         int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
+        if (s0 < jmin) s0 = jmin;
         for (int base = s0; base < s1; base += 32) {
           int j = base + lane;
-          bool ok = j < s1;
           int type = 0;
           bool hit = false;
-          if (ok) {
-            double y0 = a.spos[j], y1 = a.spos[n + j], y2 = a.spos[2 * n + j];
-            double dx = __dsub_rn(x[0], y0), dy = __dsub_rn(x[1], y1);
-            if (pass == 0) {
-              double dz = __dsub_rn(x[2], y2);
-              bool self = own >= 0 ? (a.sorig[j] == own) : (dx == 0.0 && dy == 0.0 && dz == 0.0);
-              if (self) { hit = true; type = Q_SELF; }
-              else if (dist2_exact(dx, dy, dz) < a.rc2) { hit = true; type = Q_FREE; }
-            } else {
-              double dz = __dadd_rn(x[2], y2);
-              if (dist2_exact(dx, dy, dz) < a.rc2) { hit = true; type = Q_IMAGE; }
+          if (j < s1) {
+            float dxf = xf[0] - a.spos32[j], dyf = xf[1] - a.spos32[n + j];
+            float dzf = pass == 0 ? xf[2] - a.spos32[2 * n + j] : xf[2] + a.spos32[2 * n + j];
+            float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+            bool self = pass == 0 && own >= 0 && j == own;
+            if (self) {
+              hit = true;
+              type = Q_SELF;
+            } else if (d2f < a.rc2_hi) {
+              bool in = d2f < a.rc2_lo;
+              if (!in || (pass == 0 && own < 0 && d2f == 0.0f)) {  // exact FP64 decision / zero test
+                double dx = __dsub_rn(x[0], a.spos[j]), dy = __dsub_rn(x[1], a.spos[n + j]);
+                double dz = pass == 0 ? __dsub_rn(x[2], a.spos[2 * n + j]) : __dadd_rn(x[2], a.spos[2 * n + j]);
+                if (pass == 0 && own < 0 && dx == 0.0 && dy == 0.0 && dz == 0.0) {
+                  hit = true;
+                  type = Q_SELF;
+                  in = false;
+                } else {
+                  in = dist2_exact(dx, dy, dz) < a.rc2;
+                }
+              }
+              if (in) { hit = true; type = pass == 0 ? Q_FREE : Q_IMAGE; }
             }
           }
           visit(hit, j, type);
@@ -183,11 +260,20 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
   }
 }
 
+__device__ __forceinline__ void load_table(double* tab) {
+  for (int i = threadIdx.x; i < kTabN; i += blockDim.x) tab[i] = d_erfcx_coef[i];
+  __syncthreads();
+}
+
+// Asymmetric kernel: explicit targets (or any target set), every ordered pair.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
+  __shared__ double tab[kTabN];
+  load_table(tab);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* qu = queue[wib];
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const bool need_g3 = a.mask & HSE_STRESSLET;
   for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < a.n_tgt; w += nwarps) {
     double x[3];
     int64_t own, dst;
@@ -197,29 +283,43 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
       dst = w;
     } else {  // targets are the sources, visited in cell order
       x[0] = a.spos[w]; x[1] = a.spos[a.n_src + w]; x[2] = a.spos[2 * a.n_src + w];
-      own = a.sorig[w];
-      dst = own;
+      own = w;
+      dst = a.sorig[w];
     }
+    float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
     double u[3] = {0.0, 0.0, 0.0};
     int cnt = 0;
-    for_candidates(a, x, own, lane, [&](bool hit, int j, int type) {
+    auto run = [&](int e) {
+      int j = e & 0x1fffffff, type = e >> 29;
+      Src s;
+      load_src(a, j, s);
+      if (type == Q_SELF) {
+        double c = -4.0 * a.xi / kSqrtPi;
+        for (int i = 0; i < 3; ++i) u[i] += c * s.f[i];
+        return;
+      }
+      const int64_t n = a.n_src;
+      double y2 = a.spos[2 * n + j];
+      double r[3] = {x[0] - a.spos[j], x[1] - a.spos[n + j], type == Q_IMAGE ? x[2] + y2 : x[2] - y2};
+      double sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      Radial R = radial(sd, (float)sd, a.xi, tab, need_g3);
+      if (type == Q_FREE) add_free(a.mask, R, r, s, a.xi, 1.0, u);
+      else add_image(a.mask, R, r, y2, x[2], s, a.xi, u);
+    };
+    for_candidates(a, x, xf, own, lane, 0, 0, [&](bool hit, int j, int type) {
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
       cnt += __popc(m);
       __syncwarp();
       if (cnt >= 32) {
-        int e = qu[lane];
-        eval_pair(a, x, e & 0x1fffffff, e >> 29, u);
+        run(qu[lane]);
         __syncwarp();
         if (lane < cnt - 32) qu[lane] = qu[32 + lane];
         cnt -= 32;
         __syncwarp();
       }
     });
-    if (lane < cnt) {
-      int e = qu[lane];
-      eval_pair(a, x, e & 0x1fffffff, e >> 29, u);
-    }
+    if (lane < cnt) run(qu[lane]);
     __syncwarp();
     for (int i = 0; i < 3; ++i)
       for (int off = 16; off > 0; off >>= 1) u[i] += __shfl_xor_sync(0xffffffffu, u[i], off);
@@ -228,6 +328,78 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
         double* o = a.out + i * a.n_tgt + dst;
         *o = a.add ? *o + u[i] : u[i];
       }
+    }
+  }
+}
+
+// Symmetric kernel (targets = sources): warp of sorted target p takes the
+// pairs with sorted source index j > p (free) and j >= p (image, j = p is the
+// target's own image); the partner's share goes out by atomicAdd.  The
+// output must be zeroed before the launch.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
+  __shared__ int queue[kWarpsPerBlock][kQueue];
+  __shared__ double tab[kTabN];
+  load_table(tab);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int* qu = queue[wib];
+  const int64_t n = a.n_src;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const bool need_g3 = a.mask & HSE_STRESSLET;
+  for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < n; w += nwarps) {
+    double x[3] = {a.spos[w], a.spos[n + w], a.spos[2 * n + w]};
+    float xf[3] = {a.spos32[w], a.spos32[n + w], a.spos32[2 * n + w]};
+    Src sp;
+    load_src(a, w, sp);
+    double u[3] = {0.0, 0.0, 0.0};
+    if (lane == 0 && (a.mask & HSE_STOKESLET)) {
+      double c = -4.0 * a.xi / kSqrtPi;
+      for (int i = 0; i < 3; ++i) u[i] = c * sp.f[i];
+    }
+    int cnt = 0;
+    auto run = [&](int e) {
+      int j = e & 0x1fffffff, type = e >> 29;
+      Src s;
+      load_src(a, j, s);
+      double y2 = a.spos[2 * n + j];
+      double r[3] = {x[0] - a.spos[j], x[1] - a.spos[n + j], type == Q_IMAGE ? x[2] + y2 : x[2] - y2};
+      double sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      Radial R = radial(sd, (float)sd, a.xi, tab, need_g3);
+      double v[3] = {0.0, 0.0, 0.0};
+      if (type == Q_FREE) {
+        add_free(a.mask, R, r, s, a.xi, 1.0, u);
+        add_free(a.mask, R, r, sp, a.xi, -1.0, v);  // at y_j from the target's strengths, r -> -r
+      } else {
+        add_image(a.mask, R, r, y2, x[2], s, a.xi, u);
+        if (j != w) {
+          double rp[3] = {-r[0], -r[1], r[2]};  // y_j - x^I
+          add_image(a.mask, R, rp, x[2], y2, sp, a.xi, v);
+        }
+      }
+      if (type == Q_FREE || j != w) {
+        int64_t o = a.sorig[j];
+        for (int i = 0; i < 3; ++i) atomicAdd(a.out + i * n + o, v[i]);
+      }
+    };
+    for_candidates(a, x, xf, w, lane, (int)w + 1, (int)w, [&](bool hit, int j, int type) {
+      unsigned m = __ballot_sync(0xffffffffu, hit && type != Q_SELF);
+      if (hit && type != Q_SELF) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
+      cnt += __popc(m);
+      __syncwarp();
+      if (cnt >= 32) {
+        run(qu[lane]);
+        __syncwarp();
+        if (lane < cnt - 32) qu[lane] = qu[32 + lane];
+        cnt -= 32;
+        __syncwarp();
+      }
+    });
+    if (lane < cnt) run(qu[lane]);
+    __syncwarp();
+    for (int i = 0; i < 3; ++i)
+      for (int off = 16; off > 0; off >>= 1) u[i] += __shfl_xor_sync(0xffffffffu, u[i], off);
+    if (lane == 0) {
+      int64_t o = a.sorig[w];
+      for (int i = 0; i < 3; ++i) atomicAdd(a.out + i * n + o, u[i]);
     }
   }
 }
@@ -244,11 +416,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_counts(RealArgs a, int3
       dst = w;
     } else {
       x[0] = a.spos[w]; x[1] = a.spos[a.n_src + w]; x[2] = a.spos[2 * a.n_src + w];
-      own = a.sorig[w];
-      dst = own;
+      own = w;
+      dst = a.sorig[w];
     }
+    float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
     int cf = 0, ci = 0;
-    for_candidates(a, x, own, lane, [&](bool hit, int j, int type) {
+    for_candidates(a, x, xf, own, lane, 0, 0, [&](bool hit, int j, int type) {
       unsigned mf = __ballot_sync(0xffffffffu, hit && type == Q_FREE);
       unsigned mi = __ballot_sync(0xffffffffu, hit && type == Q_IMAGE);
       cf += __popc(mf);
@@ -258,11 +431,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_counts(RealArgs a, int3
   }
 }
 
+// FP32 screening margin: the FP32 squared distance of two points inside a box
+// of side Lmax differs from the exact one by at most
+//   2 sqrt(3) |d| delta + 3 delta^2 + 2^-21 |d|^2,  delta = 1.5 2^-23 Lmax
+// (rounding of each coordinate to FP32, of the difference, of the squares and
+// sums).  Four times that bound around r_c^2 is sent to the FP64 test.
 static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add) {
   RealArgs a;
   a.n_src = n_src;
   a.n_tgt = n_tgt;
   a.spos = p->ws.spos;
+  a.spos32 = p->ws.spos32;
   a.sstr = p->ws.sstr;
   a.sorig = p->ws.val_a;
   a.cstart = p->ws.cell_start;
@@ -274,6 +453,12 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   a.xi = p->prm.xi;
   a.rc = p->prm.rc;
   a.rc2 = p->prm.rc * p->prm.rc;
+  double lmax = std::fmax(p->prm.box[0], std::fmax(p->prm.box[1], p->prm.box[2]));
+  double delta = 1.5 * std::ldexp(1.0, -23) * lmax;
+  double rc = p->prm.rc;
+  double m = 4.0 * (2.0 * std::sqrt(3.0) * rc * delta + 3.0 * delta * delta + std::ldexp(1.0, -21) * rc * rc);
+  a.rc2_lo = (float)std::fmax(0.0, a.rc2 - m) * (1.0f - 1e-6f);
+  a.rc2_hi = (float)(a.rc2 + m) * (1.0f + 1e-6f);
   for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = p->prm.ncell[d]; }
   return a;
 }
@@ -288,7 +473,12 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
                       cudaStream_t s) {
   if (n_tgt == 0) return HSE_OK;
   RealArgs a = make_args(p, n_src, n_tgt, tgt, out, add);
-  k_real<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+  if (tgt == nullptr && !add) {
+    HSE_CUDA(p, cudaMemsetAsync(out, 0, sizeof(double) * 3 * n_tgt, s));
+    k_real_sym<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+  } else {
+    k_real<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+  }
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_real");
 }
