@@ -36,6 +36,8 @@ WORKLOAD = dict(
     # parameters checked against the FP64 oracle on a target sample (tests/test_gpu_parity.py)
     xi=90.0, rc=0.0572, P=18, M=302,  # Mt = 320 = 2^6 x 5: a fast cuFFT size
 )
+# mixed-precision (FP32 arithmetic) configuration of the same workload at tolerance 1e-5
+MIXED = dict(tol=1e-5, xi=100.0)  # r_c, P, M from the plan tolerance rule
 METRIC = "Mtargets/s, N=1M stokeslet @1e-10 FP64 vs 1e-5 mixed; serve p50/p99 ms"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
@@ -275,6 +277,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_mixed:
+        out["mixed_1e-5"] = run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tps, k, dt = time_oracle(pr, mask, args.cpu_budget)
         out["cpu_baseline"] = {"value": tps / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -282,6 +286,41 @@ def run_ours(args, rank, world, local_rank):
                                          f"(FP64 direct half-space sum, OpenMP), {dt:.1f} s"}
     plan.close()
     return out
+
+
+def run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world):
+    """The same workload through the FP32-arithmetic path at tolerance 1e-5."""
+    Mx = MIXED
+    plan = pkg.Plan(WORKLOAD["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=0.0, P=0, tol=Mx["tol"],
+                    precision=pkg.HSE_MIXED)
+    plan.set_timing(True)
+    for _ in range(args.warmup):
+        plan.eval(src, st, out=vel)
+    torch.cuda.synchronize()
+    stages = {k: [] for k in pkg.hse.STAGE_NAMES}
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval(src, st, out=vel)
+        e1.record(stream)
+        s = plan.stats()
+        for k, v in s["stage_ms"].items():
+            stages[k].append(v)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    ms /= args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    prm = plan.params
+    plan.close()
+    n = src.shape[1]
+    return {"value": n * world / (float(t.item()) / 1e3) / 1e6, "unit": "Mtargets/s", "ms_per_step": float(t.item()),
+            "dtype": "f32 arithmetic (FP64 sums, close image pairs, tables)", "tol": Mx["tol"], "xi": prm["xi"],
+            "rc": prm["rc"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
+            "stage_ms": {k: round(float(np.mean(v)), 3) for k, v in stages.items()}}
 
 
 def run_real_only(args, pkg, torch, dev, W, pr):
@@ -342,6 +381,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the number of sources (smaller test runs)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-arithmetic measurement")
     ap.add_argument("--real-only", action="store_true",
                     help="profiling aid: plan without a grid, time only the real-space half")
     args = ap.parse_args()

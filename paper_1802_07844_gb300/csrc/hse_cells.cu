@@ -10,7 +10,8 @@ void free_workspace(hse_plan p) {
   Workspace& w = p->ws;
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
   cudaFree(w.cell_start); cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr);
-  cudaFree(w.prep); cudaFree(w.supp); cudaFree(w.flag); cudaFree(w.spos32);
+  cudaFree(w.prep); cudaFree(w.supp); cudaFree(w.flag); cudaFree(w.spos32); cudaFree(w.spos32lo);
+  cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
   if (w.flag_host) cudaFreeHost(w.flag_host);
   w = Workspace();
 }
@@ -33,10 +34,12 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   int64_t cap = n < 1024 ? 1024 : n;
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
   cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr); cudaFree(w.prep); cudaFree(w.supp);
-  cudaFree(w.spos32);
+  cudaFree(w.spos32); cudaFree(w.spos32lo); cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
+  w.usort = nullptr;
+  w.usort4 = nullptr;
   w.key_a = w.key_b = w.val_a = w.val_b = w.radix_hist = w.supp = nullptr;
   w.spos = w.sstr = w.prep = nullptr;
-  w.spos32 = nullptr;
+  w.spos32 = w.spos32lo = w.sstr32 = nullptr;
   w.cap = 0;
   int64_t ntiles = (cap + 2047) / 2048;
   HSE_CUDA(p, cudaMalloc(&w.key_a, sizeof(int32_t) * cap));
@@ -46,6 +49,10 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   HSE_CUDA(p, cudaMalloc(&w.radix_hist, sizeof(int32_t) * 256 * ntiles));
   HSE_CUDA(p, cudaMalloc(&w.spos, sizeof(double) * 3 * cap));
   HSE_CUDA(p, cudaMalloc(&w.spos32, sizeof(float) * 3 * cap));
+  HSE_CUDA(p, cudaMalloc(&w.spos32lo, sizeof(float) * 3 * cap));
+  HSE_CUDA(p, cudaMalloc(&w.sstr32, sizeof(float) * 12 * cap));
+  HSE_CUDA(p, cudaMalloc(&w.usort, sizeof(double) * 3 * cap));
+  HSE_CUDA(p, cudaMalloc(&w.usort4, sizeof(float4) * cap));
   HSE_CUDA(p, cudaMalloc(&w.sstr, sizeof(double) * 12 * cap));
   HSE_CUDA(p, cudaMalloc(&w.prep, sizeof(double) * (3 * (size_t)p->prm.P + ncomp) * cap));
   HSE_CUDA(p, cudaMalloc(&w.supp, sizeof(int32_t) * 4 * cap));
@@ -206,15 +213,21 @@ __global__ void k_cell_start(const int32_t* __restrict__ key, int64_t n, int64_t
 
 __global__ void k_gather_sorted(int64_t n, int rows, const int32_t* __restrict__ perm, const double* __restrict__ pos,
                                 const double* __restrict__ str, double* __restrict__ spos, float* __restrict__ spos32,
-                                double* __restrict__ sstr) {
+                                float* __restrict__ spos32lo, double* __restrict__ sstr, float* __restrict__ sstr32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = perm[i];
     for (int d = 0; d < 3; ++d) {
       double v = pos[d * n + j];
+      float hi = (float)v;
       spos[d * n + i] = v;
-      spos32[d * n + i] = (float)v;
+      spos32[d * n + i] = hi;
+      spos32lo[d * n + i] = (float)(v - (double)hi);
     }
-    for (int r = 0; r < rows; ++r) sstr[r * n + i] = str[r * n + j];
+    for (int r = 0; r < rows; ++r) {
+      double v = str[r * n + j];
+      sstr[r * n + i] = v;
+      sstr32[r * n + i] = (float)v;
+    }
   }
 }
 
@@ -265,7 +278,7 @@ hse_status build_cell_list(hse_plan p, int64_t n, const double* pos, int32_t* ce
 hse_status gather_sorted(hse_plan p, int64_t n, const double* pos, const double* str, cudaStream_t s) {
   if (n == 0) return HSE_OK;
   k_gather_sorted<<<nblocks(n, 256), 256, 0, s>>>(n, str ? p->n_rows : 0, p->ws.val_a, pos, str, p->ws.spos,
-                                                   p->ws.spos32, p->ws.sstr);
+                                                   p->ws.spos32, p->ws.spos32lo, p->ws.sstr, p->ws.sstr32);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_gather_sorted");
 }

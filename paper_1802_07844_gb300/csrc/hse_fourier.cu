@@ -22,6 +22,7 @@
 namespace hse {
 
 // ----------------------------------------------------------------------- prep
+template <typename T>
 struct PrepArgs {
   int64_t n;
   const double* spos;
@@ -31,11 +32,12 @@ struct PrepArgs {
   int P, Mt;
   double h, ox, oz, alpha, pre;
   int stride;
-  double* prep;
+  T* prep;
   int4* supp;
 };
 
-__global__ void k_prep(PrepArgs a) {
+template <typename T>
+__global__ void k_prep(PrepArgs<T> a) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = a.n;
     double x = a.spos[i], y = a.spos[n + i], z = a.spos[2 * n + i];
@@ -43,16 +45,16 @@ __global__ void k_prep(PrepArgs a) {
     int iy0 = support_start(y, a.ox, a.h, a.P, a.Mt);
     int iz0 = support_start(z, a.oz, a.h, a.P, 2 * a.Mt);
     a.supp[i] = make_int4(ix0, iy0, iz0, 0);
-    double* o = a.prep + i * (int64_t)a.stride;
+    T* o = a.prep + i * (int64_t)a.stride;
     for (int t = 0; t < a.P; ++t) {
       double dx = a.ox + (ix0 + t) * a.h - x;
       double dy = a.ox + (iy0 + t) * a.h - y;
       double dz = a.oz + (iz0 + t) * a.h - z;
-      o[t] = a.pre * exp(-a.alpha * dx * dx);
-      o[a.P + t] = exp(-a.alpha * dy * dy);
-      o[2 * a.P + t] = exp(-a.alpha * dz * dz);
+      o[t] = (T)(a.pre * exp(-a.alpha * dx * dx));
+      o[a.P + t] = (T)exp(-a.alpha * dy * dy);
+      o[2 * a.P + t] = (T)exp(-a.alpha * dz * dz);
     }
-    double* c = o + 3 * a.P;
+    T* c = o + 3 * a.P;
     int k = 0;
     double f[3] = {0, 0, 0}, g[3] = {0, 0, 0}, q[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
     if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) f[d] = a.sstr[(a.rowS + d) * n + i];
@@ -69,52 +71,53 @@ __global__ void k_prep(PrepArgs a) {
     }
     double gdq = g[0] * q[0] + g[1] * q[1] + g[2] * q[2];
     if (!a.paper) {
-      if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) c[k++] = f[d];
-      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = sgq[m];
-      if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = tau[d];
-      if (a.mask & HSE_STOKESLET) c[k++] = -2.0 * f[2];
+      if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) c[k++] = (T)f[d];
+      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)sgq[m];
+      if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = (T)tau[d];
+      if (a.mask & HSE_STOKESLET) c[k++] = (T)(-2.0 * f[2]);
       double cv[3] = {0, 0, 0};
       if (a.mask & HSE_STOKESLET) { cv[0] += -2.0 * hz * f[0]; cv[1] += -2.0 * hz * f[1]; cv[2] += 2.0 * hz * f[2]; }
       if (a.mask & HSE_STRESSLET) cv[2] += 4.0 * gdq;
       if (a.mask & HSE_ROTLET) { cv[0] += -4.0 * tau[1]; cv[1] += 4.0 * tau[0]; }
-      for (int d = 0; d < 3; ++d) c[k++] = cv[d];
-      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = 4.0 * hz * sgqI[m];
+      for (int d = 0; d < 3; ++d) c[k++] = (T)cv[d];
+      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)(4.0 * hz * sgqI[m]);
     } else {
       if (a.mask & HSE_STOKESLET) {
-        for (int d = 0; d < 3; ++d) c[k++] = f[d];
-        c[k++] = f[2];
-        c[k++] = hz * f[0]; c[k++] = hz * f[1]; c[k++] = -hz * f[2];
+        for (int d = 0; d < 3; ++d) c[k++] = (T)f[d];
+        c[k++] = (T)f[2];
+        c[k++] = (T)(hz * f[0]); c[k++] = (T)(hz * f[1]); c[k++] = (T)(-hz * f[2]);
       }
       if (a.mask & HSE_STRESSLET) {
-        for (int m = 0; m < 6; ++m) c[k++] = sgq[m];
-        c[k++] = gdq;
-        for (int m = 0; m < 6; ++m) c[k++] = hz * sgqI[m];
+        for (int m = 0; m < 6; ++m) c[k++] = (T)sgq[m];
+        c[k++] = (T)gdq;
+        for (int m = 0; m < 6; ++m) c[k++] = (T)(hz * sgqI[m]);
       }
       if (a.mask & HSE_ROTLET) {
-        for (int d = 0; d < 3; ++d) c[k++] = tau[d];
-        c[k++] = -tau[1]; c[k++] = tau[0];
+        for (int d = 0; d < 3; ++d) c[k++] = (T)tau[d];
+        c[k++] = (T)(-tau[1]); c[k++] = (T)tau[0];
       }
     }
   }
 }
 
 // --------------------------------------------------------------------- spread
+template <typename T>
 struct SpreadArgs {
   const int4* supp;
-  const double* prep;
+  const T* prep;
   const int32_t* cstart;
   int stride, P, Mt, z0, nz_tiles;
   double h, ox, oz;
   double inv_cell[3];
   int ncell[3];
-  double* out;           // component c, point (i,j,k) at out + c*cs + i*xs + j*pitch + k
+  T* out;                // component c, point (i,j,k) at out + c*cs + i*xs + j*pitch + k
   int64_t cs, xs, pitch;
 };
 
 constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
 
-template <int NC>
-__global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   __shared__ int list[256];
   __shared__ int wcount[8];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -122,9 +125,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
   const int sx = bx0 + 2 * (w & 1), sy = by0 + 4 * ((w >> 1) & 1), sz = bz0 + 4 * (w >> 2);
   const int px = sx + (lane & 1), py = sy + ((lane >> 1) & 3), pz = sz + (lane >> 3);
   const int P = a.P;
-  double acc[NC];
+  T acc[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NC; ++c) acc[c] = (T)0;
   // positions whose support can reach this tile (one grid step of slack for clamping)
   auto cell_range = [&](int lo_idx, int hi_idx, double o, int d, int& c0, int& c1) {
     double lo = o + (lo_idx - P / 2 - 1) * a.h, hi = o + (hi_idx + P / 2 + 1) * a.h;
@@ -163,9 +166,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
           if (!warp_hit) continue;
           int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
           if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
-            const double* o = a.prep + (int64_t)jj * a.stride;
-            double wv = o[dx] * o[P + dy] * o[2 * P + dz];
-            const double* cv = o + 3 * P;
+            const T* o = a.prep + (int64_t)jj * a.stride;
+            T wv = o[dx] * o[P + dy] * o[2 * P + dz];
+            const T* cv = o + 3 * P;
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] += wv * cv[c];
           }
@@ -174,44 +177,47 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
       }
     }
   if (px < a.Mt && py < a.Mt && pz < 2 * a.Mt) {
-    double* dst = a.out + px * a.xs + py * a.pitch + pz;
+    T* dst = a.out + px * a.xs + py * a.pitch + pz;
 #pragma unroll
     for (int c = 0; c < NC; ++c) dst[c * a.cs] = acc[c];
   }
 }
 
-template <int NC>
-static void launch_spread_t(const SpreadArgs& a, dim3 grid, cudaStream_t s) {
-  k_spread<NC><<<grid, 256, 0, s>>>(a);
+template <typename T, int NC>
+static void launch_spread_t(const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
+  k_spread<T, NC><<<grid, 256, 0, s>>>(a);
 }
 
-static bool launch_spread(int nc, const SpreadArgs& a, dim3 grid, cudaStream_t s) {
+template <typename T>
+static bool launch_spread(int nc, const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
   switch (nc) {
-    case 5: launch_spread_t<5>(a, grid, s); return true;
-    case 6: launch_spread_t<6>(a, grid, s); return true;
-    case 7: launch_spread_t<7>(a, grid, s); return true;
-    case 10: launch_spread_t<10>(a, grid, s); return true;
-    case 12: launch_spread_t<12>(a, grid, s); return true;
-    case 13: launch_spread_t<13>(a, grid, s); return true;
-    case 15: launch_spread_t<15>(a, grid, s); return true;
-    case 18: launch_spread_t<18>(a, grid, s); return true;
-    case 19: launch_spread_t<19>(a, grid, s); return true;
-    case 20: launch_spread_t<20>(a, grid, s); return true;
-    case 22: launch_spread_t<22>(a, grid, s); return true;
-    case 25: launch_spread_t<25>(a, grid, s); return true;
+    case 5: launch_spread_t<T, 5>(a, grid, s); return true;
+    case 6: launch_spread_t<T, 6>(a, grid, s); return true;
+    case 7: launch_spread_t<T, 7>(a, grid, s); return true;
+    case 10: launch_spread_t<T, 10>(a, grid, s); return true;
+    case 12: launch_spread_t<T, 12>(a, grid, s); return true;
+    case 13: launch_spread_t<T, 13>(a, grid, s); return true;
+    case 15: launch_spread_t<T, 15>(a, grid, s); return true;
+    case 18: launch_spread_t<T, 18>(a, grid, s); return true;
+    case 19: launch_spread_t<T, 19>(a, grid, s); return true;
+    case 20: launch_spread_t<T, 20>(a, grid, s); return true;
+    case 22: launch_spread_t<T, 22>(a, grid, s); return true;
+    case 25: launch_spread_t<T, 25>(a, grid, s); return true;
   }
   return false;
 }
 
 // --------------------------------------------------------------------- mirror
+template <typename T>
 struct MirrorArgs {
-  double* buf;
+  T* buf;
   int64_t cs, xs, pitch;
   int Mt, nc;
   int sign[kMaxComp];
 };
 
-__global__ void k_mirror(MirrorArgs a) {
+template <typename T>
+__global__ void k_mirror(MirrorArgs<T> a) {
   const int Mt = a.Mt;
   const int64_t per = (int64_t)Mt * Mt * (Mt + 1);
   const int64_t total = per * a.nc;
@@ -221,14 +227,14 @@ __global__ void k_mirror(MirrorArgs a) {
     int k = (int)(r % (Mt + 1));
     int64_t ij = r / (Mt + 1);
     int j = (int)(ij % Mt), i = (int)(ij / Mt);
-    double* col = a.buf + c * a.cs + i * a.xs + j * a.pitch;
+    T* col = a.buf + c * a.cs + i * a.xs + j * a.pitch;
     int kp = 2 * Mt - k;
-    double va = col[k];
-    double vb = kp < 2 * Mt ? col[kp] : 0.0;
+    T va = col[k];
+    T vb = kp < 2 * Mt ? col[kp] : (T)0;
     int s = a.sign[c];
     if (s != 0) {
-      col[k] = va + s * vb;
-      if (kp < 2 * Mt && kp != k) col[kp] = vb + s * va;
+      col[k] = va + (T)s * vb;
+      if (kp < 2 * Mt && kp != k) col[kp] = vb + (T)s * va;
     } else {
       col[k] = vb;
       if (kp < 2 * Mt && kp != k) col[kp] = va;
@@ -237,82 +243,94 @@ __global__ void k_mirror(MirrorArgs a) {
 }
 
 // ---------------------------------------------------------------------- scale
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { typedef double2 type; };
+template <> struct Cplx<float> { typedef float2 type; };
+
+template <typename T>
 struct ScaleArgs {
-  double2* buf;           // complex view of the spectra
-  int64_t cstride;        // complex elements per buffer
+  typename Cplx<T>::type* buf;  // complex view of the spectra
+  int64_t cstride;              // complex elements per buffer
   int Mt, mask;
   double h;
-  const double* tabB;
-  const double* tabH;
+  const T* tabB;
+  const T* tabH;
   int iS, iT, iW, iCs, iCv, iCt;  // first component index of each group, -1 if absent
 };
 
-__device__ __forceinline__ double2 cmul_i(double2 z) { return make_double2(-z.y, z.x); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cscale(double s, double2 z) { return make_double2(s * z.x, s * z.y); }
+template <typename C, typename T>
+__device__ __forceinline__ C cmk(T x, T y) { C z; z.x = x; z.y = y; return z; }
+template <typename C>
+__device__ __forceinline__ C cmul_i(C z) { return cmk<C>(-z.y, z.x); }
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C, typename T>
+__device__ __forceinline__ C cscale(T s, C z) { return cmk<C>(s * z.x, s * z.y); }
 
-__global__ void k_scale(ScaleArgs a) {
+template <typename T>
+__global__ void k_scale(ScaleArgs<T> a) {
+  typedef typename Cplx<T>::type C;
   const int Mt = a.Mt, Nx = 2 * Mt, Ny = 2 * Mt, Nzh = 2 * Mt + 1;
   const int64_t nh = (int64_t)Nx * Ny * Nzh;
-  const double dkx = 2.0 * kPi / (Nx * a.h), dkz = 2.0 * kPi / (4.0 * Mt * a.h);
+  const T dkx = (T)(2.0 * kPi / (Nx * a.h)), dkz = (T)(2.0 * kPi / (4.0 * Mt * a.h));
+  const C zero = cmk<C>((T)0, (T)0);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nh; e += (int64_t)gridDim.x * blockDim.x) {
     int jz = (int)(e % Nzh);
     int64_t t = e / Nzh;
     int iy = (int)(t % Ny), ix = (int)(t / Ny);
-    double2 T1[3], T2[3];
+    C T1[3], T2[3];
     if (ix == Mt || iy == Mt || jz == 2 * Mt) {  // Nyquist modes are dropped
-      for (int d = 0; d < 3; ++d) T1[d] = T2[d] = make_double2(0.0, 0.0);
+      for (int d = 0; d < 3; ++d) T1[d] = T2[d] = zero;
     } else {
       int wx = ix <= Mt ? ix : ix - Nx, wy = iy <= Mt ? iy : iy - Ny;
-      double k[3] = {dkx * wx, dkx * wy, dkz * jz};
-      double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+      T k[3] = {dkx * wx, dkx * wy, dkz * jz};
+      T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
       int64_t ti = ((int64_t)abs(wx) * (Mt + 1) + abs(wy)) * Nzh + jz;
-      double TH = a.tabH[ti];
-      double TB = a.tabB ? a.tabB[ti] : 0.0;
-      for (int d = 0; d < 3; ++d) T1[d] = make_double2(0.0, 0.0);
+      T TH = a.tabH[ti];
+      T TB = a.tabB ? a.tabB[ti] : (T)0;
+      for (int d = 0; d < 3; ++d) T1[d] = zero;
       auto ld = [&](int c) { return a.buf[c * a.cstride + e]; };
       if (a.iS >= 0) {  // -(k^2 I - k k) (1 + k^2/4xi^2) E B^R C1
-        double2 C[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
-        double2 kc = cadd(cadd(cscale(k[0], C[0]), cscale(k[1], C[1])), cscale(k[2], C[2]));
-        for (int d = 0; d < 3; ++d)
-          T1[d] = cadd(T1[d], cscale(-TB, cadd(cscale(k2, C[d]), cscale(-k[d], kc))));
+        C Cv[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
+        C kc = cadd(cadd(cscale(k[0], Cv[0]), cscale(k[1], Cv[1])), cscale(k[2], Cv[2]));
+        for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale(-TB, cadd(cscale(k2, Cv[d]), cscale(-k[d], kc))));
       }
       if (a.iT >= 0) {  // -i (1 + k^2/4xi^2) E B^R [(k d + k d + k d) k^2 - 2 k k k] : C
-        double2 c6[6];
+        C c6[6];
         for (int m = 0; m < 6; ++m) c6[m] = ld(a.iT + m);
         const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-        double2 Ck[3], tr = cadd(cadd(c6[0], c6[3]), c6[5]);
+        C Ck[3], tr = cadd(cadd(c6[0], c6[3]), c6[5]);
         for (int j = 0; j < 3; ++j) {
-          Ck[j] = make_double2(0.0, 0.0);
+          Ck[j] = zero;
           for (int m = 0; m < 3; ++m) Ck[j] = cadd(Ck[j], cscale(k[m], c6[sidx[j][m]]));
         }
-        double2 kCk = cadd(cadd(cscale(k[0], Ck[0]), cscale(k[1], Ck[1])), cscale(k[2], Ck[2]));
+        C kCk = cadd(cadd(cscale(k[0], Ck[0]), cscale(k[1], Ck[1])), cscale(k[2], Ck[2]));
         for (int j = 0; j < 3; ++j) {
-          double2 v = cadd(cscale(k2, cadd(cscale(2.0, Ck[j]), cscale(k[j], tr))), cscale(-2.0 * k[j], kCk));
+          C v = cadd(cscale(k2, cadd(cscale((T)2, Ck[j]), cscale(k[j], tr))), cscale((T)(-2) * k[j], kCk));
           T1[j] = cadd(T1[j], cscale(-TB, cmul_i(v)));
         }
       }
       if (a.iW >= 0) {  // -2 i E H^R (C x k)
-        double2 C[3] = {ld(a.iW), ld(a.iW + 1), ld(a.iW + 2)};
-        double2 cr[3] = {cadd(cscale(k[2], C[1]), cscale(-k[1], C[2])), cadd(cscale(k[0], C[2]), cscale(-k[2], C[0])),
-                         cadd(cscale(k[1], C[0]), cscale(-k[0], C[1]))};
-        for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale(-2.0 * TH, cmul_i(cr[d])));
+        C Cv[3] = {ld(a.iW), ld(a.iW + 1), ld(a.iW + 2)};
+        C cr[3] = {cadd(cscale(k[2], Cv[1]), cscale(-k[1], Cv[2])), cadd(cscale(k[0], Cv[2]), cscale(-k[2], Cv[0])),
+                   cadd(cscale(k[1], Cv[0]), cscale(-k[0], Cv[1]))};
+        for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale((T)(-2) * TH, cmul_i(cr[d])));
       }
       // merged harmonic corrections: phi^ = E H^R (Cs^ + i k.Cv^ + k.Ct^.k)
-      double2 ph = make_double2(0.0, 0.0);
+      C ph = zero;
       if (a.iCs >= 0) ph = ld(a.iCs);
       {
-        double2 v[3] = {ld(a.iCv), ld(a.iCv + 1), ld(a.iCv + 2)};
-        double2 kv = cadd(cadd(cscale(k[0], v[0]), cscale(k[1], v[1])), cscale(k[2], v[2]));
+        C v[3] = {ld(a.iCv), ld(a.iCv + 1), ld(a.iCv + 2)};
+        C kv = cadd(cadd(cscale(k[0], v[0]), cscale(k[1], v[1])), cscale(k[2], v[2]));
         ph = cadd(ph, cmul_i(kv));
       }
       if (a.iCt >= 0) {
-        double2 c6[6];
+        C c6[6];
         for (int m = 0; m < 6; ++m) c6[m] = ld(a.iCt + m);
-        double2 kck = cadd(cadd(cscale(k[0] * k[0], c6[0]), cscale(k[1] * k[1], c6[3])), cscale(k[2] * k[2], c6[5]));
-        kck = cadd(kck, cscale(2.0 * k[0] * k[1], c6[1]));
-        kck = cadd(kck, cscale(2.0 * k[0] * k[2], c6[2]));
-        kck = cadd(kck, cscale(2.0 * k[1] * k[2], c6[4]));
+        C kck = cadd(cadd(cscale(k[0] * k[0], c6[0]), cscale(k[1] * k[1], c6[3])), cscale(k[2] * k[2], c6[5]));
+        kck = cadd(kck, cscale((T)2 * k[0] * k[1], c6[1]));
+        kck = cadd(kck, cscale((T)2 * k[0] * k[2], c6[2]));
+        kck = cadd(kck, cscale((T)2 * k[1] * k[2], c6[4]));
         ph = cadd(ph, kck);
       }
       ph = cscale(TH, ph);
@@ -327,12 +345,13 @@ __global__ void k_scale(ScaleArgs a) {
 }
 
 // --------------------------------------------------------------------- gather
+template <typename T>
 struct GatherArgs {
   int64_t n_tgt, n_src;
   const double* tgt;      // explicit targets or null
   const double* spos;     // sorted sources (targets = sources)
   const int32_t* sorig;
-  const double* buf;      // fields T1x..T2z, buffer stride bs, real layout
+  const T* buf;           // fields T1x..T2z, buffer stride bs, real layout
   int64_t bs, xs, pitch;
   int P, Mt;
   double h, ox, oz, alpha, pre, h3;
@@ -342,12 +361,13 @@ struct GatherArgs {
 
 constexpr int kGatherWarps = 4;
 
-__global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs a) {
-  __shared__ double wsm[kGatherWarps][3][kMaxP];
+template <typename T>
+__global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
+  __shared__ T wsm[kGatherWarps][3][kMaxP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* wx = wsm[wib][0];
-  double* wy = wsm[wib][1];
-  double* wz = wsm[wib][2];
+  T* wx = wsm[wib][0];
+  T* wy = wsm[wib][1];
+  T* wz = wsm[wib][2];
   const int P = a.P;
   const int64_t nwarps = (int64_t)gridDim.x * kGatherWarps;
   for (int64_t w = blockIdx.x * (int64_t)kGatherWarps + wib; w < a.n_tgt; w += nwarps) {
@@ -368,25 +388,25 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs a) {
       double dx = a.ox + (ix0 + lane) * a.h - x;
       double dy = a.ox + (iy0 + lane) * a.h - y;
       double dz = a.oz + (iz0 + lane) * a.h - z;
-      wx[lane] = a.pre * exp(-a.alpha * dx * dx);
-      wy[lane] = exp(-a.alpha * dy * dy);
-      wz[lane] = exp(-a.alpha * dz * dz);
+      wx[lane] = (T)(a.pre * exp(-a.alpha * dx * dx));
+      wy[lane] = (T)exp(-a.alpha * dy * dy);
+      wz[lane] = (T)exp(-a.alpha * dz * dz);
     }
     __syncwarp();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int q = lane; q < P * P; q += 32) {
       int jj = q / P, kk = q - jj * P;
-      double s[6] = {0, 0, 0, 0, 0, 0};
-      const double* col = a.buf + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
+      T s[6] = {0, 0, 0, 0, 0, 0};
+      const T* col = a.buf + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
       for (int ii = 0; ii < P; ++ii) {
-        double wv = wx[ii];
-        const double* pnt = col + (int64_t)ii * a.xs;
+        T wv = wx[ii];
+        const T* pnt = col + (int64_t)ii * a.xs;
 #pragma unroll
         for (int c = 0; c < 6; ++c) s[c] += wv * pnt[c * a.bs];
       }
-      double wyz = wy[jj] * wz[kk];
+      T wyz = wy[jj] * wz[kk];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += wyz * s[c];
+      for (int c = 0; c < 6; ++c) acc[c] += (double)(wyz * s[c]);
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c)
@@ -408,9 +428,10 @@ static int blocks_for(int64_t n, int t, int cap) {
   return b < 1 ? 1 : (int)b;
 }
 
-static PrepArgs prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
+template <typename T>
+static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   const hse_params& q = p->prm;
-  PrepArgs a;
+  PrepArgs<T> a;
   a.n = n;
   a.spos = p->ws.spos;
   a.sstr = p->ws.sstr;
@@ -425,21 +446,22 @@ static PrepArgs prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   a.alpha = 2.0 * q.xi * q.xi / q.eta;
   a.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
   a.stride = 3 * q.P + ncomp;
-  a.prep = p->ws.prep;
+  a.prep = reinterpret_cast<T*>(p->ws.prep);
   a.supp = reinterpret_cast<int4*>(p->ws.supp);
   return a;
 }
 
-static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int paper, double* out, int64_t cstride,
+template <typename T>
+static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int paper, T* out, int64_t cstride,
                               int64_t xs, int64_t pitch, cudaStream_t s) {
   const hse_params& q = p->prm;
-  PrepArgs pa = prep_args(p, n_src, paper, cs.n);
+  PrepArgs<T> pa = prep_args<T>(p, n_src, paper, cs.n);
   if (n_src > 0) {
-    k_prep<<<blocks_for(n_src, 128, 152 * 32), 128, 0, s>>>(pa);
+    k_prep<T><<<blocks_for(n_src, 128, 152 * 32), 128, 0, s>>>(pa);
     ++p->n_launch;
     HSE_CUDA(p, cudaGetLastError());
   }
-  SpreadArgs a;
+  SpreadArgs<T> a;
   a.supp = pa.supp;
   a.prep = pa.prep;
   a.cstart = p->ws.cell_start;
@@ -457,10 +479,10 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.pitch = pitch;
   int nzr = 2 * q.Mt - p->zA0;
   dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, (nzr + kTZ - 1) / kTZ);
-  if (!launch_spread(cs.n, a, grid, s)) return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
+  if (!launch_spread<T>(cs.n, a, grid, s)) return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
-  MirrorArgs m;
+  MirrorArgs<T> m;
   m.buf = out;
   m.cs = cstride;
   m.xs = xs;
@@ -469,7 +491,7 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   m.nc = cs.n;
   for (int c = 0; c < cs.n; ++c) m.sign[c] = cs.mirror_sign[c];
   int64_t tot = (int64_t)q.Mt * q.Mt * (q.Mt + 1) * cs.n;
-  k_mirror<<<blocks_for(tot, 256, 152 * 64), 256, 0, s>>>(m);
+  k_mirror<T><<<blocks_for(tot, 256, 152 * 64), 256, 0, s>>>(m);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_mirror");
 }
@@ -479,37 +501,57 @@ hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStre
   CompSet cs = paper_components(p->prm.kernel_mask);
   int64_t per = (int64_t)Mt * Mt * 2 * Mt;
   HSE_CUDA(p, cudaMemsetAsync(grids, 0, sizeof(double) * per * cs.n, s));
-  return spread_into(p, n_src, cs, 1, grids, per, (int64_t)Mt * 2 * Mt, 2 * Mt, s);
+  return spread_into<double>(p, n_src, cs, 1, grids, per, (int64_t)Mt * 2 * Mt, 2 * Mt, s);
 }
 
-hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
-                         cudaStream_t s) {
+// forward / inverse zero-padded transforms of one buffer (double or float)
+static cufftResult fft_forward(hse_plan p, double* b) {
+  cufftDoubleComplex* z = reinterpret_cast<cufftDoubleComplex*>(b);
+  cufftResult r = cufftExecD2Z(p->fwd2d, b, z);
+  return r == CUFFT_SUCCESS ? cufftExecZ2Z(p->fftx, z, z, CUFFT_FORWARD) : r;
+}
+static cufftResult fft_forward(hse_plan p, float* b) {
+  cufftComplex* z = reinterpret_cast<cufftComplex*>(b);
+  cufftResult r = cufftExecR2C(p->fwd2d, b, z);
+  return r == CUFFT_SUCCESS ? cufftExecC2C(p->fftx, z, z, CUFFT_FORWARD) : r;
+}
+static cufftResult fft_inverse(hse_plan p, double* b) {
+  cufftDoubleComplex* z = reinterpret_cast<cufftDoubleComplex*>(b);
+  cufftResult r = cufftExecZ2Z(p->fftx, z, z, CUFFT_INVERSE);
+  return r == CUFFT_SUCCESS ? cufftExecZ2D(p->inv2d, z, b) : r;
+}
+static cufftResult fft_inverse(hse_plan p, float* b) {
+  cufftComplex* z = reinterpret_cast<cufftComplex*>(b);
+  cufftResult r = cufftExecC2C(p->fftx, z, z, CUFFT_INVERSE);
+  return r == CUFFT_SUCCESS ? cufftExecC2R(p->inv2d, z, b) : r;
+}
+
+template <typename T>
+static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
+                                  cudaStream_t s) {
   const hse_params& q = p->prm;
   const GridDims& g = p->g;
   const int nin = p->comps.n;
-  HSE_CUDA(p, cudaMemsetAsync(p->spec, 0, sizeof(double) * g.buf_doubles * nin, s));
-  HSE_TRY(spread_into(p, n_src, p->comps, 0, p->spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
+  T* spec = reinterpret_cast<T*>(p->spec);
+  HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nin, s));
+  HSE_TRY(spread_into<T>(p, n_src, p->comps, 0, spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
   stage_mark(p, HSE_STAGE_FFT, s);
-  // forward transforms of every component
   if (cufftSetStream(p->fwd2d, s) != CUFFT_SUCCESS || cufftSetStream(p->inv2d, s) != CUFFT_SUCCESS ||
       cufftSetStream(p->fftx, s) != CUFFT_SUCCESS)
     return set_err(p, HSE_ERR_CUFFT, "cufftSetStream");
   for (int c = 0; c < nin; ++c) {
-    double* b = p->spec + c * g.buf_doubles;
-    cufftDoubleComplex* z = reinterpret_cast<cufftDoubleComplex*>(b);
-    cufftResult r = cufftExecD2Z(p->fwd2d, b, z);
-    if (r == CUFFT_SUCCESS) r = cufftExecZ2Z(p->fftx, z, z, CUFFT_FORWARD);
+    cufftResult r = fft_forward(p, spec + c * g.buf_doubles);
     ++p->n_fft;
     if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "forward FFT: %d", (int)r);
   }
-  ScaleArgs sa;
-  sa.buf = reinterpret_cast<double2*>(p->spec);
+  ScaleArgs<T> sa;
+  sa.buf = reinterpret_cast<typename Cplx<T>::type*>(spec);
   sa.cstride = g.nh;
   sa.Mt = q.Mt;
   sa.mask = q.kernel_mask;
   sa.h = q.h;
-  sa.tabB = p->tabB;
-  sa.tabH = p->tabH;
+  sa.tabB = reinterpret_cast<const T*>(p->tabB);
+  sa.tabH = reinterpret_cast<const T*>(p->tabH);
   int k = 0;
   sa.iS = sa.iT = sa.iW = sa.iCs = sa.iCt = -1;
   if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
@@ -519,27 +561,24 @@ hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double*
   sa.iCv = k; k += 3;
   if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
   stage_mark(p, HSE_STAGE_SCALE, s);
-  k_scale<<<blocks_for(g.nh, 256, 152 * 32), 256, 0, s>>>(sa);
+  k_scale<T><<<blocks_for(g.nh, 256, 152 * 32), 256, 0, s>>>(sa);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
   stage_mark(p, HSE_STAGE_IFFT, s);
   for (int c = 0; c < 6; ++c) {
-    double* b = p->spec + c * g.buf_doubles;
-    cufftDoubleComplex* z = reinterpret_cast<cufftDoubleComplex*>(b);
-    cufftResult r = cufftExecZ2Z(p->fftx, z, z, CUFFT_INVERSE);
-    if (r == CUFFT_SUCCESS) r = cufftExecZ2D(p->inv2d, z, b);
+    cufftResult r = fft_inverse(p, spec + c * g.buf_doubles);
     ++p->n_fft;
     if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "inverse FFT: %d", (int)r);
   }
   stage_mark(p, HSE_STAGE_GATHER, s);
   if (n_tgt == 0) return HSE_OK;
-  GatherArgs ga;
+  GatherArgs<T> ga;
   ga.n_tgt = n_tgt;
   ga.n_src = n_src;
   ga.tgt = tgt;
   ga.spos = p->ws.spos;
   ga.sorig = p->ws.val_a;
-  ga.buf = p->spec;
+  ga.buf = spec;
   ga.bs = g.buf_doubles;
   ga.xs = (int64_t)g.Ny * g.pitch;
   ga.pitch = g.pitch;
@@ -553,9 +592,15 @@ hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double*
   ga.h3 = q.h * q.h * q.h;
   ga.out = out;
   ga.add = add ? 1 : 0;
-  k_gather<<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  k_gather<T><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_gather");
+}
+
+hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
+                         cudaStream_t s) {
+  if (p->prm.precision == HSE_MIXED) return fourier_space_t<float>(p, n_src, n_tgt, tgt, out, add, s);
+  return fourier_space_t<double>(p, n_src, n_tgt, tgt, out, add, s);
 }
 
 }  // namespace hse

@@ -27,7 +27,7 @@ struct GridDims {
   int Nx = 0, Ny = 0, Nz = 0;
   int64_t pitch = 0;        // doubles per real z-row
   int64_t nh = 0;           // complex points per buffer
-  int64_t buf_doubles = 0;  // doubles per buffer
+  int64_t buf_doubles = 0;  // real elements per buffer (double or float by precision)
 };
 
 // Spread-component description: which FFT input each component feeds and how
@@ -48,7 +48,11 @@ struct Workspace {
   int32_t* radix_hist = nullptr;
   int64_t hist_cap = 0;
   double* spos = nullptr;      // 3 x cap sorted source positions
-  float* spos32 = nullptr;     // the same rounded to FP32
+  float* spos32 = nullptr;     // the same rounded to FP32 (head)
+  float* spos32lo = nullptr;   // x - head, rounded to FP32 (tail)
+  float* sstr32 = nullptr;     // sorted strengths in FP32 (mixed precision)
+  double* usort = nullptr;     // 3 x cap real-space sums in sorted order (symmetric kernel)
+  float4* usort4 = nullptr;    // cap partner sums in FP32 (mixed-precision symmetric kernel)
   double* sstr = nullptr;      // rows x cap sorted strengths
   double* prep = nullptr;      // per sorted particle: 3P weights + ncomp strengths
   int32_t* supp = nullptr;     // per sorted particle: ix0, iy0, iz0, pad
@@ -70,9 +74,9 @@ struct hse_plan_s {
   int n_rows = 0;   // strength rows
   int row_S = -1, row_T = -1, row_W = -1;
   // device grids
-  double* spec = nullptr;  // n_fft_in buffers
-  double* tabB = nullptr;  // s E B^R / Np on the octant (Mt+1)(Mt+1)(2Mt+1)
-  double* tabH = nullptr;  // E H^R / Np on the octant
+  double* spec = nullptr;  // n_fft_in buffers (float elements with HSE_MIXED)
+  double* tabB = nullptr;  // s E B^R / Np on the octant (Mt+1)(Mt+1)(2Mt+1) (float with HSE_MIXED)
+  double* tabH = nullptr;  // E H^R / Np on the octant (float with HSE_MIXED)
   // zero-padded transforms split into a 2-D (y,z) transform over the Mt planes
   // that hold data (fwd2d R2C / inv2d C2R) and a 1-D transform along x over
   // all (y, kz) lines (fftx, Z2Z both directions)

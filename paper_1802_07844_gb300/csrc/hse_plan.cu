@@ -182,6 +182,12 @@ __global__ void k_tab_finish(double* __restrict__ tab, int Mt, double h, double 
   }
 }
 
+// FP64 table -> FP32 copy (mixed precision)
+__global__ void k_tab_to_float(const double* __restrict__ t, float* __restrict__ f, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    f[e] = (float)t[e];
+}
+
 static int grid_blocks(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b > 152 * 64) b = 152 * 64;
@@ -276,13 +282,27 @@ hse_status build_grids(hse_plan p) {
   p->comps = product_components(q.kernel_mask);
   q.n_fft_in = p->comps.n;
   q.n_fft_out = 6;
+  const bool mixed = q.precision == HSE_MIXED;
+  const size_t esz = mixed ? sizeof(float) : sizeof(double);
   size_t tab_elems = (size_t)(q.Mt + 1) * (q.Mt + 1) * (2 * q.Mt + 1);
-  size_t spec_bytes = (size_t)g.buf_doubles * sizeof(double) * q.n_fft_in;
+  size_t spec_bytes = (size_t)g.buf_doubles * esz * q.n_fft_in;
   HSE_CUDA(p, cudaMalloc(&p->spec, spec_bytes));
   HSE_CUDA(p, cudaMalloc(&p->tabH, tab_elems * sizeof(double)));
   if (q.kernel_mask & (HSE_STOKESLET | HSE_STRESSLET)) HSE_CUDA(p, cudaMalloc(&p->tabB, tab_elems * sizeof(double)));
   HSE_TRY(build_table(p, 0, p->tabH));
   if (p->tabB) HSE_TRY(build_table(p, 1, p->tabB));
+  if (mixed) {  // the tables are built in FP64 and rounded to FP32 once
+    for (double** tp : {&p->tabH, &p->tabB}) {
+      if (!*tp) continue;
+      float* f = nullptr;
+      HSE_CUDA(p, cudaMalloc(&f, tab_elems * sizeof(float)));
+      k_tab_to_float<<<grid_blocks((int64_t)tab_elems, 256), 256>>>(*tp, f, (int64_t)tab_elems);
+      cudaError_t e = cudaDeviceSynchronize();
+      cudaFree(*tp);
+      *tp = reinterpret_cast<double*>(f);
+      HSE_CUDA(p, e);
+    }
+  }
   // cuFFT, in place: the input is zero outside x < Mt, y < Mt, z < 2Mt, so the
   // forward transform is a 2-D (y,z) R2C over the Mt planes x < Mt followed by
   // a 1-D transform along x over every (y, kz) line; the inverse runs the x
@@ -299,19 +319,21 @@ hse_status build_grids(hse_plan p) {
   cufftSetAutoAllocation(p->fwd2d, 0);
   cufftSetAutoAllocation(p->inv2d, 0);
   cufftSetAutoAllocation(p->fftx, 0);
-  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fwd2d, 2, n2, re, 1, g.Ny * g.pitch, ce, 1, g.Ny * nzh, CUFFT_D2Z,
-                                             q.Mt, &w1), "cufftMakePlanMany64 D2Z (y,z)"));
-  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->inv2d, 2, n2, ce, 1, g.Ny * nzh, re, 1, g.Ny * g.pitch, CUFFT_Z2D,
-                                             q.Mt, &w2), "cufftMakePlanMany64 Z2D (y,z)"));
-  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fftx, 1, nx, xe, g.Ny * nzh, 1, xe, g.Ny * nzh, 1, CUFFT_Z2Z,
-                                             g.Ny * nzh, &w3), "cufftMakePlanMany64 Z2Z (x)"));
+  const cufftType t_r2c = mixed ? CUFFT_R2C : CUFFT_D2Z, t_c2r = mixed ? CUFFT_C2R : CUFFT_Z2D;
+  const cufftType t_c2c = mixed ? CUFFT_C2C : CUFFT_Z2Z;
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fwd2d, 2, n2, re, 1, g.Ny * g.pitch, ce, 1, g.Ny * nzh, t_r2c,
+                                             q.Mt, &w1), "cufftMakePlanMany64 R2C (y,z)"));
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->inv2d, 2, n2, ce, 1, g.Ny * nzh, re, 1, g.Ny * g.pitch, t_c2r,
+                                             q.Mt, &w2), "cufftMakePlanMany64 C2R (y,z)"));
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fftx, 1, nx, xe, g.Ny * nzh, 1, xe, g.Ny * nzh, 1, t_c2c,
+                                             g.Ny * nzh, &w3), "cufftMakePlanMany64 C2C (x)"));
   size_t wmax = w1 > w2 ? w1 : w2;
   p->fft_work_bytes = wmax > w3 ? wmax : w3;
   if (p->fft_work_bytes) HSE_CUDA(p, cudaMalloc(&p->fft_work, p->fft_work_bytes));
   HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fwd2d, p->fft_work), "cufftSetWorkArea"));
   HSE_TRY(cufft_check(p, cufftSetWorkArea(p->inv2d, p->fft_work), "cufftSetWorkArea"));
   HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fftx, p->fft_work), "cufftSetWorkArea"));
-  q.grid_bytes = spec_bytes + tab_elems * sizeof(double) * (p->tabB ? 2 : 1) + p->fft_work_bytes;
+  q.grid_bytes = spec_bytes + tab_elems * esz * (p->tabB ? 2 : 1) + p->fft_work_bytes;
   p->grid_ready = true;
   return HSE_OK;
 }
@@ -431,8 +453,8 @@ extern "C" hse_status hse_plan_create(int kernel_mask, const double box[3], doub
     return set_err(nullptr, HSE_ERR_INVALID, "box must be finite and positive");
   if (precision != HSE_FP64 && precision != HSE_MIXED)
     return set_err(nullptr, HSE_ERR_INVALID, "precision %d", precision);
-  if (precision == HSE_MIXED)
-    return set_err(nullptr, HSE_ERR_UNSUPPORTED, "HSE_MIXED is not available in this build");
+  if (precision == HSE_MIXED && tol > 0.0 && tol < 1e-6)
+    return set_err(nullptr, HSE_ERR_INVALID, "HSE_MIXED needs tol >= 1e-6 (FP32 arithmetic)");
   if (!(tol < 1.0)) return set_err(nullptr, HSE_ERR_INVALID, "tol must be < 1");
   hse_plan p = new (std::nothrow) hse_plan_s();
   if (!p) return set_err(nullptr, HSE_ERR_OOM, "host allocation");

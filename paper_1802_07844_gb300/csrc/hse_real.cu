@@ -42,16 +42,20 @@ __device__ const double d_erfcx_coef[HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1)] = {HS
 struct RealArgs {
   int64_t n_src, n_tgt;
   const double* spos;      // sorted sources, 3 x n_src
-  const float* spos32;     // the same in FP32 (candidate screening)
+  const float* spos32;     // the same in FP32 (candidate screening; head of the FP32 pair)
+  const float* spos32lo;   // tail: x - head in FP32
   const double* sstr;      // sorted strengths, rows x n_src
+  const float* sstr32;     // the same in FP32
   const int32_t* sorig;    // sorted -> original source index
   const int32_t* cstart;   // cell starts
   const double* tgt;       // explicit targets (3 x n_tgt) or null (targets = sources)
-  double* out;             // 3 x n_tgt in caller order
+  double* out;             // 3 x n_tgt in caller order (symmetric kernel: sorted order)
+  float4* out4;            // symmetric FP32 kernel: partner sums in sorted order
   int add;                 // accumulate into out (asymmetric kernel)
   int mask, rowS, rowT, rowW;
   double xi, rc2, rc;
   float rc2_lo, rc2_hi;    // FP32 screening thresholds
+  float img64_2;           // FP32 path: image pairs closer than this (squared) are evaluated in FP64
   double inv_cell[3];
   int ncell[3];
 };
@@ -91,12 +95,14 @@ __device__ __forceinline__ double erfcx_tab(double t, float tf, const double* ta
   return p;
 }
 
+template <typename T>
 struct Radial {
-  double er, c, a1, g2, g3;  // erfc(t)/rho, 2 xi e^{-t^2}/sqrt(pi), a1, g2, g3
+  T er, c, a1, g2, g3;  // erfc(t)/rho, 2 xi e^{-t^2}/sqrt(pi), a1, g2, g3
 };
 
-__device__ __forceinline__ Radial radial(double s, float sf, double xi, const double* tab, bool need_g3) {
-  Radial R;
+// FP64: own exp and erfcx table
+__device__ __forceinline__ Radial<double> radial(double s, float sf, double xi, const double* tab, bool need_g3) {
+  Radial<double> R;
   double inv = rsqrt(s);
   double t = xi * s * inv;
   double E = exp_neg(t * t);
@@ -112,42 +118,61 @@ __device__ __forceinline__ Radial radial(double s, float sf, double xi, const do
   return R;
 }
 
-struct Src {
-  double f[3], g[3], q[3], tau[3];
-};
-
-__device__ __forceinline__ void load_src(const RealArgs& a, int64_t j, Src& s) {
-  const int64_t n = a.n_src;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) { s.f[i] = 0.0; s.g[i] = 0.0; s.q[i] = 0.0; s.tau[i] = 0.0; }
-  if (a.mask & HSE_STOKESLET)
-    for (int i = 0; i < 3; ++i) s.f[i] = a.sstr[(a.rowS + i) * n + j];
-  if (a.mask & HSE_STRESSLET)
-    for (int i = 0; i < 3; ++i) { s.g[i] = a.sstr[(a.rowT + i) * n + j]; s.q[i] = a.sstr[(a.rowT + 3 + i) * n + j]; }
-  if (a.mask & HSE_ROTLET)
-    for (int i = 0; i < 3; ++i) s.tau[i] = a.sstr[(a.rowW + i) * n + j];
+// FP32 (mixed precision): the FP32 pipe is ~60x the FP64 one on GB300
+__device__ __forceinline__ Radial<float> radial(float s, float, float xi, const double*, bool need_g3) {
+  Radial<float> R;
+  float inv = rsqrtf(s);
+  float t = xi * s * inv;
+  float E = expf(-t * t);
+  float ec = erfcf(t);
+  float i2 = inv * inv;
+  R.c = (float)(2.0 / kSqrtPi) * xi * E;
+  R.er = ec * inv;
+  R.a1 = (R.er + R.c) * i2;
+  R.g2 = i2 * fmaf(3.0f, R.a1, 2.0f * xi * xi * R.c);
+  R.g3 = need_g3 ? -i2 * fmaf(5.0f, R.g2, 4.0f * xi * xi * xi * xi * R.c) : 0.0f;
+  return R;
 }
 
-// free-space contribution of source s at r = x - y (sign -1 gives the
+template <typename T>
+struct Src {
+  T f[3], g[3], q[3], tau[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_src(const RealArgs& a, const T* str, int64_t j, Src<T>& s) {
+  const int64_t n = a.n_src;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { s.f[i] = 0; s.g[i] = 0; s.q[i] = 0; s.tau[i] = 0; }
+  if (a.mask & HSE_STOKESLET)
+    for (int i = 0; i < 3; ++i) s.f[i] = str[(a.rowS + i) * n + j];
+  if (a.mask & HSE_STRESSLET)
+    for (int i = 0; i < 3; ++i) { s.g[i] = str[(a.rowT + i) * n + j]; s.q[i] = str[(a.rowT + 3 + i) * n + j]; }
+  if (a.mask & HSE_ROTLET)
+    for (int i = 0; i < 3; ++i) s.tau[i] = str[(a.rowW + i) * n + j];
+}
+
+// free-space contribution of source s at r = x - y (sgn_odd = -1 gives the
 // contribution at the source's position from the target's strengths when the
 // roles are swapped: S is even in r, T and W odd)
-__device__ __forceinline__ void add_free(int mask, const Radial& R, const double* r, const Src& s, double xi,
-                                         double sgn_odd, double* u) {
+template <typename T>
+__device__ __forceinline__ void add_free(int mask, const Radial<T>& R, const T* r, const Src<T>& s, T xi, T sgn_odd,
+                                         T* u) {
   if (mask & HSE_STOKESLET) {
-    double sa = R.er - R.c;
-    double rf = r[0] * s.f[0] + r[1] * s.f[1] + r[2] * s.f[2];
+    T sa = R.er - R.c;
+    T rf = r[0] * s.f[0] + r[1] * s.f[1] + r[2] * s.f[2];
     for (int i = 0; i < 3; ++i) u[i] += sa * s.f[i] + R.a1 * r[i] * rf;
   }
   if (mask & HSE_STRESSLET) {
-    double ta = -2.0 * R.g2, tb = 2.0 * xi * xi * R.c;
-    double rg = r[0] * s.g[0] + r[1] * s.g[1] + r[2] * s.g[2];
-    double rq = r[0] * s.q[0] + r[1] * s.q[1] + r[2] * s.q[2];
-    double gq = s.g[0] * s.q[0] + s.g[1] * s.q[1] + s.g[2] * s.q[2];
+    T ta = -2 * R.g2, tb = 2 * xi * xi * R.c;
+    T rg = r[0] * s.g[0] + r[1] * s.g[1] + r[2] * s.g[2];
+    T rq = r[0] * s.q[0] + r[1] * s.q[1] + r[2] * s.q[2];
+    T gq = s.g[0] * s.q[0] + s.g[1] * s.q[1] + s.g[2] * s.q[2];
     for (int i = 0; i < 3; ++i)
       u[i] += sgn_odd * (ta * r[i] * rg * rq + tb * (s.g[i] * rq + s.q[i] * rg + r[i] * gq));
   }
   if (mask & HSE_ROTLET) {
-    double wa = sgn_odd * 2.0 * R.a1;
+    T wa = sgn_odd * 2 * R.a1;
     u[0] += wa * (s.tau[1] * r[2] - s.tau[2] * r[1]);
     u[1] += wa * (s.tau[2] * r[0] - s.tau[0] * r[2]);
     u[2] += wa * (s.tau[0] * r[1] - s.tau[1] * r[0]);
@@ -156,49 +181,90 @@ __device__ __forceinline__ void add_free(int mask, const Radial& R, const double
 
 // image contribution at a target of height x3 from source s of height h,
 // rt = x - y^I
-__device__ __forceinline__ void add_image(int mask, const Radial& R, const double* r, double h, double x3,
-                                          const Src& s, double xi, double* u) {
-  const double g1 = -R.a1, g2 = R.g2;
-  double phi = 0.0, gp[3] = {0.0, 0.0, 0.0};
+template <typename T>
+__device__ __forceinline__ void add_image(int mask, const Radial<T>& R, const T* r, T h, T x3, const Src<T>& s, T xi,
+                                          T* u) {
+  const T g1 = -R.a1, g2 = R.g2;
+  T phi = 0, gp[3] = {0, 0, 0};
   if (mask & HSE_STOKESLET) {
-    double fI[3] = {s.f[0], s.f[1], -s.f[2]};
-    double sa = R.er - R.c;
-    double rf = r[0] * fI[0] + r[1] * fI[1] + r[2] * fI[2];
+    T fI[3] = {s.f[0], s.f[1], -s.f[2]};
+    T sa = R.er - R.c;
+    T rf = r[0] * fI[0] + r[1] * fI[1] + r[2] * fI[2];
     for (int i = 0; i < 3; ++i) u[i] -= sa * fI[i] + R.a1 * r[i] * rf;
-    phi += 2.0 * (-s.f[2] * R.er - h * g1 * rf);
-    for (int i = 0; i < 3; ++i) gp[i] += 2.0 * (-s.f[2] * g1 * r[i] - h * (g1 * fI[i] + g2 * r[i] * rf));
+    phi += 2 * (-s.f[2] * R.er - h * g1 * rf);
+    for (int i = 0; i < 3; ++i) gp[i] += 2 * (-s.f[2] * g1 * r[i] - h * (g1 * fI[i] + g2 * r[i] * rf));
   }
   if (mask & HSE_STRESSLET) {
-    double gI[3] = {s.g[0], s.g[1], -s.g[2]}, qI[3] = {s.q[0], s.q[1], -s.q[2]};
-    double ta = -2.0 * R.g2, tb = 2.0 * xi * xi * R.c;
-    double rg = r[0] * gI[0] + r[1] * gI[1] + r[2] * gI[2];
-    double rq = r[0] * qI[0] + r[1] * qI[1] + r[2] * qI[2];
-    double gq = gI[0] * qI[0] + gI[1] * qI[1] + gI[2] * qI[2];
+    T gI[3] = {s.g[0], s.g[1], -s.g[2]}, qI[3] = {s.q[0], s.q[1], -s.q[2]};
+    T ta = -2 * R.g2, tb = 2 * xi * xi * R.c;
+    T rg = r[0] * gI[0] + r[1] * gI[1] + r[2] * gI[2];
+    T rq = r[0] * qI[0] + r[1] * qI[1] + r[2] * qI[2];
+    T gq = gI[0] * qI[0] + gI[1] * qI[1] + gI[2] * qI[2];
     for (int i = 0; i < 3; ++i) u[i] -= ta * r[i] * rg * rq + tb * (gI[i] * rq + qI[i] * rg + r[i] * gq);
     // phi_T = 4 (gI.qI) d3G - 4 h gI.(grad grad G) qI
-    phi += 4.0 * gq * g1 * r[2] - 4.0 * h * (g1 * gq + g2 * rg * rq);
+    phi += 4 * gq * g1 * r[2] - 4 * h * (g1 * gq + g2 * rg * rq);
     for (int i = 0; i < 3; ++i) {
-      double d3i = g1 * (i == 2 ? 1.0 : 0.0) + g2 * r[2] * r[i];
-      double t3 = g2 * (gq * r[i] + gI[i] * rq + qI[i] * rg) + R.g3 * rg * rq * r[i];
-      gp[i] += 4.0 * gq * d3i - 4.0 * h * t3;
+      T d3i = g1 * (i == 2 ? 1 : 0) + g2 * r[2] * r[i];
+      T t3 = g2 * (gq * r[i] + gI[i] * rq + qI[i] * rg) + R.g3 * rg * rq * r[i];
+      gp[i] += 4 * gq * d3i - 4 * h * t3;
     }
   }
   if (mask & HSE_ROTLET) {
-    double tI[3] = {s.tau[0], s.tau[1], -s.tau[2]};
-    double wa = 2.0 * R.a1;
+    T tI[3] = {s.tau[0], s.tau[1], -s.tau[2]};
+    T wa = 2 * R.a1;
     u[0] += wa * (tI[1] * r[2] - tI[2] * r[1]);
     u[1] += wa * (tI[2] * r[0] - tI[0] * r[2]);
     u[2] += wa * (tI[0] * r[1] - tI[1] * r[0]);
-    double v0 = -s.tau[1], v1 = s.tau[0];
-    double rv = r[0] * v0 + r[1] * v1;
-    phi += 4.0 * g1 * rv;
-    gp[0] += 4.0 * (g1 * v0 + g2 * r[0] * rv);
-    gp[1] += 4.0 * (g1 * v1 + g2 * r[1] * rv);
-    gp[2] += 4.0 * (g2 * r[2] * rv);
+    T v0 = -s.tau[1], v1 = s.tau[0];
+    T rv = r[0] * v0 + r[1] * v1;
+    phi += 4 * g1 * rv;
+    gp[0] += 4 * (g1 * v0 + g2 * r[0] * rv);
+    gp[1] += 4 * (g1 * v1 + g2 * r[1] * rv);
+    gp[2] += 4 * (g2 * r[2] * rv);
   }
   for (int i = 0; i < 3; ++i) u[i] -= x3 * gp[i];
   u[2] += phi;
 }
+
+// Target position in the arithmetic type of the pair evaluation.  FP32 keeps
+// a head/tail pair so that differences of nearby points stay accurate.
+struct TgtPos {
+  double d[3];
+  float h[3], l[3];
+};
+
+// separation to sorted source j (free: x - y; image: x - y^I) and the
+// source height, in the pair arithmetic
+__device__ __forceinline__ void pair_vec(const RealArgs& a, const TgtPos& x, int64_t j, bool img, double* r,
+                                         double* h) {
+  const int64_t n = a.n_src;
+  double y2 = a.spos[2 * n + j];
+  r[0] = x.d[0] - a.spos[j];
+  r[1] = x.d[1] - a.spos[n + j];
+  r[2] = img ? x.d[2] + y2 : x.d[2] - y2;
+  *h = y2;
+}
+__device__ __forceinline__ void pair_vec(const RealArgs& a, const TgtPos& x, int64_t j, bool img, float* r,
+                                         float* h) {
+  const int64_t n = a.n_src;
+  const float* H = a.spos32;
+  const float* L = a.spos32lo;
+  r[0] = (x.h[0] - H[j]) + (x.l[0] - L[j]);
+  r[1] = (x.h[1] - H[n + j]) + (x.l[1] - L[n + j]);
+  r[2] = img ? (x.h[2] + H[2 * n + j]) + (x.l[2] + L[2 * n + j]) : (x.h[2] - H[2 * n + j]) + (x.l[2] - L[2 * n + j]);
+  *h = H[2 * n + j] + L[2 * n + j];
+}
+
+// squared length in a fixed operation order (the close-image classification
+// must be identical in the kernels that skip and that take those pairs)
+__device__ __forceinline__ float sq3(const float* r) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(r[0], r[0]), __fmul_rn(r[1], r[1])), __fmul_rn(r[2], r[2]));
+}
+__device__ __forceinline__ double sq3(const double* r) { return r[0] * r[0] + r[1] * r[1] + r[2] * r[2]; }
+
+template <typename T> __device__ __forceinline__ const T* strengths_of(const RealArgs& a);
+template <> __device__ __forceinline__ const double* strengths_of<double>(const RealArgs& a) { return a.sstr; }
+template <> __device__ __forceinline__ const float* strengths_of<float>(const RealArgs& a) { return a.sstr32; }
 
 // Candidate scan: cells around the target (free pairs) and the wall-layer
 // cells below its image (image pairs), 32 candidates per step, with the
@@ -266,6 +332,9 @@ __device__ __forceinline__ void load_table(double* tab) {
 }
 
 // Asymmetric kernel: explicit targets (or any target set), every ordered pair.
+// T is the pair arithmetic (double, or float with HSE_MIXED); sums over a
+// lane's pairs are kept in T and reduced across the warp in FP64.
+template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
   __shared__ double tab[kTabN];
@@ -274,39 +343,60 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
   int* qu = queue[wib];
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
   const bool need_g3 = a.mask & HSE_STRESSLET;
+  const T xi = (T)a.xi;
+  const T* str = strengths_of<T>(a);
   for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < a.n_tgt; w += nwarps) {
-    double x[3];
+    TgtPos x;
     int64_t own, dst;
     if (a.tgt) {
-      x[0] = a.tgt[w]; x[1] = a.tgt[a.n_tgt + w]; x[2] = a.tgt[2 * a.n_tgt + w];
+      for (int d = 0; d < 3; ++d) x.d[d] = a.tgt[d * a.n_tgt + w];
       own = -1;
       dst = w;
     } else {  // targets are the sources, visited in cell order
-      x[0] = a.spos[w]; x[1] = a.spos[a.n_src + w]; x[2] = a.spos[2 * a.n_src + w];
+      for (int d = 0; d < 3; ++d) x.d[d] = a.spos[d * a.n_src + w];
       own = w;
       dst = a.sorig[w];
     }
-    float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
-    double u[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < 3; ++d) {
+      x.h[d] = (float)x.d[d];
+      x.l[d] = (float)(x.d[d] - (double)x.h[d]);
+    }
+    const T x3 = sizeof(T) == 8 ? (T)x.d[2] : (T)(x.h[2] + x.l[2]);
+    T u[3] = {0, 0, 0};
+    double uself[3] = {0.0, 0.0, 0.0};
     int cnt = 0;
     auto run = [&](int e) {
       int j = e & 0x1fffffff, type = e >> 29;
-      Src s;
-      load_src(a, j, s);
       if (type == Q_SELF) {
-        double c = -4.0 * a.xi / kSqrtPi;
-        for (int i = 0; i < 3; ++i) u[i] += c * s.f[i];
+        if (a.mask & HSE_STOKESLET)
+          for (int i = 0; i < 3; ++i) uself[i] += -4.0 * a.xi / kSqrtPi * a.sstr[(a.rowS + i) * a.n_src + j];
         return;
       }
-      const int64_t n = a.n_src;
-      double y2 = a.spos[2 * n + j];
-      double r[3] = {x[0] - a.spos[j], x[1] - a.spos[n + j], type == Q_IMAGE ? x[2] + y2 : x[2] - y2};
-      double sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      Radial R = radial(sd, (float)sd, a.xi, tab, need_g3);
-      if (type == Q_FREE) add_free(a.mask, R, r, s, a.xi, 1.0, u);
-      else add_image(a.mask, R, r, y2, x[2], s, a.xi, u);
+      Src<T> s;
+      load_src<T>(a, str, j, s);
+      T r[3], h;
+      pair_vec(a, x, j, type == Q_IMAGE, r, &h);
+      T sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (sizeof(T) == 4 && type == Q_IMAGE && (float)sq3(r) < a.img64_2) {
+        // Close image pairs of near-wall targets: the image kernel and the wall
+        // corrections cancel to O(x3/rho) (exactly at leading order for a
+        // target's own image, rho = 2 x3), so FP32 would leave noise of
+        // eps/rho^2; these few pairs use the FP64 evaluation.
+        Src<double> sdbl;
+        load_src<double>(a, a.sstr, j, sdbl);
+        double rd[3], hd;
+        pair_vec(a, x, j, true, rd, &hd);
+        double s2 = rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2];
+        Radial<double> Rd = radial(s2, (float)s2, a.xi, tab, need_g3);
+        add_image<double>(a.mask, Rd, rd, hd, x.d[2], sdbl, a.xi, uself);
+        return;
+      }
+      Radial<T> R = radial(sd, (float)sd, xi, tab, need_g3);
+      if (type == Q_FREE) add_free<T>(a.mask, R, r, s, xi, (T)1, u);
+      else add_image<T>(a.mask, R, r, h, x3, s, xi, u);
     };
-    for_candidates(a, x, xf, own, lane, 0, 0, [&](bool hit, int j, int type) {
+    float xf[3] = {x.h[0], x.h[1], x.h[2]};
+    for_candidates(a, x.d, xf, own, lane, 0, 0, [&](bool hit, int j, int type) {
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
       cnt += __popc(m);
@@ -321,12 +411,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
     });
     if (lane < cnt) run(qu[lane]);
     __syncwarp();
-    for (int i = 0; i < 3; ++i)
-      for (int off = 16; off > 0; off >>= 1) u[i] += __shfl_xor_sync(0xffffffffu, u[i], off);
+    double ud[3];
+    for (int i = 0; i < 3; ++i) {
+      ud[i] = (double)u[i] + uself[i];
+      for (int off = 16; off > 0; off >>= 1) ud[i] += __shfl_xor_sync(0xffffffffu, ud[i], off);
+    }
     if (lane == 0) {
       for (int i = 0; i < 3; ++i) {
         double* o = a.out + i * a.n_tgt + dst;
-        *o = a.add ? *o + u[i] : u[i];
+        *o = a.add ? *o + ud[i] : ud[i];
       }
     }
   }
@@ -334,8 +427,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
 
 // Symmetric kernel (targets = sources): warp of sorted target p takes the
 // pairs with sorted source index j > p (free) and j >= p (image, j = p is the
-// target's own image); the partner's share goes out by atomicAdd.  The
-// output must be zeroed before the launch.
+// target's own image); the partner's share goes out by FP64 atomicAdd into the
+// sorted-order sums a.out (zeroed before the launch; neighbours sit at nearby
+// addresses), which k_unsort then writes in caller order.
+template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
   __shared__ double tab[kTabN];
@@ -345,42 +440,56 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
   const int64_t n = a.n_src;
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
   const bool need_g3 = a.mask & HSE_STRESSLET;
+  const T xi = (T)a.xi;
+  const T* str = strengths_of<T>(a);
   for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < n; w += nwarps) {
-    double x[3] = {a.spos[w], a.spos[n + w], a.spos[2 * n + w]};
-    float xf[3] = {a.spos32[w], a.spos32[n + w], a.spos32[2 * n + w]};
-    Src sp;
-    load_src(a, w, sp);
-    double u[3] = {0.0, 0.0, 0.0};
-    if (lane == 0 && (a.mask & HSE_STOKESLET)) {
-      double c = -4.0 * a.xi / kSqrtPi;
-      for (int i = 0; i < 3; ++i) u[i] = c * sp.f[i];
+    TgtPos x;
+    for (int d = 0; d < 3; ++d) {
+      x.d[d] = a.spos[d * n + w];
+      x.h[d] = a.spos32[d * n + w];
+      x.l[d] = a.spos32lo[d * n + w];
     }
+    const T x3 = sizeof(T) == 8 ? (T)x.d[2] : (T)(x.h[2] + x.l[2]);
+    Src<T> sp;
+    load_src<T>(a, str, w, sp);
+    T u[3] = {0, 0, 0};
+    double uself[3] = {0.0, 0.0, 0.0};
+    if (lane == 0 && (a.mask & HSE_STOKESLET))
+      for (int i = 0; i < 3; ++i) uself[i] = -4.0 * a.xi / kSqrtPi * a.sstr[(a.rowS + i) * n + w];
     int cnt = 0;
-    auto run = [&](int e) {
-      int j = e & 0x1fffffff, type = e >> 29;
-      Src s;
-      load_src(a, j, s);
-      double y2 = a.spos[2 * n + j];
-      double r[3] = {x[0] - a.spos[j], x[1] - a.spos[n + j], type == Q_IMAGE ? x[2] + y2 : x[2] - y2};
-      double sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      Radial R = radial(sd, (float)sd, a.xi, tab, need_g3);
-      double v[3] = {0.0, 0.0, 0.0};
-      if (type == Q_FREE) {
-        add_free(a.mask, R, r, s, a.xi, 1.0, u);
-        add_free(a.mask, R, r, sp, a.xi, -1.0, v);  // at y_j from the target's strengths, r -> -r
-      } else {
-        add_image(a.mask, R, r, y2, x[2], s, a.xi, u);
-        if (j != w) {
-          double rp[3] = {-r[0], -r[1], r[2]};  // y_j - x^I
-          add_image(a.mask, R, rp, x[2], y2, sp, a.xi, v);
-        }
-      }
-      if (type == Q_FREE || j != w) {
-        int64_t o = a.sorig[j];
-        for (int i = 0; i < 3; ++i) atomicAdd(a.out + i * n + o, v[i]);
+    auto partner_add = [&](int64_t j, double v0, double v1, double v2) {
+      if (sizeof(T) == 4) atomicAdd(a.out4 + j, make_float4((float)v0, (float)v1, (float)v2, 0.f));
+      else {
+        atomicAdd(a.out + j, v0);
+        atomicAdd(a.out + n + j, v1);
+        atomicAdd(a.out + 2 * n + j, v2);
       }
     };
-    for_candidates(a, x, xf, w, lane, (int)w + 1, (int)w, [&](bool hit, int j, int type) {
+    auto run = [&](int e) {
+      int j = e & 0x1fffffff, type = e >> 29;
+      Src<T> s;
+      load_src<T>(a, str, j, s);
+      T r[3], h;
+      pair_vec(a, x, j, type == Q_IMAGE, r, &h);
+      T sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      // close image pairs are left to k_close_images (FP64), see there
+      if (sizeof(T) == 4 && type == Q_IMAGE && (float)sq3(r) < a.img64_2) return;
+      Radial<T> R = radial(sd, (float)sd, xi, tab, need_g3);
+      T v[3] = {0, 0, 0};
+      if (type == Q_FREE) {
+        add_free<T>(a.mask, R, r, s, xi, (T)1, u);
+        add_free<T>(a.mask, R, r, sp, xi, (T)-1, v);  // at y_j from the target's strengths, r -> -r
+      } else {
+        add_image<T>(a.mask, R, r, h, x3, s, xi, u);
+        if (j != w) {
+          T rp[3] = {-r[0], -r[1], r[2]};  // y_j - x^I
+          add_image<T>(a.mask, R, rp, x3, h, sp, xi, v);
+        }
+      }
+      if (type == Q_FREE || j != w) partner_add(j, v[0], v[1], v[2]);
+    };
+    float xf[3] = {x.h[0], x.h[1], x.h[2]};
+    for_candidates(a, x.d, xf, w, lane, (int)w + 1, (int)w, [&](bool hit, int j, int type) {
       unsigned m = __ballot_sync(0xffffffffu, hit && type != Q_SELF);
       if (hit && type != Q_SELF) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
       cnt += __popc(m);
@@ -395,12 +504,82 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
     });
     if (lane < cnt) run(qu[lane]);
     __syncwarp();
+    double ud[3];
+    for (int i = 0; i < 3; ++i) {
+      ud[i] = (double)u[i] + uself[i];
+      for (int off = 16; off > 0; off >>= 1) ud[i] += __shfl_xor_sync(0xffffffffu, ud[i], off);
+    }
+    if (lane == 0) {
+      if (sizeof(T) == 4)  // own sum in FP64, partner sums arrive in out4
+        for (int i = 0; i < 3; ++i) a.out[i * n + w] = ud[i];
+      else
+        for (int i = 0; i < 3; ++i) atomicAdd(a.out + i * n + w, ud[i]);
+    }
+  }
+}
+
+// caller order: out[orig(i)] = sorted[i] (+ the FP32 partner sums, if any)
+__global__ void k_unsort(int64_t n, const int32_t* __restrict__ sorig, const double* __restrict__ us,
+                         const float4* __restrict__ us4, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = sorig[i];
+    float4 p = us4 ? us4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    out[o] = us[i] + (double)p.x;
+    out[n + o] = us[n + i] + (double)p.y;
+    out[2 * n + o] = us[2 * n + i] + (double)p.z;
+  }
+}
+
+// FP32 path, targets = sources: image pairs closer than sqrt(img64_2) (FP32
+// classification identical to k_real_sym<float>, which skips them).  For a
+// target near the wall the image kernel and the wall corrections cancel to
+// O(x3/rho) -- exactly at leading order for its own image, rho = 2 x3 -- so
+// these pairs are evaluated in FP64, each ordered pair by its target's warp,
+// and added to the target's FP64 sum after k_real_sym.  Only targets with
+// x3^2 < img64_2 can have such pairs (rho >= x3 + y3 > x3).
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_close_images(RealArgs a) {
+  __shared__ double tab[kTabN];
+  load_table(tab);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t n = a.n_src;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const bool need_g3 = a.mask & HSE_STRESSLET;
+  const int nx = a.ncell[0], ny = a.ncell[1], nz = a.ncell[2];
+  for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < n; w += nwarps) {
+    TgtPos x;
+    for (int d = 0; d < 3; ++d) {
+      x.d[d] = a.spos[d * n + w];
+      x.h[d] = a.spos32[d * n + w];
+      x.l[d] = a.spos32lo[d * n + w];
+    }
+    float x3f = x.h[2] + x.l[2];
+    if (x3f * x3f >= a.img64_2) continue;
+    int cx = cell_coord(x.d[0], a.inv_cell[0], nx);
+    int cy = cell_coord(x.d[1], a.inv_cell[1], ny);
+    int czi_hi = cell_coord(a.rc - x.d[2], a.inv_cell[2], nz);
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int iz = 0; iz <= czi_hi; ++iz)
+      for (int iy = (cy > 0 ? cy - 1 : 0); iy <= (cy < ny - 1 ? cy + 1 : ny - 1); ++iy) {
+        int xa = cx > 0 ? cx - 1 : 0, xb = cx < nx - 1 ? cx + 1 : nx - 1;
+        int c0 = (iz * ny + iy) * nx + xa;
+        int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
+        for (int j = s0 + lane; j < s1; j += 32) {
+          float rf[3], hf;
+          pair_vec(a, x, j, true, rf, &hf);
+          if (!(sq3(rf) < a.img64_2)) continue;
+          Src<double> sj;
+          load_src<double>(a, a.sstr, j, sj);
+          double rd[3], hd;
+          pair_vec(a, x, j, true, rd, &hd);
+          double s2 = sq3(rd);
+          Radial<double> R = radial(s2, (float)s2, a.xi, tab, need_g3);
+          add_image<double>(a.mask, R, rd, hd, x.d[2], sj, a.xi, u);
+        }
+      }
     for (int i = 0; i < 3; ++i)
       for (int off = 16; off > 0; off >>= 1) u[i] += __shfl_xor_sync(0xffffffffu, u[i], off);
-    if (lane == 0) {
-      int64_t o = a.sorig[w];
-      for (int i = 0; i < 3; ++i) atomicAdd(a.out + i * n + o, u[i]);
-    }
+    if (lane == 0)
+      for (int i = 0; i < 3; ++i) a.out[i * n + w] += u[i];
   }
 }
 
@@ -442,7 +621,9 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   a.n_tgt = n_tgt;
   a.spos = p->ws.spos;
   a.spos32 = p->ws.spos32;
+  a.spos32lo = p->ws.spos32lo;
   a.sstr = p->ws.sstr;
+  a.sstr32 = p->ws.sstr32;
   a.sorig = p->ws.val_a;
   a.cstart = p->ws.cell_start;
   a.tgt = tgt;
@@ -459,6 +640,7 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   double m = 4.0 * (2.0 * std::sqrt(3.0) * rc * delta + 3.0 * delta * delta + std::ldexp(1.0, -21) * rc * rc);
   a.rc2_lo = (float)std::fmax(0.0, a.rc2 - m) * (1.0f - 1e-6f);
   a.rc2_hi = (float)(a.rc2 + m) * (1.0f + 1e-6f);
+  a.img64_2 = (float)(a.rc2 / 256.0);
   for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = p->prm.ncell[d]; }
   return a;
 }
@@ -473,11 +655,29 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
                       cudaStream_t s) {
   if (n_tgt == 0) return HSE_OK;
   RealArgs a = make_args(p, n_src, n_tgt, tgt, out, add);
+  const bool mixed = p->prm.precision == HSE_MIXED;
+  // targets = sources: each unordered pair once (half list), the partner's
+  // share by atomics (FP64 path: 3 FP64 atomics; FP32 path: one float4 atomic)
   if (tgt == nullptr && !add) {
-    HSE_CUDA(p, cudaMemsetAsync(out, 0, sizeof(double) * 3 * n_tgt, s));
-    k_real_sym<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+    a.out = p->ws.usort;
+    a.out4 = p->ws.usort4;
+    if (mixed) {
+      HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
+      k_real_sym<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+      k_close_images<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+      ++p->n_launch;
+    } else {
+      HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_tgt, s));
+      k_real_sym<double><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+    }
+    HSE_CUDA(p, cudaGetLastError());
+    int64_t b = (n_tgt + 255) / 256;
+    k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(n_tgt, p->ws.val_a, p->ws.usort,
+                                                                     mixed ? p->ws.usort4 : nullptr, out);
+    ++p->n_launch;
   } else {
-    k_real<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+    if (mixed) k_real<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+    else k_real<double><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
   }
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_real");

@@ -257,3 +257,58 @@ def test_bench_workload_parity():
     idx = np.sort(np.random.default_rng(1802078442).choice(W["n"], 128, replace=False))
     ref = oracle.direct(W["mask"], pr.src, pr.strengths, pr.src[:, idx])
     assert oracle.rel_rms(u[:, idx], ref) < W["tol"]
+
+
+# ------------------------------------------------- mixed precision (FP32 path)
+@pytest.mark.parametrize("mask", MASKS)
+@pytest.mark.parametrize("dist", ["uniform", "near_wall"])
+def test_mixed_full_eval_tol1e5(pkg, mask, dist):
+    """FP32 arithmetic path at tolerance 1e-5 against the FP64 direct sum."""
+    pr = problem(mask, 2000, 1.0, dist, 50)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=12.0, rc=0.0, P=0, tol=1e-5, precision=pkg.HSE_MIXED)
+    u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
+    ref = oracle.direct(mask, pr.src, pr.strengths)
+    assert oracle.rel_rms(u, ref) < 1e-5
+    plan.close()
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_S | KERNEL_W])
+def test_mixed_real_part_near_fp32_rounding(pkg, mask):
+    """FP32 pair arithmetic with head/tail separations: the real-space part is
+    within a few FP32 roundings of the FP64 oracle (same cut-off)."""
+    pr = problem(mask, 3000, 1.0, "near_wall", 51)
+    xi, rc = 20.0, 0.2
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=rc, P=8, tol=0.0, precision=pkg.HSE_MIXED)
+    ur, _ = plan.eval_parts(dev(pr.src), dev(pr.strengths), fourier=False)
+    ref = (oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_REAL, xi, rc)
+           + oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_SELF, xi))
+    assert oracle.rel_rms(host(ur), ref) < 2e-6
+    plan.close()
+
+
+def test_mixed_explicit_targets(pkg):
+    mask = KERNEL_S | KERNEL_W
+    pr = problem(mask, 1500, 1.0, "near_wall", 52)
+    rng = np.random.default_rng(8)
+    tgt = np.stack([rng.uniform(0, 1, 70), rng.uniform(0, 1, 70), rng.uniform(0, 0.3, 70)])
+    tgt[:, :10] = pr.src[:, :10]
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=12.0, rc=0.0, P=0, tol=1e-5, precision=pkg.HSE_MIXED)
+    u = host(plan.eval(dev(pr.src), dev(pr.strengths), dev(tgt)))
+    assert oracle.rel_rms(u, oracle.direct(mask, pr.src, pr.strengths, tgt)) < 1e-5
+    plan.close()
+
+
+def test_mixed_bench_workload_parity():
+    """The mixed-precision benchmark configuration (N = 1M near-wall stokeslet +
+    rotlet, tolerance 1e-5) on 128 seeded targets."""
+    import bench
+    import paper_1802_07844_gb300 as pkg
+    W = bench.WORKLOAD
+    Mx = bench.MIXED
+    pr = problem(W["mask"], W["n"], 1.0, W["dist"], W["index"])
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=0.0, P=0, tol=Mx["tol"], precision=pkg.HSE_MIXED)
+    u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
+    plan.close()
+    idx = np.sort(np.random.default_rng(1802078443).choice(W["n"], 128, replace=False))
+    ref = oracle.direct(W["mask"], pr.src, pr.strengths, pr.src[:, idx])
+    assert oracle.rel_rms(u[:, idx], ref) < Mx["tol"]
