@@ -279,6 +279,11 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_mixed:
         out["mixed_1e-5"] = run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world)
+    if args.serve_requests > 0:
+        del flush
+        plan.close()
+        torch.cuda.empty_cache()
+        out["serve"] = run_serve(args, pkg, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tps, k, dt = time_oracle(pr, mask, args.cpu_budget)
         out["cpu_baseline"] = {"value": tps / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -321,6 +326,69 @@ def run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world):
             "dtype": "f32 arithmetic (FP64 sums, close image pairs, tables)", "tol": Mx["tol"], "xi": prm["xi"],
             "rc": prm["rc"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
             "stage_ms": {k: round(float(np.mean(v)), 3) for k, v in stages.items()}}
+
+
+def run_serve(args, pkg, torch, dev):
+    """Poisson stream of requests through the continuous-batching server:
+    kernel uniform over stokeslet/stresslet/rotlet, N log-uniform in [1e3, 2e5],
+    half uniform and half near-wall (TruncExp 0.05), tol 1e-10 (FP64) or 1e-5
+    (mixed) per request.  The offered load is 0.7 x the service capacity
+    measured on a closed-loop warm-up of the same request mix."""
+    from workloads import KERNEL_S, KERNEL_T, KERNEL_W, problem as mk
+    rng = np.random.default_rng(1802078440 + 4)
+    nreq = args.serve_requests
+    kinds = [KERNEL_S, KERNEL_T, KERNEL_W]
+    reqs = []
+    for i in range(nreq):
+        mask = kinds[int(rng.integers(3))]
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(2e5))))
+        dist = "uniform" if rng.uniform() < 0.5 else "near_wall"
+        tol = 1e-10 if rng.uniform() < 0.5 else 1e-5
+        pr = mk(mask, n, 1.0, dist, 4, sub=i)
+        reqs.append((mask, tol, torch.from_numpy(pr.src).to(dev), torch.from_numpy(pr.strengths).to(dev)))
+    srv = pkg.hse.Server(n_slots=args.serve_slots)
+    try:
+        return _serve_measure(srv, reqs, rng, pkg, args)
+    finally:
+        srv.close()
+
+
+def _serve_measure(srv, reqs, rng, pkg, args):
+    prec = lambda tol: pkg.HSE_MIXED if tol >= 1e-6 else pkg.HSE_FP64
+
+    def closed_loop(batch):
+        ts = [srv.submit(m, a, b, tol, prec(tol)) for m, tol, a, b in batch]
+        for t in ts:
+            srv.wait(t, 600.0)
+
+    # warm the plan cache and measure the service capacity (requests/s)
+    warm = reqs[: min(len(reqs), 3 * args.serve_slots * 8)]
+    closed_loop(warm)
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    closed_loop(warm)
+    cap = len(warm) / (time.perf_counter() - t0)
+    srv.reset_stats()
+    lam = 0.7 * cap
+    gaps = rng.exponential(1.0 / lam, size=len(reqs))
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for (m, tol, a, b), g in zip(reqs, gaps):
+        t_next += g
+        now = time.perf_counter()
+        if t_next > now:
+            time.sleep(t_next - now)
+        tickets.append(srv.submit(m, a, b, tol, prec(tol)))
+    for t in tickets:
+        srv.wait(t, 600.0)
+    st = srv.stats()
+    n_tgt = sum(int(a.shape[1]) for _, _, a, _ in reqs)
+    return {"requests": len(reqs), "slots": args.serve_slots, "offered_load_req_per_s": lam,
+            "capacity_req_per_s": cap, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "throughput_req_per_s": st["completed"] / st["busy_s"] if st["busy_s"] else None,
+            "throughput_Mtargets_per_s": st["targets_per_s"] / 1e6, "targets": n_tgt, "failed": st["failed"],
+            "plans_created": st["plans_created"], "plans_evicted": st["plans_evicted"]}
 
 
 def run_real_only(args, pkg, torch, dev, W, pr):
@@ -382,6 +450,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-arithmetic measurement")
+    ap.add_argument("--serve-requests", type=int, default=400, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--real-only", action="store_true",
                     help="profiling aid: plan without a grid, time only the real-space half")
     args = ap.parse_args()

@@ -206,6 +206,70 @@ hse_status hse_plan_set_timing(hse_plan plan, int enable);
  * timing is on).  out: host pointer. */
 hse_status hse_get_eval_stats(hse_plan plan, hse_eval_stats* out);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent evaluations.                  */
+/* ------------------------------------------------------------------------ */
+typedef struct hse_server_s* hse_server;
+
+#define HSE_PENDING 7 /* hse_server_poll: the request has not finished yet */
+
+typedef struct {
+  int n_slots;              /* concurrent evaluations (one CUDA stream and worker thread each), >= 1 */
+  size_t mem_budget_bytes;  /* device memory the server may hold for plans and work areas (0: 60% of free) */
+} hse_server_config;
+
+typedef struct {
+  int kernel_mask;          /* HSE_STOKESLET / HSE_STRESSLET / HSE_ROTLET bits */
+  int precision;            /* HSE_FP64 or HSE_MIXED */
+  double tol;               /* target relative RMS error (> 0)                   */
+  double box[3];            /* source box, as for hse_plan_create                */
+  int64_t n_src;
+  const double* src_xyz;    /* device, 3 x n_src (caller-owned until completion) */
+  const double* strengths;  /* device, rows x n_src                              */
+  int64_t n_tgt;
+  const double* tgt_xyz;    /* device or NULL (targets = sources)                */
+  double* vel;              /* device, 3 x n_tgt, written on completion          */
+} hse_request;
+
+typedef struct {
+  int64_t submitted, completed, failed, in_flight;
+  double p50_ms, p99_ms, mean_ms;  /* submit -> completion latency of completed requests */
+  double busy_s;                   /* wall time from first submission to last completion */
+  double targets_per_s;            /* completed targets / busy_s                         */
+  int64_t plans_created, plans_evicted;
+  size_t resident_bytes;           /* device bytes held by cached plans                  */
+} hse_server_stats;
+
+/*
+ * A server evaluates independent requests (Sec. 3 sums of any kernel mix,
+ * size and tolerance) with continuous batching: requests queue on submission;
+ * each worker slot takes the oldest request whose estimated device memory
+ * (grids, tables and cell-list work areas) fits the budget next to the work
+ * already admitted, checks out a resident plan with the request's parameters
+ * (or builds one, evicting idle plans least recently used), and evaluates on
+ * its own stream, so work of different requests overlaps on the GPU.  xi is
+ * chosen from N and the box (xi = 0.7 (N/V)^(1/3) rounded to a factor-sqrt(2)
+ * ladder, so plans are shared between requests); r_c, M and P come from tol.
+ * The caller keeps the request's arrays alive until the request completes.
+ */
+hse_status hse_server_create(const hse_server_config* cfg, hse_server* out);
+/* Queue a request; *ticket identifies it.  Never blocks on GPU work. */
+hse_status hse_server_submit(hse_server srv, const hse_request* req, uint64_t* ticket);
+/* HSE_OK when finished, HSE_PENDING while queued or running, else the
+ * request's error status. */
+hse_status hse_server_poll(hse_server srv, uint64_t ticket);
+/* Wait at most timeout_s seconds: HSE_OK, the request's error, or
+ * HSE_ERR_TIMEOUT (the request keeps running). */
+hse_status hse_server_wait(hse_server srv, uint64_t ticket, double timeout_s);
+hse_status hse_server_get_stats(hse_server srv, hse_server_stats* out);
+/* Text of a failed request's error ("" when it succeeded or is pending); valid
+ * until the server is destroyed. */
+const char* hse_server_error_text(hse_server srv, uint64_t ticket);
+/* Reset the latency record (not the plan cache). */
+hse_status hse_server_reset_stats(hse_server srv);
+/* Waits for admitted work, fails queued requests, frees plans. */
+hse_status hse_server_destroy(hse_server srv);
+
 /*
  * hse_cell_list_noalloc -- the cell list of hse_cell_list (same cell ids,
  * permutation and cell starts, bit for bit) without any device allocation.
@@ -239,7 +303,8 @@ hse_status hse_plan_destroy(hse_plan plan);
 const char* hse_status_string(hse_status status);
 
 /* Text of the last failure of a plan (valid until the next call on the plan);
- * "" when none.  A NULL plan gives the last failure of hse_plan_create. */
+ * "" when none.  A NULL plan gives the calling thread's last failure outside a
+ * plan (hse_plan_create, servers, the no-allocation entry point). */
 const char* hse_last_error(hse_plan plan);
 
 #ifdef __cplusplus

@@ -328,3 +328,41 @@ cudaError_t cell_list_on_buffers(int64_t n, const double* pos, const double inv_
 }
 
 }  // namespace hse
+
+namespace hse {
+
+// Stable sort of caller-computed keys (with values) in key_a/val_a, and the
+// starts of ncells key ranges.  Used by the batched instances (keys =
+// instance * cells per instance + cell).
+cudaError_t sort_keys_and_starts(int64_t n, int64_t ncells, int32_t* key_a, int32_t* val_a, int32_t* key_b,
+                                 int32_t* val_b, int32_t* hist, int32_t* start_out, cudaStream_t s) {
+  if (n == 0) return cudaMemsetAsync(start_out, 0, sizeof(int32_t) * (ncells + 1), s);
+  int bits = 0;
+  while ((int64_t(1) << bits) < ncells) ++bits;
+  int passes = (bits + 7) / 8;
+  int64_t ntiles = (n + kTile - 1) / kTile;
+  int32_t *ka = key_a, *va = val_a, *kb = key_b, *vb = val_b;
+  cudaError_t e;
+  for (int ps = 0; ps < passes; ++ps) {
+    k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ka, n, 8 * ps, ntiles, hist);
+    k_scan_excl<<<1, 1024, 0, s>>>(hist, 256 * ntiles);
+    k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ka, va, n, 8 * ps, ntiles, hist, kb, vb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int32_t* tk = ka; ka = kb; kb = tk;
+    int32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != key_a) {
+    e = cudaMemcpyAsync(key_a, ka, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(val_a, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_cell_start<<<nblocks(n + 1, 256), 256, 0, s>>>(key_a, n, ncells, start_out);
+  return cudaGetLastError();
+}
+
+hse_status gather_sorted_batch(hse_plan p, int64_t n, const double* pos, const double* str, cudaStream_t s) {
+  return gather_sorted(p, n, pos, str, s);
+}
+
+}  // namespace hse

@@ -112,6 +112,8 @@ struct SpreadArgs {
   int ncell[3];
   T* out;                // component c, point (i,j,k) at out + c*cs + i*xs + j*pitch + k
   int64_t cs, xs, pitch;
+  int64_t is;            // batched instances: instance stride of out (blockIdx.z = inst * nz_tiles + tile)
+  int ncells_inst;       // cells per instance in the cell list
 };
 
 constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
@@ -121,7 +123,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   __shared__ int list[256];
   __shared__ int wcount[8];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int bx0 = kTX * blockIdx.x, by0 = kTY * blockIdx.y, bz0 = a.z0 + kTZ * blockIdx.z;
+  const int inst = blockIdx.z / a.nz_tiles, ztile = blockIdx.z - inst * a.nz_tiles;
+  const int cbase = inst * a.ncells_inst;
+  const int bx0 = kTX * blockIdx.x, by0 = kTY * blockIdx.y, bz0 = a.z0 + kTZ * ztile;
   const int sx = bx0 + 2 * (w & 1), sy = by0 + 4 * ((w >> 1) & 1), sz = bz0 + 4 * (w >> 2);
   const int px = sx + (lane & 1), py = sy + ((lane >> 1) & 3), pz = sz + (lane >> 3);
   const int P = a.P;
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   const int nx = a.ncell[0], ny = a.ncell[1];
   for (int cz = cz0; cz <= cz1; ++cz)
     for (int cy = cy0; cy <= cy1; ++cy) {
-      int c0 = (cz * ny + cy) * nx + cx0;
+      int c0 = cbase + (cz * ny + cy) * nx + cx0;
       int s0 = a.cstart[c0], s1 = a.cstart[c0 + (cx1 - cx0) + 1];
       for (int base = s0; base < s1; base += 256) {
         int j = base + tid;
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
       }
     }
   if (px < a.Mt && py < a.Mt && pz < 2 * a.Mt) {
-    T* dst = a.out + px * a.xs + py * a.pitch + pz;
+    T* dst = a.out + inst * a.is + px * a.xs + py * a.pitch + pz;
 #pragma unroll
     for (int c = 0; c < NC; ++c) dst[c * a.cs] = acc[c];
   }
@@ -214,20 +218,24 @@ struct MirrorArgs {
   int64_t cs, xs, pitch;
   int Mt, nc;
   int sign[kMaxComp];
+  int n_inst;
+  int64_t is;  // instance stride
 };
 
 template <typename T>
 __global__ void k_mirror(MirrorArgs<T> a) {
   const int Mt = a.Mt;
   const int64_t per = (int64_t)Mt * Mt * (Mt + 1);
-  const int64_t total = per * a.nc;
+  const int64_t total = per * a.nc * a.n_inst;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(e / per);
-    int64_t r = e - c * per;
+    int64_t ci = e / per;
+    int c = (int)(ci % a.nc);
+    int64_t inst = ci / a.nc;
+    int64_t r = e - ci * per;
     int k = (int)(r % (Mt + 1));
     int64_t ij = r / (Mt + 1);
     int j = (int)(ij % Mt), i = (int)(ij / Mt);
-    T* col = a.buf + c * a.cs + i * a.xs + j * a.pitch;
+    T* col = a.buf + c * a.cs + inst * a.is + i * a.xs + j * a.pitch;
     int kp = 2 * Mt - k;
     T va = col[k];
     T vb = kp < 2 * Mt ? col[kp] : (T)0;
@@ -256,6 +264,8 @@ struct ScaleArgs {
   const T* tabB;
   const T* tabH;
   int iS, iT, iW, iCs, iCv, iCt;  // first component index of each group, -1 if absent
+  int n_inst;
+  int64_t istride;                // complex elements between instances of one component
 };
 
 template <typename C, typename T>
@@ -274,9 +284,12 @@ __global__ void k_scale(ScaleArgs<T> a) {
   const int64_t nh = (int64_t)Nx * Ny * Nzh;
   const T dkx = (T)(2.0 * kPi / (Nx * a.h)), dkz = (T)(2.0 * kPi / (4.0 * Mt * a.h));
   const C zero = cmk<C>((T)0, (T)0);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nh; e += (int64_t)gridDim.x * blockDim.x) {
-    int jz = (int)(e % Nzh);
-    int64_t t = e / Nzh;
+  for (int64_t ee = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ee < nh * a.n_inst;
+       ee += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t inst = ee / nh, el = ee - inst * nh;
+    const int64_t e = inst * a.istride + el;  // element of component 0 of this instance
+    int jz = (int)(el % Nzh);
+    int64_t t = el / Nzh;
     int iy = (int)(t % Ny), ix = (int)(t / Ny);
     C T1[3], T2[3];
     if (ix == Mt || iy == Mt || jz == 2 * Mt) {  // Nyquist modes are dropped
@@ -353,6 +366,8 @@ struct GatherArgs {
   const int32_t* sorig;
   const T* buf;           // fields T1x..T2z, buffer stride bs, real layout
   int64_t bs, xs, pitch;
+  const int32_t* inst_of; // batched instances: instance of each sorted target (null: one)
+  int64_t is;             // instance stride of the fields
   int P, Mt;
   double h, ox, oz, alpha, pre, h3;
   double* out;
@@ -383,6 +398,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
     int ix0 = support_start(x, a.ox, a.h, P, a.Mt);
     int iy0 = support_start(y, a.ox, a.h, P, a.Mt);
     int iz0 = support_start(z, a.oz, a.h, P, 2 * a.Mt);
+    const T* fields = a.buf + (a.inst_of ? a.inst_of[w] * a.is : 0);
     __syncwarp();
     if (lane < P) {
       double dx = a.ox + (ix0 + lane) * a.h - x;
@@ -397,7 +413,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
     for (int q = lane; q < P * P; q += 32) {
       int jj = q / P, kk = q - jj * P;
       T s[6] = {0, 0, 0, 0, 0, 0};
-      const T* col = a.buf + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
+      const T* col = fields + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
       for (int ii = 0; ii < P; ++ii) {
         T wv = wx[ii];
         const T* pnt = col + (int64_t)ii * a.xs;
@@ -453,7 +469,7 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
 
 template <typename T>
 static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int paper, T* out, int64_t cstride,
-                              int64_t xs, int64_t pitch, cudaStream_t s) {
+                              int64_t xs, int64_t pitch, cudaStream_t s, int n_inst = 1, int64_t istride = 0) {
   const hse_params& q = p->prm;
   PrepArgs<T> pa = prep_args<T>(p, n_src, paper, cs.n);
   if (n_src > 0) {
@@ -477,8 +493,11 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.cs = cstride;
   a.xs = xs;
   a.pitch = pitch;
+  a.is = istride;
+  a.ncells_inst = q.ncell[0] * q.ncell[1] * q.ncell[2];
   int nzr = 2 * q.Mt - p->zA0;
-  dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, (nzr + kTZ - 1) / kTZ);
+  a.nz_tiles = (nzr + kTZ - 1) / kTZ;
+  dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, a.nz_tiles * n_inst);
   if (!launch_spread<T>(cs.n, a, grid, s)) return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
@@ -489,8 +508,10 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   m.pitch = pitch;
   m.Mt = q.Mt;
   m.nc = cs.n;
+  m.n_inst = n_inst;
+  m.is = istride;
   for (int c = 0; c < cs.n; ++c) m.sign[c] = cs.mirror_sign[c];
-  int64_t tot = (int64_t)q.Mt * q.Mt * (q.Mt + 1) * cs.n;
+  int64_t tot = (int64_t)q.Mt * q.Mt * (q.Mt + 1) * cs.n * n_inst;
   k_mirror<T><<<blocks_for(tot, 256, 152 * 64), 256, 0, s>>>(m);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_mirror");
@@ -560,6 +581,8 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   if (q.kernel_mask & HSE_STOKESLET) { sa.iCs = k; k += 1; }
   sa.iCv = k; k += 3;
   if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  sa.n_inst = 1;
+  sa.istride = 0;
   stage_mark(p, HSE_STAGE_SCALE, s);
   k_scale<T><<<blocks_for(g.nh, 256, 152 * 32), 256, 0, s>>>(sa);
   ++p->n_launch;
@@ -582,6 +605,8 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   ga.bs = g.buf_doubles;
   ga.xs = (int64_t)g.Ny * g.pitch;
   ga.pitch = g.pitch;
+  ga.inst_of = nullptr;
+  ga.is = 0;
   ga.P = q.P;
   ga.Mt = q.Mt;
   ga.h = q.h;
@@ -595,6 +620,89 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   k_gather<T><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_gather");
+}
+
+// Batched instances: n_inst instances sharing the plan's grid, particles sorted
+// by (instance, cell) in the plan's workspace, inst_of per sorted particle.
+// spec: component-major buffers, component c of instance i at (c n_inst + i)
+// buffers; fwd / inv: batched 3-D transforms over n_fft_in * n_inst and
+// 6 * n_inst buffers.  Adds the Fourier part of every particle to out
+// (concatenated order).
+template <typename T>
+static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* specv,
+                                        cufftHandle fwd, cufftHandle inv, double* out, cudaStream_t s) {
+  const hse_params& q = p->prm;
+  const GridDims& g = p->g;
+  const int nin = p->comps.n;
+  T* spec = reinterpret_cast<T*>(specv);
+  const int64_t cs = g.buf_doubles * n_inst;
+  HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * cs * nin, s));
+  HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, cs, (int64_t)g.Ny * g.pitch, g.pitch, s, n_inst,
+                         g.buf_doubles));
+  cufftSetStream(fwd, s);
+  cufftSetStream(inv, s);
+  cufftResult r;
+  if (sizeof(T) == 8) r = cufftExecD2Z(fwd, (double*)spec, (cufftDoubleComplex*)spec);
+  else r = cufftExecR2C(fwd, (float*)spec, (cufftComplex*)spec);
+  ++p->n_fft;
+  if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "batched forward FFT: %d", (int)r);
+  ScaleArgs<T> sa;
+  sa.buf = reinterpret_cast<typename Cplx<T>::type*>(spec);
+  sa.cstride = g.nh * n_inst;
+  sa.istride = g.nh;
+  sa.n_inst = n_inst;
+  sa.Mt = q.Mt;
+  sa.mask = q.kernel_mask;
+  sa.h = q.h;
+  sa.tabB = reinterpret_cast<const T*>(p->tabB);
+  sa.tabH = reinterpret_cast<const T*>(p->tabH);
+  int k = 0;
+  sa.iS = sa.iT = sa.iW = sa.iCs = sa.iCt = -1;
+  if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
+  if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
+  if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
+  if (q.kernel_mask & HSE_STOKESLET) { sa.iCs = k; k += 1; }
+  sa.iCv = k; k += 3;
+  if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  k_scale<T><<<blocks_for(g.nh * n_inst, 256, 152 * 32), 256, 0, s>>>(sa);
+  ++p->n_launch;
+  HSE_CUDA(p, cudaGetLastError());
+  if (sizeof(T) == 8) r = cufftExecZ2D(inv, (cufftDoubleComplex*)spec, (double*)spec);
+  else r = cufftExecC2R(inv, (cufftComplex*)spec, (float*)spec);
+  ++p->n_fft;
+  if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "batched inverse FFT: %d", (int)r);
+  GatherArgs<T> ga;
+  ga.n_tgt = n_total;
+  ga.n_src = n_total;
+  ga.tgt = nullptr;
+  ga.spos = p->ws.spos;
+  ga.sorig = p->ws.val_a;
+  ga.buf = spec;
+  ga.bs = cs;
+  ga.xs = (int64_t)g.Ny * g.pitch;
+  ga.pitch = g.pitch;
+  ga.inst_of = inst_of;
+  ga.is = g.buf_doubles;
+  ga.P = q.P;
+  ga.Mt = q.Mt;
+  ga.h = q.h;
+  ga.ox = -0.5 * q.P * q.h;
+  ga.oz = -(double)q.Mt * q.h;
+  ga.alpha = 2.0 * q.xi * q.xi / q.eta;
+  ga.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
+  ga.h3 = q.h * q.h * q.h;
+  ga.out = out;
+  ga.add = 1;
+  k_gather<T><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), "batched k_gather");
+}
+
+hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* spec,
+                               cufftHandle fwd, cufftHandle inv, double* out, cudaStream_t s) {
+  if (p->prm.precision == HSE_MIXED)
+    return fourier_space_batch_t<float>(p, n_total, n_inst, inst_of, spec, fwd, inv, out, s);
+  return fourier_space_batch_t<double>(p, n_total, n_inst, inst_of, spec, fwd, inv, out, s);
 }
 
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,

@@ -103,6 +103,8 @@ void free_grids(hse_plan p);
 hse_status ensure_workspace(hse_plan p, int64_t n);
 void free_workspace(hse_plan p);
 CompSet product_components(int mask);
+hse_status plan_estimate(int mask, const double box[3], double xi, double tol, int precision, size_t* bytes,
+                         int* M_out, int* P_out);
 CompSet paper_components(int mask);
 
 // ----------------------------------------------------------- stage launchers
@@ -118,6 +120,11 @@ hse_status neighbor_counts(hse_plan p, int64_t n_src, int64_t n_tgt, const doubl
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
                          cudaStream_t s);
 hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStream_t s);
+cudaError_t sort_keys_and_starts(int64_t n, int64_t ncells, int32_t* key_a, int32_t* val_a, int32_t* key_b,
+                                 int32_t* val_b, int32_t* hist, int32_t* start_out, cudaStream_t s);
+hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of, double* out, cudaStream_t s);
+hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* spec,
+                               cufftHandle fwd, cufftHandle inv, double* out, cudaStream_t s);
 
 inline void stage_mark(hse_plan p, int i, cudaStream_t s) {
   if (p->timing) cudaEventRecord(p->ev[i], s);

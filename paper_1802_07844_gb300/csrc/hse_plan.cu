@@ -10,7 +10,8 @@
 
 namespace hse {
 
-static std::string g_create_error;
+// text of the last failure outside a plan, per calling thread
+static thread_local std::string g_create_error;
 
 hse_status set_err(hse_plan p, hse_status s, const char* fmt, ...) {
   char buf[512];
@@ -214,9 +215,19 @@ static hse_status build_table(hse_plan p, int kind, double* tab) {
   cudaError_t e = cudaMalloc(&b, nb * sizeof(double));
   if (e != cudaSuccess) { cudaFree(a); return cuda_check(p, e, "cudaMalloc table scratch"); }
   hse_status st = HSE_OK;
+  // Every thread sets the same (device maximum) limit, so plans built
+  // concurrently from several threads cannot lower it under each other.
+  int dev = 0, smax = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncSetAttribute(k_tab_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  cudaFuncSetAttribute(k_cos_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   do {
     size_t sm1 = sizeof(double) * (nfz / 2 + 1 + nfz);
-    cudaFuncSetAttribute(k_tab_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (sm1 > (size_t)smax) {
+      st = set_err(p, HSE_ERR_UNSUPPORTED, "grid too large for the table precompute (Mt = %d)", Mt);
+      break;
+    }
     k_tab_pass1<<<dim3(nh, nh), 256, sm1>>>(kind, nf, nfz, h, R, oz, a);             // a[mx][my][iz]
     if ((st = cuda_check(p, cudaGetLastError(), "k_tab_pass1")) != HSE_OK) break;
     auto pass = [&](const double* in, double* out, int n0, int n1, int n2, int axis, int nout, int np, double sc) {
@@ -224,7 +235,6 @@ static hse_status build_table(hse_plan p, int kind, double* tab) {
       o[axis] = nout;
       int64_t tot = (int64_t)o[0] * o[1] * o[2];
       size_t smb = sizeof(double) * np;
-      cudaFuncSetAttribute(k_cos_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
       k_cos_pass<<<grid_blocks(tot, 256), 256, smb>>>(in, out, n0, n1, n2, axis, nout, np, sc);
       return cuda_check(p, cudaGetLastError(), "k_cos_pass");
     };
@@ -436,6 +446,28 @@ static hse_status choose_params(hse_plan p, double xi, double rc, int P, double 
   if (M > 0) M = fft_friendly(M + P) - P;  // grow M so that Mt = M + P has a fast FFT size
   q.P = P;
   q.M = M;
+  return HSE_OK;
+}
+
+// Device bytes a plan with these settings will hold (grids, tables, an FFT
+// work area of one buffer), without creating it.  Host-only.
+hse_status plan_estimate(int mask, const double box[3], double xi, double tol, int precision, size_t* bytes,
+                         int* M_out, int* P_out) {
+  hse_plan_s tmp;
+  hse_params& q = tmp.prm;
+  q.kernel_mask = mask;
+  q.precision = precision;
+  for (int d = 0; d < 3; ++d) q.box[d] = box[d];
+  q.L = std::fmax(box[0], std::fmax(box[1], box[2]));
+  HSE_TRY(choose_params(&tmp, xi, 0.0, 0, tol));
+  int Mt = q.M + q.P;
+  size_t esz = precision == HSE_MIXED ? 4 : 8;
+  size_t buf = (size_t)(2 * Mt) * (2 * Mt) * (2 * (2 * Mt + 1)) * esz;
+  size_t tab = (size_t)(Mt + 1) * (Mt + 1) * (2 * Mt + 1) * esz;
+  int ncomp = product_components(mask).n;
+  *bytes = buf * (ncomp + 1) + 2 * tab;
+  if (M_out) *M_out = q.M;
+  if (P_out) *P_out = q.P;
   return HSE_OK;
 }
 

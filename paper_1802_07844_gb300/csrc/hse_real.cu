@@ -58,7 +58,15 @@ struct RealArgs {
   float img64_2;           // FP32 path: image pairs closer than this (squared) are evaluated in FP64
   double inv_cell[3];
   int ncell[3];
+  // batched instances: instance of each sorted particle (null: one instance)
+  // and cells per instance; an instance's cells follow each other in the list
+  const int32_t* inst_of;
+  int ncells_inst;
 };
+
+__device__ __forceinline__ int cell_base(const RealArgs& a, int64_t sorted_idx) {
+  return a.inst_of ? a.inst_of[sorted_idx] * a.ncells_inst : 0;
+}
 
 enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2 };
 constexpr int kWarpsPerBlock = 4;
@@ -272,7 +280,7 @@ template <> __device__ __forceinline__ const float* strengths_of<float>(const Re
 // sorted source index from below (half list of the symmetric kernel).
 template <typename Visit>
 __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* x, const float* xf, int64_t own,
-                                               int lane, int free_min, int img_min, Visit&& visit) {
+                                               int lane, int free_min, int img_min, int base, Visit&& visit) {
   int cx = cell_coord(x[0], a.inv_cell[0], a.ncell[0]);
   int cy = cell_coord(x[1], a.inv_cell[1], a.ncell[1]);
   int cz = cell_coord(x[2], a.inv_cell[2], a.ncell[2]);
@@ -289,7 +297,7 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
       for (int iy = (cy > 0 ? cy - 1 : 0); iy <= (cy < ny - 1 ? cy + 1 : ny - 1); ++iy) {
         // x-neighbours are contiguous in the cell numbering
         int xa = cx > 0 ? cx - 1 : 0, xb = cx < nx - 1 ? cx + 1 : nx - 1;
-        int c0 = (iz * ny + iy) * nx + xa;
+        int c0 = base + (iz * ny + iy) * nx + xa;
         int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
         if (s0 < jmin) s0 = jmin;
         for (int base = s0; base < s1; base += 32) {
@@ -396,7 +404,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
       else add_image<T>(a.mask, R, r, h, x3, s, xi, u);
     };
     float xf[3] = {x.h[0], x.h[1], x.h[2]};
-    for_candidates(a, x.d, xf, own, lane, 0, 0, [&](bool hit, int j, int type) {
+    const int base = a.tgt ? 0 : cell_base(a, w);
+    for_candidates(a, x.d, xf, own, lane, 0, 0, base, [&](bool hit, int j, int type) {
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
       cnt += __popc(m);
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
       if (type == Q_FREE || j != w) partner_add(j, v[0], v[1], v[2]);
     };
     float xf[3] = {x.h[0], x.h[1], x.h[2]};
-    for_candidates(a, x.d, xf, w, lane, (int)w + 1, (int)w, [&](bool hit, int j, int type) {
+    for_candidates(a, x.d, xf, w, lane, (int)w + 1, (int)w, cell_base(a, w), [&](bool hit, int j, int type) {
       unsigned m = __ballot_sync(0xffffffffu, hit && type != Q_SELF);
       if (hit && type != Q_SELF) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
       cnt += __popc(m);
@@ -557,11 +566,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_close_images(RealArgs a
     int cx = cell_coord(x.d[0], a.inv_cell[0], nx);
     int cy = cell_coord(x.d[1], a.inv_cell[1], ny);
     int czi_hi = cell_coord(a.rc - x.d[2], a.inv_cell[2], nz);
+    const int base = cell_base(a, w);
     double u[3] = {0.0, 0.0, 0.0};
     for (int iz = 0; iz <= czi_hi; ++iz)
       for (int iy = (cy > 0 ? cy - 1 : 0); iy <= (cy < ny - 1 ? cy + 1 : ny - 1); ++iy) {
         int xa = cx > 0 ? cx - 1 : 0, xb = cx < nx - 1 ? cx + 1 : nx - 1;
-        int c0 = (iz * ny + iy) * nx + xa;
+        int c0 = base + (iz * ny + iy) * nx + xa;
         int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
         for (int j = s0 + lane; j < s1; j += 32) {
           float rf[3], hf;
@@ -600,7 +610,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_counts(RealArgs a, int3
     }
     float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
     int cf = 0, ci = 0;
-    for_candidates(a, x, xf, own, lane, 0, 0, [&](bool hit, int j, int type) {
+    for_candidates(a, x, xf, own, lane, 0, 0, a.tgt ? 0 : cell_base(a, w), [&](bool hit, int j, int type) {
       unsigned mf = __ballot_sync(0xffffffffu, hit && type == Q_FREE);
       unsigned mi = __ballot_sync(0xffffffffu, hit && type == Q_IMAGE);
       cf += __popc(mf);
@@ -642,6 +652,8 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   a.rc2_hi = (float)(a.rc2 + m) * (1.0f + 1e-6f);
   a.img64_2 = (float)(a.rc2 / 256.0);
   for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = p->prm.ncell[d]; }
+  a.inst_of = nullptr;
+  a.ncells_inst = p->prm.ncell[0] * p->prm.ncell[1] * p->prm.ncell[2];
   return a;
 }
 
@@ -681,6 +693,35 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
   }
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_real");
+}
+
+// Batched instances (targets = sources, every instance sharing the plan's
+// parameters): sorted particles of all instances, inst_of per sorted particle,
+// cell lists of the instances one after another.  Writes the real-space sums
+// of every particle in concatenated (unsorted) order to out.
+hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of, double* out, cudaStream_t s) {
+  if (n_total == 0) return HSE_OK;
+  RealArgs a = make_args(p, n_total, n_total, nullptr, nullptr, false);
+  a.inst_of = inst_of;
+  const bool mixed = p->prm.precision == HSE_MIXED;
+  a.out = p->ws.usort;
+  a.out4 = p->ws.usort4;
+  if (mixed) {
+    HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_total, s));
+    k_real_sym<float><<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
+    k_close_images<<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
+    p->n_launch += 2;
+  } else {
+    HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_total, s));
+    k_real_sym<double><<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
+    ++p->n_launch;
+  }
+  HSE_CUDA(p, cudaGetLastError());
+  int64_t b = (n_total + 255) / 256;
+  k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(n_total, p->ws.val_a, p->ws.usort,
+                                                                   mixed ? p->ws.usort4 : nullptr, out);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), "real_space_batch");
 }
 
 hse_status neighbor_counts(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, int32_t* na, int32_t* nb,

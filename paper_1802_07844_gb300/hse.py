@@ -46,6 +46,28 @@ class hse_eval_stats(ctypes.Structure):
                 ("stage_ms", ctypes.c_double * HSE_N_STAGES)]
 
 
+HSE_PENDING = 7
+
+
+class hse_server_config(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class hse_request(ctypes.Structure):
+    _fields_ = [("kernel_mask", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("box", ctypes.c_double * 3), ("n_src", ctypes.c_int64), ("src_xyz", ctypes.c_void_p),
+                ("strengths", ctypes.c_void_p), ("n_tgt", ctypes.c_int64), ("tgt_xyz", ctypes.c_void_p),
+                ("vel", ctypes.c_void_p)]
+
+
+class hse_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("busy_s", ctypes.c_double), ("targets_per_s", ctypes.c_double),
+                ("plans_created", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_size_t)]
+
+
 class HseError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -55,7 +77,9 @@ class HseError(RuntimeError):
 _lib = None
 _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
-          "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats", "hse_cell_list_noalloc")
+          "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats", "hse_cell_list_noalloc",
+          "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
+          "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text")
 
 
 def load(path: str = LIB_PATH):
@@ -78,6 +102,15 @@ def load(path: str = LIB_PATH):
     L.hse_spread_grids.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(ctypes.c_int), vp]
     L.hse_plan_destroy.argtypes = [vp]
     L.hse_plan_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hse_server_create.argtypes = [ctypes.POINTER(hse_server_config), ctypes.POINTER(vp)]
+    L.hse_server_submit.argtypes = [vp, ctypes.POINTER(hse_request), ctypes.POINTER(ctypes.c_uint64)]
+    L.hse_server_poll.argtypes = [vp, ctypes.c_uint64]
+    L.hse_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
+    L.hse_server_get_stats.argtypes = [vp, ctypes.POINTER(hse_server_stats)]
+    L.hse_server_reset_stats.argtypes = [vp]
+    L.hse_server_destroy.argtypes = [vp]
+    L.hse_server_error_text.argtypes = [vp, ctypes.c_uint64]
+    L.hse_server_error_text.restype = ctypes.c_char_p
     L.hse_cell_list_noalloc.argtypes = [i64, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), dp, dp,
                                         dp, vp]
     L.hse_get_eval_stats.argtypes = [vp, ctypes.POINTER(hse_eval_stats)]
@@ -167,6 +200,104 @@ def hse_cell_list_noalloc(n, pos_ptr, box, ncell, cell_ptr, perm_ptr, start_ptr,
     b = (ctypes.c_double * 3)(*[float(v) for v in box])
     c = (ctypes.c_int * 3)(*[int(v) for v in ncell])
     _check(load().hse_cell_list_noalloc(n, pos_ptr, b, c, cell_ptr, perm_ptr, start_ptr, stream))
+
+
+def hse_server_create(n_slots, mem_budget_bytes=0):
+    cfg = hse_server_config(int(n_slots), int(mem_budget_bytes))
+    out = ctypes.c_void_p()
+    _check(load().hse_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def hse_server_submit(srv, req: hse_request) -> int:
+    t = ctypes.c_uint64()
+    _check(load().hse_server_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def hse_server_poll(srv, ticket) -> int:
+    return load().hse_server_poll(srv, ticket)
+
+
+def hse_server_wait(srv, ticket, timeout_s) -> int:
+    return load().hse_server_wait(srv, ticket, float(timeout_s))
+
+
+def hse_server_get_stats(srv) -> dict:
+    st = hse_server_stats()
+    _check(load().hse_server_get_stats(srv, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in hse_server_stats._fields_}
+
+
+def hse_server_reset_stats(srv):
+    _check(load().hse_server_reset_stats(srv))
+
+
+def hse_server_error_text(srv, ticket) -> str:
+    return load().hse_server_error_text(srv, ticket).decode()
+
+
+def hse_server_destroy(srv):
+    _check(load().hse_server_destroy(srv))
+
+
+def server_xi(n, box=(1.0, 1.0, 1.0)):
+    """The xi a server picks for n sources (0.7 (N/V)^(1/3) on a sqrt(2) ladder)."""
+    import math
+    v = box[0] * box[1] * box[2]
+    xi = 0.7 * ((max(n, 1) / v) ** (1.0 / 3.0))
+    return 2.0 ** (round(2.0 * math.log2(xi)) / 2.0)
+
+
+class Server:
+    """Continuous-batching server; requests reference torch CUDA tensors that
+    the caller keeps alive until completion."""
+
+    def __init__(self, n_slots=3, mem_budget_bytes=0):
+        self.handle = hse_server_create(n_slots, mem_budget_bytes)
+        self._keep = {}
+
+    def submit(self, kernel_mask, src, strengths, tol, precision=HSE_FP64, tgt=None, box=(1.0, 1.0, 1.0), out=None):
+        import torch
+        n_src = src.shape[1]
+        n_tgt = n_src if tgt is None else tgt.shape[1]
+        if out is None:
+            out = torch.empty((3, n_tgt), dtype=torch.float64, device=src.device)
+        req = hse_request(int(kernel_mask), int(precision), float(tol), (ctypes.c_double * 3)(*box), n_src,
+                          Plan._ptr(src), Plan._ptr(strengths), n_tgt, Plan._ptr(tgt), Plan._ptr(out))
+        t = hse_server_submit(self.handle, req)
+        self._keep[t] = (src, strengths, tgt, out)
+        return t
+
+    def poll(self, ticket):
+        return hse_server_poll(self.handle, ticket)
+
+    def wait(self, ticket, timeout_s=600.0):
+        st = hse_server_wait(self.handle, ticket, timeout_s)
+        if st not in (HSE_OK, HSE_ERR_TIMEOUT):
+            raise HseError(st, f"request {ticket} failed: {hse_server_error_text(self.handle, ticket)}")
+        return st
+
+    def result(self, ticket):
+        return self._keep[ticket][3]
+
+    def stats(self):
+        return hse_server_get_stats(self.handle)
+
+    def reset_stats(self):
+        hse_server_reset_stats(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            hse_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hse_status_string(status) -> str:

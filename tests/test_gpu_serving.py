@@ -1,0 +1,86 @@
+"""Serving with continuous batching: requests of mixed kernel, size, precision
+and distribution overlap on the GPU, and each result equals the same request
+evaluated alone (same plan parameters) and the FP64 direct sum within its
+tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import KERNEL_S, KERNEL_T, KERNEL_W, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1802_07844_gb300 as p
+    return p
+
+
+def _requests():
+    rng = np.random.default_rng(1802078444)
+    masks = [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W]
+    out = []
+    for i in range(12):
+        mask = masks[i % 4]
+        n = int(np.exp(rng.uniform(np.log(1000), np.log(12000))))
+        dist = "near_wall" if i % 2 else "uniform"
+        tol = 1e-10 if i % 3 else 1e-5
+        out.append((mask, n, dist, tol, i))
+    return out
+
+
+def test_mix_equals_alone_and_oracle(pkg):
+    srv = pkg.hse.Server(n_slots=3)
+    try:
+        _mix_equals_alone(pkg, srv)
+    finally:
+        srv.close()
+
+
+def _mix_equals_alone(pkg, srv):
+    reqs = []
+    for mask, n, dist, tol, i in _requests():
+        pr = problem(mask, n, 1.0, dist, 60, sub=i)
+        prec = pkg.HSE_MIXED if tol >= 1e-6 else pkg.HSE_FP64
+        src = torch.from_numpy(pr.src).cuda()
+        st = torch.from_numpy(pr.strengths).cuda()
+        t = srv.submit(mask, src, st, tol, prec)
+        reqs.append((t, pr, prec, tol, src, st))
+    for t, *_ in reqs:
+        assert srv.wait(t, 300.0) == pkg.hse.HSE_OK
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    for t, pr, prec, tol, src, st in reqs:
+        mixed = srv.result(t).cpu().numpy()
+        n = pr.src.shape[1]
+        plan = pkg.Plan(pr.mask, (1.0, 1.0, 1.0), xi=pkg.hse.server_xi(n), rc=0.0, P=0, tol=tol, precision=prec)
+        alone = plan.eval(src, st).cpu().numpy()
+        plan.close()
+        # same plan parameters: only the atomic summation order can differ
+        assert oracle.rel_rms(mixed, alone) < (1e-13 if prec == pkg.HSE_FP64 else 1e-6)
+        idx = np.sort(np.random.default_rng(t).choice(n, 32, replace=False))
+        ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src[:, idx])
+        assert oracle.rel_rms(mixed[:, idx], ref) < tol
+
+
+def test_bounded_wait_and_memory_admission(pkg):
+    pr = problem(KERNEL_S, 200_000, 1.0, "uniform", 61)
+    src = torch.from_numpy(pr.src).cuda()
+    st = torch.from_numpy(pr.strengths).cuda()
+    srv = pkg.hse.Server(n_slots=1)
+    t = srv.submit(KERNEL_S, src, st, 1e-10, pkg.HSE_FP64)
+    # a host-side wait with a short limit returns a timeout, not a hang
+    assert srv.wait(t, 1e-4) == pkg.hse.HSE_ERR_TIMEOUT
+    assert srv.wait(t, 300.0) == pkg.hse.HSE_OK
+    srv.close()
+    # a request whose grids cannot fit the server's budget is refused at submission
+    small = pkg.hse.Server(n_slots=1, mem_budget_bytes=16 << 20)
+    with pytest.raises(pkg.HseError) as e:
+        small.submit(KERNEL_S, src, st, 1e-10, pkg.HSE_FP64)
+    assert e.value.status == pkg.hse.HSE_ERR_OOM
+    small.close()
