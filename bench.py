@@ -284,6 +284,9 @@ def run_ours(args, rank, world, local_rank):
         plan.close()
         torch.cuda.empty_cache()
         out["serve"] = run_serve(args, pkg, torch, dev)
+    if args.batch_instances > 0:
+        torch.cuda.empty_cache()
+        out["batch"] = run_batch(args, pkg, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tps, k, dt = time_oracle(pr, mask, args.cpu_budget)
         out["cpu_baseline"] = {"value": tps / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -391,6 +394,65 @@ def _serve_measure(srv, reqs, rng, pkg, args):
             "plans_created": st["plans_created"], "plans_evicted": st["plans_evicted"]}
 
 
+def run_batch(args, pkg, torch, dev):
+    """Many small independent sums in one call: stokeslet / stresslet 50/50, N
+    log-uniform in [200, 2e4], uniform positions in the unit box, N(0,1)
+    strengths, FP32 arithmetic at tol 1e-5, xi autotuned per group.  A step is
+    one hse_batch_eval over all instances (inputs resident on the device)."""
+    from workloads import KERNEL_S, KERNEL_T, problem as mk
+    import oracle
+    n_inst = args.batch_instances
+    rng = np.random.default_rng(1802078440 + 3)
+    probs = []
+    for i in range(n_inst):
+        mask = KERNEL_S if i % 2 == 0 else KERNEL_T
+        n = int(np.exp(rng.uniform(np.log(200), np.log(2e4))))
+        probs.append(mk(mask, n, 1.0, "uniform", 3, sub=i))
+    items = [(p.mask, torch.from_numpy(p.src).to(dev), torch.from_numpy(p.strengths).to(dev)) for p in probs]
+    outs = [torch.empty((3, p.src.shape[1]), dtype=torch.float64, device=dev) for p in probs]
+    n_tot = sum(p.src.shape[1] for p in probs)
+    b = pkg.hse.Batch(1e-5, pkg.HSE_MIXED, autotune=True)
+    try:
+        t0 = time.perf_counter()
+        b.eval(items, outs)  # first call: plans, autotuning, cuFFT plans
+        torch.cuda.synchronize()
+        t_first = time.perf_counter() - t0
+        for _ in range(max(0, args.warmup - 1)):
+            b.eval(items, outs)
+        torch.cuda.synchronize()
+        s0 = b.stats()
+        stream = torch.cuda.current_stream()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.eval(items, outs)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        s1 = b.stats()
+    finally:
+        b.close()
+    ms_step = float(np.mean(ms))
+    # error against the FP64 direct sum, over all targets of sampled instances
+    erng = np.random.default_rng(1802078440 + 97)
+    errs = []
+    for i in sorted(erng.choice(n_inst, size=min(16, n_inst), replace=False)):
+        p = probs[i]
+        ref = oracle.direct(p.mask, p.src, p.strengths)
+        errs.append(oracle.rel_rms(outs[i].cpu().numpy(), ref))
+    steps = max(1, args.steps)
+    return {"instances": n_inst, "targets": n_tot, "value": n_tot / (ms_step / 1e3) / 1e6, "unit": "Mtargets/s",
+            "instances_per_s": n_inst / (ms_step / 1e3), "ms_per_step": ms_step,
+            "first_call_s": t_first, "tol": 1e-5, "dtype": "f32 arithmetic (FP64 sums, close image pairs, tables)",
+            "chunks_per_step": (s1["chunks"] - s0["chunks"]) / steps,
+            "gpu_launches_per_step": (s1["kernel_launches"] - s0["kernel_launches"]) / steps,
+            "fft_execs_per_step": (s1["fft_execs"] - s0["fft_execs"]) / steps,
+            "plans": s1["plans"], "autotuned_groups": s1["autotuned_groups"],
+            "err_vs_oracle_max": float(max(errs)),
+            "err_sample": f"{len(errs)} seeded instances, all their targets, FP64 direct sum"}
+
+
 def run_real_only(args, pkg, torch, dev, W, pr):
     plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0)
     src = torch.from_numpy(pr.src).to(dev)
@@ -452,6 +514,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-arithmetic measurement")
     ap.add_argument("--serve-requests", type=int, default=400, help="requests of the serving run (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--batch-instances", type=int, default=4096,
+                    help="instances of the batched small-systems run (0: skip)")
     ap.add_argument("--real-only", action="store_true",
                     help="profiling aid: plan without a grid, time only the real-space half")
     args = ap.parse_args()

@@ -270,6 +270,71 @@ hse_status hse_server_reset_stats(hse_server srv);
 /* Waits for admitted work, fails queued requests, frees plans. */
 hse_status hse_server_destroy(hse_server srv);
 
+/* ------------------------------------------------------------------------ */
+/* Batched instances: many small independent systems in few launches.         */
+/* ------------------------------------------------------------------------ */
+typedef struct hse_batch_s* hse_batch;
+
+typedef struct {
+  int kernel_mask;          /* HSE_STOKESLET / HSE_STRESSLET / HSE_ROTLET bits   */
+  int64_t n;                /* particles (>= 1); targets are the sources         */
+  const double* src_xyz;    /* device, 3 x n                                     */
+  const double* strengths;  /* device, rows x n in the order of hse_eval         */
+  double* vel;              /* device, 3 x n, overwritten                        */
+} hse_instance;
+
+typedef struct {
+  int64_t instances, particles;  /* evaluated so far                          */
+  int64_t chunks;                /* launch groups (one pass of every stage)   */
+  int64_t kernel_launches;       /* this library's kernels                    */
+  int64_t fft_execs;             /* batched cuFFT executions                  */
+  int64_t plans;                 /* (mask, xi) groups with a resident plan    */
+  int64_t autotuned_groups;      /* groups whose xi the autotuner timed       */
+  size_t grid_bytes;             /* component-major grids of the largest chunk */
+  size_t fft_work_bytes;         /* shared work area of the batched cuFFT plans */
+  size_t particle_bytes;         /* per-particle work arrays (grow-only)      */
+  size_t plan_bytes;             /* grids and tables held by the group plans  */
+  double stage_ms[HSE_N_STAGES]; /* summed stage times of all timed chunks     */
+} hse_batch_stats;
+
+/*
+ * A batch evaluates many independent instances of the Sec. 3 sums, each a
+ * set of particles in the same box (targets = sources, as hse_eval with
+ * tgt_xyz == NULL), to one tolerance and precision.  Instances are grouped by
+ * kernel mask and xi (xi = 0.7 (N/V)^(1/3) on a factor-sqrt(2) ladder, or the
+ * ladder level the autotuner found fastest for the group); each group has one
+ * plan (r_c, M, P from tol) and is evaluated in chunks of many instances, every
+ * stage of Sec. 4-5 one launch over the whole chunk: one cell list over all
+ * instances (key = instance, cell), one real-space launch, one spread, batched
+ * pruned FFTs (a few cuFFT executions over all instances' grids), one k-space
+ * scaling, one gather.
+ * Results equal those of hse_eval on a plan with the same parameters, up to
+ * summation order.
+ *   tol, precision    as for hse_plan_create (xi, r_c, P chosen from tol).
+ *   box               host {L1, L2, L3}, shared by all instances.
+ *   mem_budget_bytes  device bytes for the grids of one chunk (0: half the
+ *                     free memory at creation).
+ *   autotune          1: on the first chunk of each group, time the ladder
+ *                     levels next to the default xi and keep the fastest
+ *                     (every level meets tol, so results stay valid).
+ */
+hse_status hse_batch_create(double tol, int precision, const double box[3], size_t mem_budget_bytes, int autotune,
+                            hse_batch* out);
+/* Evaluate n_inst instances (host array of descriptors, device data) on the
+ * stream; returns after the last chunk has been queued (the input check
+ * synchronises the stream once per chunk).  Errors: HSE_ERR_INVALID (bad
+ * descriptor or data; text from hse_batch_last_error), HSE_ERR_OOM,
+ * HSE_ERR_CUDA, HSE_ERR_CUFFT. */
+hse_status hse_batch_eval(hse_batch batch, int n_inst, const hse_instance* inst, void* cuda_stream);
+hse_status hse_batch_get_stats(hse_batch batch, hse_batch_stats* out);
+/* Enable (1) or disable (0) CUDA-event timing of the stages of every chunk
+ * (stage_ms of the stats; synchronises the stream once per chunk). */
+hse_status hse_batch_set_timing(hse_batch batch, int enable);
+/* Text of the batch's last failure ("" when none). */
+const char* hse_batch_last_error(hse_batch batch);
+/* Waits for the device, frees plans, grids and cuFFT plans. */
+hse_status hse_batch_destroy(hse_batch batch);
+
 /*
  * hse_cell_list_noalloc -- the cell list of hse_cell_list (same cell ids,
  * permutation and cell starts, bit for bit) without any device allocation.

@@ -17,6 +17,9 @@
 //          rotlet A^W = -2 i eps k, tables including exp(-(1-eta)k^2/4xi^2);
 //  IFFT    cuFFT Z2D of the 6 fields T1, T2;
 //  gather  u_F(x) = h^3 sum over the P^3 support of W(x - x_j) (T1 - x3 T2).
+#include <algorithm>
+#include <type_traits>
+
 #include "hse_internal.cuh"
 
 namespace hse {
@@ -266,6 +269,7 @@ struct ScaleArgs {
   int iS, iT, iW, iCs, iCv, iCt;  // first component index of each group, -1 if absent
   int n_inst;
   int64_t istride;                // complex elements between instances of one component
+  int64_t xstride;                // complex elements between kx planes of one buffer
 };
 
 template <typename C, typename T>
@@ -287,10 +291,11 @@ __global__ void k_scale(ScaleArgs<T> a) {
   for (int64_t ee = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ee < nh * a.n_inst;
        ee += (int64_t)gridDim.x * blockDim.x) {
     const int64_t inst = ee / nh, el = ee - inst * nh;
-    const int64_t e = inst * a.istride + el;  // element of component 0 of this instance
     int jz = (int)(el % Nzh);
     int64_t t = el / Nzh;
     int iy = (int)(t % Ny), ix = (int)(t / Ny);
+    // element of component 0 of this instance
+    const int64_t e = inst * a.istride + ix * a.xstride + (int64_t)iy * Nzh + jz;
     C T1[3], T2[3];
     if (ix == Mt || iy == Mt || jz == 2 * Mt) {  // Nyquist modes are dropped
       for (int d = 0; d < 3; ++d) T1[d] = T2[d] = zero;
@@ -583,6 +588,7 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
   sa.n_inst = 1;
   sa.istride = 0;
+  sa.xstride = (int64_t)g.Ny * (g.Nz / 2 + 1);
   stage_mark(p, HSE_STAGE_SCALE, s);
   k_scale<T><<<blocks_for(g.nh, 256, 152 * 32), 256, 0, s>>>(sa);
   ++p->n_launch;
@@ -628,28 +634,160 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
 // buffers; fwd / inv: batched 3-D transforms over n_fft_in * n_inst and
 // 6 * n_inst buffers.  Adds the Fourier part of every particle to out
 // (concatenated order).
+// ------------------------------------------------------- batched transforms
+// One exec of a batched plan: kind 0 = 2-D (y,z) R2C over `batch` planes at
+// real offset `off`; 1 = 2-D C2R likewise; 2 / 3 = 1-D x transform, forward /
+// inverse, over `batch` lines starting at complex offset `off`, element
+// stride `stride`.
+struct FftExec {
+  int kind;
+  int64_t off, batch, stride;
+};
+
+constexpr int64_t kBatchPlanes = 2048;     // planes per 2-D exec (about 0.3-1 GB of data)
+constexpr int64_t kBatchLines = 1 << 20;   // lines per 1-D exec
+
+static std::vector<FftExec> batch_schedule(const GridDims& g, int nc, int C, bool forward) {
+  const int64_t nzh = g.Nz / 2 + 1, plane = (int64_t)g.Ny * g.pitch, planec = (int64_t)g.Ny * nzh;
+  const int64_t nbuf = (int64_t)nc * C, Mt = g.Mt;
+  const int64_t gb = std::max<int64_t>(1, std::min<int64_t>(kBatchLines / planec, nbuf));
+  std::vector<FftExec> ex;
+  if (forward) {
+    // 2-D over the data planes x < Mt of every buffer (one contiguous half),
+    // then x lines of every buffer
+    const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(kBatchPlanes / nbuf, Mt));
+    for (int64_t x0 = 0; x0 < Mt; x0 += gx)
+      ex.push_back({0, x0 * nbuf * plane, std::min(gx, Mt - x0) * nbuf, 0});
+    for (int64_t j0 = 0; j0 < nbuf; j0 += gb)
+      ex.push_back({2, j0 * planec, std::min(gb, nbuf - j0) * planec, nbuf * planec});
+  } else {
+    // x lines of the 6 output components, then 2-D over the planes x < Mt the
+    // gather reads, one x plane at a time (the outputs are contiguous in it)
+    const int64_t nout = 6LL * C;
+    for (int64_t j0 = 0; j0 < nout; j0 += gb)
+      ex.push_back({3, j0 * planec, std::min(gb, nout - j0) * planec, nbuf * planec});
+    for (int64_t x = 0; x < Mt; ++x) ex.push_back({1, x * nbuf * plane, nout, 0});
+  }
+  return ex;
+}
+
+static cufftHandle find_plan(const BatchFFT& f, int kind, int64_t batch, int64_t stride) {
+  const int k = kind == 3 ? 2 : kind;
+  for (const auto& e : f.plans)
+    if (e.kind == k && e.batch == batch && e.stride == stride) return e.h;
+  return 0;
+}
+
+hse_status batch_fft_prepare(hse_plan p, BatchFFT& f, int n_inst, char** work, int64_t* work_cap) {
+  const GridDims& g = p->g;
+  const bool mixed = p->prm.precision == HSE_MIXED;
+  const long long nzh = g.Nz / 2 + 1;
+  const long long plane = (long long)g.Ny * g.pitch, planec = (long long)g.Ny * nzh;
+  std::vector<FftExec> ex = batch_schedule(g, p->comps.n, n_inst, true);
+  std::vector<FftExec> ex2 = batch_schedule(g, p->comps.n, n_inst, false);
+  ex.insert(ex.end(), ex2.begin(), ex2.end());
+  size_t need = 0;
+  for (const FftExec& e : ex) {
+    const int kind = e.kind == 3 ? 2 : e.kind;
+    bool found = false;
+    for (const auto& q : f.plans)
+      if (q.kind == kind && q.batch == e.batch && q.stride == e.stride) {
+        found = true;
+        need = std::max(need, q.work);
+      }
+    if (found) continue;
+    BatchFFT::Entry en{kind, e.batch, e.stride, 0, 0};
+    if (cufftCreate(&en.h) != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "cufftCreate");
+    cufftSetAutoAllocation(en.h, 0);
+    cufftResult r;
+    if (kind == 0 || kind == 1) {
+      long long n2[2] = {g.Ny, g.Nz}, re[2] = {g.Ny, g.pitch}, ce[2] = {g.Ny, nzh};
+      if (kind == 0)
+        r = cufftMakePlanMany64(en.h, 2, n2, re, 1, plane, ce, 1, planec, mixed ? CUFFT_R2C : CUFFT_D2Z, e.batch,
+                                &en.work);
+      else
+        r = cufftMakePlanMany64(en.h, 2, n2, ce, 1, planec, re, 1, plane, mixed ? CUFFT_C2R : CUFFT_Z2D, e.batch,
+                                &en.work);
+    } else {
+      long long nx[1] = {g.Nx}, xe[1] = {g.Nx};
+      r = cufftMakePlanMany64(en.h, 1, nx, xe, e.stride, 1, xe, e.stride, 1, mixed ? CUFFT_C2C : CUFFT_Z2Z, e.batch,
+                              &en.work);
+    }
+    if (r != CUFFT_SUCCESS) {
+      cufftDestroy(en.h);
+      return set_err(p, r == CUFFT_ALLOC_FAILED ? HSE_ERR_OOM : HSE_ERR_CUFFT, "batched cuFFT plan (kind %d): %d",
+                     kind, (int)r);
+    }
+    need = std::max(need, en.work);
+    f.plans.push_back(en);
+  }
+  if ((int64_t)need > *work_cap) {
+    cudaFree(*work);  // synchronises with work in flight
+    *work = nullptr;
+    *work_cap = 0;
+    HSE_CUDA(p, cudaMalloc(work, need));
+    *work_cap = (int64_t)need;
+  }
+  for (const auto& q : f.plans)
+    if (q.work && cufftSetWorkArea(q.h, *work) != CUFFT_SUCCESS)
+      return set_err(p, HSE_ERR_CUFFT, "cufftSetWorkArea");
+  return HSE_OK;
+}
+
+void batch_fft_destroy(BatchFFT& f) {
+  for (auto& e : f.plans) cufftDestroy(e.h);
+  f.plans.clear();
+}
+
+template <typename T>
+static hse_status run_schedule(hse_plan p, const BatchFFT& f, const std::vector<FftExec>& ex, T* spec,
+                               cudaStream_t s) {
+  typedef typename std::conditional<sizeof(T) == 8, cufftDoubleComplex, cufftComplex>::type C;
+  for (const FftExec& e : ex) {
+    cufftHandle h = find_plan(f, e.kind, e.batch, e.stride);
+    if (!h) return set_err(p, HSE_ERR_CUFFT, "batched cuFFT plan missing (kind %d)", e.kind);
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "cufftSetStream");
+    cufftResult r;
+    if (e.kind == 0) {
+      T* x = spec + e.off;
+      if (sizeof(T) == 8) r = cufftExecD2Z(h, (double*)x, (cufftDoubleComplex*)x);
+      else r = cufftExecR2C(h, (float*)x, (cufftComplex*)x);
+    } else if (e.kind == 1) {
+      T* x = spec + e.off;
+      if (sizeof(T) == 8) r = cufftExecZ2D(h, (cufftDoubleComplex*)x, (double*)x);
+      else r = cufftExecC2R(h, (cufftComplex*)x, (float*)x);
+    } else {
+      C* z = reinterpret_cast<C*>(spec) + e.off;
+      const int dir = e.kind == 2 ? CUFFT_FORWARD : CUFFT_INVERSE;
+      if (sizeof(T) == 8) r = cufftExecZ2Z(h, (cufftDoubleComplex*)z, (cufftDoubleComplex*)z, dir);
+      else r = cufftExecC2C(h, (cufftComplex*)z, (cufftComplex*)z, dir);
+    }
+    ++p->n_fft;
+    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "batched FFT exec (kind %d): %d", e.kind, (int)r);
+  }
+  return HSE_OK;
+}
+
+// Alg. 1 over C instances at once, on slab-major grids (see BatchFFT).
 template <typename T>
 static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* specv,
-                                        cufftHandle fwd, cufftHandle inv, double* out, cudaStream_t s) {
+                                        const BatchFFT& f, double* out, cudaStream_t s) {
   const hse_params& q = p->prm;
   const GridDims& g = p->g;
   const int nin = p->comps.n;
   T* spec = reinterpret_cast<T*>(specv);
-  const int64_t cs = g.buf_doubles * n_inst;
-  HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * cs * nin, s));
-  HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, cs, (int64_t)g.Ny * g.pitch, g.pitch, s, n_inst,
-                         g.buf_doubles));
-  cufftSetStream(fwd, s);
-  cufftSetStream(inv, s);
-  cufftResult r;
-  if (sizeof(T) == 8) r = cufftExecD2Z(fwd, (double*)spec, (cufftDoubleComplex*)spec);
-  else r = cufftExecR2C(fwd, (float*)spec, (cufftComplex*)spec);
-  ++p->n_fft;
-  if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "batched forward FFT: %d", (int)r);
+  const int64_t nzh = g.Nz / 2 + 1, plane = (int64_t)g.Ny * g.pitch, planec = (int64_t)g.Ny * nzh;
+  const int64_t nbuf = (int64_t)nin * n_inst;
+  HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nbuf, s));
+  HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, plane * n_inst, plane * nbuf, g.pitch, s, n_inst, plane));
+  stage_mark(p, HSE_STAGE_FFT, s);
+  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, n_inst, true), spec, s));
+  stage_mark(p, HSE_STAGE_SCALE, s);
   ScaleArgs<T> sa;
   sa.buf = reinterpret_cast<typename Cplx<T>::type*>(spec);
-  sa.cstride = g.nh * n_inst;
-  sa.istride = g.nh;
+  sa.cstride = planec * n_inst;
+  sa.istride = planec;
+  sa.xstride = planec * nbuf;
   sa.n_inst = n_inst;
   sa.Mt = q.Mt;
   sa.mask = q.kernel_mask;
@@ -667,10 +805,9 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   k_scale<T><<<blocks_for(g.nh * n_inst, 256, 152 * 32), 256, 0, s>>>(sa);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
-  if (sizeof(T) == 8) r = cufftExecZ2D(inv, (cufftDoubleComplex*)spec, (double*)spec);
-  else r = cufftExecC2R(inv, (cufftComplex*)spec, (float*)spec);
-  ++p->n_fft;
-  if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "batched inverse FFT: %d", (int)r);
+  stage_mark(p, HSE_STAGE_IFFT, s);
+  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, n_inst, false), spec, s));
+  stage_mark(p, HSE_STAGE_GATHER, s);
   GatherArgs<T> ga;
   ga.n_tgt = n_total;
   ga.n_src = n_total;
@@ -678,11 +815,11 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   ga.spos = p->ws.spos;
   ga.sorig = p->ws.val_a;
   ga.buf = spec;
-  ga.bs = cs;
-  ga.xs = (int64_t)g.Ny * g.pitch;
+  ga.bs = plane * n_inst;
+  ga.xs = plane * nbuf;
   ga.pitch = g.pitch;
   ga.inst_of = inst_of;
-  ga.is = g.buf_doubles;
+  ga.is = plane;
   ga.P = q.P;
   ga.Mt = q.Mt;
   ga.h = q.h;
@@ -699,10 +836,10 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
 }
 
 hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* spec,
-                               cufftHandle fwd, cufftHandle inv, double* out, cudaStream_t s) {
+                               BatchFFT& f, double* out, cudaStream_t s) {
   if (p->prm.precision == HSE_MIXED)
-    return fourier_space_batch_t<float>(p, n_total, n_inst, inst_of, spec, fwd, inv, out, s);
-  return fourier_space_batch_t<double>(p, n_total, n_inst, inst_of, spec, fwd, inv, out, s);
+    return fourier_space_batch_t<float>(p, n_total, n_inst, inst_of, spec, f, out, s);
+  return fourier_space_batch_t<double>(p, n_total, n_inst, inst_of, spec, f, out, s);
 }
 
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,

@@ -102,6 +102,7 @@ hse_status build_grids(hse_plan p);           // tables, buffers, cuFFT plans
 void free_grids(hse_plan p);
 hse_status ensure_workspace(hse_plan p, int64_t n);
 void free_workspace(hse_plan p);
+void free_workspace(Workspace& w);
 CompSet product_components(int mask);
 hse_status plan_estimate(int mask, const double box[3], double xi, double tol, int precision, size_t* bytes,
                          int* M_out, int* P_out);
@@ -123,8 +124,26 @@ hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStre
 cudaError_t sort_keys_and_starts(int64_t n, int64_t ncells, int32_t* key_a, int32_t* val_a, int32_t* key_b,
                                  int32_t* val_b, int32_t* hist, int32_t* start_out, cudaStream_t s);
 hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of, double* out, cudaStream_t s);
+// cuFFT plans for the batched grids of one plan.  The batched grids are
+// slab-major: real element (buffer b, x, y, z) at (x * nbuf + b) * Ny * pitch
+// + y * pitch + z, buffer b = component * C + instance, so that the data planes
+// x < Mt of every buffer are one contiguous half and each x line has one
+// stride.  Plans are made per (kind, batch, stride) on first use.
+struct BatchFFT {
+  struct Entry {
+    int kind;
+    int64_t batch, stride;
+    cufftHandle h;
+    size_t work;
+  };
+  std::vector<Entry> plans;
+};
+// Make the plans a chunk of n_inst instances needs and point them at a shared
+// work area, grown (synchronously) when a plan needs more.
+hse_status batch_fft_prepare(hse_plan p, BatchFFT& f, int n_inst, char** work, int64_t* work_cap);
+void batch_fft_destroy(BatchFFT& f);
 hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* spec,
-                               cufftHandle fwd, cufftHandle inv, double* out, cudaStream_t s);
+                               BatchFFT& f, double* out, cudaStream_t s);
 
 inline void stage_mark(hse_plan p, int i, cudaStream_t s) {
   if (p->timing) cudaEventRecord(p->ev[i], s);

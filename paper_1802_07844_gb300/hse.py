@@ -68,6 +68,19 @@ class hse_server_stats(ctypes.Structure):
                 ("resident_bytes", ctypes.c_size_t)]
 
 
+class hse_instance(ctypes.Structure):
+    _fields_ = [("kernel_mask", ctypes.c_int), ("n", ctypes.c_int64), ("src_xyz", ctypes.c_void_p),
+                ("strengths", ctypes.c_void_p), ("vel", ctypes.c_void_p)]
+
+
+class hse_batch_stats(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int64), ("particles", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("fft_execs", ctypes.c_int64), ("plans", ctypes.c_int64),
+                ("autotuned_groups", ctypes.c_int64), ("grid_bytes", ctypes.c_size_t),
+                ("fft_work_bytes", ctypes.c_size_t), ("particle_bytes", ctypes.c_size_t),
+                ("plan_bytes", ctypes.c_size_t), ("stage_ms", ctypes.c_double * 8)]
+
+
 class HseError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -79,7 +92,9 @@ _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_get_params", "hse_ev
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
           "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
-          "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text")
+          "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_batch_create",
+          "hse_batch_eval", "hse_batch_get_stats", "hse_batch_last_error", "hse_batch_destroy",
+          "hse_batch_set_timing")
 
 
 def load(path: str = LIB_PATH):
@@ -111,6 +126,14 @@ def load(path: str = LIB_PATH):
     L.hse_server_destroy.argtypes = [vp]
     L.hse_server_error_text.argtypes = [vp, ctypes.c_uint64]
     L.hse_server_error_text.restype = ctypes.c_char_p
+    L.hse_batch_create.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                                   ctypes.c_int, ctypes.POINTER(vp)]
+    L.hse_batch_eval.argtypes = [vp, ctypes.c_int, ctypes.POINTER(hse_instance), vp]
+    L.hse_batch_get_stats.argtypes = [vp, ctypes.POINTER(hse_batch_stats)]
+    L.hse_batch_last_error.argtypes = [vp]
+    L.hse_batch_last_error.restype = ctypes.c_char_p
+    L.hse_batch_destroy.argtypes = [vp]
+    L.hse_batch_set_timing.argtypes = [vp, ctypes.c_int]
     L.hse_cell_list_noalloc.argtypes = [i64, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), dp, dp,
                                         dp, vp]
     L.hse_get_eval_stats.argtypes = [vp, ctypes.POINTER(hse_eval_stats)]
@@ -119,7 +142,7 @@ def load(path: str = LIB_PATH):
     L.hse_last_error.argtypes = [vp]
     L.hse_last_error.restype = ctypes.c_char_p
     for n in _NAMES:
-        if getattr(L, n).restype is None and n not in ("hse_status_string", "hse_last_error"):
+        if getattr(L, n).restype is None and n not in ("hse_status_string", "hse_last_error", "hse_batch_last_error"):
             getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -292,6 +315,79 @@ class Server:
             hse_server_destroy(self.handle)
             self.handle = None
             self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hse_batch_create(tol, precision=HSE_FP64, box=(1.0, 1.0, 1.0), mem_budget_bytes=0, autotune=0):
+    out = ctypes.c_void_p()
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    _check(load().hse_batch_create(float(tol), int(precision), b, int(mem_budget_bytes), int(autotune),
+                                   ctypes.byref(out)))
+    return out
+
+
+def hse_batch_last_error(batch) -> str:
+    return load().hse_batch_last_error(batch).decode()
+
+
+def hse_batch_eval(batch, instances, stream=0):
+    """instances: a ctypes array of hse_instance (device pointers)."""
+    st = load().hse_batch_eval(batch, len(instances), instances, stream)
+    if st != HSE_OK:
+        raise HseError(st, hse_batch_last_error(batch))
+
+
+def hse_batch_get_stats(batch) -> dict:
+    st = hse_batch_stats()
+    _check(load().hse_batch_get_stats(batch, ctypes.byref(st)))
+    out = {name: getattr(st, name) for name, _ in hse_batch_stats._fields_ if name != "stage_ms"}
+    out["stage_ms"] = {STAGE_NAMES[i]: st.stage_ms[i] for i in range(8)}
+    return out
+
+
+def hse_batch_set_timing(batch, enable):
+    _check(load().hse_batch_set_timing(batch, 1 if enable else 0))
+
+
+def hse_batch_destroy(batch):
+    _check(load().hse_batch_destroy(batch))
+
+
+class Batch:
+    """Evaluates lists of independent instances (targets = sources) grouped by
+    kernel mask and xi; every stage is one launch per chunk of instances."""
+
+    def __init__(self, tol, precision=HSE_FP64, box=(1.0, 1.0, 1.0), mem_budget_bytes=0, autotune=False):
+        self.handle = hse_batch_create(tol, precision, box, mem_budget_bytes, 1 if autotune else 0)
+
+    def eval(self, items, outs=None):
+        """items: list of (kernel_mask, src (3,n), strengths (rows,n)) torch CUDA
+        float64 tensors.  Returns the list of (3,n) velocity tensors."""
+        import torch
+        arr = (hse_instance * len(items))()
+        if outs is None:
+            outs = [torch.empty((3, src.shape[1]), dtype=torch.float64, device=src.device) for _, src, _ in items]
+        for i, (mask, src, strengths) in enumerate(items):
+            arr[i] = hse_instance(int(mask), src.shape[1], Plan._ptr(src), Plan._ptr(strengths), Plan._ptr(outs[i]))
+        stream = torch.cuda.current_stream().cuda_stream if items else 0
+        hse_batch_eval(self.handle, arr, stream)
+        return outs
+
+    def stats(self):
+        return hse_batch_get_stats(self.handle)
+
+    def set_timing(self, enable=True):
+        hse_batch_set_timing(self.handle, enable)
+
+    def close(self):
+        if self.handle is not None:
+            hse_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -1,0 +1,143 @@
+"""Batched small instances: one launch per stage over many independent
+systems.  Each instance's result equals the same system evaluated alone on a
+plan with the same parameters (only summation order differs) and the FP64
+direct half-space sum within the tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import KERNEL_S, KERNEL_T, KERNEL_W, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1802_07844_gb300 as p
+    return p
+
+
+def _instances(count, seed, masks, lo=200, hi=4000, index=70):
+    """N log-uniform in [lo, hi], kernels cycling through masks, distributions
+    alternating uniform / near-wall."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        mask = masks[i % len(masks)]
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        dist = "near_wall" if i % 2 else "uniform"
+        out.append(problem(mask, n, 1.0, dist, index, sub=i))
+    return out
+
+
+def _to_dev(probs):
+    return [(pr.mask, torch.from_numpy(pr.src).cuda(), torch.from_numpy(pr.strengths).cuda()) for pr in probs]
+
+
+def _alone(pkg, mask, src, st, tol, prec):
+    n = src.shape[1]
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=pkg.hse.server_xi(n), rc=0.0, P=0, tol=tol, precision=prec)
+    try:
+        return plan.eval(src, st).cpu().numpy()
+    finally:
+        plan.close()
+
+
+def _oracle_check(pr, u, tol, seed=0):
+    """Relative RMS error over all targets (the Sec. 6 definition).  A small
+    sample would not do: |u| is heavy-tailed (close pairs dominate), so the
+    norm of a few sampled reference values fluctuates far more than the
+    error does."""
+    ref = oracle.direct(pr.mask, pr.src, pr.strengths)
+    return oracle.rel_rms(u, ref)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_batch_equals_alone_and_oracle(pkg, prec, tol):
+    probs = _instances(40, 1802078450 + prec, [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W,
+                                              KERNEL_S | KERNEL_T | KERNEL_W])
+    items = _to_dev(probs)
+    b = pkg.hse.Batch(tol, prec)
+    try:
+        outs = b.eval(items)
+        torch.cuda.synchronize()
+        stats = b.stats()
+    finally:
+        b.close()
+    assert stats["instances"] == len(probs)
+    assert stats["particles"] == sum(p.src.shape[1] for p in probs)
+    # far fewer chunks (launch groups) than instances
+    assert stats["chunks"] == stats["plans"] < len(probs)
+    for i, (pr, (mask, src, st), u) in enumerate(zip(probs, items, outs)):
+        u = u.cpu().numpy()
+        assert np.isfinite(u).all()
+        alone = _alone(pkg, mask, src, st, tol, prec)
+        assert oracle.rel_rms(u, alone) < (1e-12 if prec == 0 else 2e-6), i
+        assert _oracle_check(pr, u, tol, seed=i) < tol, i
+
+
+def test_batch_chunking_and_reuse(pkg):
+    """A small memory budget splits groups into several chunks; results do not
+    depend on how instances are chunked, and a batch object can be reused."""
+    probs = _instances(24, 1802078452, [KERNEL_S | KERNEL_W], lo=300, hi=1500)
+    items = _to_dev(probs)
+    big = pkg.hse.Batch(1e-8, 0)
+    small = pkg.hse.Batch(1e-8, 0, mem_budget_bytes=8 << 20)
+    try:
+        ref = [u.cpu().numpy() for u in big.eval(items)]
+        for _ in range(2):
+            got = [u.cpu().numpy() for u in small.eval(items)]
+            for a, r in zip(got, ref):
+                assert oracle.rel_rms(a, r) < 1e-12
+        s_big, s_small = big.stats(), small.stats()
+    finally:
+        big.close()
+        small.close()
+    assert s_small["chunks"] > 2 * s_big["chunks"]
+    assert s_small["instances"] == 2 * len(probs)
+
+
+def test_batch_autotune_meets_tolerance(pkg):
+    probs = _instances(30, 1802078453, [KERNEL_S, KERNEL_T], lo=500, hi=3000)
+    items = _to_dev(probs)
+    b = pkg.hse.Batch(1e-8, 0, autotune=True)
+    try:
+        outs = b.eval(items)
+        outs2 = b.eval(items)  # tuned levels are reused
+        stats = b.stats()
+    finally:
+        b.close()
+    assert stats["autotuned_groups"] >= 2
+    for i, (pr, u, u2) in enumerate(zip(probs, outs, outs2)):
+        u, u2 = u.cpu().numpy(), u2.cpu().numpy()
+        assert _oracle_check(pr, u, 1e-8, seed=i) < 1e-8
+        assert _oracle_check(pr, u2, 1e-8, seed=i) < 1e-8
+
+
+def test_batch_edge_cases(pkg):
+    b = pkg.hse.Batch(1e-8, 0)
+    try:
+        assert b.eval([]) == []
+        # single-particle and two-particle instances (self and one pair)
+        probs = [problem(KERNEL_S | KERNEL_W, 1, 1.0, "near_wall", 71), problem(KERNEL_T, 2, 1.0, "uniform", 72)]
+        items = _to_dev(probs)
+        outs = b.eval(items)
+        for pr, u in zip(probs, outs):
+            ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src)
+            assert oracle.rel_rms(u.cpu().numpy(), ref) < 1e-8
+        # a point below the wall is rejected; the batch stays usable
+        bad = problem(KERNEL_S, 50, 1.0, "uniform", 73)
+        src = bad.src.copy()
+        src[2, 7] = -0.1
+        with pytest.raises(pkg.hse.HseError) as e:
+            b.eval([(KERNEL_S, torch.from_numpy(src).cuda(), torch.from_numpy(bad.strengths).cuda())])
+        assert e.value.status == pkg.hse.HSE_ERR_INVALID
+        assert "outside" in str(e.value)
+        outs = b.eval(items)
+        ref = oracle.direct(probs[0].mask, probs[0].src, probs[0].strengths, probs[0].src)
+        assert oracle.rel_rms(outs[0].cpu().numpy(), ref) < 1e-8
+    finally:
+        b.close()

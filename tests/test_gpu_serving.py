@@ -63,9 +63,10 @@ def _mix_equals_alone(pkg, srv):
         plan.close()
         # same plan parameters: only the atomic summation order can differ
         assert oracle.rel_rms(mixed, alone) < (1e-13 if prec == pkg.HSE_FP64 else 1e-6)
-        idx = np.sort(np.random.default_rng(t).choice(n, 32, replace=False))
-        ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src[:, idx])
-        assert oracle.rel_rms(mixed[:, idx], ref) < tol
+        # error over all targets (Sec. 6): sampled norms of the heavy-tailed
+        # reference fluctuate more than the error
+        ref = oracle.direct(pr.mask, pr.src, pr.strengths)
+        assert oracle.rel_rms(mixed, ref) < tol
 
 
 def test_bounded_wait_and_memory_admission(pkg):
