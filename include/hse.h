@@ -295,6 +295,8 @@ typedef struct {
   size_t particle_bytes;         /* per-particle work arrays (grow-only)      */
   size_t plan_bytes;             /* grids and tables held by the group plans  */
   double stage_ms[HSE_N_STAGES]; /* summed stage times of all timed chunks     */
+  int64_t graphs_captured;       /* stage sequences captured as CUDA graphs   */
+  int64_t graph_launches;        /* chunks run by replaying a captured graph  */
 } hse_batch_stats;
 
 /*
@@ -314,9 +316,10 @@ typedef struct {
  *   box               host {L1, L2, L3}, shared by all instances.
  *   mem_budget_bytes  device bytes for the grids of one chunk (0: half the
  *                     free memory at creation).
- *   autotune          1: on the first chunk of each group, time the ladder
- *                     levels next to the default xi and keep the fastest
- *                     (every level meets tol, so results stay valid).
+ *   autotune          1: on the first instances of each group, time xi
+ *                     ladder levels walking down from the default while each
+ *                     step is faster per particle (else up), and keep the
+ *                     fastest; every level meets tol, so results stay valid.
  */
 hse_status hse_batch_create(double tol, int precision, const double box[3], size_t mem_budget_bytes, int autotune,
                             hse_batch* out);
@@ -328,8 +331,15 @@ hse_status hse_batch_create(double tol, int precision, const double box[3], size
 hse_status hse_batch_eval(hse_batch batch, int n_inst, const hse_instance* inst, void* cuda_stream);
 hse_status hse_batch_get_stats(hse_batch batch, hse_batch_stats* out);
 /* Enable (1) or disable (0) CUDA-event timing of the stages of every chunk
- * (stage_ms of the stats; synchronises the stream once per chunk). */
+ * (stage_ms of the stats; synchronises the stream once per chunk).  Timed
+ * chunks are launched directly, not from graphs. */
 hse_status hse_batch_set_timing(hse_batch batch, int enable);
+/* Replay (1, the default) or not (0) each chunk's stage sequence from a CUDA
+ * graph.  A chunk's stages after the input check (sort, real space, spread,
+ * transforms, scaling, gather, scatter) are captured once per chunk shape and
+ * replayed when the same instance sizes come again; the graph reads the
+ * caller's arrays through a device descriptor table, so they may change. */
+hse_status hse_batch_set_graphs(hse_batch batch, int enable);
 /* Text of the batch's last failure ("" when none). */
 const char* hse_batch_last_error(hse_batch batch);
 /* Waits for the device, frees plans, grids and cuFFT plans. */

@@ -84,6 +84,24 @@ struct Bucket {
 
 constexpr double kMaxXStride = 256.0 * (1 << 20);
 
+// A captured stage sequence of one chunk (sort ... scatter).  It bakes in
+// sizes, the group's plan and the addresses of the batch's work arrays, so it
+// is replayed only when all of them match; the caller's arrays are read
+// through the device descriptor table and may change between calls.
+constexpr int kGraphPtrs = 22;
+struct GraphEntry {
+  const void* bucket;
+  int m;
+  int64_t n_tot, nmax;
+  const void* ptrs[kGraphPtrs];
+  cudaGraphExec_t exec;
+  int64_t launches, ffts;
+  uint64_t last_use;
+};
+constexpr size_t kMaxGraphs = 64;
+constexpr size_t kTrialInstances = 256;  // instances timed per autotuner trial
+constexpr int kTuneSteps = 4;            // ladder steps tried in each direction
+
 double ladder_xi(int k) { return std::exp2(k / 2.0); }
 int ladder_level(int64_t n, const double box[3]) {
   double v = box[0] * box[1] * box[2];
@@ -114,6 +132,10 @@ struct hse_batch_s {
   int64_t fft_work_cap = 0;
   hse::Workspace ws;           // cell-list and particle work arrays, lent to the plan in use
   bool timing = false;
+  bool graphs = true;          // replay captured stage sequences
+  cudaStream_t cap = nullptr;  // capture stream (never executes work)
+  std::vector<GraphEntry> graph_cache;
+  uint64_t tick = 0;
   int* d_flag = nullptr;
   int* h_flag = nullptr;
   std::string err;
@@ -268,7 +290,106 @@ hse_status prepare_chunk(hse_batch b, Bucket* k, const Chunk& c) {
   return HSE_OK;
 }
 
-hse_status run_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const Chunk& c, cudaStream_t s) {
+// Stages after the input check: sort, sorted copy, instance index, real
+// space, Fourier space, scatter to the instances.  *launches / *ffts count
+// this library's kernels and the cuFFT executions.
+hse_status enqueue_stages(hse_batch b, Bucket* k, const Chunk& c, int64_t nmax, cudaStream_t s, int64_t* launches,
+                          int64_t* ffts) {
+  hse_plan p = k->plan;
+  const hse_params& q = p->prm;
+  const int ncells = q.ncell[0] * q.ncell[1] * q.ncell[2];
+  const int64_t nkeys = (int64_t)ncells * c.m;
+  hse::stage_mark(p, HSE_STAGE_CELLS, s);
+  BTRY(bcuda(b,
+             hse::sort_keys_and_starts(c.n_tot, nkeys, p->ws.key_a, p->ws.val_a, p->ws.key_b, p->ws.val_b,
+                                       p->ws.radix_hist, p->ws.cell_start, s),
+             "sort"));
+  int bits = 0;
+  while ((int64_t(1) << bits) < nkeys) ++bits;
+  const int sort_launches = 3 * ((bits + 7) / 8) + 1;
+  p->n_launch = 0;
+  p->n_fft = 0;
+  if (hse::gather_sorted(p, c.n_tot, b->d_pos, b->d_str, s) != HSE_OK)
+    return berr(b, HSE_ERR_CUDA, hse_last_error(p));
+  k_inst_of<<<(unsigned)std::min<int64_t>((c.n_tot + 255) / 256, 152 * 32), 256, 0, s>>>(p->ws.key_a, c.n_tot,
+                                                                                        ncells, b->inst_of);
+  BTRY(bcuda(b, cudaGetLastError(), "k_inst_of"));
+  hse::stage_mark(p, HSE_STAGE_REAL, s);
+  hse_status st = hse::real_space_batch(p, c.n_tot, b->inst_of, b->d_res, s);
+  hse::stage_mark(p, HSE_STAGE_SPREAD, s);
+  if (st == HSE_OK) st = hse::fourier_space_batch(p, c.n_tot, c.m, b->inst_of, b->spec, k->fft, b->d_res, s);
+  if (st != HSE_OK) return berr(b, st, hse_last_error(p));
+  dim3 grid((unsigned)std::min<int64_t>((nmax + 255) / 256, 64), (unsigned)std::min(c.m, 65535));
+  k_batch_scatter<<<grid, 256, 0, s>>>(b->d_desc, c.m, c.n_tot, b->d_res);
+  BTRY(bcuda(b, cudaGetLastError(), "k_batch_scatter"));
+  *launches = p->n_launch + sort_launches + 2;  // + k_inst_of, k_batch_scatter
+  *ffts = p->n_fft;
+  return HSE_OK;
+}
+
+void graph_ptrs(hse_batch b, const void** v) {
+  const hse::Workspace& w = b->ws;
+  const void* a[kGraphPtrs] = {b->spec,    b->fft_work, b->d_pos,  b->d_str,     b->d_res, b->inst_of, b->d_desc,
+                               w.key_a,    w.val_a,     w.key_b,   w.val_b,      w.radix_hist, w.cell_start, w.spos,
+                               w.spos32,   w.spos32lo,  w.sstr,    w.sstr32,     w.usort,  w.prep,
+                               w.supp,     w.usort4};
+  for (int i = 0; i < kGraphPtrs; ++i) v[i] = a[i];
+}
+
+// The chunk's stages as a replayed CUDA graph: found in the cache, or
+// captured on the batch's capture stream and instantiated.
+hse_status graph_stages(hse_batch b, Bucket* k, const Chunk& c, int64_t nmax, cudaStream_t s, int64_t* launches,
+                        int64_t* ffts) {
+  const void* ptrs[kGraphPtrs];
+  graph_ptrs(b, ptrs);
+  GraphEntry* hit = nullptr;
+  for (auto& g : b->graph_cache)
+    if (g.bucket == k && g.m == c.m && g.n_tot == c.n_tot && g.nmax == nmax &&
+        std::equal(ptrs, ptrs + kGraphPtrs, g.ptrs)) {
+      hit = &g;
+      break;
+    }
+  if (!hit) {
+    if (b->graph_cache.size() >= kMaxGraphs) {
+      auto lru = std::min_element(b->graph_cache.begin(), b->graph_cache.end(),
+                                  [](const GraphEntry& x, const GraphEntry& y) { return x.last_use < y.last_use; });
+      cudaGraphExecDestroy(lru->exec);
+      b->graph_cache.erase(lru);
+    }
+    GraphEntry g{};
+    g.bucket = k;
+    g.m = c.m;
+    g.n_tot = c.n_tot;
+    g.nmax = nmax;
+    std::copy(ptrs, ptrs + kGraphPtrs, g.ptrs);
+    BTRY(bcuda(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"));
+    hse_status st = enqueue_stages(b, k, c, nmax, b->cap, &g.launches, &g.ffts);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (st != HSE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    BTRY(bcuda(b, e, "cudaStreamEndCapture"));
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    BTRY(bcuda(b, e, "cudaGraphInstantiate"));
+    ++b->st.graphs_captured;
+    b->graph_cache.push_back(g);
+    hit = &b->graph_cache.back();
+  }
+  hit->last_use = ++b->tick;
+  BTRY(bcuda(b, cudaGraphLaunch(hit->exec, s), "cudaGraphLaunch"));
+  ++b->st.graph_launches;
+  *launches = hit->launches;
+  *ffts = hit->ffts;
+  return HSE_OK;
+}
+
+// One chunk: descriptor upload, concatenation and input check (one stream
+// synchronisation), then the stages, replayed from a graph when allowed.
+hse_status run_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const Chunk& c, cudaStream_t s,
+                     bool allow_graph) {
   hse_plan p = k->plan;
   const hse_params& q = p->prm;
   int64_t off = 0, nmax = 0;
@@ -291,30 +412,9 @@ hse_status run_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const Chu
   BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
   if (*b->h_flag & 1) return berr(b, HSE_ERR_INVALID, "an instance has a point non-finite or outside the box");
   if (*b->h_flag & 2) return berr(b, HSE_ERR_INVALID, "an instance has a non-finite strength");
-  const int64_t nkeys = (int64_t)ncells * c.m;
-  hse::stage_mark(p, HSE_STAGE_CELLS, s);
-  BTRY(bcuda(b,
-             hse::sort_keys_and_starts(c.n_tot, nkeys, p->ws.key_a, p->ws.val_a, p->ws.key_b, p->ws.val_b,
-                                       p->ws.radix_hist, p->ws.cell_start, s),
-             "sort"));
-  int bits = 0;
-  while ((int64_t(1) << bits) < nkeys) ++bits;
-  const int sort_launches = 3 * ((bits + 7) / 8) + 1;
-  p->n_launch = 0;
-  p->n_fft = 0;
-  if (hse::gather_sorted(p, c.n_tot, b->d_pos, b->d_str, s) != HSE_OK)
-    return berr(b, HSE_ERR_CUDA, hse_last_error(p));
-  k_inst_of<<<(unsigned)std::min<int64_t>((c.n_tot + 255) / 256, 152 * 32), 256, 0, s>>>(p->ws.key_a, c.n_tot,
-                                                                                        ncells, b->inst_of);
-  BTRY(bcuda(b, cudaGetLastError(), "k_inst_of"));
-  hse::stage_mark(p, HSE_STAGE_REAL, s);
-  hse_status st = hse::real_space_batch(p, c.n_tot, b->inst_of, b->d_res, s);
-  hse::stage_mark(p, HSE_STAGE_SPREAD, s);
-  if (st == HSE_OK)
-    st = hse::fourier_space_batch(p, c.n_tot, c.m, b->inst_of, b->spec, k->fft, b->d_res, s);
-  if (st != HSE_OK) return berr(b, st, hse_last_error(p));
-  k_batch_scatter<<<grid, 256, 0, s>>>(b->d_desc, c.m, c.n_tot, b->d_res);
-  BTRY(bcuda(b, cudaGetLastError(), "k_batch_scatter"));
+  int64_t launches = 0, ffts = 0;
+  if (allow_graph && b->graphs && !b->timing) BTRY(graph_stages(b, k, c, nmax, s, &launches, &ffts));
+  else BTRY(enqueue_stages(b, k, c, nmax, s, &launches, &ffts));
   hse::stage_mark(p, HSE_N_STAGES, s);
   if (b->timing) {
     // per-chunk stage times (synchronises on the chunk's last event)
@@ -325,58 +425,73 @@ hse_status run_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const Chu
     }
   }
   b->st.chunks += 1;
-  b->st.kernel_launches += p->n_launch + sort_launches + 3;  // + k_batch_gather, k_inst_of, k_batch_scatter
-  b->st.fft_execs += p->n_fft;
+  b->st.kernel_launches += launches + 1;  // + k_batch_gather
+  b->st.fft_execs += ffts;
   b->st.particles += c.n_tot;
   return HSE_OK;
 }
 
-hse_status run_group(hse_batch b, int mask, int level, const hse_instance* inst, const std::vector<int>& idx,
-                     cudaStream_t s) {
+// Seconds per particle of the group's first instances at ladder level lv (a
+// warm-up pass, then a timed one).  The instances evaluated keep a valid
+// result: every level meets tol.
+hse_status trial(hse_batch b, int mask, int lv, const hse_instance* inst, const std::vector<int>& idx,
+                 cudaStream_t s, double* t, int* covered) {
+  hse_status st = HSE_OK;
+  Bucket* k = get_bucket(b, mask, ladder_xi(lv), &st);
+  if (!k) return st;
+  WorkspaceLease lease(k->plan, &b->ws);
+  Chunk c = next_chunk(b, k, inst, idx.data(), (int)std::min<size_t>(idx.size(), kTrialInstances));
+  BTRY(prepare_chunk(b, k, c));
+  BTRY(run_chunk(b, k, inst, c, s, false));
+  BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
+  auto t0 = std::chrono::steady_clock::now();
+  BTRY(run_chunk(b, k, inst, c, s, false));
+  BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
+  *t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / (double)c.n_tot;
+  *covered = c.m;
+  return HSE_OK;
+}
+
+struct Job {
+  Bucket* k;
+  Chunk c;
+};
+
+// Pick the group's level (autotuning it once per (mask, default level)) and
+// append its remaining chunks to the job list.
+hse_status plan_group(hse_batch b, int mask, int level, const hse_instance* inst, const std::vector<int>& idx,
+                      cudaStream_t s, std::vector<Job>* jobs) {
   const std::pair<int, int> key(mask, level);
   hse_status st = HSE_OK;
   int done = 0;
   if (b->autotune && !b->tuned.count(key)) {
-    // Time the first chunk at the ladder levels next to the default and keep
-    // the fastest per instance.  Every level meets tol, so the instances a
-    // trial evaluated hold a valid result whichever trial wrote them last.
-    double best = 1e300;
-    int best_level = level;
-    for (int lv = level - 1; lv <= level + 1; ++lv) {
-      Bucket* k = get_bucket(b, mask, ladder_xi(lv), &st);
-      if (!k) {
-        if (lv == level) return st;
-        continue;
-      }
-      WorkspaceLease lease(k->plan, &b->ws);
-      Chunk c = next_chunk(b, k, inst, idx.data(), (int)idx.size());
-      st = prepare_chunk(b, k, c);
-      if (st != HSE_OK) {
-        if (lv == level) return st;
-        continue;
-      }
-      BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
-      auto t0 = std::chrono::steady_clock::now();
-      BTRY(run_chunk(b, k, inst, c, s));
-      BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
-      double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / c.m;
-      if (dt < best) {
-        best = dt;
+    // Walk the xi ladder from the default level, downwards while each step is
+    // faster per particle, else upwards; keep the fastest level.
+    double best = 0.0, t = 0.0;
+    int cov = 0, best_level = level;
+    BTRY(trial(b, mask, level, inst, idx, s, &best, &cov));
+    done = std::max(done, cov);
+    for (int dir : {-1, +1}) {
+      for (int step = 1; step <= kTuneSteps; ++step) {
+        const int lv = level + dir * step;
+        if (trial(b, mask, lv, inst, idx, s, &t, &cov) != HSE_OK) break;  // e.g. no valid plan there
+        done = std::max(done, cov);
+        if (t >= best) break;
+        best = t;
         best_level = lv;
       }
-      done = std::max(done, c.m);
+      if (best_level != level) break;  // improved going down: no need to go up
     }
+    b->err.clear();
     b->tuned[key] = best_level;
     ++b->st.autotuned_groups;
   }
   auto it = b->tuned.find(key);
   Bucket* k = get_bucket(b, mask, ladder_xi(it != b->tuned.end() ? it->second : level), &st);
   if (!k) return st;
-  WorkspaceLease lease(k->plan, &b->ws);
   while (done < (int)idx.size()) {
     Chunk c = next_chunk(b, k, inst, idx.data() + done, (int)idx.size() - done);
-    BTRY(prepare_chunk(b, k, c));
-    BTRY(run_chunk(b, k, inst, c, s));
+    jobs->push_back({k, c});
     done += c.m;
   }
   return HSE_OK;
@@ -408,11 +523,13 @@ extern "C" hse_status hse_batch_create(double tol, int precision, const double b
     }
     b->budget = fr / 2;
   }
-  if (cudaMalloc(&b->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&b->h_flag, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&b->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&b->h_flag, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->d_flag);
+    if (b->h_flag) cudaFreeHost(b->h_flag);
     delete b;
-    return hse::set_err(nullptr, HSE_ERR_OOM, "hse_batch_create: flag");
+    return hse::set_err(nullptr, HSE_ERR_OOM, "hse_batch_create: flag or stream");
   }
   *out = b;
   return HSE_OK;
@@ -432,7 +549,18 @@ extern "C" hse_status hse_batch_eval(hse_batch b, int n_inst, const hse_instance
     groups[std::make_pair(I.kernel_mask, ladder_level(I.n, b->box))].push_back(i);
   }
   b->st.instances += n_inst;
-  for (auto& kv : groups) BTRY(run_group(b, kv.first.first, kv.first.second, inst, kv.second, s));
+  std::vector<Job> jobs;
+  for (auto& kv : groups) BTRY(plan_group(b, kv.first.first, kv.first.second, inst, kv.second, s, &jobs));
+  // size every work array for the largest chunk first, so that no array moves
+  // while chunks run and captured graphs stay valid from call to call
+  for (const Job& j : jobs) {
+    WorkspaceLease lease(j.k->plan, &b->ws);
+    BTRY(prepare_chunk(b, j.k, j.c));
+  }
+  for (const Job& j : jobs) {
+    WorkspaceLease lease(j.k->plan, &b->ws);
+    BTRY(run_chunk(b, j.k, inst, j.c, s, true));
+  }
   return HSE_OK;
 }
 
@@ -458,11 +586,19 @@ extern "C" hse_status hse_batch_set_timing(hse_batch b, int enable) {
   return HSE_OK;
 }
 
+extern "C" hse_status hse_batch_set_graphs(hse_batch b, int enable) {
+  if (!b) return HSE_ERR_INVALID;
+  b->graphs = enable != 0;
+  return HSE_OK;
+}
+
 extern "C" const char* hse_batch_last_error(hse_batch b) { return b ? b->err.c_str() : ""; }
 
 extern "C" hse_status hse_batch_destroy(hse_batch b) {
   if (!b) return HSE_ERR_INVALID;
   cudaDeviceSynchronize();
+  for (auto& g : b->graph_cache) cudaGraphExecDestroy(g.exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
   for (Bucket* k : b->buckets) {
     hse::batch_fft_destroy(k->fft);
     hse_plan_destroy(k->plan);

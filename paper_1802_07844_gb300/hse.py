@@ -78,7 +78,8 @@ class hse_batch_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("fft_execs", ctypes.c_int64), ("plans", ctypes.c_int64),
                 ("autotuned_groups", ctypes.c_int64), ("grid_bytes", ctypes.c_size_t),
                 ("fft_work_bytes", ctypes.c_size_t), ("particle_bytes", ctypes.c_size_t),
-                ("plan_bytes", ctypes.c_size_t), ("stage_ms", ctypes.c_double * 8)]
+                ("plan_bytes", ctypes.c_size_t), ("stage_ms", ctypes.c_double * 8),
+                ("graphs_captured", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
 
 
 class HseError(RuntimeError):
@@ -94,7 +95,7 @@ _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_get_params", "hse_ev
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
           "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_batch_create",
           "hse_batch_eval", "hse_batch_get_stats", "hse_batch_last_error", "hse_batch_destroy",
-          "hse_batch_set_timing")
+          "hse_batch_set_timing", "hse_batch_set_graphs")
 
 
 def load(path: str = LIB_PATH):
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH):
     L.hse_batch_last_error.restype = ctypes.c_char_p
     L.hse_batch_destroy.argtypes = [vp]
     L.hse_batch_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hse_batch_set_graphs.argtypes = [vp, ctypes.c_int]
     L.hse_cell_list_noalloc.argtypes = [i64, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), dp, dp,
                                         dp, vp]
     L.hse_get_eval_stats.argtypes = [vp, ctypes.POINTER(hse_eval_stats)]
@@ -354,6 +356,10 @@ def hse_batch_set_timing(batch, enable):
     _check(load().hse_batch_set_timing(batch, 1 if enable else 0))
 
 
+def hse_batch_set_graphs(batch, enable):
+    _check(load().hse_batch_set_graphs(batch, 1 if enable else 0))
+
+
 def hse_batch_destroy(batch):
     _check(load().hse_batch_destroy(batch))
 
@@ -383,6 +389,9 @@ class Batch:
 
     def set_timing(self, enable=True):
         hse_batch_set_timing(self.handle, enable)
+
+    def set_graphs(self, enable=True):
+        hse_batch_set_graphs(self.handle, enable)
 
     def close(self):
         if self.handle is not None:

@@ -141,3 +141,36 @@ def test_batch_edge_cases(pkg):
         assert oracle.rel_rms(outs[0].cpu().numpy(), ref) < 1e-8
     finally:
         b.close()
+
+
+def test_batch_graph_replay(pkg):
+    """The second call with the same instance sizes replays captured graphs;
+    results match direct launches, also when the caller's arrays (same sizes,
+    new data at new addresses) change between calls."""
+    probs = _instances(20, 1802078454, [KERNEL_S, KERNEL_S | KERNEL_W], lo=300, hi=2000)
+    items = _to_dev(probs)
+    # same sizes, new data: another draw of the same instances' shapes
+    probs2 = [problem(p.mask, p.src.shape[1], 1.0, "uniform", 74, sub=i) for i, p in enumerate(probs)]
+    items2 = _to_dev(probs2)
+    g = pkg.hse.Batch(1e-10, 0)
+    d = pkg.hse.Batch(1e-10, 0)
+    d.set_graphs(False)
+    try:
+        first = [u.cpu().numpy() for u in g.eval(items)]
+        replay = [u.cpu().numpy() for u in g.eval(items)]
+        replay2 = [u.cpu().numpy() for u in g.eval(items2)]
+        direct = [u.cpu().numpy() for u in d.eval(items)]
+        direct2 = [u.cpu().numpy() for u in d.eval(items2)]
+        sg, sd = g.stats(), d.stats()
+    finally:
+        g.close()
+        d.close()
+    assert sg["graphs_captured"] == sg["chunks"] // 3
+    assert sg["graph_launches"] == sg["chunks"]
+    assert sd["graphs_captured"] == 0 and sd["graph_launches"] == 0
+    for a, b_, c in zip(first, replay, direct):
+        assert oracle.rel_rms(b_, c) < 1e-13
+        assert oracle.rel_rms(a, c) < 1e-13
+    for pr, a, c in zip(probs2, replay2, direct2):
+        assert oracle.rel_rms(a, c) < 1e-13
+    assert _oracle_check(probs2[0], replay2[0], 1e-10) < 1e-10
