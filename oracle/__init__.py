@@ -6,7 +6,8 @@ product path (the CUDA library and its Python binding) never imports it.  It
 shares no code with the CUDA path.
 
 Contents
-  * ``hs_oracle.c``   -- plain FP64 C: direct half-space sums (Sec. 3), the
+  * ``hs_oracle.c``   -- plain FP64 C: direct half-space sums (Sec. 3) and
+    free-space sums (Sec. 2, mask bit ``FREE_SPACE``), the
     real-space / smooth / self split (Sec. 4, Appendix), cell lists and
     brute-force neighbour counts (Sec. 5.1), the spread grids (Alg. 1 step 5).
   * ``se_fourier.py`` -- numpy restatement of the Fourier part (Alg. 1 steps
@@ -26,6 +27,7 @@ import threading
 import numpy as np
 
 KERNEL_S, KERNEL_T, KERNEL_W = 1, 2, 4
+FREE_SPACE = 8  # mask bit: the free-space sums of Sec. 2 (no wall, no images, no corrections)
 PART_DIRECT, PART_REAL, PART_SMOOTH, PART_SELF = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -116,7 +118,8 @@ def half_space_sum(mask, src, strengths, tgt=None, part=PART_DIRECT, xi=0.0, rc=
 
 
 def direct(mask, src, strengths, tgt=None):
-    """Plain FP64 O(N N_t) half-space sum (Sec. 3, eq. v_sum_halfspace)."""
+    """Plain FP64 O(N N_t) half-space sum (Sec. 3, eq. v_sum_halfspace); with
+    the FREE_SPACE bit in ``mask`` the free-space sum of Sec. 2."""
     return half_space_sum(mask, src, strengths, tgt, PART_DIRECT)
 
 
@@ -168,11 +171,15 @@ def neighbor_counts(src, rc, tgt=None):
 
 
 def spread(mask, src, strengths, xi, h, P, Mt):
-    """Spread grids C1/C2/C3 of Alg. 1 step 5, shape (ncomp, Mt, Mt, 2 Mt)."""
+    """Spread grids C1/C2/C3 of Alg. 1 step 5, shape (ncomp, Mt, Mt, 2 Mt)
+    (C1 only with the FREE_SPACE bit)."""
     src = _c64(src)
     strengths = _c64(strengths)
     n = src.shape[1]
-    ncomp = (7 if mask & KERNEL_S else 0) + (13 if mask & KERNEL_T else 0) + (5 if mask & KERNEL_W else 0)
+    if mask & FREE_SPACE:
+        ncomp = (3 if mask & KERNEL_S else 0) + (6 if mask & KERNEL_T else 0) + (3 if mask & KERNEL_W else 0)
+    else:
+        ncomp = (7 if mask & KERNEL_S else 0) + (13 if mask & KERNEL_T else 0) + (5 if mask & KERNEL_W else 0)
     grids = np.zeros((ncomp, Mt, Mt, 2 * Mt))
     lib().oracle_spread(int(mask), n, _d(src), _d(strengths), float(xi), float(h), int(P), int(Mt), _d(grids))
     return grids

@@ -40,6 +40,11 @@
  *   Taylor series in s is used.  Self term (Sec. 4 and Appendix): -4 xi/sqrt(pi) f
  *   for the stokeslet only.
  *
+ * Free space (Sec. 2, mask bit OR_FREE = 8): the same sums without the wall --
+ * only the free-space kernels S8(r) f, T8(r)(g q), W8(r) tau, no images and no
+ * harmonic corrections; the Ewald split, the self term and the cut-off rule are
+ * the same as above with the image terms dropped.
+ *
  * Layouts: positions and strengths are component-major ("SoA"): x[0..n),
  * y[n..2n), z[2n..3n).  Strength blocks follow the kernel bits in the order
  * S (f: 3n), T (g: 3n then q: 3n), W (tau: 3n).
@@ -54,6 +59,7 @@
 #define OR_S 1
 #define OR_T 2
 #define OR_W 4
+#define OR_FREE 8
 
 #define PART_DIRECT 0
 #define PART_REAL 1
@@ -240,7 +246,7 @@ static void load_strengths(int mask, long n, long m, const double* str, double* 
  * out: 3 x n_tgt, component-major, overwritten.                               */
 int oracle_sum(int mask, int part, double xi, double rc, long n_src, const double* src, const double* str,
                long n_tgt, const double* tgt, int tgt_is_src, double* out) {
-  if (n_src < 0 || n_tgt < 0 || mask <= 0 || mask > 7) return 1;
+  if (n_src < 0 || n_tgt < 0 || (mask & 7) == 0 || mask > 15) return 1;
   if (tgt_is_src) { tgt = src; n_tgt = n_src; }
   double rc2 = rc * rc;
   int cut = (part == PART_REAL && rc > 0.0);
@@ -272,8 +278,8 @@ int oracle_sum(int mask, int part, double xi, double rc, long n_src, const doubl
         coefs(part, xi, sqrt(s), s, &G, &K);
         add_kernels(mask, &K, r, f, g, q, tau, 1.0, u);
       }
-      /* image pair and wall corrections, both at rt */
-      int usei = 1;
+      /* image pair and wall corrections, both at rt (none in free space) */
+      int usei = !(mask & OR_FREE);
       if (cut && !(st < rc2)) usei = 0;
       if (usei) {
         coefs(part, xi, sqrt(st), st, &G, &K);
@@ -414,12 +420,16 @@ static void splat(double* grid, int Mt, int P, double h, double xi, double eta, 
  *      C3 = y3 sym(g^I q^I) at y^I                             [6]
  *   W: C1 = tau at y, +tau^I at y^I                            [3]
  *      C2 = v = (-tau2, tau1) at y^I                           [2]
+ * In free space (mask bit OR_FREE) only C1 at the sources y:
+ *   S: f [3]    T: sym(g q) [6]    W: tau [3]
  * grids: ncomp x Mt x Mt x 2Mt (z fastest), zeroed here.  Returns ncomp.     */
 int oracle_spread(int mask, long n, const double* src, const double* str, double xi, double h, int P, int Mt,
                   double* grids) {
   double eta = P * xi * xi * h * h / (0.95 * 0.95 * OR_PI);
   long cs = (long)Mt * Mt * 2 * Mt;
-  int ncomp = ((mask & OR_S) ? 7 : 0) + ((mask & OR_T) ? 13 : 0) + ((mask & OR_W) ? 5 : 0);
+  const int free_space = (mask & OR_FREE) != 0;
+  int ncomp = free_space ? ((mask & OR_S) ? 3 : 0) + ((mask & OR_T) ? 6 : 0) + ((mask & OR_W) ? 3 : 0)
+                         : ((mask & OR_S) ? 7 : 0) + ((mask & OR_T) ? 13 : 0) + ((mask & OR_W) ? 5 : 0);
   memset(grids, 0, sizeof(double) * cs * ncomp);
   double ox = -0.5 * P * h, oz = -(double)Mt * h;
   for (long m = 0; m < n; ++m) {
@@ -432,6 +442,21 @@ int oracle_spread(int mask, long n, const double* src, const double* str, double
     int iz0 = support_start(y[2], oz, h, P, 2 * Mt);
     int izI = 2 * Mt - (iz0 + P - 1);
     double* gp = grids;
+    if (free_space) {
+      if (mask & OR_S) {
+        splat(gp, Mt, P, h, xi, eta, y, ix0, iy0, iz0, f, 3, cs);
+        gp += 3 * cs;
+      }
+      if (mask & OR_T) {
+        double sg[6];
+        int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+        for (int c = 0; c < 6; ++c) sg[c] = 0.5 * (g[ia[c]] * q[ib[c]] + g[ib[c]] * q[ia[c]]);
+        splat(gp, Mt, P, h, xi, eta, y, ix0, iy0, iz0, sg, 6, cs);
+        gp += 6 * cs;
+      }
+      if (mask & OR_W) splat(gp, Mt, P, h, xi, eta, y, ix0, iy0, iz0, tau, 3, cs);
+      continue;
+    }
     if (mask & OR_S) {
       double fI[3] = {f[0], f[1], -f[2]};
       double c1[3] = {f[0], f[1], f[2]};

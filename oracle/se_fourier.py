@@ -18,6 +18,9 @@ Steps, in the paper's order:
   10   trapezoidal quadrature with the same truncated Gaussian at each target:
        u_F = <T1> - x3 <T2>.
 
+Free space (Sec. 2, mask bit FREE_SPACE): C1 is spread at the sources only,
+there is no harmonic potential (phi = 0, T2 = 0), and u_F = <T1>.
+
 Readings of the paper used here:
   * Continuous transform pair K^(k) = int K e^{-ik.x} dx; gradients map to i k.
     Then A^W = -2 i eps k (the printed +2 i eps k has the opposite sign to the
@@ -39,7 +42,7 @@ import math
 
 import numpy as np
 
-from . import KERNEL_S, KERNEL_T, KERNEL_W, spread
+from . import FREE_SPACE, KERNEL_S, KERNEL_T, KERNEL_W, spread
 
 C_WINDOW = 0.95
 
@@ -143,38 +146,48 @@ def fourier_part(mask, src, strengths, xi, L, M, P, tgt=None):
 
     T1 = [np.zeros(pad, np.complex128) for _ in range(3)]
     phi = np.zeros(pad, np.complex128)
+    free = bool(mask & FREE_SPACE)  # Sec. 2: C1 at the sources only, no phi
     c = 0
     if mask & KERNEL_S:
         C1 = [fft_pad(grids[c + i]) for i in range(3)]
-        C2 = fft_pad(grids[c + 3])
-        C3 = [fft_pad(grids[c + 4 + i]) for i in range(3)]
-        c += 7
         kC1 = sum(K[i] * C1[i] for i in range(3))
         for j in range(3):  # A^S = -(k^2 I - k k)(1 + k^2/4xi^2)
             T1[j] += -s_fac * E * TB * (k2 * C1[j] - K[j] * kC1)
-        phi += 2.0 * GF * (-C2 - 1j * sum(K[i] * C3[i] for i in range(3)))
+        if free:
+            c += 3
+        else:
+            C2 = fft_pad(grids[c + 3])
+            C3 = [fft_pad(grids[c + 4 + i]) for i in range(3)]
+            c += 7
+            phi += 2.0 * GF * (-C2 - 1j * sum(K[i] * C3[i] for i in range(3)))
     if mask & KERNEL_T:
         C1 = _sym([fft_pad(grids[c + i]) for i in range(6)])
-        C2 = fft_pad(grids[c + 6])
-        C3 = _sym([fft_pad(grids[c + 7 + i]) for i in range(6)])
-        c += 13
         # A^T_jlm C_lm = -i (1 + k^2/4xi^2) [ (k_m d_jl + k_j d_lm + k_l d_mj) k^2 - 2 k_j k_l k_m ] C_lm
         trC = C1[0][0] + C1[1][1] + C1[2][2]
         Ck = [sum(C1[j][m] * K[m] for m in range(3)) for j in range(3)]
         kCk = sum(K[j] * Ck[j] for j in range(3))
         for j in range(3):
             T1[j] += -1j * s_fac * E * TB * (k2 * (2.0 * Ck[j] + K[j] * trC) - 2.0 * K[j] * kCk)
-        kC3k = sum(K[j] * C3[j][m] * K[m] for j in range(3) for m in range(3))
-        phi += GF * (4j * K[2] * C2 + 4.0 * kC3k)
+        if free:
+            c += 6
+        else:
+            C2 = fft_pad(grids[c + 6])
+            C3 = _sym([fft_pad(grids[c + 7 + i]) for i in range(6)])
+            c += 13
+            kC3k = sum(K[j] * C3[j][m] * K[m] for j in range(3) for m in range(3))
+            phi += GF * (4j * K[2] * C2 + 4.0 * kC3k)
     if mask & KERNEL_W:
         C1 = [fft_pad(grids[c + i]) for i in range(3)]
-        C2 = [fft_pad(grids[c + 3 + i]) for i in range(2)]
-        c += 5
         # A^W_jl = -2 i eps_jlm k_m :  (A^W C)_j = -2 i (C x k)_j
         cross = [C1[1] * K[2] - C1[2] * K[1], C1[2] * K[0] - C1[0] * K[2], C1[0] * K[1] - C1[1] * K[0]]
         for j in range(3):
             T1[j] += -2j * E * TH * cross[j]
-        phi += 4.0 * GF * 1j * (K[0] * C2[0] + K[1] * C2[1])
+        if free:
+            c += 3
+        else:
+            C2 = [fft_pad(grids[c + 3 + i]) for i in range(2)]
+            c += 5
+            phi += 4.0 * GF * 1j * (K[0] * C2[0] + K[1] * C2[1])
     T1[2] = T1[2] + phi
     T2 = [1j * K[j] * phi for j in range(3)]
     fields = []

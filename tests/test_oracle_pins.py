@@ -168,6 +168,125 @@ def test_divergence_free(mask):
 
 
 # --------------------------------------------------------------------------
+# free space (Sec. 2): the sums without the wall
+# --------------------------------------------------------------------------
+FREE = oracle.FREE_SPACE
+
+
+def oseen_dipole(x, y, g, q, step=1e-5):
+    """sum_k q_k d/dy_k [S8(x - y) g] (central FD, Richardson) -- the force
+    dipole of the free-space stokeslet."""
+    def d(hh):
+        out = np.zeros(3)
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = hh
+            out += q[k] * (_s8(x - y - e, g) - _s8(x - y + e, g)) / (2 * hh)
+        return out
+    return (4 * d(step) - d(2 * step)) / 3
+
+
+def test_free_space_stokeslet_is_oseen_tensor():
+    """Sec. 2: the free-space stokeslet sum is the Oseen tensor S8(r) f summed
+    over the other sources."""
+    pr = problem(KERNEL_S, 12, 1.0, "uniform", 40)
+    tg = _rand_targets(6, 0.0, 1.0)
+    u = oracle.direct(KERNEL_S | FREE, pr.src, pr.strengths, tg)
+    ref = np.zeros_like(u)
+    for p in range(tg.shape[1]):
+        for m in range(pr.src.shape[1]):
+            ref[:, p] += _s8(tg[:, p] - pr.src[:, m], pr.strengths[:, m])
+    assert oracle.rel_rms(u, ref) < 1e-14
+
+
+def test_free_space_rotlet_and_stresslet_are_oseen_dipoles():
+    """Free-space rotlet = antisymmetric and stresslet (g perpendicular to q) =
+    symmetric force dipole of the Oseen tensor (finite differences in the
+    source position)."""
+    for trial in range(4):
+        y = np.array([RNG.uniform(0.2, 0.8), RNG.uniform(0.2, 0.8), RNG.uniform(0.05, 0.8)])
+        g, q = RNG.standard_normal(3), RNG.standard_normal(3)
+        q -= (q @ g) / (g @ g) * g
+        tg = _rand_targets(5, 0.0, 1.0)
+        uw = oracle.direct(KERNEL_W | FREE, y[:, None], np.cross(g, q)[:, None], tg)
+        ut = oracle.direct(KERNEL_T | FREE, y[:, None], np.concatenate([g, q])[:, None], tg)
+        dgq = np.stack([oseen_dipole(tg[:, p], y, g, q) for p in range(tg.shape[1])], axis=1)
+        dqg = np.stack([oseen_dipole(tg[:, p], y, q, g) for p in range(tg.shape[1])], axis=1)
+        assert oracle.rel_rms(uw, -(dgq - dqg)) < 1e-7
+        assert oracle.rel_rms(ut, -(dgq + dqg)) < 1e-7
+
+
+@pytest.mark.parametrize("mask,order", [(KERNEL_S, 1), (KERNEL_T, 2), (KERNEL_W, 3)])
+def test_free_space_is_far_wall_limit(mask, order):
+    """Far from the wall the half-space sum (pinned above by no-slip and Blake)
+    tends to the free-space sum: lifting every point by H leaves a difference
+    O(H^-1) for the stokeslet (its image system decays like a stokeslet),
+    O(H^-2) for the stresslet, and O(H^-3) for the rotlet (at O(H^-2) the image
+    rotlet, -v/(2H^2) with v = (-tau2, tau1, 0), cancels the -x3 grad(phi_W)
+    term, +v/(2H^2))."""
+    pr = problem(mask, 40, 1.0, "uniform", 41)
+    tg = _rand_targets(20, 0.0, 1.0)
+    diffs = []
+    for H in (1e2, 1e3):
+        lift = np.array([[0.0], [0.0], [H]])
+        uh = oracle.direct(mask, pr.src + lift, pr.strengths, tg + lift)
+        uf = oracle.direct(mask | FREE, pr.src + lift, pr.strengths, tg + lift)
+        diffs.append(oracle.rel_rms(uh, uf))
+    ratio = diffs[0] / diffs[1]
+    assert 10 ** order / 2 < ratio < 10 ** order * 2
+    assert diffs[1] < 10.0 ** (-2 * order)
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W])
+def test_free_space_divergence_free(mask):
+    pr = problem(mask, 20, 1.0, "uniform", 42)
+    x0 = _rand_targets(6, 0.1, 0.9)
+
+    def div_at(hs):
+        div = np.zeros(x0.shape[1])
+        scale = np.zeros(x0.shape[1])
+        for d in range(3):
+            e = np.zeros((3, 1))
+            e[d] = hs
+            up = oracle.direct(mask | FREE, pr.src, pr.strengths, x0 + e)
+            um = oracle.direct(mask | FREE, pr.src, pr.strengths, x0 - e)
+            div += (up[d] - um[d]) / (2 * hs)
+            scale += np.abs((up - um) / (2 * hs)).max(axis=0)
+        return div, scale
+
+    d1, scale = div_at(2e-4)
+    d2, _ = div_at(4e-4)
+    assert np.all(np.abs((4 * d1 - d2) / 3) < 1e-8 * scale)
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_T | KERNEL_W])
+@pytest.mark.parametrize("xi", [2.5, 9.0])
+def test_free_space_split_identity(mask, xi):
+    """Sec. 4 for the free-space kernels: direct = real (no cut-off) + smooth + self."""
+    pr = problem(mask, 80, 1.0, "uniform", 43)
+    d = oracle.direct(mask | FREE, pr.src, pr.strengths)
+    r, s, sf = oracle.ewald_split(mask | FREE, pr.src, pr.strengths, xi)
+    assert oracle.rel_rms(r + s + sf, d) < 1e-13
+    # the free-space parts differ from the half-space ones (images dropped)
+    rh = oracle.ewald_split(mask, pr.src, pr.strengths, xi)[0]
+    assert oracle.rel_rms(r, rh) > 1e-6
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W])
+def test_free_space_fourier_part_converges_to_smooth_sum(mask):
+    """Alg. 1 with C1 at the sources only (no images, no phi) computes the
+    free-space smooth part: spectral convergence as k_inf/xi and P grow."""
+    pr = problem(mask, 40, 1.0, "uniform", 44)
+    xi = 4.0
+    smooth = oracle.half_space_sum(mask | FREE, pr.src, pr.strengths, None, oracle.PART_SMOOTH, xi)
+    errs = [oracle.rel_rms(se.fourier_part(mask | FREE, pr.src, pr.strengths, xi, 1.0, M, P), smooth)
+            for M, P in [(12, 12), (16, 20)]]
+    assert errs[0] < 2e-6
+    assert errs[1] < 1e-10
+    assert errs[1] < 1e-3 * errs[0]
+
+
+# --------------------------------------------------------------------------
 # Ewald split (Sec. 4, Appendix)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W])
