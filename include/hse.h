@@ -52,8 +52,12 @@ typedef enum {
   HSE_ERR_UNSUPPORTED = 6  /* valid request this build does not support           */
 } hse_status;
 
-/* kernel bit mask; several bits may be combined, the sums are added */
-enum { HSE_STOKESLET = 1, HSE_STRESSLET = 2, HSE_ROTLET = 4 };
+/* kernel bit mask; several bits may be combined, the sums are added.
+ * HSE_FREE_SPACE (with at least one kernel bit) selects the free-space sums of
+ * Sec. 2 instead: the same kernels without the wall -- no images, no harmonic
+ * corrections (u = sum S8(r) f, T8(r)(g q), W8(r) tau); the box, the Ewald
+ * split, the self term and every entry point are otherwise unchanged. */
+enum { HSE_STOKESLET = 1, HSE_STRESSLET = 2, HSE_ROTLET = 4, HSE_FREE_SPACE = 8 };
 /* arithmetic of the path: HSE_FP64 everywhere (for tolerances down to 1e-10),
  * HSE_MIXED: FP32 real space, spreading, FFT and gather (tolerances >= 1e-6) */
 enum { HSE_FP64 = 0, HSE_MIXED = 1 };

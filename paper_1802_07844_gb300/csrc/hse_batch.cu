@@ -543,7 +543,7 @@ extern "C" hse_status hse_batch_eval(hse_batch b, int n_inst, const hse_instance
   std::map<std::pair<int, int>, std::vector<int>> groups;
   for (int i = 0; i < n_inst; ++i) {
     const hse_instance& I = inst[i];
-    if (I.kernel_mask <= 0 || I.kernel_mask > 7 || I.n < 1 || I.n > (int64_t(1) << 28) || !I.src_xyz ||
+    if (!hse::valid_mask(I.kernel_mask) || I.n < 1 || I.n > (int64_t(1) << 28) || !I.src_xyz ||
         !I.strengths || !I.vel)
       return berr(b, HSE_ERR_INVALID, "instance " + std::to_string(i) + ": bad descriptor");
     groups[std::make_pair(I.kernel_mask, ladder_level(I.n, b->box))].push_back(i);

@@ -73,7 +73,11 @@ __global__ void k_prep(PrepArgs<T> a) {
       sgqI[m] = 0.5 * (gI[ia[m]] * qI[ib[m]] + gI[ib[m]] * qI[ia[m]]);
     }
     double gdq = g[0] * q[0] + g[1] * q[1] + g[2] * q[2];
-    if (!a.paper) {
+    if (a.mask & HSE_FREE_SPACE) {  // Sec. 2: C1 only (same in both component sets)
+      if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) c[k++] = (T)f[d];
+      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)sgq[m];
+      if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = (T)tau[d];
+    } else if (!a.paper) {
       if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) c[k++] = (T)f[d];
       if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)sgq[m];
       if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = (T)tau[d];
@@ -198,9 +202,11 @@ static void launch_spread_t(const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
 template <typename T>
 static bool launch_spread(int nc, const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
   switch (nc) {
+    case 3: launch_spread_t<T, 3>(a, grid, s); return true;
     case 5: launch_spread_t<T, 5>(a, grid, s); return true;
     case 6: launch_spread_t<T, 6>(a, grid, s); return true;
     case 7: launch_spread_t<T, 7>(a, grid, s); return true;
+    case 9: launch_spread_t<T, 9>(a, grid, s); return true;
     case 10: launch_spread_t<T, 10>(a, grid, s); return true;
     case 12: launch_spread_t<T, 12>(a, grid, s); return true;
     case 13: launch_spread_t<T, 13>(a, grid, s); return true;
@@ -270,6 +276,7 @@ struct ScaleArgs {
   int n_inst;
   int64_t istride;                // complex elements between instances of one component
   int64_t xstride;                // complex elements between kx planes of one buffer
+  int nout;                       // 6 (T1, T2) or 3 (free space: T1 only, no phi)
 };
 
 template <typename C, typename T>
@@ -337,7 +344,7 @@ __global__ void k_scale(ScaleArgs<T> a) {
       // merged harmonic corrections: phi^ = E H^R (Cs^ + i k.Cv^ + k.Ct^.k)
       C ph = zero;
       if (a.iCs >= 0) ph = ld(a.iCs);
-      {
+      if (a.iCv >= 0) {
         C v[3] = {ld(a.iCv), ld(a.iCv + 1), ld(a.iCv + 2)};
         C kv = cadd(cadd(cscale(k[0], v[0]), cscale(k[1], v[1])), cscale(k[2], v[2]));
         ph = cadd(ph, cmul_i(kv));
@@ -355,10 +362,9 @@ __global__ void k_scale(ScaleArgs<T> a) {
       T1[2] = cadd(T1[2], ph);
       for (int d = 0; d < 3; ++d) T2[d] = cmul_i(cscale(k[d], ph));
     }
-    for (int d = 0; d < 3; ++d) {
-      a.buf[d * a.cstride + e] = T1[d];
-      a.buf[(3 + d) * a.cstride + e] = T2[d];
-    }
+    for (int d = 0; d < 3; ++d) a.buf[d * a.cstride + e] = T1[d];
+    if (a.nout == 6)
+      for (int d = 0; d < 3; ++d) a.buf[(3 + d) * a.cstride + e] = T2[d];
   }
 }
 
@@ -381,7 +387,8 @@ struct GatherArgs {
 
 constexpr int kGatherWarps = 4;
 
-template <typename T>
+// NF = 6 fields (T1, T2: u = <T1> - x3 <T2>) or 3 (free space: u = <T1>)
+template <typename T, int NF>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
   __shared__ T wsm[kGatherWarps][3][kMaxP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -414,27 +421,31 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
       wz[lane] = (T)exp(-a.alpha * dz * dz);
     }
     __syncwarp();
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) acc[c] = 0.0;
     for (int q = lane; q < P * P; q += 32) {
       int jj = q / P, kk = q - jj * P;
-      T s[6] = {0, 0, 0, 0, 0, 0};
+      T s[NF];
+#pragma unroll
+      for (int c = 0; c < NF; ++c) s[c] = 0;
       const T* col = fields + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
       for (int ii = 0; ii < P; ++ii) {
         T wv = wx[ii];
         const T* pnt = col + (int64_t)ii * a.xs;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s[c] += wv * pnt[c * a.bs];
+        for (int c = 0; c < NF; ++c) s[c] += wv * pnt[c * a.bs];
       }
       T wyz = wy[jj] * wz[kk];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += (double)(wyz * s[c]);
+      for (int c = 0; c < NF; ++c) acc[c] += (double)(wyz * s[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
+    for (int c = 0; c < NF; ++c)
       for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
     if (lane == 0) {
       for (int d = 0; d < 3; ++d) {
-        double v = a.h3 * (acc[d] - z * acc[3 + d]);
+        double v = a.h3 * (NF == 6 ? acc[d] - z * acc[(3 + d) % NF] : acc[d]);
         double* o = a.out + d * a.n_tgt + dst;
         *o = a.add ? *o + v : v;
       }
@@ -506,6 +517,7 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   if (!launch_spread<T>(cs.n, a, grid, s)) return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
+  if (free_space(q.kernel_mask)) return HSE_OK;  // no images: C1 is the source-located grid
   MirrorArgs<T> m;
   m.buf = out;
   m.cs = cstride;
@@ -583,9 +595,13 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
   if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
   if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
-  if (q.kernel_mask & HSE_STOKESLET) { sa.iCs = k; k += 1; }
-  sa.iCv = k; k += 3;
-  if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  if ((q.kernel_mask & HSE_STOKESLET) && !free_space(q.kernel_mask)) { sa.iCs = k; k += 1; }
+  sa.iCv = -1;
+  if (!free_space(q.kernel_mask)) {
+    sa.iCv = k; k += 3;
+    if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  }
+  sa.nout = q.n_fft_out;
   sa.n_inst = 1;
   sa.istride = 0;
   sa.xstride = (int64_t)g.Ny * (g.Nz / 2 + 1);
@@ -594,7 +610,7 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
   stage_mark(p, HSE_STAGE_IFFT, s);
-  for (int c = 0; c < 6; ++c) {
+  for (int c = 0; c < q.n_fft_out; ++c) {
     cufftResult r = fft_inverse(p, spec + c * g.buf_doubles);
     ++p->n_fft;
     if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "inverse FFT: %d", (int)r);
@@ -623,7 +639,8 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   ga.h3 = q.h * q.h * q.h;
   ga.out = out;
   ga.add = add ? 1 : 0;
-  k_gather<T><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  if (q.n_fft_out == 6) k_gather<T, 6><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  else k_gather<T, 3><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_gather");
 }
@@ -647,7 +664,7 @@ struct FftExec {
 constexpr int64_t kBatchPlanes = 2048;     // planes per 2-D exec (about 0.3-1 GB of data)
 constexpr int64_t kBatchLines = 1 << 20;   // lines per 1-D exec
 
-static std::vector<FftExec> batch_schedule(const GridDims& g, int nc, int C, bool forward) {
+static std::vector<FftExec> batch_schedule(const GridDims& g, int nc, int n_out, int C, bool forward) {
   const int64_t nzh = g.Nz / 2 + 1, plane = (int64_t)g.Ny * g.pitch, planec = (int64_t)g.Ny * nzh;
   const int64_t nbuf = (int64_t)nc * C, Mt = g.Mt;
   const int64_t gb = std::max<int64_t>(1, std::min<int64_t>(kBatchLines / planec, nbuf));
@@ -661,9 +678,9 @@ static std::vector<FftExec> batch_schedule(const GridDims& g, int nc, int C, boo
     for (int64_t j0 = 0; j0 < nbuf; j0 += gb)
       ex.push_back({2, j0 * planec, std::min(gb, nbuf - j0) * planec, nbuf * planec});
   } else {
-    // x lines of the 6 output components, then 2-D over the planes x < Mt the
-    // gather reads, one x plane at a time (the outputs are contiguous in it)
-    const int64_t nout = 6LL * C;
+    // x lines of the n_out output components, then 2-D over the planes x < Mt
+    // the gather reads, one x plane at a time (the outputs are contiguous in it)
+    const int64_t nout = (int64_t)n_out * C;
     for (int64_t j0 = 0; j0 < nout; j0 += gb)
       ex.push_back({3, j0 * planec, std::min(gb, nout - j0) * planec, nbuf * planec});
     for (int64_t x = 0; x < Mt; ++x) ex.push_back({1, x * nbuf * plane, nout, 0});
@@ -683,8 +700,8 @@ hse_status batch_fft_prepare(hse_plan p, BatchFFT& f, int n_inst, char** work, i
   const bool mixed = p->prm.precision == HSE_MIXED;
   const long long nzh = g.Nz / 2 + 1;
   const long long plane = (long long)g.Ny * g.pitch, planec = (long long)g.Ny * nzh;
-  std::vector<FftExec> ex = batch_schedule(g, p->comps.n, n_inst, true);
-  std::vector<FftExec> ex2 = batch_schedule(g, p->comps.n, n_inst, false);
+  std::vector<FftExec> ex = batch_schedule(g, p->comps.n, p->prm.n_fft_out, n_inst, true);
+  std::vector<FftExec> ex2 = batch_schedule(g, p->comps.n, p->prm.n_fft_out, n_inst, false);
   ex.insert(ex.end(), ex2.begin(), ex2.end());
   size_t need = 0;
   for (const FftExec& e : ex) {
@@ -781,7 +798,7 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nbuf, s));
   HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, plane * n_inst, plane * nbuf, g.pitch, s, n_inst, plane));
   stage_mark(p, HSE_STAGE_FFT, s);
-  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, n_inst, true), spec, s));
+  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, true), spec, s));
   stage_mark(p, HSE_STAGE_SCALE, s);
   ScaleArgs<T> sa;
   sa.buf = reinterpret_cast<typename Cplx<T>::type*>(spec);
@@ -799,14 +816,18 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
   if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
   if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
-  if (q.kernel_mask & HSE_STOKESLET) { sa.iCs = k; k += 1; }
-  sa.iCv = k; k += 3;
-  if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  if ((q.kernel_mask & HSE_STOKESLET) && !free_space(q.kernel_mask)) { sa.iCs = k; k += 1; }
+  sa.iCv = -1;
+  if (!free_space(q.kernel_mask)) {
+    sa.iCv = k; k += 3;
+    if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
+  }
+  sa.nout = q.n_fft_out;
   k_scale<T><<<blocks_for(g.nh * n_inst, 256, 152 * 32), 256, 0, s>>>(sa);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
   stage_mark(p, HSE_STAGE_IFFT, s);
-  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, n_inst, false), spec, s));
+  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, false), spec, s));
   stage_mark(p, HSE_STAGE_GATHER, s);
   GatherArgs<T> ga;
   ga.n_tgt = n_total;
@@ -830,7 +851,9 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   ga.h3 = q.h * q.h * q.h;
   ga.out = out;
   ga.add = 1;
-  k_gather<T><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  if (q.n_fft_out == 6)
+    k_gather<T, 6><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  else k_gather<T, 3><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "batched k_gather");
 }

@@ -34,6 +34,11 @@ struct GridDims {
 // its image half is formed from the source-located accumulation A:
 //   mirror_sign = +1/-1 : C(k) = A(k) + s A(2Mt - k)   (C1 type: source + image)
 //   mirror_sign =  0    : C(k) = A(2Mt - k)            (image-only corrections)
+// kernel mask: at least one of HSE_STOKESLET / HSE_STRESSLET / HSE_ROTLET,
+// optionally HSE_FREE_SPACE
+inline bool valid_mask(int m) { return (m & 7) != 0 && (m & ~15) == 0; }
+inline bool free_space(int m) { return (m & HSE_FREE_SPACE) != 0; }
+
 struct CompSet {
   int n = 0;
   int mirror_sign[kMaxComp];

@@ -46,6 +46,12 @@ static hse_status cufft_check(hse_plan p, cufftResult r, const char* what) {
 CompSet product_components(int mask) {
   CompSet c;
   auto add = [&](int s) { c.mirror_sign[c.n++] = s; };
+  if (free_space(mask)) {  // Sec. 2: C1 at the sources only, no mirror, no corrections
+    if (mask & HSE_STOKESLET) for (int i = 0; i < 3; ++i) add(0);
+    if (mask & HSE_STRESSLET) for (int i = 0; i < 6; ++i) add(0);
+    if (mask & HSE_ROTLET) for (int i = 0; i < 3; ++i) add(0);
+    return c;
+  }
   if (mask & HSE_STOKESLET) { add(-1); add(-1); add(+1); }                   // -f^I  = (-f1,-f2,+f3)
   if (mask & HSE_STRESSLET) { add(-1); add(-1); add(+1); add(-1); add(+1); add(-1); }  // -sym(g^I q^I)
   if (mask & HSE_ROTLET) { add(+1); add(+1); add(-1); }                      // +tau^I
@@ -56,6 +62,7 @@ CompSet product_components(int mask) {
 }
 
 CompSet paper_components(int mask) {
+  if (free_space(mask)) return product_components(mask);
   CompSet c;
   auto add = [&](int s) { c.mirror_sign[c.n++] = s; };
   if (mask & HSE_STOKESLET) { add(-1); add(-1); add(+1); for (int i = 0; i < 4; ++i) add(0); }
@@ -291,7 +298,7 @@ hse_status build_grids(hse_plan p) {
   p->zA0 = q.Mt - q.P / 2 + 1;
   p->comps = product_components(q.kernel_mask);
   q.n_fft_in = p->comps.n;
-  q.n_fft_out = 6;
+  q.n_fft_out = free_space(q.kernel_mask) ? 3 : 6;  // T1 (and T2 with a wall)
   const bool mixed = q.precision == HSE_MIXED;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   size_t tab_elems = (size_t)(q.Mt + 1) * (q.Mt + 1) * (2 * q.Mt + 1);
@@ -378,7 +385,8 @@ static double est_real(int mask, double xi, double rc, double L) {
   double e = std::exp(-xi * xi * rc * rc), m = 0.0;
   if (mask & HSE_STOKESLET) {
     const double a = rc / L;
-    m = std::fmax(m, std::sqrt(rc / (kPi * L)) * std::fmax(1.0, 0.5 * xi * rc) * (1.0 + 6.0 * a * a * a));
+    const double wall = free_space(mask) ? 1.0 : std::fmax(1.0, 0.5 * xi * rc) * (1.0 + 6.0 * a * a * a);
+    m = std::fmax(m, std::sqrt(rc / (kPi * L)) * wall);
   }
   if (mask & HSE_STRESSLET) m = std::fmax(m, std::sqrt(28.0 * std::pow(xi, 4) * std::pow(rc, 3) / (9.0 * kPi * L)));
   if (mask & HSE_ROTLET) m = std::fmax(m, std::sqrt(2.0 / (3.0 * kPi * L * rc)));
@@ -490,7 +498,7 @@ extern "C" hse_status hse_plan_create(int kernel_mask, const double box[3], doub
                                       int precision, hse_plan* out) {
   if (!out) return set_err(nullptr, HSE_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (kernel_mask <= 0 || kernel_mask > 7) return set_err(nullptr, HSE_ERR_INVALID, "kernel_mask %d", kernel_mask);
+  if (!valid_mask(kernel_mask)) return set_err(nullptr, HSE_ERR_INVALID, "kernel_mask %d", kernel_mask);
   if (!box || !(box[0] > 0) || !(box[1] > 0) || !(box[2] > 0) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
       !std::isfinite(box[2]))
     return set_err(nullptr, HSE_ERR_INVALID, "box must be finite and positive");

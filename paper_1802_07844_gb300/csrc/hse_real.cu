@@ -287,7 +287,8 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
   const int64_t n = a.n_src;
   const int nx = a.ncell[0], ny = a.ncell[1], nz = a.ncell[2];
   // images only reach targets with x3 < rc, and come from sources with y3 < rc - x3
-  bool want_img = x[2] < a.rc;
+  // (none in free space)
+  bool want_img = x[2] < a.rc && !(a.mask & HSE_FREE_SPACE);
   int czi_hi = want_img ? cell_coord(a.rc - x[2], a.inv_cell[2], nz) : -1;
   for (int pass = 0; pass < 2; ++pass) {
     int z0 = pass == 0 ? (cz > 0 ? cz - 1 : 0) : 0;
@@ -676,8 +677,10 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
     if (mixed) {
       HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
       k_real_sym<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
-      k_close_images<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
-      ++p->n_launch;
+      if (!free_space(p->prm.kernel_mask)) {
+        k_close_images<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+        ++p->n_launch;
+      }
     } else {
       HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_tgt, s));
       k_real_sym<double><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
@@ -709,8 +712,11 @@ hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of,
   if (mixed) {
     HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_total, s));
     k_real_sym<float><<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
-    k_close_images<<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
-    p->n_launch += 2;
+    ++p->n_launch;
+    if (!free_space(p->prm.kernel_mask)) {
+      k_close_images<<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
+      ++p->n_launch;
+    }
   } else {
     HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_total, s));
     k_real_sym<double><<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);

@@ -244,7 +244,7 @@ extern "C" hse_status hse_server_create(const hse_server_config* cfg, hse_server
 
 extern "C" hse_status hse_server_submit(hse_server srv, const hse_request* req, uint64_t* ticket) {
   if (!srv || !req || !ticket) return HSE_ERR_INVALID;
-  if (req->kernel_mask <= 0 || req->kernel_mask > 7 || !(req->tol > 0.0) || req->n_src < 0 || req->n_tgt < 0 ||
+  if (!hse::valid_mask(req->kernel_mask) || !(req->tol > 0.0) || req->n_src < 0 || req->n_tgt < 0 ||
       !(req->box[0] > 0) || !(req->box[1] > 0) || !(req->box[2] > 0))
     return set_err(nullptr, HSE_ERR_INVALID, "hse_server_submit: bad request");
   Record r;

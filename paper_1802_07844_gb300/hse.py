@@ -13,7 +13,7 @@ import ctypes
 import os
 
 HSE_OK, HSE_ERR_INVALID, HSE_ERR_OOM, HSE_ERR_CUDA, HSE_ERR_CUFFT, HSE_ERR_TIMEOUT, HSE_ERR_UNSUPPORTED = range(7)
-HSE_STOKESLET, HSE_STRESSLET, HSE_ROTLET = 1, 2, 4
+HSE_STOKESLET, HSE_STRESSLET, HSE_ROTLET, HSE_FREE_SPACE = 1, 2, 4, 8
 HSE_FP64, HSE_MIXED = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
