@@ -70,6 +70,11 @@ typedef struct {
   double L;          /* max(L1, L2, L3): side of the cubic Fourier domain         */
   double xi;         /* Ewald parameter                                            */
   double rc;         /* real-space cut-off radius                                  */
+  double rc64;       /* HSE_FP64, targets = sources: pairs closer than rc64 are     *
+                      * evaluated in FP64, pairs in [rc64, rc) in FP32 (their      *
+                      * screened kernels are small enough that FP32 rounding stays  *
+                      * below 1/10 of the real-space truncation error); rc64 >= rc  *
+                      * means FP64 throughout.  0 under HSE_MIXED.                   */
   int P;             /* Gaussian support width in grid points (even)               */
   int M;             /* basic grid size, h = L / M                                 */
   int Mt;            /* extended grid size M + P; grid Mt x Mt x 2 Mt              */
@@ -109,6 +114,11 @@ hse_status hse_plan_set_grid(hse_plan plan, int M);
 
 /* Copy the plan's parameters to *out (host). */
 hse_status hse_plan_get_params(hse_plan plan, hse_params* out);
+
+/* Override the FP64/FP32 split radius rc64 of an HSE_FP64 plan (see
+ * hse_params); rc64 >= rc evaluates every real-space pair in FP64.
+ * HSE_ERR_INVALID for rc64 < 0 or an HSE_MIXED plan. */
+hse_status hse_plan_set_rc64(hse_plan plan, double rc64);
 
 /*
  * hse_eval -- velocities at the targets.

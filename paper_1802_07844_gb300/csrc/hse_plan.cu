@@ -438,6 +438,19 @@ static hse_status choose_params(hse_plan p, double xi, double rc, int P, double 
   }
   q.xi = xi;
   q.rc = rc;
+  // FP64 path: pairs with xi rho above the split use FP32.  The FP32 error of a
+  // pair is ~ kappa eps32 |K_R(rho)| |c|; summed over the shell [rc64, rc) it
+  // behaves like kappa eps32 times the truncation estimate evaluated at rc64
+  // (the same sum, started at rc64), so rc64 is where that estimate reaches
+  // 0.1 / (kappa eps32) times its value at rc (kappa = 16, eps32 = 2^-24).
+  q.rc64 = 0.0;
+  if (q.precision == HSE_FP64) {
+    const double target = est_real(mask, xi, rc, L) * (0.1 / (16.0 * std::ldexp(1.0, -24)));
+    const double lo = 1.5 / xi;  // never FP32 for xi rho < 1.5
+    if (lo >= rc) q.rc64 = rc;
+    else if (est_real(mask, xi, lo, L) <= target) q.rc64 = lo;
+    else q.rc64 = bisect_down([&](double r) { return est_real(mask, xi, r, L); }, lo, rc, target);
+  }
   int M = 0;
   if (tol > 0.0) {
     double R = std::sqrt(6.0) * 1.2 * L;  // L~ <= 1.2 L for the supports used here
@@ -544,6 +557,14 @@ extern "C" hse_status hse_plan_set_grid(hse_plan p, int M) {
   if (M < 4) return set_err(p, HSE_ERR_INVALID, "M = %d < 4", M);
   p->prm.M = M;
   return build_grids(p);
+}
+
+extern "C" hse_status hse_plan_set_rc64(hse_plan p, double rc64) {
+  if (!p) return HSE_ERR_INVALID;
+  if (!(rc64 >= 0.0) || p->prm.precision != HSE_FP64)
+    return set_err(p, HSE_ERR_INVALID, "rc64 needs an HSE_FP64 plan and rc64 >= 0");
+  p->prm.rc64 = rc64;
+  return HSE_OK;
 }
 
 extern "C" hse_status hse_plan_get_params(hse_plan p, hse_params* out) {

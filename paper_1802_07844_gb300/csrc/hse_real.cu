@@ -56,6 +56,8 @@ struct RealArgs {
   double xi, rc2, rc;
   float rc2_lo, rc2_hi;    // FP32 screening thresholds
   float img64_2;           // FP32 path: image pairs closer than this (squared) are evaluated in FP64
+  float far2;              // FP64 symmetric kernel: pairs with FP32 distance^2 >= far2 take the
+                           // FP32 evaluation (0: none)
   double inv_cell[3];
   int ncell[3];
   // batched instances: instance of each sorted particle (null: one instance)
@@ -68,7 +70,7 @@ __device__ __forceinline__ int cell_base(const RealArgs& a, int64_t sorted_idx) 
   return a.inst_of ? a.inst_of[sorted_idx] * a.ncells_inst : 0;
 }
 
-enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2 };
+enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2, Q_FAR = 4 };  // Q_FAR: flag on FREE / IMAGE
 constexpr int kWarpsPerBlock = 4;
 constexpr int kQueue = 64;
 constexpr int kTabN = HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1);
@@ -147,16 +149,18 @@ struct Src {
   T f[3], g[3], q[3], tau[3];
 };
 
-template <typename T>
+// KM: the kernel bits known at compile time (0: read them from a.mask)
+template <typename T, int KM = 0>
 __device__ __forceinline__ void load_src(const RealArgs& a, const T* str, int64_t j, Src<T>& s) {
   const int64_t n = a.n_src;
+  const int mask = KM ? KM : a.mask;
 #pragma unroll
   for (int i = 0; i < 3; ++i) { s.f[i] = 0; s.g[i] = 0; s.q[i] = 0; s.tau[i] = 0; }
-  if (a.mask & HSE_STOKESLET)
+  if (mask & HSE_STOKESLET)
     for (int i = 0; i < 3; ++i) s.f[i] = str[(a.rowS + i) * n + j];
-  if (a.mask & HSE_STRESSLET)
+  if (mask & HSE_STRESSLET)
     for (int i = 0; i < 3; ++i) { s.g[i] = str[(a.rowT + i) * n + j]; s.q[i] = str[(a.rowT + 3 + i) * n + j]; }
-  if (a.mask & HSE_ROTLET)
+  if (mask & HSE_ROTLET)
     for (int i = 0; i < 3; ++i) s.tau[i] = str[(a.rowW + i) * n + j];
 }
 
@@ -326,7 +330,10 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
                   in = dist2_exact(dx, dy, dz) < a.rc2;
                 }
               }
-              if (in) { hit = true; type = pass == 0 ? Q_FREE : Q_IMAGE; }
+              if (in) {
+                hit = true;
+                type = (pass == 0 ? Q_FREE : Q_IMAGE) | (a.far2 > 0.0f && d2f >= a.far2 ? Q_FAR : 0);
+              }
             }
           }
           visit(hit, j, type);
@@ -440,17 +447,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
 // target's own image); the partner's share goes out by FP64 atomicAdd into the
 // sorted-order sums a.out (zeroed before the launch; neighbours sit at nearby
 // addresses), which k_unsort then writes in caller order.
-template <typename T>
+// FP64 pairs arithmetic with a.far2 > 0: pairs in the outer shell (FP32
+// distance^2 >= far2) are queued separately and evaluated in FP32 -- their
+// screened kernels are small, so FP32 rounding stays far below the truncation
+// error -- with the partner's share sent by one float4 atomic into a.out4.
+template <typename T, int KM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
+  __shared__ int queue_far[kWarpsPerBlock][kQueue];
   __shared__ double tab[kTabN];
   load_table(tab);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* qu = queue[wib];
+  int* qf = queue_far[wib];
   const int64_t n = a.n_src;
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-  const bool need_g3 = a.mask & HSE_STRESSLET;
+  const bool need_g3 = KM & HSE_STRESSLET;
   const T xi = (T)a.xi;
+  const float xi32 = (float)a.xi;
   const T* str = strengths_of<T>(a);
   for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < n; w += nwarps) {
     TgtPos x;
@@ -460,13 +474,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
       x.l[d] = a.spos32lo[d * n + w];
     }
     const T x3 = sizeof(T) == 8 ? (T)x.d[2] : (T)(x.h[2] + x.l[2]);
+    const float x3f = x.h[2] + x.l[2];
     Src<T> sp;
-    load_src<T>(a, str, w, sp);
+    load_src<T, KM>(a, str, w, sp);
     T u[3] = {0, 0, 0};
+    float uf[3] = {0.f, 0.f, 0.f};  // FP32 shell pairs
     double uself[3] = {0.0, 0.0, 0.0};
-    if (lane == 0 && (a.mask & HSE_STOKESLET))
+    if (lane == 0 && (KM & HSE_STOKESLET))
       for (int i = 0; i < 3; ++i) uself[i] = -4.0 * a.xi / kSqrtPi * a.sstr[(a.rowS + i) * n + w];
-    int cnt = 0;
+    int cnt = 0, cntf = 0;
     auto partner_add = [&](int64_t j, double v0, double v1, double v2) {
       if (sizeof(T) == 4) atomicAdd(a.out4 + j, make_float4((float)v0, (float)v1, (float)v2, 0.f));
       else {
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
     auto run = [&](int e) {
       int j = e & 0x1fffffff, type = e >> 29;
       Src<T> s;
-      load_src<T>(a, str, j, s);
+      load_src<T, KM>(a, str, j, s);
       T r[3], h;
       pair_vec(a, x, j, type == Q_IMAGE, r, &h);
       T sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
@@ -487,22 +503,52 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
       Radial<T> R = radial(sd, (float)sd, xi, tab, need_g3);
       T v[3] = {0, 0, 0};
       if (type == Q_FREE) {
-        add_free<T>(a.mask, R, r, s, xi, (T)1, u);
-        add_free<T>(a.mask, R, r, sp, xi, (T)-1, v);  // at y_j from the target's strengths, r -> -r
+        add_free<T>(KM, R, r, s, xi, (T)1, u);
+        add_free<T>(KM, R, r, sp, xi, (T)-1, v);  // at y_j from the target's strengths, r -> -r
       } else {
-        add_image<T>(a.mask, R, r, h, x3, s, xi, u);
+        add_image<T>(KM, R, r, h, x3, s, xi, u);
         if (j != w) {
           T rp[3] = {-r[0], -r[1], r[2]};  // y_j - x^I
-          add_image<T>(a.mask, R, rp, x3, h, sp, xi, v);
+          add_image<T>(KM, R, rp, x3, h, sp, xi, v);
         }
       }
       if (type == Q_FREE || j != w) partner_add(j, v[0], v[1], v[2]);
     };
+    // FP32 evaluation of an outer-shell pair (only queued when T is double)
+    auto run_far = [&](int e) {
+      int j = e & 0x1fffffff, type = e >> 29;
+      Src<float> s, spf;
+      load_src<float, KM>(a, a.sstr32, j, s);
+      load_src<float, KM>(a, a.sstr32, w, spf);
+      float r[3], h;
+      pair_vec(a, x, j, type == Q_IMAGE, r, &h);
+      float sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      Radial<float> R = radial(sd, sd, xi32, nullptr, need_g3);
+      float v[3] = {0.f, 0.f, 0.f};
+      if (type == Q_FREE) {
+        add_free<float>(KM, R, r, s, xi32, 1.f, uf);
+        add_free<float>(KM, R, r, spf, xi32, -1.f, v);
+      } else {
+        add_image<float>(KM, R, r, h, x3f, s, xi32, uf);
+        if (j != w) {
+          float rp[3] = {-r[0], -r[1], r[2]};
+          add_image<float>(KM, R, rp, x3f, h, spf, xi32, v);
+        }
+      }
+      if (type == Q_FREE || j != w) atomicAdd(a.out4 + j, make_float4(v[0], v[1], v[2], 0.f));
+    };
     float xf[3] = {x.h[0], x.h[1], x.h[2]};
     for_candidates(a, x.d, xf, w, lane, (int)w + 1, (int)w, cell_base(a, w), [&](bool hit, int j, int type) {
-      unsigned m = __ballot_sync(0xffffffffu, hit && type != Q_SELF);
-      if (hit && type != Q_SELF) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | (type << 29);
+      const bool use = hit && type != Q_SELF;
+      const bool far = use && (type & Q_FAR);
+      const int t = type & ~Q_FAR;
+      unsigned m = __ballot_sync(0xffffffffu, use && !far);
+      unsigned mf = __ballot_sync(0xffffffffu, far);
+      const unsigned below = (1u << lane) - 1;
+      if (use && !far) qu[cnt + __popc(m & below)] = j | (t << 29);
+      if (far) qf[cntf + __popc(mf & below)] = j | (t << 29);
       cnt += __popc(m);
+      cntf += __popc(mf);
       __syncwarp();
       if (cnt >= 32) {
         run(qu[lane]);
@@ -511,12 +557,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
         cnt -= 32;
         __syncwarp();
       }
+      if constexpr (sizeof(T) == 8) {  // the FP32 path never queues shell pairs
+        if (cntf >= 32) {
+          run_far(qf[lane]);
+          __syncwarp();
+          if (lane < cntf - 32) qf[lane] = qf[32 + lane];
+          cntf -= 32;
+          __syncwarp();
+        }
+      }
     });
     if (lane < cnt) run(qu[lane]);
+    if constexpr (sizeof(T) == 8)
+      if (lane < cntf) run_far(qf[lane]);
     __syncwarp();
     double ud[3];
     for (int i = 0; i < 3; ++i) {
-      ud[i] = (double)u[i] + uself[i];
+      ud[i] = (double)u[i] + (double)uf[i] + uself[i];
       for (int off = 16; off > 0; off >>= 1) ud[i] += __shfl_xor_sync(0xffffffffu, ud[i], off);
     }
     if (lane == 0) {
@@ -652,10 +709,33 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   a.rc2_lo = (float)std::fmax(0.0, a.rc2 - m) * (1.0f - 1e-6f);
   a.rc2_hi = (float)(a.rc2 + m) * (1.0f + 1e-6f);
   a.img64_2 = (float)(a.rc2 / 256.0);
+  a.far2 = 0.0f;
   for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = p->prm.ncell[d]; }
   a.inst_of = nullptr;
   a.ncells_inst = p->prm.ncell[0] * p->prm.ncell[1] * p->prm.ncell[2];
   return a;
+}
+
+// symmetric kernel specialised on the kernel bits (1..7)
+template <typename T>
+static void launch_real_sym(int mask, int blocks, const RealArgs& a, cudaStream_t s) {
+  switch (mask & 7) {
+    case 1: k_real_sym<T, 1><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 2: k_real_sym<T, 2><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 3: k_real_sym<T, 3><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 4: k_real_sym<T, 4><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 5: k_real_sym<T, 5><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 6: k_real_sym<T, 6><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    default: k_real_sym<T, 7><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+  }
+}
+
+// FP64 plans: enable the FP32 outer shell [rc64, rc) of the symmetric kernel
+static bool shell32(hse_plan p, RealArgs& a) {
+  const double r64 = p->prm.rc64;
+  if (p->prm.precision != HSE_FP64 || !(r64 > 0.0) || r64 >= p->prm.rc) return false;
+  a.far2 = (float)(r64 * r64);
+  return true;
 }
 
 static int warp_blocks(int64_t n_tgt) {
@@ -676,19 +756,20 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
     a.out4 = p->ws.usort4;
     if (mixed) {
       HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
-      k_real_sym<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+      launch_real_sym<float>(a.mask, warp_blocks(n_tgt), a, s);
       if (!free_space(p->prm.kernel_mask)) {
         k_close_images<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
         ++p->n_launch;
       }
     } else {
       HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_tgt, s));
-      k_real_sym<double><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+      if (shell32(p, a)) HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
+      launch_real_sym<double>(a.mask, warp_blocks(n_tgt), a, s);
     }
     HSE_CUDA(p, cudaGetLastError());
     int64_t b = (n_tgt + 255) / 256;
-    k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(n_tgt, p->ws.val_a, p->ws.usort,
-                                                                     mixed ? p->ws.usort4 : nullptr, out);
+    k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(
+        n_tgt, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, out);
     ++p->n_launch;
   } else {
     if (mixed) k_real<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
@@ -711,7 +792,7 @@ hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of,
   a.out4 = p->ws.usort4;
   if (mixed) {
     HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_total, s));
-    k_real_sym<float><<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
+    launch_real_sym<float>(a.mask, warp_blocks(n_total), a, s);
     ++p->n_launch;
     if (!free_space(p->prm.kernel_mask)) {
       k_close_images<<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
@@ -719,13 +800,14 @@ hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of,
     }
   } else {
     HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_total, s));
-    k_real_sym<double><<<warp_blocks(n_total), kWarpsPerBlock * 32, 0, s>>>(a);
+    if (shell32(p, a)) HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_total, s));
+    launch_real_sym<double>(a.mask, warp_blocks(n_total), a, s);
     ++p->n_launch;
   }
   HSE_CUDA(p, cudaGetLastError());
   int64_t b = (n_total + 255) / 256;
-  k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(n_total, p->ws.val_a, p->ws.usort,
-                                                                   mixed ? p->ws.usort4 : nullptr, out);
+  k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(
+      n_total, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, out);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "real_space_batch");
 }

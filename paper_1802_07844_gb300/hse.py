@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhse.so")
 class hse_params(ctypes.Structure):
     _fields_ = [
         ("kernel_mask", ctypes.c_int), ("precision", ctypes.c_int), ("box", ctypes.c_double * 3),
-        ("L", ctypes.c_double), ("xi", ctypes.c_double), ("rc", ctypes.c_double), ("P", ctypes.c_int),
+        ("L", ctypes.c_double), ("xi", ctypes.c_double), ("rc", ctypes.c_double), ("rc64", ctypes.c_double),
+        ("P", ctypes.c_int),
         ("M", ctypes.c_int), ("Mt", ctypes.c_int), ("h", ctypes.c_double), ("eta", ctypes.c_double),
         ("ncell", ctypes.c_int * 3), ("n_fft_in", ctypes.c_int), ("n_fft_out", ctypes.c_int),
         ("grid_bytes", ctypes.c_size_t),
@@ -89,7 +90,7 @@ class HseError(RuntimeError):
 
 
 _lib = None
-_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
+_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
           "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH):
     L.hse_plan_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
     L.hse_plan_set_grid.argtypes = [vp, ctypes.c_int]
+    L.hse_plan_set_rc64.argtypes = [vp, ctypes.c_double]
     L.hse_plan_get_params.argtypes = [vp, ctypes.POINTER(hse_params)]
     L.hse_eval.argtypes = [vp, i64, dp, dp, i64, dp, dp, vp]
     L.hse_eval_parts.argtypes = [vp, i64, dp, dp, i64, dp, dp, dp, vp]
@@ -167,6 +169,12 @@ def hse_plan_create(kernel_mask, box, xi, rc, P, tol, precision=HSE_FP64):
     _check(L.hse_plan_create(int(kernel_mask), b, float(xi), float(rc), int(P), float(tol), int(precision),
                              ctypes.byref(out)))
     return out
+
+
+def hse_plan_set_rc64(plan, rc64):
+    """FP64 plans: pairs closer than rc64 in FP64, the shell [rc64, rc) in FP32
+    (rc64 >= rc: FP64 throughout)."""
+    _check(load().hse_plan_set_rc64(plan, float(rc64)), plan)
 
 
 def hse_plan_set_grid(plan, M):
@@ -421,6 +429,10 @@ class Plan:
         self.handle = hse_plan_create(kernel_mask, box, xi, rc, P, tol, precision)
         if M is not None:
             hse_plan_set_grid(self.handle, M)
+        self.params = hse_plan_get_params(self.handle)
+
+    def set_rc64(self, rc64):
+        hse_plan_set_rc64(self.handle, rc64)
         self.params = hse_plan_get_params(self.handle)
 
     def set_grid(self, M):

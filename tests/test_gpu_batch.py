@@ -75,7 +75,10 @@ def test_batch_equals_alone_and_oracle(pkg, prec, tol):
         u = u.cpu().numpy()
         assert np.isfinite(u).all()
         alone = _alone(pkg, mask, src, st, tol, prec)
-        assert oracle.rel_rms(u, alone) < (1e-12 if prec == 0 else 2e-6), i
+        # same plan parameters; only summation order differs (FP64 atomics, and
+        # float4 atomics for the FP32 outer shell of the FP64 path): equal to
+        # well within the tolerance
+        assert oracle.rel_rms(u, alone) < (tol / 10 if prec == 0 else 2e-6), i
         assert _oracle_check(pr, u, tol, seed=i) < tol, i
 
 
@@ -91,7 +94,7 @@ def test_batch_chunking_and_reuse(pkg):
         for _ in range(2):
             got = [u.cpu().numpy() for u in small.eval(items)]
             for a, r in zip(got, ref):
-                assert oracle.rel_rms(a, r) < 1e-12
+                assert oracle.rel_rms(a, r) < 1e-9  # tol / 10
         s_big, s_small = big.stats(), small.stats()
     finally:
         big.close()
@@ -169,8 +172,8 @@ def test_batch_graph_replay(pkg):
     assert sg["graph_launches"] == sg["chunks"]
     assert sd["graphs_captured"] == 0 and sd["graph_launches"] == 0
     for a, b_, c in zip(first, replay, direct):
-        assert oracle.rel_rms(b_, c) < 1e-13
-        assert oracle.rel_rms(a, c) < 1e-13
+        assert oracle.rel_rms(b_, c) < 1e-11  # tol / 10
+        assert oracle.rel_rms(a, c) < 1e-11
     for pr, a, c in zip(probs2, replay2, direct2):
-        assert oracle.rel_rms(a, c) < 1e-13
+        assert oracle.rel_rms(a, c) < 1e-11
     assert _oracle_check(probs2[0], replay2[0], 1e-10) < 1e-10

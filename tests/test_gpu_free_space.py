@@ -54,6 +54,8 @@ def test_free_real_part(pkg, mask, prec):
     pr = problem(mask, 2000, 1.0, "near_wall", 51)
     xi, rc = 14.0, 0.3
     plan = pkg.Plan(mask | FREE, (1.0, 1.0, 1.0), xi=xi, rc=rc, P=12, tol=0.0, M=40, precision=prec)
+    if prec == 0:
+        plan.set_rc64(rc)  # every pair in FP64: rounding-level parity
     ur, _ = plan.eval_parts(dev(pr.src), dev(pr.strengths))
     ref = (oracle.half_space_sum(mask | FREE, pr.src, pr.strengths, None, oracle.PART_REAL, xi, rc)
            + oracle.half_space_sum(mask | FREE, pr.src, pr.strengths, None, oracle.PART_SELF, xi))

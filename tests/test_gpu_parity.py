@@ -3,7 +3,9 @@ the CPU oracle on the same seeded inputs.
 
 Bars: integer stages (cell ids, permutation, cell starts, neighbour counts)
 bit-exact; spread grids and the real-space part to FP64 rounding (1e-12
-relative); the Fourier part to the numpy restatement of Alg. 1 at rounding
+relative; the real part with every pair in FP64, and with the default FP32
+outer shell within a fraction of the cut-off's own truncation error); the
+Fourier part to the numpy restatement of Alg. 1 at rounding
 level and to the smooth split within its truncation; full evaluations within
 the requested relative RMS tolerance (Sec. 6 definition).
 """
@@ -99,10 +101,33 @@ def test_real_part_matches_oracle(pkg, mask, dist):
     pr = problem(mask, 2000, 1.0, dist, 33)
     xi, rc = 14.0, 0.3
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=rc, P=12, tol=0.0, M=40)
+    plan.set_rc64(rc)  # every pair in FP64: rounding-level parity
     ur, _ = plan.eval_parts(dev(pr.src), dev(pr.strengths))
     ref = (oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_REAL, xi, rc)
            + oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_SELF, xi))
     assert oracle.rel_rms(host(ur), ref) < 1e-13
+    plan.close()
+
+
+@pytest.mark.parametrize("mask", MASKS)
+@pytest.mark.parametrize("dist", ["uniform", "near_wall"])
+def test_real_part_fp32_shell(pkg, mask, dist):
+    """FP64 plans evaluate the outer shell [rc64, rc) of each neighbourhood in
+    FP32.  The error this adds stays well below the truncation error that the
+    cut-off rc itself makes (oracle: real part at rc vs without cut-off)."""
+    pr = problem(mask, 2000, 1.0, dist, 33)
+    xi, rc = 14.0, 0.3
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=rc, P=12, tol=0.0, M=40)
+    rc64 = plan.params["rc64"]
+    assert 1.5 / xi <= rc64 < rc
+    ur, _ = plan.eval_parts(dev(pr.src), dev(pr.strengths))
+    self_ = oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_SELF, xi)
+    ref = oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_REAL, xi, rc) + self_
+    full = oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_REAL, xi, 0.0) + self_
+    trunc = oracle.rel_rms(ref, full)
+    err = oracle.rel_rms(host(ur), ref)
+    assert err < 0.3 * trunc
+    assert err > 1e-15  # the shell really ran in FP32
     plan.close()
 
 

@@ -62,7 +62,8 @@ def _mix_equals_alone(pkg, srv):
         alone = plan.eval(src, st).cpu().numpy()
         plan.close()
         # same plan parameters: only the atomic summation order can differ
-        assert oracle.rel_rms(mixed, alone) < (1e-13 if prec == pkg.HSE_FP64 else 1e-6)
+        # (FP64 atomics; float4 atomics for the FP32 outer shell of FP64 plans)
+        assert oracle.rel_rms(mixed, alone) < (tol / 10 if prec == pkg.HSE_FP64 else 1e-6)
         # error over all targets (Sec. 6): sampled norms of the heavy-tailed
         # reference fluctuate more than the error
         ref = oracle.direct(pr.mask, pr.src, pr.strengths)
