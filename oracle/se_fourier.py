@@ -226,3 +226,148 @@ def gather(fields, tgt, xi, h, P, Mt, eta):
         for d in range(3):
             out[d, p] = np.sum(w * fields[d][sl]) - x[2] * np.sum(w * fields[3 + d][sl])
     return out
+
+
+# ---------------------------------------------------------------------------
+# Variant with the wall corrections spread and gathered through window
+# derivatives.  In the continuous method i k C^ is the transform of the
+# divergence of the smeared field and k k C^ that of minus its second
+# derivatives, so the harmonic potential can be spread as ONE scalar grid
+#   D(x) = sum_images [ cs W + cv . grad W - ct : grad grad W ](x - y^I)
+# with phi^ = G^ D^ (G^ = E H^R), and the gather of T2 = grad phi can use
+# the window's gradient on the phi grid instead:  <grad phi>(x) =
+# h^3 sum_j grad_x W(x - x_j) phi_j.  Both are the same integrals as Alg. 1's
+# C2/C3 and T2 terms, discretised differently; they agree to the truncation
+# error of the window (tests pin both against the smooth sum).
+#   stokeslet: cs = -2 f3, cv = -2 y3 f^I           (phi_S = 2 G (-C2 - i k.C3))
+#   stresslet: cv = (0, 0, 4 g.q), ct = 4 y3 sym(g^I q^I)
+#                                                   (phi_T = G (4 i k3 C2 + 4 k C3 k))
+#   rotlet:    cv = 4 (-tau2, tau1, 0)              (phi_W = 4 G i k.C2)
+# ---------------------------------------------------------------------------
+def _window(c, o, h, P, n, alpha):
+    i0 = _support(c, o, h, P, n)
+    d = o + (i0 + np.arange(P)) * h - c
+    w = np.exp(-alpha * d * d)
+    return i0, w, -2.0 * alpha * d * w, (4.0 * alpha * alpha * d * d - 2.0 * alpha) * w
+
+
+def _correction_grid(mask, src, strengths, xi, h, P, Mt, eta):
+    alpha = 2.0 * xi ** 2 / eta
+    pre = (2.0 * xi ** 2 / (np.pi * eta)) ** 1.5
+    ox, oz = -0.5 * P * h, -Mt * h
+    D = np.zeros((Mt, Mt, 2 * Mt))
+    n = src.shape[1]
+    ia, ib = [0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]
+    for m in range(n):
+        y = src[:, m]
+        yI = np.array([y[0], y[1], -y[2]])
+        row = 0
+        cs, cv, ct = 0.0, np.zeros(3), np.zeros(6)
+        if mask & KERNEL_S:
+            f = strengths[row:row + 3, m]
+            row += 3
+            cs += -2.0 * f[2]
+            cv += -2.0 * y[2] * np.array([f[0], f[1], -f[2]])
+        if mask & KERNEL_T:
+            g, q = strengths[row:row + 3, m], strengths[row + 3:row + 6, m]
+            row += 6
+            gI, qI = g * [1, 1, -1], q * [1, 1, -1]
+            cv[2] += 4.0 * (gI @ qI)
+            ct += 4.0 * y[2] * np.array([0.5 * (gI[ia[c]] * qI[ib[c]] + gI[ib[c]] * qI[ia[c]]) for c in range(6)])
+        if mask & KERNEL_W:
+            tau = strengths[row:row + 3, m]
+            cv += 4.0 * np.array([-tau[1], tau[0], 0.0])
+        ix, wx, dx, ddx = _window(yI[0], ox, h, P, Mt, alpha)
+        iy, wy, dy, ddy = _window(yI[1], ox, h, P, Mt, alpha)
+        iz, wz, dz, ddz = _window(yI[2], oz, h, P, 2 * Mt, alpha)
+        fac = [(wx, dx, ddx), (wy, dy, ddy), (wz, dz, ddz)]
+
+        def term(ox_, oy_, oz_):
+            return np.einsum('i,j,k->ijk', fac[0][ox_], fac[1][oy_], fac[2][oz_])
+        blk = cs * term(0, 0, 0) + cv[0] * term(1, 0, 0) + cv[1] * term(0, 1, 0) + cv[2] * term(0, 0, 1)
+        for c in range(6):
+            o = [0, 0, 0]
+            o[ia[c]] += 1
+            o[ib[c]] += 1
+            blk -= (1.0 if ia[c] == ib[c] else 2.0) * ct[c] * term(*o)
+        D[ix:ix + P, iy:iy + P, iz:iz + P] += pre * blk
+    return D
+
+
+def fourier_part_derivative(mask, src, strengths, xi, L, M, P, tgt=None):
+    """u_F at the targets by the derivative variant (see above): C1 as in Alg.
+    1, the harmonic potential from one spread grid D, T2 never formed."""
+    src = np.ascontiguousarray(src, np.float64)
+    h, Mt, eta = geometry(L, M, P, xi)
+    if not (0.0 < eta < 1.0):
+        raise ValueError("eta must lie in (0, 1)")
+    free = bool(mask & FREE_SPACE)
+    grids = spread(mask, src, strengths, xi, h, P, Mt)
+    pad = (2 * Mt, 2 * Mt, 4 * Mt)
+
+    def fft_pad(g):
+        buf = np.zeros(pad)
+        buf[:Mt, :Mt, :2 * Mt] = g
+        return np.fft.fftn(buf)
+
+    ks = [2.0 * np.pi * np.fft.fftfreq(n, d=h) for n in pad]
+    K = np.meshgrid(*ks, indexing="ij")
+    k2 = K[0] ** 2 + K[1] ** 2 + K[2] ** 2
+    nyq = np.zeros(pad, bool)
+    for d, n in enumerate(pad):
+        sl = [slice(None)] * 3
+        sl[d] = n // 2
+        nyq[tuple(sl)] = True
+    E = np.exp(-(1.0 - eta) * k2 / (4.0 * xi ** 2))
+    s_fac = 1.0 + k2 / (4.0 * xi ** 2)
+    TH = precompute_table("H", Mt, h)
+    TB = precompute_table("B", Mt, h) if mask & (KERNEL_S | KERNEL_T) else None
+    T1 = [np.zeros(pad, np.complex128) for _ in range(3)]
+    c = 0
+    if mask & KERNEL_S:
+        C1 = [fft_pad(grids[c + i]) for i in range(3)]
+        c += 3 if free else 7
+        kC1 = sum(K[i] * C1[i] for i in range(3))
+        for j in range(3):
+            T1[j] += -s_fac * E * TB * (k2 * C1[j] - K[j] * kC1)
+    if mask & KERNEL_T:
+        C1 = _sym([fft_pad(grids[c + i]) for i in range(6)])
+        c += 6 if free else 13
+        trC = C1[0][0] + C1[1][1] + C1[2][2]
+        Ck = [sum(C1[j][m] * K[m] for m in range(3)) for j in range(3)]
+        kCk = sum(K[j] * Ck[j] for j in range(3))
+        for j in range(3):
+            T1[j] += -1j * s_fac * E * TB * (k2 * (2.0 * Ck[j] + K[j] * trC) - 2.0 * K[j] * kCk)
+    if mask & KERNEL_W:
+        C1 = [fft_pad(grids[c + i]) for i in range(3)]
+        c += 3 if free else 5
+        cross = [C1[1] * K[2] - C1[2] * K[1], C1[2] * K[0] - C1[0] * K[2], C1[0] * K[1] - C1[1] * K[0]]
+        for j in range(3):
+            T1[j] += -2j * E * TH * cross[j]
+    phi = np.zeros(pad, np.complex128)
+    if not free:
+        phi = E * TH * fft_pad(_correction_grid(mask, src, strengths, xi, h, P, Mt, eta))
+        T1[2] = T1[2] + phi
+    fields = [np.real(np.fft.ifftn(np.where(nyq, 0.0, F)))[:Mt, :Mt, :2 * Mt] for F in T1 + [phi]]
+    tg = src if tgt is None else np.ascontiguousarray(tgt, np.float64)
+    alpha = 2.0 * xi ** 2 / eta
+    pre = (2.0 * xi ** 2 / (np.pi * eta)) ** 1.5 * h ** 3
+    ox, oz = -0.5 * P * h, -Mt * h
+    out = np.zeros((3, tg.shape[1]))
+    for p in range(tg.shape[1]):
+        x = tg[:, p]
+        ix, wx, dx, _ = _window(x[0], ox, h, P, Mt, alpha)
+        iy, wy, dy, _ = _window(x[1], ox, h, P, Mt, alpha)
+        iz, wz, dz, _ = _window(x[2], oz, h, P, 2 * Mt, alpha)
+        sl = (slice(ix, ix + P), slice(iy, iy + P), slice(iz, iz + P))
+        W = pre * np.einsum('i,j,k->ijk', wx, wy, wz)
+        for d in range(3):
+            out[d, p] = np.sum(W * fields[d][sl])
+        if not free:
+            ph = fields[3][sl]
+            # grad_x W(x - x_j) = -(dW/d(x_j - x)): minus the window derivative
+            grad = [-pre * np.sum(np.einsum('i,j,k->ijk', *f) * ph)
+                    for f in ((dx, wy, wz), (wx, dy, wz), (wx, wy, dz))]
+            for d in range(3):
+                out[d, p] -= x[2] * grad[d]
+    return out

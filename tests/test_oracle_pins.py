@@ -513,3 +513,35 @@ def test_neighbor_counts_vs_kdtree():
     imgs = pts * [1, 1, -1]
     cnt_i = np.array([len(x) for x in cKDTree(imgs).query_ball_point(pts, rc)])
     assert np.array_equal(b, cnt_i)
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W])
+def test_fourier_derivative_variant_converges_to_smooth_sum(mask):
+    """The derivative variant of Alg. 1 (harmonic potential spread as one scalar
+    grid through window derivatives, grad(phi) gathered with the window's
+    gradient) computes the same smooth part: spectral convergence to the smooth
+    sum, and agreement with the paper's C2/C3/T2 route to well below the
+    truncation error of either."""
+    pr = problem(mask, 40, 1.0, "uniform", 3)
+    xi = 4.0
+    smooth = oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_SMOOTH, xi)
+    errs, diffs = [], []
+    for M, P in [(12, 12), (16, 20)]:
+        a = se.fourier_part(mask, pr.src, pr.strengths, xi, 1.0, M, P)
+        b = se.fourier_part_derivative(mask, pr.src, pr.strengths, xi, 1.0, M, P)
+        errs.append(oracle.rel_rms(b, smooth))
+        diffs.append(oracle.rel_rms(b, a))
+    # at the coarse grid the two discretisations differ by about their error
+    assert errs[0] < 5e-6
+    assert diffs[0] < 3 * errs[0]
+    assert errs[1] < 1e-10
+    assert diffs[1] < 1e-10
+
+
+def test_fourier_derivative_variant_free_space_is_alg1():
+    """Without a wall there is no potential: the variant is Alg. 1 itself."""
+    pr = problem(KERNEL_S | KERNEL_W, 30, 1.0, "uniform", 45)
+    m = KERNEL_S | KERNEL_W | FREE
+    a = se.fourier_part(m, pr.src, pr.strengths, 4.0, 1.0, 12, 12)
+    b = se.fourier_part_derivative(m, pr.src, pr.strengths, 4.0, 1.0, 12, 12)
+    assert oracle.rel_rms(b, a) < 1e-14
