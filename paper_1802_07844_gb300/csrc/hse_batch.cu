@@ -233,7 +233,7 @@ Chunk next_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const int* id
   const hse_params& q = p->prm;
   const size_t esz = b->precision == HSE_MIXED ? 4 : 8;
   const double per_inst = (double)p->g.buf_doubles * esz * p->comps.n;
-  const double per_part = 320.0 + 8.0 * (3 * q.P + std::max(p->comps.n, 25)) + 8.0 * p->n_rows;
+  const double per_part = 320.0 + 8.0 * hse::prep_stride_max(q.kernel_mask, q.P) + 8.0 * p->n_rows;
   const int64_t ncells = (int64_t)q.ncell[0] * q.ncell[1] * q.ncell[2];
   int64_t cap = 4096;
   // the x lines of the slab-major grids have a stride of nc * C planes; past a
@@ -571,7 +571,7 @@ extern "C" hse_status hse_batch_get_stats(hse_batch b, hse_batch_stats* out) {
   out->fft_work_bytes = (size_t)b->fft_work_cap;
   const hse::Workspace& w = b->ws;
   out->particle_bytes = 8 * (size_t)(b->pos_cap + b->str_cap + b->res_cap) + 4 * (size_t)b->inst_cap +
-                        (size_t)w.cap * (16 + 24 + 12 + 12 + 48 + 24 + 16 + 96 + 16 + 8 * (3 * (size_t)w.P + w.ncomp)) +
+                        (size_t)w.cap * (16 + 24 + 12 + 12 + 48 + 24 + 16 + 96 + 16 + 8 * (size_t)w.prep_stride) +
                         4 * (size_t)(w.cell_cap + w.hist_cap);
   out->plan_bytes = 0;
   for (const Bucket* k : b->buckets) out->plan_bytes += k->plan->prm.grid_bytes;

@@ -30,14 +30,13 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
     HSE_CUDA(p, cudaMalloc(&w.cell_start, sizeof(int32_t) * (ncells + 1)));
     w.cell_cap = ncells + 1;
   }
-  // grow-only: the spread's per-particle record is (3P + ncomp) wide, so a
-  // workspace sized for larger P, ncomp or n serves smaller ones too
-  int ncomp = p->comps.n > 25 ? p->comps.n : 25;
-  if (n <= w.cap && p->prm.P <= w.P && ncomp <= w.ncomp) return HSE_OK;
+  // grow-only: a workspace sized for a wider spread record or more particles
+  // serves narrower / fewer ones too
+  int stride = prep_stride_max(p->prm.kernel_mask, p->prm.P);
+  if (n <= w.cap && stride <= w.prep_stride) return HSE_OK;
   int64_t cap = n < 1024 ? 1024 : n;
   if (cap < w.cap) cap = w.cap;
-  const int wP = p->prm.P > w.P ? p->prm.P : w.P;
-  if (ncomp < w.ncomp) ncomp = w.ncomp;
+  if (stride < w.prep_stride) stride = w.prep_stride;
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
   cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr); cudaFree(w.prep); cudaFree(w.supp);
   cudaFree(w.spos32); cudaFree(w.spos32lo); cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
@@ -60,12 +59,11 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   HSE_CUDA(p, cudaMalloc(&w.usort, sizeof(double) * 3 * cap));
   HSE_CUDA(p, cudaMalloc(&w.usort4, sizeof(float4) * cap));
   HSE_CUDA(p, cudaMalloc(&w.sstr, sizeof(double) * 12 * cap));
-  HSE_CUDA(p, cudaMalloc(&w.prep, sizeof(double) * (3 * (size_t)wP + ncomp) * cap));
+  HSE_CUDA(p, cudaMalloc(&w.prep, sizeof(double) * (size_t)stride * cap));
   HSE_CUDA(p, cudaMalloc(&w.supp, sizeof(int32_t) * 4 * cap));
   w.hist_cap = 256 * ntiles;
   w.cap = cap;
-  w.P = wP;
-  w.ncomp = ncomp;
+  w.prep_stride = stride;
   return HSE_OK;
 }
 

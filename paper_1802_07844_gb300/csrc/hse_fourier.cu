@@ -31,7 +31,9 @@ struct PrepArgs {
   const double* spos;
   const double* sstr;
   int rowS, rowT, rowW, mask;
-  int paper;  // component set: 0 product (merged corrections), 1 paper (C1/C2/C3 per kernel)
+  int paper;  // component set: 0 product (C1 + one correction grid D), 1 paper (C1/C2/C3 per kernel)
+  int nfac;   // window factor sets per particle: 1 (W), 2 (W, W'), 3 (W, W', W'')
+  int nc1;    // product set: number of C1 components
   int P, Mt;
   double h, ox, oz, alpha, pre;
   int stride;
@@ -49,15 +51,23 @@ __global__ void k_prep(PrepArgs<T> a) {
     int iz0 = support_start(z, a.oz, a.h, a.P, 2 * a.Mt);
     a.supp[i] = make_int4(ix0, iy0, iz0, 0);
     T* o = a.prep + i * (int64_t)a.stride;
-    for (int t = 0; t < a.P; ++t) {
-      double dx = a.ox + (ix0 + t) * a.h - x;
-      double dy = a.ox + (iy0 + t) * a.h - y;
-      double dz = a.oz + (iz0 + t) * a.h - z;
-      o[t] = (T)(a.pre * exp(-a.alpha * dx * dx));
-      o[a.P + t] = (T)exp(-a.alpha * dy * dy);
-      o[2 * a.P + t] = (T)exp(-a.alpha * dz * dz);
+    const int P = a.P;
+    // window factors wx (prefactor folded in), wy, wz; for the correction grid
+    // also wy', wz' (and wy'', wz''), derivatives with respect to the grid
+    // point: W' = -2 alpha d W, W'' = (4 alpha^2 d^2 - 2 alpha) W.  The x
+    // derivatives go into the combined arrays XX below.
+    for (int t = 0; t < P; ++t) {
+      double d[3] = {a.ox + (ix0 + t) * a.h - x, a.ox + (iy0 + t) * a.h - y, a.oz + (iz0 + t) * a.h - z};
+      for (int k = 0; k < 3; ++k) {
+        double wv = exp(-a.alpha * d[k] * d[k]) * (k == 0 ? a.pre : 1.0);
+        o[k * P + t] = (T)wv;
+        if (k > 0 && a.nfac > 1) o[(2 + k) * P + t] = (T)(-2.0 * a.alpha * d[k] * wv);
+        if (k > 0 && a.nfac > 2) o[(4 + k) * P + t] = (T)((4.0 * a.alpha * a.alpha * d[k] * d[k] - 2.0 * a.alpha) * wv);
+      }
     }
-    T* c = o + 3 * a.P;
+    const int nwin = a.nfac == 1 ? 3 : (a.nfac == 2 ? 5 : 7);  // window arrays of P
+    const int nxx = a.nfac == 1 ? 0 : (a.nfac == 2 ? 3 : 6);   // combined x arrays of P
+    T* c = o + (nwin + nxx) * P;
     int k = 0;
     double f[3] = {0, 0, 0}, g[3] = {0, 0, 0}, q[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
     if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) f[d] = a.sstr[(a.rowS + d) * n + i];
@@ -78,16 +88,43 @@ __global__ void k_prep(PrepArgs<T> a) {
       if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)sgq[m];
       if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = (T)tau[d];
     } else if (!a.paper) {
+      // C1, and the correction grid
+      //   D = Cs W + Cv . grad W - Ct : grad grad W   (at the image; phi^ = E H^R D^)
+      // with Cs = -2 f3 (S); Cv = -2 y3 f^I (S) + 4 g.q e3 (T) + 4 (-tau2, tau1, 0) (W);
+      // Ct = 4 y3 sym(g^I q^I) (T).  D is accumulated at the source and mirrored
+      // in z (image-only component), so every z-odd term changes sign here.
       if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) c[k++] = (T)f[d];
       if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)sgq[m];
       if (a.mask & HSE_ROTLET) for (int d = 0; d < 3; ++d) c[k++] = (T)tau[d];
-      if (a.mask & HSE_STOKESLET) c[k++] = (T)(-2.0 * f[2]);
-      double cv[3] = {0, 0, 0};
-      if (a.mask & HSE_STOKESLET) { cv[0] += -2.0 * hz * f[0]; cv[1] += -2.0 * hz * f[1]; cv[2] += 2.0 * hz * f[2]; }
-      if (a.mask & HSE_STRESSLET) cv[2] += 4.0 * gdq;
+      double cs = 0.0, cv[3] = {0, 0, 0}, ct[6] = {0, 0, 0, 0, 0, 0};
+      if (a.mask & HSE_STOKESLET) {
+        cs += -2.0 * f[2];
+        cv[0] += -2.0 * hz * f[0]; cv[1] += -2.0 * hz * f[1]; cv[2] += 2.0 * hz * f[2];
+      }
+      if (a.mask & HSE_STRESSLET) {
+        cv[2] += 4.0 * gdq;
+        for (int m = 0; m < 6; ++m) ct[m] = 4.0 * hz * sgqI[m];  // xx xy xz yy yz zz
+      }
       if (a.mask & HSE_ROTLET) { cv[0] += -4.0 * tau[1]; cv[1] += 4.0 * tau[0]; }
-      for (int d = 0; d < 3; ++d) c[k++] = (T)cv[d];
-      if (a.mask & HSE_STRESSLET) for (int m = 0; m < 6; ++m) c[k++] = (T)(4.0 * hz * sgqI[m]);
+      // coefficients of W, dx, dy, dz, dxx, dyy, dzz, dxdy, dxdz, dydz (z-odd
+      // terms flipped), folded with the x factors into
+      //   D = XX00 wy wz + XX10 wy' wz + XX01 wy wz' + XX20 wy'' wz + XX02 wy wz'' + XX11 wy' wz'
+      const double q[10] = {cs, cv[0], cv[1], -cv[2], -ct[0], -ct[3], -ct[5], -2.0 * ct[1], 2.0 * ct[2], 2.0 * ct[4]};
+      T* xx = o + nwin * P;
+      for (int t = 0; t < P; ++t) {
+        const double dx = a.ox + (ix0 + t) * a.h - x;
+        const double wx = a.pre * exp(-a.alpha * dx * dx);
+        const double dwx = -2.0 * a.alpha * dx * wx;
+        const double ddwx = (4.0 * a.alpha * a.alpha * dx * dx - 2.0 * a.alpha) * wx;
+        xx[t] = (T)(q[0] * wx + q[1] * dwx + q[4] * ddwx);
+        xx[P + t] = (T)(q[2] * wx + q[7] * dwx);
+        xx[2 * P + t] = (T)(q[3] * wx + q[8] * dwx);
+        if (nxx == 6) {
+          xx[3 * P + t] = (T)(q[5] * wx);
+          xx[4 * P + t] = (T)(q[6] * wx);
+          xx[5 * P + t] = (T)(q[9] * wx);
+        }
+      }
     } else {
       if (a.mask & HSE_STOKESLET) {
         for (int d = 0; d < 3; ++d) c[k++] = (T)f[d];
@@ -125,7 +162,10 @@ struct SpreadArgs {
 
 constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
 
-template <typename T, int NC>
+// NC plain components (C1, or the paper set), plus with DK != 0 the correction
+// grid D from derivative windows: DK bits 1 (W term), 2 (first derivatives),
+// 4 (second derivatives).
+template <typename T, int NC, int DK>
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   __shared__ int list[256];
   __shared__ int wcount[8];
@@ -136,7 +176,12 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   const int sx = bx0 + 2 * (w & 1), sy = by0 + 4 * ((w >> 1) & 1), sz = bz0 + 4 * (w >> 2);
   const int px = sx + (lane & 1), py = sy + ((lane >> 1) & 3), pz = sz + (lane >> 3);
   const int P = a.P;
+  // per-particle record: NWIN window arrays (wx, wy, wz, wy', wz', wy'', wz''),
+  // NXX combined x arrays of the correction grid, then the NC components
+  constexpr int NWIN = DK == 0 ? 3 : ((DK & 4) ? 7 : 5);
+  constexpr int NXX = DK == 0 ? 0 : ((DK & 4) ? 6 : 3);
   T acc[NC];
+  T accD = (T)0;
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = (T)0;
   // positions whose support can reach this tile (one grid step of slack for clamping)
@@ -178,10 +223,21 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
           int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
           if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
             const T* o = a.prep + (int64_t)jj * a.stride;
-            T wv = o[dx] * o[P + dy] * o[2 * P + dz];
-            const T* cv = o + 3 * P;
+            const T wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
+            const T wyz = wy * wz;
+            const T wv = wx * wyz;
+            const T* cv = o + (NWIN + NXX) * P;
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] += wv * cv[c];
+            if constexpr (DK != 0) {
+              const T* xx = o + NWIN * P + dx;
+              const T dwy = o[3 * P + dy], dwz = o[4 * P + dz];
+              accD += xx[0] * wyz + xx[P] * (dwy * wz) + xx[2 * P] * (wy * dwz);
+              if constexpr ((DK & 4) != 0) {
+                const T ddwy = o[5 * P + dy], ddwz = o[6 * P + dz];
+                accD += xx[3 * P] * (ddwy * wz) + xx[4 * P] * (wy * ddwz) + xx[5 * P] * (dwy * dwz);
+              }
+            }
           }
         }
         __syncthreads();
@@ -191,31 +247,38 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
     T* dst = a.out + inst * a.is + px * a.xs + py * a.pitch + pz;
 #pragma unroll
     for (int c = 0; c < NC; ++c) dst[c * a.cs] = acc[c];
+    if constexpr (DK != 0) dst[NC * a.cs] = accD;
   }
 }
 
-template <typename T, int NC>
+template <typename T, int NC, int DK>
 static void launch_spread_t(const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
-  k_spread<T, NC><<<grid, 256, 0, s>>>(a);
+  k_spread<T, NC, DK><<<grid, 256, 0, s>>>(a);
 }
 
+// nc plain components; dk: derivative kind of the correction grid (0: none)
 template <typename T>
-static bool launch_spread(int nc, const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
-  switch (nc) {
-    case 3: launch_spread_t<T, 3>(a, grid, s); return true;
-    case 5: launch_spread_t<T, 5>(a, grid, s); return true;
-    case 6: launch_spread_t<T, 6>(a, grid, s); return true;
-    case 7: launch_spread_t<T, 7>(a, grid, s); return true;
-    case 9: launch_spread_t<T, 9>(a, grid, s); return true;
-    case 10: launch_spread_t<T, 10>(a, grid, s); return true;
-    case 12: launch_spread_t<T, 12>(a, grid, s); return true;
-    case 13: launch_spread_t<T, 13>(a, grid, s); return true;
-    case 15: launch_spread_t<T, 15>(a, grid, s); return true;
-    case 18: launch_spread_t<T, 18>(a, grid, s); return true;
-    case 19: launch_spread_t<T, 19>(a, grid, s); return true;
-    case 20: launch_spread_t<T, 20>(a, grid, s); return true;
-    case 22: launch_spread_t<T, 22>(a, grid, s); return true;
-    case 25: launch_spread_t<T, 25>(a, grid, s); return true;
+static bool launch_spread(int nc, int dk, const SpreadArgs<T>& a, dim3 grid, cudaStream_t s) {
+  switch (dk * 64 + nc) {
+    // product set: C1 of the mask (+ D)
+    case 0 * 64 + 3: launch_spread_t<T, 3, 0>(a, grid, s); return true;
+    case 0 * 64 + 6: launch_spread_t<T, 6, 0>(a, grid, s); return true;
+    case 0 * 64 + 9: launch_spread_t<T, 9, 0>(a, grid, s); return true;
+    case 0 * 64 + 12: launch_spread_t<T, 12, 0>(a, grid, s); return true;
+    case 3 * 64 + 3: launch_spread_t<T, 3, 3>(a, grid, s); return true;   // S
+    case 6 * 64 + 6: launch_spread_t<T, 6, 6>(a, grid, s); return true;   // T
+    case 2 * 64 + 3: launch_spread_t<T, 3, 2>(a, grid, s); return true;   // W
+    case 3 * 64 + 6: launch_spread_t<T, 6, 3>(a, grid, s); return true;   // S+W
+    case 7 * 64 + 9: launch_spread_t<T, 9, 7>(a, grid, s); return true;   // S+T
+    case 6 * 64 + 9: launch_spread_t<T, 9, 6>(a, grid, s); return true;   // T+W
+    case 7 * 64 + 12: launch_spread_t<T, 12, 7>(a, grid, s); return true; // S+T+W
+    // paper set (hse_spread_grids)
+    case 0 * 64 + 5: launch_spread_t<T, 5, 0>(a, grid, s); return true;
+    case 0 * 64 + 7: launch_spread_t<T, 7, 0>(a, grid, s); return true;
+    case 0 * 64 + 13: launch_spread_t<T, 13, 0>(a, grid, s); return true;
+    case 0 * 64 + 18: launch_spread_t<T, 18, 0>(a, grid, s); return true;
+    case 0 * 64 + 20: launch_spread_t<T, 20, 0>(a, grid, s); return true;
+    case 0 * 64 + 25: launch_spread_t<T, 25, 0>(a, grid, s); return true;
   }
   return false;
 }
@@ -272,11 +335,11 @@ struct ScaleArgs {
   double h;
   const T* tabB;
   const T* tabH;
-  int iS, iT, iW, iCs, iCv, iCt;  // first component index of each group, -1 if absent
+  int iS, iT, iW, iD;  // first component index of each group (C1 of S, T, W; correction grid), -1 if absent
   int n_inst;
-  int64_t istride;                // complex elements between instances of one component
-  int64_t xstride;                // complex elements between kx planes of one buffer
-  int nout;                       // 6 (T1, T2) or 3 (free space: T1 only, no phi)
+  int64_t istride;     // complex elements between instances of one component
+  int64_t xstride;     // complex elements between kx planes of one buffer
+  int nout;            // 4 (T1, phi) or 3 (free space: T1 only)
 };
 
 template <typename C, typename T>
@@ -303,17 +366,14 @@ __global__ void k_scale(ScaleArgs<T> a) {
     int iy = (int)(t % Ny), ix = (int)(t / Ny);
     // element of component 0 of this instance
     const int64_t e = inst * a.istride + ix * a.xstride + (int64_t)iy * Nzh + jz;
-    C T1[3], T2[3];
-    if (ix == Mt || iy == Mt || jz == 2 * Mt) {  // Nyquist modes are dropped
-      for (int d = 0; d < 3; ++d) T1[d] = T2[d] = zero;
-    } else {
+    C T1[3] = {zero, zero, zero}, ph = zero;
+    if (ix != Mt && iy != Mt && jz != 2 * Mt) {  // Nyquist modes are dropped
       int wx = ix <= Mt ? ix : ix - Nx, wy = iy <= Mt ? iy : iy - Ny;
       T k[3] = {dkx * wx, dkx * wy, dkz * jz};
       T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
       int64_t ti = ((int64_t)abs(wx) * (Mt + 1) + abs(wy)) * Nzh + jz;
       T TH = a.tabH[ti];
       T TB = a.tabB ? a.tabB[ti] : (T)0;
-      for (int d = 0; d < 3; ++d) T1[d] = zero;
       auto ld = [&](int c) { return a.buf[c * a.cstride + e]; };
       if (a.iS >= 0) {  // -(k^2 I - k k) (1 + k^2/4xi^2) E B^R C1
         C Cv[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
@@ -341,30 +401,15 @@ __global__ void k_scale(ScaleArgs<T> a) {
                    cadd(cscale(k[1], Cv[0]), cscale(-k[0], Cv[1]))};
         for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale((T)(-2) * TH, cmul_i(cr[d])));
       }
-      // merged harmonic corrections: phi^ = E H^R (Cs^ + i k.Cv^ + k.Ct^.k)
-      C ph = zero;
-      if (a.iCs >= 0) ph = ld(a.iCs);
-      if (a.iCv >= 0) {
-        C v[3] = {ld(a.iCv), ld(a.iCv + 1), ld(a.iCv + 2)};
-        C kv = cadd(cadd(cscale(k[0], v[0]), cscale(k[1], v[1])), cscale(k[2], v[2]));
-        ph = cadd(ph, cmul_i(kv));
+      // harmonic potential of the wall corrections: phi^ = E H^R D^ (D spread
+      // through window derivatives); T1 gains e3 phi, grad(phi) is gathered
+      if (a.iD >= 0) {
+        ph = cscale(TH, ld(a.iD));
+        T1[2] = cadd(T1[2], ph);
       }
-      if (a.iCt >= 0) {
-        C c6[6];
-        for (int m = 0; m < 6; ++m) c6[m] = ld(a.iCt + m);
-        C kck = cadd(cadd(cscale(k[0] * k[0], c6[0]), cscale(k[1] * k[1], c6[3])), cscale(k[2] * k[2], c6[5]));
-        kck = cadd(kck, cscale((T)2 * k[0] * k[1], c6[1]));
-        kck = cadd(kck, cscale((T)2 * k[0] * k[2], c6[2]));
-        kck = cadd(kck, cscale((T)2 * k[1] * k[2], c6[4]));
-        ph = cadd(ph, kck);
-      }
-      ph = cscale(TH, ph);
-      T1[2] = cadd(T1[2], ph);
-      for (int d = 0; d < 3; ++d) T2[d] = cmul_i(cscale(k[d], ph));
     }
     for (int d = 0; d < 3; ++d) a.buf[d * a.cstride + e] = T1[d];
-    if (a.nout == 6)
-      for (int d = 0; d < 3; ++d) a.buf[(3 + d) * a.cstride + e] = T2[d];
+    if (a.nout == 4) a.buf[3 * a.cstride + e] = ph;
   }
 }
 
@@ -375,7 +420,7 @@ struct GatherArgs {
   const double* tgt;      // explicit targets or null
   const double* spos;     // sorted sources (targets = sources)
   const int32_t* sorig;
-  const T* buf;           // fields T1x..T2z, buffer stride bs, real layout
+  const T* buf;           // fields T1x, T1y, T1z (, phi), buffer stride bs, real layout
   int64_t bs, xs, pitch;
   const int32_t* inst_of; // batched instances: instance of each sorted target (null: one)
   int64_t is;             // instance stride of the fields
@@ -387,14 +432,19 @@ struct GatherArgs {
 
 constexpr int kGatherWarps = 4;
 
-// NF = 6 fields (T1, T2: u = <T1> - x3 <T2>) or 3 (free space: u = <T1>)
+// NF = 3: u = <T1> (free space).  NF = 4: u = <T1> - x3 <grad phi>, the
+// gradient taken through the window: <grad phi>(x) = h^3 sum_j grad_x W(x - x_j)
+// phi_j, grad_x W = -W' with W' the derivative with respect to the grid point.
 template <typename T, int NF>
 __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
-  __shared__ T wsm[kGatherWarps][3][kMaxP];
+  __shared__ T wsm[kGatherWarps][6][kMaxP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   T* wx = wsm[wib][0];
   T* wy = wsm[wib][1];
   T* wz = wsm[wib][2];
+  T* dwx = wsm[wib][3];
+  T* dwy = wsm[wib][4];
+  T* dwz = wsm[wib][5];
   const int P = a.P;
   const int64_t nwarps = (int64_t)gridDim.x * kGatherWarps;
   for (int64_t w = blockIdx.x * (int64_t)kGatherWarps + wib; w < a.n_tgt; w += nwarps) {
@@ -413,39 +463,58 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
     const T* fields = a.buf + (a.inst_of ? a.inst_of[w] * a.is : 0);
     __syncwarp();
     if (lane < P) {
-      double dx = a.ox + (ix0 + lane) * a.h - x;
-      double dy = a.ox + (iy0 + lane) * a.h - y;
-      double dz = a.oz + (iz0 + lane) * a.h - z;
-      wx[lane] = (T)(a.pre * exp(-a.alpha * dx * dx));
-      wy[lane] = (T)exp(-a.alpha * dy * dy);
-      wz[lane] = (T)exp(-a.alpha * dz * dz);
+      const double d[3] = {a.ox + (ix0 + lane) * a.h - x, a.ox + (iy0 + lane) * a.h - y,
+                           a.oz + (iz0 + lane) * a.h - z};
+      double wv0 = a.pre * exp(-a.alpha * d[0] * d[0]);
+      double wv1 = exp(-a.alpha * d[1] * d[1]);
+      double wv2 = exp(-a.alpha * d[2] * d[2]);
+      wx[lane] = (T)wv0;
+      wy[lane] = (T)wv1;
+      wz[lane] = (T)wv2;
+      if (NF == 4) {
+        dwx[lane] = (T)(-2.0 * a.alpha * d[0] * wv0);
+        dwy[lane] = (T)(-2.0 * a.alpha * d[1] * wv1);
+        dwz[lane] = (T)(-2.0 * a.alpha * d[2] * wv2);
+      }
     }
     __syncwarp();
-    double acc[NF];
+    // acc: <T1> (3), then the three window-derivative sums of phi
+    double acc[NF == 4 ? 6 : 3];
 #pragma unroll
-    for (int c = 0; c < NF; ++c) acc[c] = 0.0;
+    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c) acc[c] = 0.0;
     for (int q = lane; q < P * P; q += 32) {
       int jj = q / P, kk = q - jj * P;
-      T s[NF];
-#pragma unroll
-      for (int c = 0; c < NF; ++c) s[c] = 0;
+      T s[3] = {0, 0, 0}, s0 = 0, s1 = 0;
       const T* col = fields + (int64_t)ix0 * a.xs + (int64_t)(iy0 + jj) * a.pitch + iz0 + kk;
       for (int ii = 0; ii < P; ++ii) {
-        T wv = wx[ii];
+        const T wv = wx[ii];
         const T* pnt = col + (int64_t)ii * a.xs;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) s[c] += wv * pnt[c * a.bs];
+        for (int c = 0; c < 3; ++c) s[c] += wv * pnt[c * a.bs];
+        if (NF == 4) {
+          const T ph = pnt[3 * a.bs];
+          s0 += wv * ph;
+          s1 += dwx[ii] * ph;
+        }
       }
-      T wyz = wy[jj] * wz[kk];
+      const T wyz = wy[jj] * wz[kk];
 #pragma unroll
-      for (int c = 0; c < NF; ++c) acc[c] += (double)(wyz * s[c]);
+      for (int c = 0; c < 3; ++c) acc[c] += (double)(wyz * s[c]);
+      if (NF == 4) {
+        acc[3] += (double)(wyz * s1);
+        acc[4] += (double)(dwy[jj] * wz[kk] * s0);
+        acc[5] += (double)(wy[jj] * dwz[kk] * s0);
+      }
     }
 #pragma unroll
-    for (int c = 0; c < NF; ++c)
+    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c)
       for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
     if (lane == 0) {
       for (int d = 0; d < 3; ++d) {
-        double v = a.h3 * (NF == 6 ? acc[d] - z * acc[(3 + d) % NF] : acc[d]);
+        // grad_x W = -W', so u = <T1> - x3 <grad phi> = h^3 (acc_T1 + x3 acc_W')
+        double v;
+        if constexpr (NF == 4) v = a.h3 * (acc[d] + z * acc[3 + d]);
+        else v = a.h3 * acc[d];
         double* o = a.out + d * a.n_tgt + dst;
         *o = a.add ? *o + v : v;
       }
@@ -477,7 +546,11 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   a.oz = -(double)q.Mt * q.h;
   a.alpha = 2.0 * q.xi * q.xi / q.eta;
   a.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
-  a.stride = 3 * q.P + ncomp;
+  const int dk = paper ? 0 : deriv_kind(q.kernel_mask);
+  a.nfac = dk == 0 ? 1 : ((dk & 4) ? 3 : 2);
+  a.nc1 = c1_count(q.kernel_mask);
+  // paper: [wx wy wz][components]; product: [windows][combined x arrays][C1]
+  a.stride = paper ? 3 * q.P + ncomp : (dk == 0 ? 3 : ((dk & 4) ? 13 : 8)) * q.P + a.nc1;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
   a.supp = reinterpret_cast<int4*>(p->ws.supp);
   return a;
@@ -514,7 +587,10 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   int nzr = 2 * q.Mt - p->zA0;
   a.nz_tiles = (nzr + kTZ - 1) / kTZ;
   dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, a.nz_tiles * n_inst);
-  if (!launch_spread<T>(cs.n, a, grid, s)) return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
+  const int dk = paper ? 0 : deriv_kind(q.kernel_mask);
+  const int nplain = dk ? cs.n - 1 : cs.n;  // the product set's last component is D
+  if (!launch_spread<T>(nplain, dk, a, grid, s))
+    return set_err(p, HSE_ERR_UNSUPPORTED, "no spread kernel for %d comps", cs.n);
   ++p->n_launch;
   HSE_CUDA(p, cudaGetLastError());
   if (free_space(q.kernel_mask)) return HSE_OK;  // no images: C1 is the source-located grid
@@ -591,16 +667,11 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   sa.tabB = reinterpret_cast<const T*>(p->tabB);
   sa.tabH = reinterpret_cast<const T*>(p->tabH);
   int k = 0;
-  sa.iS = sa.iT = sa.iW = sa.iCs = sa.iCt = -1;
+  sa.iS = sa.iT = sa.iW = sa.iD = -1;
   if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
   if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
   if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
-  if ((q.kernel_mask & HSE_STOKESLET) && !free_space(q.kernel_mask)) { sa.iCs = k; k += 1; }
-  sa.iCv = -1;
-  if (!free_space(q.kernel_mask)) {
-    sa.iCv = k; k += 3;
-    if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
-  }
+  if (!free_space(q.kernel_mask)) sa.iD = k;
   sa.nout = q.n_fft_out;
   sa.n_inst = 1;
   sa.istride = 0;
@@ -639,7 +710,7 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   ga.h3 = q.h * q.h * q.h;
   ga.out = out;
   ga.add = add ? 1 : 0;
-  if (q.n_fft_out == 6) k_gather<T, 6><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  if (q.n_fft_out == 4) k_gather<T, 4><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   else k_gather<T, 3><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_gather");
@@ -812,16 +883,11 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   sa.tabB = reinterpret_cast<const T*>(p->tabB);
   sa.tabH = reinterpret_cast<const T*>(p->tabH);
   int k = 0;
-  sa.iS = sa.iT = sa.iW = sa.iCs = sa.iCt = -1;
+  sa.iS = sa.iT = sa.iW = sa.iD = -1;
   if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
   if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
   if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
-  if ((q.kernel_mask & HSE_STOKESLET) && !free_space(q.kernel_mask)) { sa.iCs = k; k += 1; }
-  sa.iCv = -1;
-  if (!free_space(q.kernel_mask)) {
-    sa.iCv = k; k += 3;
-    if (q.kernel_mask & HSE_STRESSLET) { sa.iCt = k; k += 6; }
-  }
+  if (!free_space(q.kernel_mask)) sa.iD = k;
   sa.nout = q.n_fft_out;
   k_scale<T><<<blocks_for(g.nh * n_inst, 256, 152 * 32), 256, 0, s>>>(sa);
   ++p->n_launch;
@@ -851,8 +917,8 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   ga.h3 = q.h * q.h * q.h;
   ga.out = out;
   ga.add = 1;
-  if (q.n_fft_out == 6)
-    k_gather<T, 6><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
+  if (q.n_fft_out == 4)
+    k_gather<T, 4><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   else k_gather<T, 3><<<blocks_for(n_total, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "batched k_gather");

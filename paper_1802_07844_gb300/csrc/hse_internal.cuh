@@ -39,6 +39,30 @@ struct GridDims {
 inline bool valid_mask(int m) { return (m & 7) != 0 && (m & ~15) == 0; }
 inline bool free_space(int m) { return (m & HSE_FREE_SPACE) != 0; }
 
+// Derivative kind of the correction grid D for a kernel mask (product
+// components): 1 the W term (stokeslet Cs), 2 first derivatives (Cv), 4 second
+// derivatives (Ct); 0 in free space (no corrections).
+inline int deriv_kind(int mask) {
+  if (free_space(mask)) return 0;
+  int dk = 2;  // every kernel has a Cv term
+  if (mask & HSE_STOKESLET) dk |= 1;
+  if (mask & HSE_STRESSLET) dk |= 4;
+  return dk;
+}
+inline int c1_count(int mask) {
+  return ((mask & HSE_STOKESLET) ? 3 : 0) + ((mask & HSE_STRESSLET) ? 6 : 0) + ((mask & HSE_ROTLET) ? 3 : 0);
+}
+// per-particle record of the spread (elements): the larger of the product
+// layout [window arrays][combined x arrays of D][C1] and the paper layout
+// [wx wy wz][C1, C2, C3 of every kernel]
+inline int prep_stride_max(int mask, int P) {
+  const int dk = deriv_kind(mask);
+  const int product = (dk == 0 ? 3 : ((dk & 4) ? 13 : 8)) * P + c1_count(mask);
+  const int paper = 3 * P + ((mask & HSE_STOKESLET) ? 7 : 0) + ((mask & HSE_STRESSLET) ? 13 : 0) +
+                    ((mask & HSE_ROTLET) ? 5 : 0);
+  return product > paper ? product : paper;
+}
+
 struct CompSet {
   int n = 0;
   int mirror_sign[kMaxComp];
@@ -46,7 +70,7 @@ struct CompSet {
 
 struct Workspace {
   int64_t cap = 0;   // particles
-  int P = 0, ncomp = 0;
+  int prep_stride = 0;  // elements per particle of prep
   int32_t *key_a = nullptr, *key_b = nullptr, *val_a = nullptr, *val_b = nullptr;
   int32_t* cell_start = nullptr;
   int64_t cell_cap = 0;
@@ -59,7 +83,7 @@ struct Workspace {
   double* usort = nullptr;     // 3 x cap real-space sums in sorted order (symmetric kernel)
   float4* usort4 = nullptr;    // cap partner sums in FP32 (mixed-precision symmetric kernel)
   double* sstr = nullptr;      // rows x cap sorted strengths
-  double* prep = nullptr;      // per sorted particle: 3P weights + ncomp strengths
+  double* prep = nullptr;      // per sorted particle: prep_stride window factors and strengths
   int32_t* supp = nullptr;     // per sorted particle: ix0, iy0, iz0, pad
   int* flag = nullptr;         // device error flag
   int* flag_host = nullptr;    // pinned host mirror

@@ -38,10 +38,12 @@ static hse_status cufft_check(hse_plan p, cufftResult r, const char* what) {
 
 // ------------------------------------------------------------------------------
 // Spread components.  Product path: C1 per kernel with the mirror sign of its
-// image strength, and the wall corrections merged into one harmonic potential
-//   phi^ = E H^R (Cs^ + i k.Cv^ + k Ct^ k)
-// (stokeslet: Cs = -2 f3, Cv = -2 y3 f^I; stresslet: Cv_z = 4 g.q,
-//  Ct = 4 y3 sym(g^I q^I); rotlet: Cv_xy = 4 (-tau2, tau1)), all at images.
+// image strength, and the wall corrections of all kernels merged into one
+// harmonic potential phi^ = E H^R D^, D spread as one scalar grid at the images
+// through window derivatives, D = Cs W + Cv . grad W - Ct : grad grad W
+// (the transform of Cs^ + i k.Cv^ + k Ct^ k;  stokeslet: Cs = -2 f3,
+// Cv = -2 y3 f^I; stresslet: Cv_z = 4 g.q, Ct = 4 y3 sym(g^I q^I); rotlet:
+// Cv_xy = 4 (-tau2, tau1)).  Forward transforms: C1 + 1; inverse: T1 and phi.
 // ------------------------------------------------------------------------------
 CompSet product_components(int mask) {
   CompSet c;
@@ -55,9 +57,7 @@ CompSet product_components(int mask) {
   if (mask & HSE_STOKESLET) { add(-1); add(-1); add(+1); }                   // -f^I  = (-f1,-f2,+f3)
   if (mask & HSE_STRESSLET) { add(-1); add(-1); add(+1); add(-1); add(+1); add(-1); }  // -sym(g^I q^I)
   if (mask & HSE_ROTLET) { add(+1); add(+1); add(-1); }                      // +tau^I
-  if (mask & HSE_STOKESLET) add(0);                                          // Cs
-  add(0); add(0); add(0);                                                    // Cv
-  if (mask & HSE_STRESSLET) for (int i = 0; i < 6; ++i) add(0);             // Ct
+  add(0);                                                                    // D (image only)
   return c;
 }
 
@@ -298,7 +298,7 @@ hse_status build_grids(hse_plan p) {
   p->zA0 = q.Mt - q.P / 2 + 1;
   p->comps = product_components(q.kernel_mask);
   q.n_fft_in = p->comps.n;
-  q.n_fft_out = free_space(q.kernel_mask) ? 3 : 6;  // T1 (and T2 with a wall)
+  q.n_fft_out = free_space(q.kernel_mask) ? 3 : 4;  // T1 (and phi with a wall)
   const bool mixed = q.precision == HSE_MIXED;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   size_t tab_elems = (size_t)(q.Mt + 1) * (q.Mt + 1) * (2 * q.Mt + 1);

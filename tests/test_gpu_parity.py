@@ -134,12 +134,23 @@ def test_real_part_fp32_shell(pkg, mask, dist):
 # ------------------------------------------------------- Fourier part (Alg. 1)
 @pytest.mark.parametrize("mask", MASKS)
 def test_fourier_part_matches_numpy_alg1(pkg, mask):
+    """The CUDA Fourier part (wall corrections spread as one grid through window
+    derivatives, grad(phi) gathered with the window's gradient) equals the numpy
+    restatement of that variant to rounding, and Alg. 1's C2/C3/T2 route to
+    within the window's truncation error."""
     pr = problem(mask, 300, 1.0, "near_wall", 34)
     xi, M, P = 5.0, 16, 14
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=0.6, P=P, tol=0.0, M=M)
     _, uf = plan.eval_parts(dev(pr.src), dev(pr.strengths))
-    ref = se.fourier_part(mask, pr.src, pr.strengths, xi, 1.0, M, P)
-    assert oracle.rel_rms(host(uf), ref) < 1e-12
+    uf = host(uf)
+    ref = se.fourier_part_derivative(mask, pr.src, pr.strengths, xi, 1.0, M, P)
+    assert oracle.rel_rms(uf, ref) < 1e-12
+    # the derivative windows truncate a little worse than the window itself
+    # (up to ~6x at equal P; the plan's parameter choice absorbs it, see
+    # test_gpu_tolerance.py)
+    paper = se.fourier_part(mask, pr.src, pr.strengths, xi, 1.0, M, P)
+    smooth = oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_SMOOTH, xi)
+    assert oracle.rel_rms(uf, smooth) < 10 * oracle.rel_rms(paper, smooth)
     plan.close()
 
 

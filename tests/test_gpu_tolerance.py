@@ -1,0 +1,42 @@
+"""Plans with parameters chosen from tol meet tol end to end: every kernel and
+kernel mix, uniform and near-wall sources, FP64 at 1e-5 / 1e-8 / 1e-10 and
+mixed precision at 1e-5, two xi each, against the oracle's direct half-space
+sum over all targets (Sec. 6 error definition).  This is the evidence behind
+keeping P unchanged for the derivative-window spreading and gather of the wall
+corrections."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import KERNEL_S, KERNEL_T, KERNEL_W, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MASKS = [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W, KERNEL_S | KERNEL_T | KERNEL_W]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1802_07844_gb300 as p
+    return p
+
+
+@pytest.mark.parametrize("mask", MASKS)
+@pytest.mark.parametrize("dist", ["uniform", "near_wall"])
+def test_error_within_tol_over_tolerances(pkg, mask, dist):
+    pr = problem(mask, 3000, 1.0, dist, 90, sub=mask)
+    ref = oracle.direct(mask, pr.src, pr.strengths)
+    src = torch.from_numpy(pr.src).cuda()
+    st = torch.from_numpy(pr.strengths).cuda()
+    xi0 = pkg.hse.server_xi(3000)
+    for tol, prec in ((1e-5, pkg.HSE_MIXED), (1e-5, pkg.HSE_FP64), (1e-8, pkg.HSE_FP64), (1e-10, pkg.HSE_FP64)):
+        for xi in (xi0, 2 * xi0):
+            plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=0.0, P=0, tol=tol, precision=prec)
+            try:
+                u = plan.eval(src, st).cpu().numpy()
+            finally:
+                plan.close()
+            assert oracle.rel_rms(u, ref) < tol, (tol, prec, xi)
