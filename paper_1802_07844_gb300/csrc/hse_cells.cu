@@ -11,7 +11,7 @@ void free_workspace(hse_plan p) { free_workspace(p->ws); }
 void free_workspace(Workspace& w) {
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
   cudaFree(w.cell_start); cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr);
-  cudaFree(w.prep); cudaFree(w.supp); cudaFree(w.flag); cudaFree(w.spos32); cudaFree(w.spos32lo);
+  cudaFree(w.prep); cudaFree(w.prep32); cudaFree(w.supp); cudaFree(w.flag); cudaFree(w.spos32); cudaFree(w.spos32lo);
   cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
   if (w.flag_host) cudaFreeHost(w.flag_host);
   w = Workspace();
@@ -38,12 +38,13 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   if (cap < w.cap) cap = w.cap;
   if (stride < w.prep_stride) stride = w.prep_stride;
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
-  cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr); cudaFree(w.prep); cudaFree(w.supp);
+  cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr); cudaFree(w.prep); cudaFree(w.prep32); cudaFree(w.supp);
   cudaFree(w.spos32); cudaFree(w.spos32lo); cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
   w.usort = nullptr;
   w.usort4 = nullptr;
   w.key_a = w.key_b = w.val_a = w.val_b = w.radix_hist = w.supp = nullptr;
   w.spos = w.sstr = w.prep = nullptr;
+  w.prep32 = nullptr;
   w.spos32 = w.spos32lo = w.sstr32 = nullptr;
   w.cap = 0;
   int64_t ntiles = (cap + 2047) / 2048;
@@ -60,6 +61,7 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   HSE_CUDA(p, cudaMalloc(&w.usort4, sizeof(float4) * cap));
   HSE_CUDA(p, cudaMalloc(&w.sstr, sizeof(double) * 12 * cap));
   HSE_CUDA(p, cudaMalloc(&w.prep, sizeof(double) * (size_t)stride * cap));
+  HSE_CUDA(p, cudaMalloc(&w.prep32, sizeof(float) * (size_t)stride * cap));
   HSE_CUDA(p, cudaMalloc(&w.supp, sizeof(int32_t) * 4 * cap));
   w.hist_cap = 256 * ntiles;
   w.cap = cap;

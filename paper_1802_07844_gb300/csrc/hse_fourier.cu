@@ -38,12 +38,13 @@ struct PrepArgs {
   double h, ox, oz, alpha, pre;
   int stride;
   T* prep;
+  float* prep32;  // FP64 plans: the same record in FP32 (null otherwise)
   int4* supp;
 };
 
 template <typename T>
-__global__ void k_prep(PrepArgs<T> a) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void prep_one(const PrepArgs<T>& a, int64_t i) {
+  {
     const int64_t n = a.n;
     double x = a.spos[i], y = a.spos[n + i], z = a.spos[2 * n + i];
     int ix0 = support_start(x, a.ox, a.h, a.P, a.Mt);
@@ -144,11 +145,28 @@ __global__ void k_prep(PrepArgs<T> a) {
   }
 }
 
+template <typename T>
+__global__ void k_prep(PrepArgs<T> a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    prep_one(a, i);
+    if (a.prep32) {  // FP32 copy of the record for the spread's small-weight part
+      const T* o = a.prep + i * (int64_t)a.stride;
+      float* o32 = a.prep32 + i * (int64_t)a.stride;
+      for (int t = 0; t < a.stride; ++t) o32[t] = (float)o[t];
+    }
+  }
+}
+
 // --------------------------------------------------------------------- spread
 template <typename T>
 struct SpreadArgs {
   const int4* supp;
   const T* prep;
+  // FP64 spread: (warp, particle) pairs whose weights on the warp's points are
+  // all below e^{-lnthr} of the window's peak take the FP32 record
+  const float* prep32;   // null: FP64 throughout
+  const float* spos32;   // sorted positions (FP32 heads)
+  float ah2, lnthr;      // alpha h^2 (window exponent per squared grid step), ln(1/threshold)
   const int32_t* cstart;
   int stride, P, Mt, z0, nz_tiles;
   double h, ox, oz;
@@ -158,6 +176,7 @@ struct SpreadArgs {
   int64_t cs, xs, pitch;
   int64_t is;            // batched instances: instance stride of out (blockIdx.z = inst * nz_tiles + tile)
   int ncells_inst;       // cells per instance in the cell list
+  int64_t n_src;         // sorted particles (rows of spos32)
 };
 
 constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
@@ -182,8 +201,12 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   constexpr int NXX = DK == 0 ? 0 : ((DK & 4) ? 6 : 3);
   T acc[NC];
   T accD = (T)0;
+  float acc32[NC];
+  float accD32 = 0.f;
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = (T)0;
+  for (int c = 0; c < NC; ++c) { acc[c] = (T)0; acc32[c] = 0.f; }
+  const bool split = sizeof(T) == 8 && a.prep32 != nullptr;
+  const float inv_h = (float)(1.0 / a.h), oxf = (float)a.ox, ozf = (float)a.oz;
   // positions whose support can reach this tile (one grid step of slack for clamping)
   auto cell_range = [&](int lo_idx, int hi_idx, double o, int d, int& c0, int& c1) {
     double lo = o + (lo_idx - P / 2 - 1) * a.h, hi = o + (hi_idx + P / 2 + 1) * a.h;
@@ -221,7 +244,41 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
                           s.z <= sz + 3 && s.z + P - 1 >= sz;
           if (!warp_hit) continue;
           int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
-          if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
+          bool small = false;
+          if constexpr (sizeof(T) == 8) {
+            if (split) {
+              // distance (grid steps) from the particle to the warp's 2 x 4 x 4
+              // points, less half a step for the FP32 position: if even the
+              // nearest point has weight below the threshold, so do all
+              const int64_t n = a.n_src;
+              const float gx = (a.spos32[jj] - oxf) * inv_h, gy = (a.spos32[n + jj] - oxf) * inv_h;
+              const float gz = (a.spos32[2 * n + jj] - ozf) * inv_h;
+              const float ex = fmaxf(0.f, fmaxf((float)sx - gx, gx - (float)(sx + 1)) - 0.5f);
+              const float ey = fmaxf(0.f, fmaxf((float)sy - gy, gy - (float)(sy + 3)) - 0.5f);
+              const float ez = fmaxf(0.f, fmaxf((float)sz - gz, gz - (float)(sz + 3)) - 0.5f);
+              small = a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr;
+            }
+          }
+          if (small) {
+            if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
+              const float* o = a.prep32 + (int64_t)jj * a.stride;
+              const float wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
+              const float wyz = wy * wz;
+              const float wv = wx * wyz;
+              const float* cv = o + (NWIN + NXX) * P;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) acc32[c] += wv * cv[c];
+              if constexpr (DK != 0) {
+                const float* xx = o + NWIN * P + dx;
+                const float dwy = o[3 * P + dy], dwz = o[4 * P + dz];
+                accD32 += xx[0] * wyz + xx[P] * (dwy * wz) + xx[2 * P] * (wy * dwz);
+                if constexpr ((DK & 4) != 0) {
+                  const float ddwy = o[5 * P + dy], ddwz = o[6 * P + dz];
+                  accD32 += xx[3 * P] * (ddwy * wz) + xx[4 * P] * (wy * ddwz) + xx[5 * P] * (dwy * dwz);
+                }
+              }
+            }
+          } else if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
             const T* o = a.prep + (int64_t)jj * a.stride;
             const T wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
             const T wyz = wy * wz;
@@ -244,6 +301,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
       }
     }
   if (px < a.Mt && py < a.Mt && pz < 2 * a.Mt) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] += (T)acc32[c];
+    accD += (T)accD32;
     T* dst = a.out + inst * a.is + px * a.xs + py * a.pitch + pz;
 #pragma unroll
     for (int c = 0; c < NC; ++c) dst[c * a.cs] = acc[c];
@@ -552,6 +612,7 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   // paper: [wx wy wz][components]; product: [windows][combined x arrays][C1]
   a.stride = paper ? 3 * q.P + ncomp : (dk == 0 ? 3 : ((dk & 4) ? 13 : 8)) * q.P + a.nc1;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
+  a.prep32 = (sizeof(T) == 8 && !paper) ? p->ws.prep32 : nullptr;
   a.supp = reinterpret_cast<int4*>(p->ws.supp);
   return a;
 }
@@ -569,6 +630,13 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   SpreadArgs<T> a;
   a.supp = pa.supp;
   a.prep = pa.prep;
+  a.prep32 = pa.prep32;
+  a.spos32 = p->ws.spos32;
+  a.n_src = n_src;
+  // FP32 below 1e-5 of the window's peak: those terms carry relative errors
+  // <~ 4 eps32 1e-5 ~ 3e-12 of the largest contribution of their particle
+  a.ah2 = (float)(pa.alpha * q.h * q.h);
+  a.lnthr = (float)std::log(1e5);
   a.cstart = p->ws.cell_start;
   a.stride = pa.stride;
   a.P = q.P;

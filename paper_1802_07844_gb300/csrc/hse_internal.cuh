@@ -84,6 +84,7 @@ struct Workspace {
   float4* usort4 = nullptr;    // cap partner sums in FP32 (mixed-precision symmetric kernel)
   double* sstr = nullptr;      // rows x cap sorted strengths
   double* prep = nullptr;      // per sorted particle: prep_stride window factors and strengths
+  float* prep32 = nullptr;     // the same record in FP32 (the FP64 spread's small-weight part)
   int32_t* supp = nullptr;     // per sorted particle: ix0, iy0, iz0, pad
   int* flag = nullptr;         // device error flag
   int* flag_host = nullptr;    // pinned host mirror
