@@ -209,12 +209,21 @@ typedef struct {
   int n_kernel_launches;            /* kernels of this library launched by the last evaluation */
   int n_fft_execs;                  /* cuFFT executions of the last evaluation                  */
   int timing;                       /* 1 when stage_ms is valid                                 */
-  double stage_ms[HSE_N_STAGES];    /* device time of each stage (CUDA events on the stream)   */
+  double stage_ms[HSE_N_STAGES];    /* device time of each stage (CUDA events on its stream)   */
+  int overlapped;                   /* 1: the real stage ran concurrently with SPREAD..GATHER  */
+  double total_ms;                  /* first to last event of the evaluation                   */
 } hse_eval_stats;
 
 /* Enable (1) or disable (0) CUDA-event timing of the stages of hse_eval and
- * hse_eval_parts.  Timing adds one event record per stage on the stream. */
+ * hse_eval_parts.  Timing adds one event record per stage on the stream; with
+ * overlapped halves (hse_plan_set_overlap) stage times are per stream and
+ * overlap in time. */
 hse_status hse_plan_set_timing(hse_plan plan, int enable);
+/* 1: with both halves requested, run the real-space stage on one internal
+ * stream and the Fourier stages on another (higher priority), joined on the
+ * caller's stream before the call's work ends; 0 (default): one after the
+ * other on the caller's stream. */
+hse_status hse_plan_set_overlap(hse_plan plan, int enable);
 
 /* Statistics of the last evaluation (synchronises on its last event when
  * timing is on).  out: host pointer. */

@@ -28,6 +28,18 @@ static hse_status prepare_sources(hse_plan p, int64_t n_src, const double* src, 
   return gather_sorted(p, n_src, src, need_str ? str : nullptr, s);
 }
 
+static hse_status ensure_overlap_streams(hse_plan p) {
+  if (p->s_real) return HSE_OK;
+  int lo = 0, hi = 0;
+  HSE_CUDA(p, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  HSE_CUDA(p, cudaStreamCreateWithPriority(&p->s_real, cudaStreamNonBlocking, lo));
+  HSE_CUDA(p, cudaStreamCreateWithPriority(&p->s_four, cudaStreamNonBlocking, hi));
+  HSE_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  HSE_CUDA(p, cudaEventCreateWithFlags(&p->ev_real, cudaEventDisableTiming));
+  HSE_CUDA(p, cudaEventCreateWithFlags(&p->ev_four, cudaEventDisableTiming));
+  return HSE_OK;
+}
+
 static hse_status eval_impl(hse_plan p, int64_t n_src, const double* src, const double* str, int64_t n_tgt,
                             const double* tgt, double* u_real, double* u_four, void* stream) {
   if (!p) return HSE_ERR_INVALID;
@@ -44,6 +56,30 @@ static hse_status eval_impl(hse_plan p, int64_t n_src, const double* src, const 
   if (n_src == 0) {
     if (u_real) HSE_CUDA(p, cudaMemsetAsync(u_real, 0, sizeof(double) * 3 * n_tgt, s));
     if (u_four) HSE_CUDA(p, cudaMemsetAsync(u_four, 0, sizeof(double) * 3 * n_tgt, s));
+    return HSE_OK;
+  }
+  p->last_overlap = false;
+  if (p->overlap && u_real && u_four) {
+    // The two halves share only read-only inputs: run them concurrently, the
+    // Fourier part at higher priority, and let its gather (which adds into
+    // out when out is shared) wait for the real part.
+    HSE_TRY(ensure_overlap_streams(p));
+    HSE_CUDA(p, cudaEventRecord(p->ev_fork, s));
+    HSE_CUDA(p, cudaStreamWaitEvent(p->s_real, p->ev_fork, 0));
+    HSE_CUDA(p, cudaStreamWaitEvent(p->s_four, p->ev_fork, 0));
+    stage_mark(p, HSE_STAGE_REAL, p->s_real);
+    HSE_TRY(real_space(p, n_src, n_tgt, tgt, u_real, false, p->s_real));
+    if (p->timing) HSE_CUDA(p, cudaEventRecord(p->ev_real_end, p->s_real));
+    HSE_CUDA(p, cudaEventRecord(p->ev_real, p->s_real));
+    stage_mark(p, HSE_STAGE_SPREAD, p->s_four);
+    HSE_TRY(fourier_space(p, n_src, n_tgt, tgt, u_four, u_four == u_real, p->s_four,
+                          u_four == u_real ? p->ev_real : nullptr));
+    stage_mark(p, HSE_N_STAGES, p->s_four);
+    HSE_CUDA(p, cudaEventRecord(p->ev_four, p->s_four));
+    HSE_CUDA(p, cudaStreamWaitEvent(s, p->ev_real, 0));
+    HSE_CUDA(p, cudaStreamWaitEvent(s, p->ev_four, 0));
+    p->last_overlap = true;
+    p->ev_recorded = p->timing;
     return HSE_OK;
   }
   stage_mark(p, HSE_STAGE_REAL, s);
@@ -115,14 +151,22 @@ extern "C" hse_status hse_spread_grids(hse_plan p, int64_t n_src, const double* 
   return spread_paper_grids(p, n_src, grids, s);
 }
 
+extern "C" hse_status hse_plan_set_overlap(hse_plan p, int enable) {
+  if (!p) return HSE_ERR_INVALID;
+  p->overlap = enable != 0;
+  return HSE_OK;
+}
+
 extern "C" hse_status hse_plan_set_timing(hse_plan p, int enable) {
   if (!p) return HSE_ERR_INVALID;
   if (enable && !p->timing) {
     for (int i = 0; i <= HSE_N_STAGES; ++i) HSE_CUDA(p, cudaEventCreate(&p->ev[i]));
+    HSE_CUDA(p, cudaEventCreate(&p->ev_real_end));
     p->timing = true;
   } else if (!enable && p->timing) {
     cudaDeviceSynchronize();
     for (int i = 0; i <= HSE_N_STAGES; ++i) cudaEventDestroy(p->ev[i]);
+    cudaEventDestroy(p->ev_real_end);
     p->timing = false;
   }
   p->ev_recorded = false;
@@ -135,13 +179,21 @@ extern "C" hse_status hse_get_eval_stats(hse_plan p, hse_eval_stats* out) {
   out->n_fft_execs = p->n_fft;
   out->timing = 0;
   for (int i = 0; i < HSE_N_STAGES; ++i) out->stage_ms[i] = 0.0;
+  out->overlapped = p->last_overlap ? 1 : 0;
+  out->total_ms = 0.0;
   if (p->timing && p->ev_recorded) {
     HSE_CUDA(p, cudaEventSynchronize(p->ev[HSE_N_STAGES]));
+    if (p->last_overlap) HSE_CUDA(p, cudaEventSynchronize(p->ev_real_end));
     for (int i = 0; i < HSE_N_STAGES; ++i) {
+      // concurrent halves: the real stage ends at its own event
+      cudaEvent_t end = (p->last_overlap && i == HSE_STAGE_REAL) ? p->ev_real_end : p->ev[i + 1];
       float ms = 0.f;
-      HSE_CUDA(p, cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]));
+      HSE_CUDA(p, cudaEventElapsedTime(&ms, p->ev[i], end));
       out->stage_ms[i] = ms;
     }
+    float tot = 0.f;
+    HSE_CUDA(p, cudaEventElapsedTime(&tot, p->ev[HSE_STAGE_CHECK], p->ev[HSE_N_STAGES]));
+    out->total_ms = tot;
     out->timing = 1;
   }
   return HSE_OK;

@@ -710,7 +710,7 @@ static cufftResult fft_inverse(hse_plan p, float* b) {
 
 template <typename T>
 static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, cudaEvent_t gather_after) {
   const hse_params& q = p->prm;
   const GridDims& g = p->g;
   const int nin = p->comps.n;
@@ -756,6 +756,7 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   }
   stage_mark(p, HSE_STAGE_GATHER, s);
   if (n_tgt == 0) return HSE_OK;
+  if (gather_after) HSE_CUDA(p, cudaStreamWaitEvent(s, gather_after, 0));
   GatherArgs<T> ga;
   ga.n_tgt = n_tgt;
   ga.n_src = n_src;
@@ -1000,9 +1001,9 @@ hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const in
 }
 
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
-                         cudaStream_t s) {
-  if (p->prm.precision == HSE_MIXED) return fourier_space_t<float>(p, n_src, n_tgt, tgt, out, add, s);
-  return fourier_space_t<double>(p, n_src, n_tgt, tgt, out, add, s);
+                         cudaStream_t s, cudaEvent_t gather_after) {
+  if (p->prm.precision == HSE_MIXED) return fourier_space_t<float>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
+  return fourier_space_t<double>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
 }
 
 }  // namespace hse

@@ -118,6 +118,15 @@ struct hse_plan_s {
   // statistics of the last evaluation
   bool timing = false;
   cudaEvent_t ev[HSE_N_STAGES + 1] = {};
+  // concurrent halves (hse_plan_set_overlap): real space on a low-priority
+  // stream, the Fourier part on a high-priority one, joined on the caller's.
+  // Off by default: on GB300 both halves are FP64-issue-bound and measured no
+  // faster together (1M near-wall S+W: 1106 vs 1109 ms).
+  bool overlap = false;
+  cudaStream_t s_real = nullptr, s_four = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_real = nullptr, ev_four = nullptr;
+  cudaEvent_t ev_real_end = nullptr;  // timing: end of the real stage on its stream
+  bool last_overlap = false;
   bool ev_recorded = false;
   int n_launch = 0;
   int n_fft = 0;
@@ -148,8 +157,9 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
                       cudaStream_t s);
 hse_status neighbor_counts(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, int32_t* a, int32_t* b,
                            cudaStream_t s);
+// gather_after: an event the gather waits for (the real part writing out), or null
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
-                         cudaStream_t s);
+                         cudaStream_t s, cudaEvent_t gather_after = nullptr);
 hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStream_t s);
 cudaError_t sort_keys_and_starts(int64_t n, int64_t ncells, int32_t* key_a, int32_t* val_a, int32_t* key_b,
                                  int32_t* val_b, int32_t* hist, int32_t* start_out, cudaStream_t s);

@@ -576,8 +576,17 @@ extern "C" hse_status hse_plan_get_params(hse_plan p, hse_params* out) {
 extern "C" hse_status hse_plan_destroy(hse_plan p) {
   if (!p) return HSE_ERR_INVALID;
   cudaDeviceSynchronize();
-  if (p->timing)
+  if (p->timing) {
     for (int i = 0; i <= HSE_N_STAGES; ++i) cudaEventDestroy(p->ev[i]);
+    cudaEventDestroy(p->ev_real_end);
+  }
+  if (p->s_real) {
+    cudaStreamDestroy(p->s_real);
+    cudaStreamDestroy(p->s_four);
+    cudaEventDestroy(p->ev_fork);
+    cudaEventDestroy(p->ev_real);
+    cudaEventDestroy(p->ev_four);
+  }
   free_grids(p);
   free_workspace(p);
   delete p;

@@ -44,7 +44,8 @@ STAGE_NAMES = ("check", "cells", "real", "spread", "fft", "scale", "ifft", "gath
 
 class hse_eval_stats(ctypes.Structure):
     _fields_ = [("n_kernel_launches", ctypes.c_int), ("n_fft_execs", ctypes.c_int), ("timing", ctypes.c_int),
-                ("stage_ms", ctypes.c_double * HSE_N_STAGES)]
+                ("stage_ms", ctypes.c_double * HSE_N_STAGES), ("overlapped", ctypes.c_int),
+                ("total_ms", ctypes.c_double)]
 
 
 HSE_PENDING = 7
@@ -92,7 +93,7 @@ class HseError(RuntimeError):
 _lib = None
 _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
-          "hse_last_error", "hse_plan_set_timing", "hse_get_eval_stats", "hse_cell_list_noalloc",
+          "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
           "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_batch_create",
           "hse_batch_eval", "hse_batch_get_stats", "hse_batch_last_error", "hse_batch_destroy",
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
     L.hse_spread_grids.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(ctypes.c_int), vp]
     L.hse_plan_destroy.argtypes = [vp]
     L.hse_plan_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hse_plan_set_overlap.argtypes = [vp, ctypes.c_int]
     L.hse_server_create.argtypes = [ctypes.POINTER(hse_server_config), ctypes.POINTER(vp)]
     L.hse_server_submit.argtypes = [vp, ctypes.POINTER(hse_request), ctypes.POINTER(ctypes.c_uint64)]
     L.hse_server_poll.argtypes = [vp, ctypes.c_uint64]
@@ -217,11 +219,16 @@ def hse_plan_set_timing(plan, enable):
     _check(load().hse_plan_set_timing(plan, int(bool(enable))), plan)
 
 
+def hse_plan_set_overlap(plan, enable):
+    _check(load().hse_plan_set_overlap(plan, int(bool(enable))), plan)
+
+
 def hse_get_eval_stats(plan) -> dict:
     st = hse_eval_stats()
     _check(load().hse_get_eval_stats(plan, ctypes.byref(st)), plan)
     return {"n_kernel_launches": st.n_kernel_launches, "n_fft_execs": st.n_fft_execs, "timing": bool(st.timing),
-            "stage_ms": dict(zip(STAGE_NAMES, list(st.stage_ms)))}
+            "stage_ms": dict(zip(STAGE_NAMES, list(st.stage_ms))), "overlapped": bool(st.overlapped),
+            "total_ms": st.total_ms}
 
 
 HSE_NOALLOC_MAX_POINTS = 262144
@@ -505,6 +512,9 @@ class Plan:
 
     def set_timing(self, enable=True):
         hse_plan_set_timing(self.handle, enable)
+
+    def set_overlap(self, enable=True):
+        hse_plan_set_overlap(self.handle, enable)
 
     def stats(self):
         return hse_get_eval_stats(self.handle)

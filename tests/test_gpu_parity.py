@@ -348,3 +348,33 @@ def test_mixed_bench_workload_parity():
     idx = np.sort(np.random.default_rng(1802078443).choice(W["n"], 128, replace=False))
     ref = oracle.direct(W["mask"], pr.src, pr.strengths, pr.src[:, idx])
     assert oracle.rel_rms(u[:, idx], ref) < Mx["tol"]
+
+
+@pytest.mark.parametrize("explicit", [False, True])
+def test_overlapped_halves_equal_sequential(pkg, explicit):
+    """With overlap on, the real-space and Fourier stages run on two internal
+    streams concurrently and the gather waits for the real part; the result
+    equals the sequential evaluation (up to atomic summation order), with and
+    without stage timing, and hse_eval_parts still splits it."""
+    mask = KERNEL_S | KERNEL_W
+    pr = problem(mask, 20000, 1.0, "near_wall", 36)
+    tgt = None
+    if explicit:
+        rng = np.random.default_rng(37)
+        tgt = dev(np.stack([rng.uniform(0, 1, 3000), rng.uniform(0, 1, 3000), rng.uniform(0, 1, 3000)]))
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=30.0, rc=0.0, P=0, tol=1e-10)
+    src, st = dev(pr.src), dev(pr.strengths)
+    plan.set_overlap(False)
+    seq = host(plan.eval(src, st, tgt))
+    plan.set_overlap(True)
+    for timing in (False, True):
+        plan.set_timing(timing)
+        par = host(plan.eval(src, st, tgt))
+        s = plan.stats()
+        assert s["overlapped"]
+        assert oracle.rel_rms(par, seq) < 1e-12
+        if timing:
+            assert s["total_ms"] > 0 and s["stage_ms"]["real"] > 0 and s["stage_ms"]["fft"] > 0
+    ur, uf = plan.eval_parts(src, st, tgt)
+    assert oracle.rel_rms(host(ur) + host(uf), seq) < 1e-12
+    plan.close()
