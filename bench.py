@@ -52,6 +52,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # 37 flops for a free pair and 92 for an image pair with its wall corrections.
 # Pairs in the outer shell [rc64, rc) run the same formulas in FP32; they are
 # charged the same flops against the FP32 peak.
+# DRAM bytes of one k_real_sym<double, 5> launch per point, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum = 16.1 MB + 0 at N = 100k of
+# this workload); the kernel reads positions, strengths and cell lists about
+# once, so the figure is scaled by the number of points.
+REAL_TRAFFIC_BYTES_PER_POINT = 161.0
 FLOPS_RADIAL = 82
 FLOPS_FREE_DIR = 37
 FLOPS_IMAGE_DIR = 92
@@ -280,7 +285,9 @@ def run_ours(args, rank, world, local_rank):
         roof = {"kernel": "k_scale", "bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs", "achieved": byts / (avg["scale"] / 1e3) / 1e9}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = REAL_TRAFFIC_BYTES_PER_POINT * W["n"] if dom == "real" else None
+    if dom == "real":
+        roof["traffic_source"] = "ncu dram bytes of one launch at N = 100k, scaled by points"
     roof["stage_ms"] = {k: round(v, 3) for k, v in avg.items()}
     if overlapped:
         roof["stage_ms_note"] = ("device time of each stage on its own stream: the real-space stage runs "
