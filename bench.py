@@ -62,6 +62,26 @@ FLOPS_FREE_DIR = 37
 FLOPS_IMAGE_DIR = 92
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """Largest value over the ranks (the slowest replica sets the job time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_problem(rank: int, n: int):
+    """The bench workload's inputs for one replica: same recipe, own seed."""
+    return problem(WORKLOAD["mask"], n, 1.0, WORKLOAD["dist"], WORKLOAD["index"], sub=rank)
+
+
+def whole_job_rate(points_per_rank: int, world: int, ms_max: float) -> float:
+    """Mtargets/s of the whole job: every rank's points over the slowest rank's time."""
+    return points_per_rank * world / (ms_max / 1e3) / 1e6
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -158,7 +178,7 @@ def run_ours(args, rank, world, local_rank):
     if args.n:
         W["n"] = args.n
     mask = W["mask"]
-    pr = problem(mask, W["n"], 1.0, W["dist"], W["index"], sub=rank)
+    pr = replica_problem(rank, W["n"])
     if args.real_only:
         return run_real_only(args, pkg, torch, dev, W, pr)
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
@@ -213,11 +233,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     ms_step = total_ms / args.steps
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_step_max = float(t.item())
-    value = W["n"] * world / (ms_step_max / 1e3) / 1e6
+    ms_step_max = max_over_ranks(ms_step, world, dev)
+    value = whole_job_rate(W["n"], world, ms_step_max)
 
     # end-to-end: pinned host inputs in, velocities out, inside the timed region
     h_src = torch.from_numpy(pr.src).pin_memory()
@@ -242,10 +259,7 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
     e_ms /= e2e_steps
-    t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = W["n"] * world / (float(t.item()) / 1e3) / 1e6
+    e2e_value = whole_job_rate(W["n"], world, max_over_ranks(e_ms, world, dev))
     h2d = h_src.numel() * 8 + h_st.numel() * 8
     d2h = h_vel.numel() * 8
 
@@ -350,13 +364,11 @@ def run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world):
         e1.synchronize()
         ms += e0.elapsed_time(e1)
     ms /= args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = max_over_ranks(ms, world, dev)
     prm = plan.params
     plan.close()
     n = src.shape[1]
-    return {"value": n * world / (float(t.item()) / 1e3) / 1e6, "unit": "Mtargets/s", "ms_per_step": float(t.item()),
+    return {"value": whole_job_rate(n, world, ms_max), "unit": "Mtargets/s", "ms_per_step": ms_max,
             "dtype": "f32 arithmetic (FP64 sums, close image pairs, tables)", "tol": Mx["tol"], "xi": prm["xi"],
             "rc": prm["rc"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
             "stage_ms": {k: round(float(np.mean(v)), 3) for k, v in stages.items()}}
