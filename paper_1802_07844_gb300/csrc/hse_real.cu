@@ -332,7 +332,12 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
               }
               if (in) {
                 hit = true;
-                type = (pass == 0 ? Q_FREE : Q_IMAGE) | (a.far2 > 0.0f && d2f >= a.far2 ? Q_FAR : 0);
+                // FP32 for the outer shell, unless an end point is within rho/64
+                // of the wall: there the free and image contributions of a
+                // source cancel to O(height/rho), which would amplify rounding
+                const float hmin = fminf(xf[2], a.spos32[2 * n + j]);
+                const bool far = a.far2 > 0.0f && d2f >= a.far2 && 4096.0f * hmin * hmin >= d2f;
+                type = (pass == 0 ? Q_FREE : Q_IMAGE) | (far ? Q_FAR : 0);
               }
             }
           }

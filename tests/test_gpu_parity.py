@@ -378,3 +378,25 @@ def test_overlapped_halves_equal_sequential(pkg, explicit):
     ur, uf = plan.eval_parts(src, st, tgt)
     assert oracle.rel_rms(host(ur) + host(uf), seq) < 1e-12
     plan.close()
+
+
+def test_fp32_shell_near_wall_dense(pkg):
+    """Dense near-wall sources (the regime of the 1M benchmark): the FP32 outer
+    shell must not amplify rounding for points close to the wall, where the
+    free and image contributions of a source cancel to O(height / rho).  Shell
+    vs all-FP64 real part, globally and within the wall layer."""
+    mask = KERNEL_S | KERNEL_W
+    pr = problem(mask, 200000, 1.0, "near_wall", 38)
+    xi = 90.0 * 0.2 ** (1.0 / 3.0)
+    rc = 5.15 / xi
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=rc, P=12, tol=0.0)
+    assert plan.params["rc64"] < rc
+    src, st = dev(pr.src), dev(pr.strengths)
+    shell = host(plan.eval_parts(src, st, fourier=False)[0])
+    plan.set_rc64(rc)
+    fp64 = host(plan.eval_parts(src, st, fourier=False)[0])
+    plan.close()
+    assert oracle.rel_rms(shell, fp64) < 1e-12
+    wall = pr.src[2] < 0.002
+    assert wall.sum() > 1000
+    assert oracle.rel_rms(shell[:, wall], fp64[:, wall]) < 1e-12
