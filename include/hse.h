@@ -74,7 +74,8 @@ typedef struct {
                       * evaluated in FP64, pairs in [rc64, rc) in FP32 (their      *
                       * screened kernels are small enough that FP32 rounding stays  *
                       * below 1/10 of the real-space truncation error); rc64 >= rc  *
-                      * means FP64 throughout.  0 under HSE_MIXED.                   */
+                      * means FP64 throughout (also for the spread's small-weight   *
+                      * part, which otherwise runs in FP32).  0 under HSE_MIXED.     */
   int P;             /* Gaussian support width in grid points (even)               */
   int M;             /* basic grid size, h = L / M                                 */
   int Mt;            /* extended grid size M + P; grid Mt x Mt x 2 Mt              */
@@ -116,7 +117,7 @@ hse_status hse_plan_set_grid(hse_plan plan, int M);
 hse_status hse_plan_get_params(hse_plan plan, hse_params* out);
 
 /* Override the FP64/FP32 split radius rc64 of an HSE_FP64 plan (see
- * hse_params); rc64 >= rc evaluates every real-space pair in FP64.
+ * hse_params); rc64 >= rc evaluates everything in FP64.
  * HSE_ERR_INVALID for rc64 < 0 or an HSE_MIXED plan. */
 hse_status hse_plan_set_rc64(hse_plan plan, double rc64);
 

@@ -612,7 +612,10 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   // paper: [wx wy wz][components]; product: [windows][combined x arrays][C1]
   a.stride = paper ? 3 * q.P + ncomp : (dk == 0 ? 3 : ((dk & 4) ? 13 : 8)) * q.P + a.nc1;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
-  a.prep32 = (sizeof(T) == 8 && !paper) ? p->ws.prep32 : nullptr;
+  // FP64 plans split small window weights to FP32 unless the plan asks for
+  // FP64 throughout (rc64 >= rc)
+  const bool split = sizeof(T) == 8 && !paper && q.precision == HSE_FP64 && q.rc64 < q.rc;
+  a.prep32 = split ? p->ws.prep32 : nullptr;
   a.supp = reinterpret_cast<int4*>(p->ws.supp);
   return a;
 }
@@ -637,6 +640,7 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   // <~ 4 eps32 1e-5 ~ 3e-12 of the largest contribution of their particle
   a.ah2 = (float)(pa.alpha * q.h * q.h);
   a.lnthr = (float)std::log(1e5);
+
   a.cstart = p->ws.cell_start;
   a.stride = pa.stride;
   a.P = q.P;
