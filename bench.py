@@ -33,8 +33,10 @@ from workloads import KERNEL_S, KERNEL_W, problem  # noqa: E402
 WORKLOAD = dict(
     name="hs_stokeslet_rotlet_n1m_nearwall",
     mask=KERNEL_S | KERNEL_W, n=1_000_000, dist="near_wall", index=2, tol=1e-10,
-    # parameters checked against the FP64 oracle on a target sample (tests/test_gpu_parity.py)
-    xi=90.0, rc=0.0572, P=18, M=302,  # Mt = 320 = 2^6 x 5: a fast cuFFT size
+    # parameters checked against the FP64 oracle on a target sample (tests/test_gpu_parity.py):
+    # xi r_c = 4.8, k_inf / xi = pi M / xi = 10.9, P = 18 give 3.0e-11 on 3000 targets (P = 16:
+    # 3.2e-10; xi = 90 with the same grid: 7.3e-11); Mt = 320 = 2^6 x 5 is a fast cuFFT size
+    xi=87.0, rc=0.0552, P=18, M=302,
 )
 # mixed-precision (FP32 arithmetic) configuration of the same workload at tolerance 1e-5
 MIXED = dict(tol=1e-5, xi=100.0)  # r_c, P, M from the plan tolerance rule
@@ -508,7 +510,14 @@ def run_batch(args, pkg, torch, dev):
 
 
 def run_real_only(args, pkg, torch, dev, W, pr):
-    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0)
+    if args.mixed:  # the mixed-precision leg's parameters, real-space half only
+        full = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=MIXED["xi"], rc=0.0, P=0, tol=MIXED["tol"],
+                        precision=pkg.HSE_MIXED, M=None)
+        rc, P = full.params["rc"], full.params["P"]
+        full.close()
+        plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=MIXED["xi"], rc=rc, P=P, tol=0.0, precision=pkg.HSE_MIXED)
+    else:
+        plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0)
     src = torch.from_numpy(pr.src).to(dev)
     st = torch.from_numpy(pr.strengths).to(dev)
     for _ in range(args.warmup):
@@ -520,7 +529,8 @@ def run_real_only(args, pkg, torch, dev, W, pr):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
     plan.close()
-    return {"profiling_run": "real-space half only", "n": W["n"], "ms_per_step": dt * 1e3}
+    return {"profiling_run": "real-space half only" + (" (mixed precision)" if args.mixed else ""), "n": W["n"],
+            "ms_per_step": dt * 1e3}
 
 
 # ---------------------------------------------------------- reference arm
@@ -572,6 +582,7 @@ def main():
                     help="instances of the batched small-systems run (0: skip)")
     ap.add_argument("--real-only", action="store_true",
                     help="profiling aid: plan without a grid, time only the real-space half")
+    ap.add_argument("--mixed", action="store_true", help="with --real-only: the mixed-precision leg's plan")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

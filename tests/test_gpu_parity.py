@@ -282,7 +282,8 @@ def test_workload_uniform_100k_tol1e10(pkg, mask):
 
 def test_bench_workload_parity():
     """The benchmark workload and parameters (stokeslet + rotlet, N = 1M,
-    near-wall, FP64, tolerance 1e-10), checked on 128 seeded targets."""
+    near-wall, FP64, tolerance 1e-10), checked on 2000 seeded targets (a
+    sample large enough that the heavy-tailed reference norm settles)."""
     import bench
     import paper_1802_07844_gb300 as pkg
     W = bench.WORKLOAD
@@ -290,7 +291,7 @@ def test_bench_workload_parity():
     plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
     u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
     plan.close()
-    idx = np.sort(np.random.default_rng(1802078442).choice(W["n"], 128, replace=False))
+    idx = np.sort(np.random.default_rng(1802078442).choice(W["n"], 2000, replace=False))
     ref = oracle.direct(W["mask"], pr.src, pr.strengths, pr.src[:, idx])
     assert oracle.rel_rms(u[:, idx], ref) < W["tol"]
 
