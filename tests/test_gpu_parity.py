@@ -337,16 +337,17 @@ def test_mixed_explicit_targets(pkg):
 
 def test_mixed_bench_workload_parity():
     """The mixed-precision benchmark configuration (N = 1M near-wall stokeslet +
-    rotlet, tolerance 1e-5) on 128 seeded targets."""
+    rotlet, tolerance 1e-5) on 2000 seeded targets."""
     import bench
     import paper_1802_07844_gb300 as pkg
     W = bench.WORKLOAD
     Mx = bench.MIXED
     pr = problem(W["mask"], W["n"], 1.0, W["dist"], W["index"])
-    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=0.0, P=0, tol=Mx["tol"], precision=pkg.HSE_MIXED)
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=Mx["rc"], P=Mx["P"], tol=0.0, M=Mx["M"],
+                    precision=pkg.HSE_MIXED)
     u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
     plan.close()
-    idx = np.sort(np.random.default_rng(1802078443).choice(W["n"], 128, replace=False))
+    idx = np.sort(np.random.default_rng(1802078443).choice(W["n"], 2000, replace=False))
     ref = oracle.direct(W["mask"], pr.src, pr.strengths, pr.src[:, idx])
     assert oracle.rel_rms(u[:, idx], ref) < Mx["tol"]
 
