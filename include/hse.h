@@ -81,7 +81,7 @@ typedef struct {
   int Mt;            /* extended grid size M + P; grid Mt x Mt x 2 Mt              */
   double h;          /* grid spacing                                               */
   double eta;        /* Gaussian shape parameter P xi^2 h^2 / (c^2 pi), c = 0.95  */
-  int ncell[3];      /* real-space cell list dimensions (cell side >= rc)          */
+  int ncell[3];      /* real-space cell list dimensions (cell side >= rc / 2)      */
   int n_fft_in;      /* number of forward FFTs per evaluation                      */
   int n_fft_out;     /* number of inverse FFTs per evaluation (6)                  */
   size_t grid_bytes; /* device bytes held by grids and tables                      */

@@ -18,6 +18,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kSqrtPi = 1.77245385090551602730;
 constexpr double kWindowC = 0.95;  // Alg. 1 step 4
 constexpr int kMaxP = 32;          // support width limit (one warp lane per point)
+constexpr int kCellReach = 2;      // real-space cells per r_c (cell side >= r_c / kCellReach)
 constexpr int kMaxComp = 25;       // most spread components of any kernel combination
 
 // Layout of the FFT buffers: padded grid Nx x Ny x Nz = 2Mt x 2Mt x 4Mt, in-place

@@ -530,7 +530,10 @@ extern "C" hse_status hse_plan_create(int kernel_mask, const double box[3], doub
   hse_status st = choose_params(p, xi, rc, P, tol);
   if (st == HSE_OK) {
     for (int d = 0; d < 3; ++d) {
-      double nc = std::floor(box[d] / q.rc);
+      // cells of side >= r_c / kCellReach: the neighbour scan covers
+      // (2 kCellReach + 1)^3 cells, 15.6 r_c^3 of candidates for a reach of 2
+      // against 27 r_c^3 with cells of side r_c
+      double nc = std::floor(box[d] * kCellReach / q.rc);
       if (nc < 1) nc = 1;
       if (nc > 1024) nc = 1024;
       q.ncell[d] = (int)nc;

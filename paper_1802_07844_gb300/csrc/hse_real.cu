@@ -295,13 +295,14 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
   bool want_img = x[2] < a.rc && !(a.mask & HSE_FREE_SPACE);
   int czi_hi = want_img ? cell_coord(a.rc - x[2], a.inv_cell[2], nz) : -1;
   for (int pass = 0; pass < 2; ++pass) {
-    int z0 = pass == 0 ? (cz > 0 ? cz - 1 : 0) : 0;
-    int z1 = pass == 0 ? (cz < nz - 1 ? cz + 1 : nz - 1) : czi_hi;
+    constexpr int R = kCellReach;
+    int z0 = pass == 0 ? (cz > R - 1 ? cz - R : 0) : 0;
+    int z1 = pass == 0 ? (cz < nz - R ? cz + R : nz - 1) : czi_hi;
     int jmin = pass == 0 ? free_min : img_min;
     for (int iz = z0; iz <= z1; ++iz)
-      for (int iy = (cy > 0 ? cy - 1 : 0); iy <= (cy < ny - 1 ? cy + 1 : ny - 1); ++iy) {
+      for (int iy = (cy > R - 1 ? cy - R : 0); iy <= (cy < ny - R ? cy + R : ny - 1); ++iy) {
         // x-neighbours are contiguous in the cell numbering
-        int xa = cx > 0 ? cx - 1 : 0, xb = cx < nx - 1 ? cx + 1 : nx - 1;
+        int xa = cx > R - 1 ? cx - R : 0, xb = cx < nx - R ? cx + R : nx - 1;
         int c0 = base + (iz * ny + iy) * nx + xa;
         int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
         if (s0 < jmin) s0 = jmin;
@@ -631,9 +632,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_close_images(RealArgs a
     int czi_hi = cell_coord(a.rc - x.d[2], a.inv_cell[2], nz);
     const int base = cell_base(a, w);
     double u[3] = {0.0, 0.0, 0.0};
+    constexpr int R = kCellReach;
     for (int iz = 0; iz <= czi_hi; ++iz)
-      for (int iy = (cy > 0 ? cy - 1 : 0); iy <= (cy < ny - 1 ? cy + 1 : ny - 1); ++iy) {
-        int xa = cx > 0 ? cx - 1 : 0, xb = cx < nx - 1 ? cx + 1 : nx - 1;
+      for (int iy = (cy > R - 1 ? cy - R : 0); iy <= (cy < ny - R ? cy + R : ny - 1); ++iy) {
+        int xa = cx > R - 1 ? cx - R : 0, xb = cx < nx - R ? cx + R : nx - 1;
         int c0 = base + (iz * ny + iy) * nx + xa;
         int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
         for (int j = s0 + lane; j < s1; j += 32) {

@@ -144,7 +144,9 @@ def test_fourier_part_matches_numpy_alg1(pkg, mask):
     _, uf = plan.eval_parts(dev(pr.src), dev(pr.strengths))
     uf = host(uf)
     ref = se.fourier_part_derivative(mask, pr.src, pr.strengths, xi, 1.0, M, P)
-    assert oracle.rel_rms(uf, ref) < 1e-12
+    # rounding level; the stresslet's second-derivative terms of D cancel, so
+    # its sums are the most sensitive to the accumulation order
+    assert oracle.rel_rms(uf, ref) < 5e-12
     # the derivative windows truncate a little worse than the window itself
     # (up to ~6x at equal P; the plan's parameter choice absorbs it, see
     # test_gpu_tolerance.py)
