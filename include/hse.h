@@ -61,6 +61,12 @@ enum { HSE_STOKESLET = 1, HSE_STRESSLET = 2, HSE_ROTLET = 4, HSE_FREE_SPACE = 8 
 /* arithmetic of the path: HSE_FP64 everywhere (for tolerances down to 1e-10),
  * HSE_MIXED: FP32 real space, spreading, FFT and gather (tolerances >= 1e-6) */
 enum { HSE_FP64 = 0, HSE_MIXED = 1 };
+/* transforms of the Fourier part (hse_plan_set_fft): HSE_FFT_DF64 runs the
+ * zero-padded FFTs and the scaling of HSE_FP64 plans in double-float (~48-bit)
+ * arithmetic on the FP32 pipe, HSE_FFT_CUFFT in cuFFT double (HSE_MIXED plans:
+ * cuFFT single); HSE_FFT_AUTO picks HSE_FFT_DF64 for HSE_FP64 plans with
+ * tol >= 1e-12 or explicit parameters, HSE_FFT_CUFFT otherwise. */
+enum { HSE_FFT_AUTO = 0, HSE_FFT_CUFFT = 1, HSE_FFT_DF64 = 2 };
 
 /* Parameters of a plan, as chosen or given (Alg. 1 notation). */
 typedef struct {
@@ -84,6 +90,7 @@ typedef struct {
   int ncell[3];      /* real-space cell list dimensions (cell side >= rc / 2)      */
   int n_fft_in;      /* number of forward FFTs per evaluation                      */
   int n_fft_out;     /* number of inverse FFTs per evaluation (6)                  */
+  int fft;           /* transforms: HSE_FFT_DF64 or HSE_FFT_CUFFT (see hse_plan_set_fft) */
   size_t grid_bytes; /* device bytes held by grids and tables                      */
 } hse_params;
 
@@ -120,6 +127,13 @@ hse_status hse_plan_get_params(hse_plan plan, hse_params* out);
  * hse_params); rc64 >= rc evaluates everything in FP64.
  * HSE_ERR_INVALID for rc64 < 0 or an HSE_MIXED plan. */
 hse_status hse_plan_set_rc64(hse_plan plan, double rc64);
+
+/* Choose the transforms of the Fourier part (HSE_FFT_AUTO, HSE_FFT_CUFFT or
+ * HSE_FFT_DF64; hse_params.fft reports the choice).  Builds what the choice
+ * needs when the grids exist (synchronous).  HSE_ERR_INVALID for an unknown
+ * mode or HSE_FFT_DF64 on an HSE_MIXED plan; HSE_ERR_UNSUPPORTED when the grid
+ * has a length with a prime factor other than 2, 3, 5. */
+hse_status hse_plan_set_fft(hse_plan plan, int mode);
 
 /*
  * hse_eval -- velocities at the targets.
@@ -208,7 +222,7 @@ enum {
 
 typedef struct {
   int n_kernel_launches;            /* kernels of this library launched by the last evaluation */
-  int n_fft_execs;                  /* cuFFT executions of the last evaluation                  */
+  int n_fft_execs;                  /* 3-D transforms (one per buffer) of the last evaluation   */
   int timing;                       /* 1 when stage_ms is valid                                 */
   double stage_ms[HSE_N_STAGES];    /* device time of each stage (CUDA events on its stream)   */
   int overlapped;                   /* 1: the real stage ran concurrently with SPREAD..GATHER  */

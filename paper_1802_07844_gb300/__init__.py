@@ -9,6 +9,6 @@ C ABI of ``include/hse.h`` (cuFFT for the transforms).
 
 ``hse`` is the ctypes binding; ``build`` compiles the library in-tree.
 """
-from .hse import (HSE_FP64, HSE_FREE_SPACE, HSE_MIXED, HSE_ROTLET, HSE_STOKESLET, HSE_STRESSLET, Batch, HseError, Plan,  # noqa: F401
+from .hse import (HSE_FFT_AUTO, HSE_FFT_CUFFT, HSE_FFT_DF64, HSE_FP64, HSE_FREE_SPACE, HSE_MIXED, HSE_ROTLET, HSE_STOKESLET, HSE_STRESSLET, Batch, HseError, Plan,  # noqa: F401
                   hse_cell_list, hse_eval, hse_eval_parts, hse_get_eval_stats, hse_plan_set_timing, hse_neighbor_counts, hse_plan_create,
-                  hse_plan_destroy, hse_plan_get_params, hse_plan_set_grid, hse_spread_grids, load)
+                  hse_plan_destroy, hse_plan_get_params, hse_plan_set_fft, hse_plan_set_grid, hse_spread_grids, load)

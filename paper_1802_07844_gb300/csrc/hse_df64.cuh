@@ -1,0 +1,103 @@
+// hse_df64.cuh -- double-float ("df64") arithmetic on the FP32 pipe.
+//
+// A df64 value is the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits.  Sums and products use the
+// error-free transformations of Knuth (two-sum), Dekker (fast two-sum) and the
+// FMA two-product; the addition is the cheap ("sloppy") variant that adds the
+// low parts without their own error term, whose error is bounded relative to
+// |a| + |b| (enough for transforms, whose error analysis is norm-wise).
+// Reference: Y. Hida, X. S. Li, D. H. Bailey, "Library for double-double and
+// quad-double arithmetic" (2007), and A. Thall, "Extended-precision
+// floating-point numbers for GPU computation" (2006).
+//
+// GB300 issues 128 FP32 lanes per SM and clock against 2 FP64 instructions, so
+// a df64 operation of 5-11 FP32 instructions is several times cheaper than its
+// FP64 counterpart; double <-> float conversions run at the FP64 rate and are
+// kept to the edges of a computation.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace hse {
+
+struct df {
+  float hi, lo;
+  __device__ __forceinline__ df() {}
+  __device__ __forceinline__ df(float h, float l) : hi(h), lo(l) {}
+  // exact for integers of magnitude < 2^24
+  __device__ __forceinline__ df(int i) : hi((float)i), lo(0.f) {}
+  // rounds to ~48 bits (FP64-pipe conversions)
+  __device__ __forceinline__ df(double d) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+  }
+  __device__ __forceinline__ double to_double() const { return (double)hi + (double)lo; }
+};
+
+// s + e == a + b exactly, provided |a| >= |b| or a == 0
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df operator+(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+// product with a float that is exact in df64 (an integer or a power of two)
+__device__ __forceinline__ df operator*(df a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df operator*(float b, df a) { return a * b; }
+__device__ __forceinline__ df operator*(df a, int i) { return a * (float)i; }
+
+// complex df64, laid out like a complex double (16 bytes)
+struct __align__(16) cdf {
+  df x, y;
+};
+
+__device__ __forceinline__ cdf cdf_make(df x, df y) {
+  cdf r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+__device__ __forceinline__ cdf operator+(cdf a, cdf b) { return cdf_make(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cdf operator-(cdf a, cdf b) { return cdf_make(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cdf operator*(cdf a, cdf b) {
+  return cdf_make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ cdf operator*(df s, cdf a) { return cdf_make(s * a.x, s * a.y); }
+__device__ __forceinline__ cdf conj(cdf a) { return cdf_make(a.x, -a.y); }
+// multiply by -i (forward transforms) or +i (inverse)
+template <bool FWD>
+__device__ __forceinline__ cdf mul_mi(cdf a) {
+  return FWD ? cdf_make(a.y, -a.x) : cdf_make(-a.y, a.x);
+}
+
+__device__ __forceinline__ cdf ld_cdf(const float4* p) {
+  const float4 v = *p;
+  return cdf_make(df(v.x, v.y), df(v.z, v.w));
+}
+__device__ __forceinline__ cdf ldg_cdf(const float4* p) {
+  const float4 v = __ldg(p);
+  return cdf_make(df(v.x, v.y), df(v.z, v.w));
+}
+__device__ __forceinline__ void st_cdf(float4* p, cdf a) { *p = make_float4(a.x.hi, a.x.lo, a.y.hi, a.y.lo); }
+
+}  // namespace hse

@@ -1,0 +1,429 @@
+// hse_fft64.cu -- zero-padded 3-D transforms of the FP64 path in double-float
+// (df64) arithmetic on the FP32 pipe.
+//
+// The Fourier part of the method (Sec. 4: spread, zero-padded 3-D FFT, scale,
+// inverse FFT, gather) spends most of its FP64 time in the transforms, and on
+// GB300 cuFFT's double kernels are bound by the FP64 pipe (2 instructions per
+// SM and clock).  These transforms do the same linear maps with ~48-bit
+// double-float arithmetic on the 64x wider FP32 pipe; their rounding error
+// (~1e-14 of the data norm) is far below the tolerances the FP64 path serves.
+//
+// Storage: a complex df64 value occupies the 16 bytes of a complex double
+// ({re.hi, re.lo, im.hi, im.lo}), so the grids keep their layout.  The forward
+// z pass reads the spread's doubles and writes df64 half spectra in place;
+// every later pass, and the scaling, stays df64; the inverse z pass writes
+// doubles back for the gather.  Only those two passes convert.
+//
+// Each pass is a batched 1-D transform of lines.  A block holds LPB lines in
+// shared memory (element e of line l at e * LPB + l) and runs a mixed-radix
+// Stockham autosort transform over them (radices 4, 2, 5, 3), each thread
+// keeping its butterflies in registers across the barrier between the reads
+// and the writes of a pass.
+#include <cmath>
+#include <vector>
+
+#include "hse_df64.cuh"
+#include "hse_internal.cuh"
+
+namespace hse {
+
+// ---------------------------------------------------------------- schedule
+constexpr int kMaxPass = 24;
+
+struct FftSteps {
+  int N;                 // line length (complex points)
+  int npass;
+  int R[kMaxPass];       // radix of each pass
+  int Ns[kMaxPass];      // product of the earlier radices
+  int step[kMaxPass];    // N / (Ns R): twiddle index step
+  unsigned magic[kMaxPass];  // ceil(2^32 / Ns) (exact j / Ns for j, Ns < 2^16)
+  float kc[10];          // hi / lo of sin(2pi/3), cos(2pi/5), cos(4pi/5), sin(2pi/5), sin(4pi/5)
+};
+
+static bool make_steps(int N, FftSteps* st) {
+  if (N < 2 || N >= 65536) return false;
+  FftSteps s{};
+  s.N = N;
+  int rem = N, Ns = 1;
+  while (rem > 1) {
+    int R = rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 5 == 0 ? 5 : rem % 3 == 0 ? 3 : 0;
+    if (R == 0 || s.npass == kMaxPass) return false;
+    s.R[s.npass] = R;
+    s.Ns[s.npass] = Ns;
+    s.step[s.npass] = N / (Ns * R);
+    s.magic[s.npass] = Ns == 1 ? 0u : (unsigned)((((uint64_t)1 << 32) + Ns - 1) / Ns);
+    ++s.npass;
+    Ns *= R;
+    rem /= R;
+  }
+  const double c[5] = {std::sin(2 * M_PI / 3), std::cos(2 * M_PI / 5), std::cos(4 * M_PI / 5), std::sin(2 * M_PI / 5),
+                       std::sin(4 * M_PI / 5)};
+  for (int i = 0; i < 5; ++i) {
+    float h = (float)c[i];
+    s.kc[2 * i] = h;
+    s.kc[2 * i + 1] = (float)(c[i] - (double)h);
+  }
+  *st = s;
+  return true;
+}
+
+// threads per line: one radix-4 butterfly each when 4 | N, else one radix-2
+static int threads_per_line(int N) { return N % 4 == 0 ? N / 4 : N / 2; }
+
+// lines per block: a power of two, at most 512 threads and 16 lines
+static int lines_per_block_log2(int N) {
+  int tpl = threads_per_line(N), lsh = 0;
+  while (lsh < 4 && (tpl << (lsh + 1)) <= 512) ++lsh;
+  return lsh;
+}
+
+// ------------------------------------------------------------- butterflies
+template <bool FWD>
+__device__ __forceinline__ void dft2(cdf* v) {
+  const cdf a = v[0], b = v[1];
+  v[0] = a + b;
+  v[1] = a - b;
+}
+template <bool FWD>
+__device__ __forceinline__ void dft4(cdf* v) {
+  const cdf a0 = v[0] + v[2], a1 = v[0] - v[2];
+  const cdf b0 = v[1] + v[3], b1 = mul_mi<FWD>(v[1] - v[3]);
+  v[0] = a0 + b0;
+  v[2] = a0 - b0;
+  v[1] = a1 + b1;
+  v[3] = a1 - b1;
+}
+template <bool FWD>
+__device__ __forceinline__ void dft3(cdf* v, const float* kc) {
+  const df s3(kc[0], kc[1]);
+  const cdf t = v[1] + v[2];
+  const cdf a = v[0] - df(0.5f, 0.f) * t;
+  const cdf b = mul_mi<FWD>(s3 * (v[1] - v[2]));
+  v[0] = v[0] + t;
+  v[1] = a + b;
+  v[2] = a - b;
+}
+template <bool FWD>
+__device__ __forceinline__ void dft5(cdf* v, const float* kc) {
+  const df c1(kc[2], kc[3]), c2(kc[4], kc[5]), s1(kc[6], kc[7]), s2(kc[8], kc[9]);
+  const cdf t1 = v[1] + v[4], t2 = v[2] + v[3];
+  const cdf t3 = v[1] - v[4], t4 = v[2] - v[3];
+  const cdf a1 = v[0] + (c1 * t1 + c2 * t2);
+  const cdf a2 = v[0] + (c2 * t1 + c1 * t2);
+  const cdf b1 = mul_mi<FWD>(s1 * t3 + s2 * t4);
+  const cdf b2 = mul_mi<FWD>(s2 * t3 - s1 * t4);
+  v[0] = v[0] + (t1 + t2);
+  v[1] = a1 + b1;
+  v[4] = a1 - b1;
+  v[2] = a2 + b2;
+  v[3] = a2 - b2;
+}
+
+template <bool FWD>
+__device__ __forceinline__ cdf twiddle(const float4* __restrict__ tw, int idx) {
+  const cdf w = ldg_cdf(tw + idx);
+  return FWD ? w : conj(w);
+}
+
+// One Stockham pass (radix R, Ns = product of the earlier radices) over the
+// block's lines: butterfly j < N / R reads elements j + t N / R, multiplies
+// element t by w_N^{t (j mod Ns) N / (Ns R)}, transforms, and writes output t
+// to (j div Ns) Ns R + (j mod Ns) + t Ns.  A thread takes butterflies tj (and
+// tj + TPL) of line l: with TPL = N / 4 (or N / 2 when 4 does not divide N)
+// radices 2 and 3 need at most two butterflies per thread, 4 and 5 one.
+template <int R, bool FWD>
+__device__ __forceinline__ void stockham_pass(float4* s, int N, int Ns, int step, unsigned magic, const float* kc,
+                                              int tpl, int lsh, int l, int tj, const float4* __restrict__ tw) {
+  constexpr int MB = R <= 3 ? 2 : 1;
+  const int nb = N / R;
+  cdf v[MB][R];
+  int dst[MB];
+#pragma unroll
+  for (int m = 0; m < MB; ++m) {
+    const int j = tj + m * tpl;
+    dst[m] = -1;
+    if (j < nb) {
+      const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, magic);
+      const int k = j - q * Ns;
+#pragma unroll
+      for (int t = 0; t < R; ++t) v[m][t] = ld_cdf(s + ((j + t * nb) << lsh) + l);
+      if (k != 0) {
+#pragma unroll
+        for (int t = 1; t < R; ++t) v[m][t] = v[m][t] * twiddle<FWD>(tw, t * k * step);
+      }
+      if (R == 2) dft2<FWD>(v[m]);
+      else if (R == 4) dft4<FWD>(v[m]);
+      else if (R == 3) dft3<FWD>(v[m], kc);
+      else dft5<FWD>(v[m], kc);
+      dst[m] = q * Ns * R + k;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < MB; ++m)
+    if (dst[m] >= 0) {
+#pragma unroll
+      for (int t = 0; t < R; ++t) st_cdf(s + ((dst[m] + t * Ns) << lsh) + l, v[m][t]);
+    }
+  __syncthreads();
+}
+
+// all passes; the result is in natural order in s.  The schedule lives in
+// device memory (uniform loads) so that the pass loop indexes it freely.
+template <bool FWD>
+__device__ __forceinline__ void transform_block(float4* s, const FftSteps* __restrict__ st, int lsh,
+                                                const float4* __restrict__ tw) {
+  const int tpl = blockDim.x >> lsh;
+  const int l = threadIdx.x & ((1 << lsh) - 1), tj = threadIdx.x >> lsh;
+  const int N = st->N, npass = st->npass;
+  const float* kc = st->kc;
+  for (int p = 0; p < npass; ++p) {
+    const int Ns = st->Ns[p], step = st->step[p];
+    const unsigned magic = st->magic[p];
+    switch (st->R[p]) {
+      case 4: stockham_pass<4, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      case 2: stockham_pass<2, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      case 5: stockham_pass<5, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      default: stockham_pass<3, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+    }
+  }
+}
+
+// ------------------------------------------------------------ line geometry
+// Line b (< nlines) of a pass: r = b mod n0, g1 = (b div n0) mod n1,
+// g2 = b div (n0 n1); it starts at g2 s2 + g1 s1 + r ls and its elements are
+// es apart (units: complex values for C2C passes, doubles for the z passes).
+struct LineGeo {
+  long long nlines, n0, n1, ls, s1, s2, es;
+};
+
+__device__ __forceinline__ long long line_start(const LineGeo& g, long long b) {
+  const long long t = b / g.n0, r = b - t * g.n0;
+  const long long g2 = t / g.n1, g1 = t - g2 * g.n1;
+  return g2 * g.s2 + g1 * g.s1 + r * g.ls;
+}
+
+// table of w_N^k = exp(-2 pi i k / N), k < N, rounded from FP64
+__global__ void k_twiddles(int N, float4* __restrict__ tw) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)k / (double)N, &sn, &cs);
+    const df c(cs), si(sn);
+    tw[k] = make_float4(c.hi, c.lo, si.hi, si.lo);
+  }
+}
+
+// ------------------------------------------------------------ C2C passes
+template <bool FWD>
+__global__ void __launch_bounds__(512, 1) k_fft_lines(float4* __restrict__ data, LineGeo g,
+                                                      const FftSteps* __restrict__ st, int lsh,
+                                                      const float4* __restrict__ tw) {
+  extern __shared__ float4 sm[];
+  __shared__ long long start[16];
+  const int lpb = 1 << lsh, n = st->N << lsh;
+  for (long long b0 = (long long)blockIdx.x * lpb; b0 < g.nlines; b0 += (long long)gridDim.x * lpb) {
+    if (threadIdx.x < lpb) start[threadIdx.x] = b0 + threadIdx.x < g.nlines ? line_start(g, b0 + threadIdx.x) : -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const long long o = start[i & (lpb - 1)];
+      sm[i] = o >= 0 ? data[o + (long long)(i >> lsh) * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    transform_block<FWD>(sm, st, lsh, tw);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const long long o = start[i & (lpb - 1)];
+      if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = sm[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------- real <-> half spectrum (z)
+// A real line of 2N doubles x (contiguous) is transformed as the N complex
+// values z_n = x_2n + i x_2n+1: with Z = DFT_N z, the half spectrum of x is
+// X_k = (Z_k + conj Z_{N-k}) / 2 - i w^k (Z_k - conj Z_{N-k}) / 2, k = 0..N,
+// w = exp(-2 pi i / 2N), written in place over the line (2N + 2 doubles hold
+// N + 1 complex df64 values).  The inverse forms Z_k = (X_k + conj X_{N-k})
+// + i conj(w^k) (X_k - conj X_{N-k}), transforms back (unnormalised, like a
+// C2R transform) and writes the first nkeep doubles of the line.
+template <bool FWD>
+__global__ void __launch_bounds__(512, 1) k_fft_z(double* __restrict__ data, LineGeo g, const FftSteps* __restrict__ st,
+                                                  int lsh, const float4* __restrict__ tw,
+                                                  const float4* __restrict__ tw2, int nkeep) {
+  extern __shared__ float4 sm[];
+  __shared__ long long start[16];
+  const int lpb = 1 << lsh, N = st->N;
+  for (long long b0 = (long long)blockIdx.x * lpb; b0 < g.nlines; b0 += (long long)gridDim.x * lpb) {
+    if (threadIdx.x < lpb) start[threadIdx.x] = b0 + threadIdx.x < g.nlines ? line_start(g, b0 + threadIdx.x) : -1;
+    __syncthreads();
+    for (int l = 0; l < lpb; ++l) {
+      const long long o = start[l];
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        cdf z = cdf_make(df(0.f, 0.f), df(0.f, 0.f));
+        if (o >= 0) {
+          if (FWD) {
+            const double2 x = *reinterpret_cast<const double2*>(data + o + 2 * k);
+            z = cdf_make(df(x.x), df(x.y));
+          } else {
+            const float4* X = reinterpret_cast<const float4*>(data + o);
+            const cdf xk = ld_cdf(X + k), xn = conj(ld_cdf(X + N - k));
+            const cdf wk = conj(ldg_cdf(tw2 + k));
+            z = (xk + xn) + mul_mi<false>(wk * (xk - xn));
+          }
+        }
+        st_cdf(sm + (k << lsh) + l, z);
+      }
+    }
+    __syncthreads();
+    transform_block<FWD>(sm, st, lsh, tw);
+    for (int l = 0; l < lpb; ++l) {
+      const long long o = start[l];
+      if (o < 0) continue;
+      if (FWD) {
+        float4* X = reinterpret_cast<float4*>(data + o);
+        const df half(0.5f, 0.f);
+        for (int k = threadIdx.x; k <= N; k += blockDim.x) {
+          const cdf zk = ld_cdf(sm + ((k == N ? 0 : k) << lsh) + l);
+          const cdf zn = conj(ld_cdf(sm + ((k == 0 ? 0 : N - k) << lsh) + l));
+          const cdf ev = half * (zk + zn), od = half * (zk - zn);
+          st_cdf(X + k, ev + mul_mi<true>(ldg_cdf(tw2 + k) * od));
+        }
+      } else {
+        for (int k = threadIdx.x; 2 * k < nkeep; k += blockDim.x) {
+          const cdf z = ld_cdf(sm + (k << lsh) + l);
+          if (2 * k + 1 < nkeep)
+            *reinterpret_cast<double2*>(data + o + 2 * k) = make_double2(z.x.to_double(), z.y.to_double());
+          else
+            data[o + 2 * k] = z.x.to_double();
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ driver
+struct Fft64Tables {
+  FftSteps sx, sz;           // x / y lines (length Nx = Ny) and z half-lines (Nz / 2)
+  FftSteps* d_steps = nullptr;  // device copies {sx, sz}
+  float4* tw = nullptr;      // twiddles of lengths Nx, Nz / 2 and Nz, back to back
+};
+
+static Fft64Tables* tables(hse_plan p) { return reinterpret_cast<Fft64Tables*>(p->fft64); }
+
+// lengths whose schedule uses radices 2, 3, 4, 5 only and whose line fits
+// one block (threads_per_line <= 512)
+bool fft64_supported(int Nx, int Ny, int Nz) {
+  FftSteps a, b;
+  return Nx == Ny && Nz % 2 == 0 && make_steps(Nx, &a) && make_steps(Nz / 2, &b) && threads_per_line(Nx) <= 512 &&
+         threads_per_line(Nz / 2) <= 512;
+}
+
+hse_status fft64_prepare(hse_plan p) {
+  if (p->fft64) return HSE_OK;
+  const GridDims& g = p->g;
+  if (!fft64_supported(g.Nx, g.Ny, g.Nz))
+    return set_err(p, HSE_ERR_UNSUPPORTED, "df64 FFT: grid %d x %d x %d", g.Nx, g.Ny, g.Nz);
+  Fft64Tables* t = new Fft64Tables();
+  make_steps(g.Nx, &t->sx);
+  make_steps(g.Nz / 2, &t->sz);
+  const int n1 = g.Nx, nh = g.Nz / 2;
+  cudaError_t e = cudaMalloc(&t->tw, sizeof(float4) * (n1 + nh + 2 * nh));
+  if (e != cudaSuccess) {
+    delete t;
+    return cuda_check(p, e, "cudaMalloc(df64 twiddles)");
+  }
+  p->fft64 = t;
+  HSE_CUDA(p, cudaMalloc(&t->d_steps, 2 * sizeof(FftSteps)));
+  HSE_CUDA(p, cudaMemcpy(t->d_steps, &t->sx, sizeof(FftSteps), cudaMemcpyHostToDevice));
+  HSE_CUDA(p, cudaMemcpy(t->d_steps + 1, &t->sz, sizeof(FftSteps), cudaMemcpyHostToDevice));
+  k_twiddles<<<(n1 + 255) / 256, 256>>>(n1, t->tw);
+  k_twiddles<<<(nh + 255) / 256, 256>>>(nh, t->tw + n1);
+  k_twiddles<<<(2 * nh + 255) / 256, 256>>>(2 * nh, t->tw + n1 + nh);
+  HSE_CUDA(p, cudaGetLastError());
+  HSE_CUDA(p, cudaDeviceSynchronize());
+  static bool attr = false;
+  if (!attr) {
+    // a block holds (threads / TPL) lines of N points: at most 512 threads and
+    // TPL >= N / 4, so at most 2048 points, 32 KB
+    const int cap = 64 * 1024;
+    cudaFuncSetAttribute(k_fft_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute(k_fft_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute(k_fft_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute(k_fft_z<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    attr = true;
+  }
+  return HSE_OK;
+}
+
+void fft64_destroy(hse_plan p) {
+  Fft64Tables* t = tables(p);
+  if (!t) return;
+  cudaFree(t->tw);
+  cudaFree(t->d_steps);
+  delete t;
+  p->fft64 = nullptr;
+}
+
+static unsigned grid_for(long long nlines, int lsh) {
+  long long blocks = (nlines + (1 << lsh) - 1) >> lsh;
+  const long long cap = 152LL * 3 * 32;
+  return (unsigned)(blocks < cap ? blocks : cap);
+}
+
+static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fwd, cudaStream_t s) {
+  const Fft64Tables* t = tables(p);
+  const int lsh = lines_per_block_log2(t->sx.N);
+  const unsigned threads = (unsigned)(threads_per_line(t->sx.N) << lsh);
+  const size_t shm = sizeof(float4) * ((size_t)t->sx.N << lsh);
+  if (geo.nlines <= 0) return HSE_OK;
+  float4* c = reinterpret_cast<float4*>(buf);
+  if (fwd) k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw);
+  else k_fft_lines<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), "k_fft_lines");
+}
+
+static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, int nkeep, cudaStream_t s) {
+  const Fft64Tables* t = tables(p);
+  const int N = t->sz.N, lsh = lines_per_block_log2(N);
+  const unsigned threads = (unsigned)(threads_per_line(N) << lsh);
+  const size_t shm = sizeof(float4) * ((size_t)N << lsh);
+  if (geo.nlines <= 0) return HSE_OK;
+  const float4* tw = t->tw + t->sx.N;
+  const float4* tw2 = tw + N;
+  if (fwd) k_fft_z<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep);
+  else k_fft_z<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), fwd ? "k_fft_z<fwd>" : "k_fft_z<inv>");
+}
+
+// Geometry of the grids: buffer b's real element (x, y, z) at
+// x * xs + b * bs + y * pitch + z (doubles), nb buffers transformed together.
+// Data occupy x < Mt, y < Mt, z < 2 Mt and the rest of the real grid is zero
+// on input.  As complex values the half spectrum (kx, ky, kz) of buffer b sits
+// at (kx * xs + b * bs) / 2 + ky * nzh + kz.
+hse_status fft64_forward(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s) {
+  const GridDims& g = p->g;
+  const long long Mt = g.Mt, nzh = g.Nz / 2 + 1, pitch = g.pitch;
+  // z: lines (x < Mt, b, y < Mt)
+  HSE_TRY(run_z(p, base, LineGeo{Mt * nb * Mt, Mt, nb, pitch, bs, xs, 1}, true, 0, s));
+  // y: lines (x < Mt, b, kz), elements y
+  HSE_TRY(run_lines(p, base, LineGeo{Mt * nb * nzh, nzh, nb, 1, bs / 2, xs / 2, nzh}, true, s));
+  // x: lines (b, y, kz) of every buffer, elements x
+  return run_lines(p, base, LineGeo{(long long)nb * g.Ny * nzh, (long long)g.Ny * nzh, nb, 1, bs / 2, 0, xs / 2},
+                   true, s);
+}
+
+// Inverse (unnormalised): df64 half spectra -> doubles at x < Mt, y < Mt,
+// z < 2 Mt of each of the nb buffers (the rest is left undefined).
+hse_status fft64_inverse(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s) {
+  const GridDims& g = p->g;
+  const long long Mt = g.Mt, nzh = g.Nz / 2 + 1, pitch = g.pitch;
+  HSE_TRY(run_lines(p, base, LineGeo{(long long)nb * g.Ny * nzh, (long long)g.Ny * nzh, nb, 1, bs / 2, 0, xs / 2},
+                    false, s));
+  HSE_TRY(run_lines(p, base, LineGeo{Mt * nb * nzh, nzh, nb, 1, bs / 2, xs / 2, nzh}, false, s));
+  return run_z(p, base, LineGeo{Mt * nb * Mt, Mt, nb, pitch, bs, xs, 1}, false, (int)(2 * Mt), s);
+}
+
+}  // namespace hse

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "hse_df64.cuh"
 #include "hse_internal.cuh"
 
 namespace hse {
@@ -383,9 +384,14 @@ __global__ void k_mirror(MirrorArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------- scale
+// T: arithmetic of the scaling (double, float, or df for double-float
+// spectra); Tab<T>: element type of the kernel tables it reads
 template <typename T> struct Cplx;
 template <> struct Cplx<double> { typedef double2 type; };
 template <> struct Cplx<float> { typedef float2 type; };
+template <> struct Cplx<df> { typedef cdf type; };
+template <typename T> struct Tab { typedef T type; };
+template <> struct Tab<df> { typedef double type; };
 
 template <typename T>
 struct ScaleArgs {
@@ -393,8 +399,8 @@ struct ScaleArgs {
   int64_t cstride;              // complex elements per buffer
   int Mt, mask;
   double h;
-  const T* tabB;
-  const T* tabH;
+  const typename Tab<T>::type* tabB;
+  const typename Tab<T>::type* tabH;
   int iS, iT, iW, iD;  // first component index of each group (C1 of S, T, W; correction grid), -1 if absent
   int n_inst;
   int64_t istride;     // complex elements between instances of one component
@@ -432,8 +438,8 @@ __global__ void k_scale(ScaleArgs<T> a) {
       T k[3] = {dkx * wx, dkx * wy, dkz * jz};
       T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
       int64_t ti = ((int64_t)abs(wx) * (Mt + 1) + abs(wy)) * Nzh + jz;
-      T TH = a.tabH[ti];
-      T TB = a.tabB ? a.tabB[ti] : (T)0;
+      T TH = (T)a.tabH[ti];
+      T TB = a.tabB ? (T)a.tabB[ti] : (T)0;
       auto ld = [&](int c) { return a.buf[c * a.cstride + e]; };
       if (a.iS >= 0) {  // -(k^2 I - k k) (1 + k^2/4xi^2) E B^R C1
         C Cv[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
@@ -712,6 +718,37 @@ static cufftResult fft_inverse(hse_plan p, float* b) {
   return r == CUFFT_SUCCESS ? cufftExecC2R(p->inv2d, z, b) : r;
 }
 
+// Scale the spectra of n_inst instances (component c of instance i, mode
+// (kx, ky, kz) at c cstride + i istride + kx xstride + ky nzh + kz complex
+// elements) in the arithmetic S, in place.
+template <typename S>
+static hse_status launch_scale(hse_plan p, void* spec, int64_t cstride, int n_inst, int64_t istride, int64_t xstride,
+                               cudaStream_t s) {
+  const hse_params& q = p->prm;
+  const GridDims& g = p->g;
+  ScaleArgs<S> sa;
+  sa.buf = reinterpret_cast<typename Cplx<S>::type*>(spec);
+  sa.cstride = cstride;
+  sa.Mt = q.Mt;
+  sa.mask = q.kernel_mask;
+  sa.h = q.h;
+  sa.tabB = reinterpret_cast<const typename Tab<S>::type*>(p->tabB);
+  sa.tabH = reinterpret_cast<const typename Tab<S>::type*>(p->tabH);
+  int k = 0;
+  sa.iS = sa.iT = sa.iW = sa.iD = -1;
+  if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
+  if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
+  if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
+  if (!free_space(q.kernel_mask)) sa.iD = k;
+  sa.nout = q.n_fft_out;
+  sa.n_inst = n_inst;
+  sa.istride = istride;
+  sa.xstride = xstride;
+  k_scale<S><<<blocks_for(g.nh * n_inst, 256, 152 * 32), 256, 0, s>>>(sa);
+  ++p->n_launch;
+  return cuda_check(p, cudaGetLastError(), "k_scale");
+}
+
 template <typename T>
 static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
                                   cudaStream_t s, cudaEvent_t gather_after) {
@@ -722,41 +759,35 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nin, s));
   HSE_TRY(spread_into<T>(p, n_src, p->comps, 0, spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
   stage_mark(p, HSE_STAGE_FFT, s);
-  if (cufftSetStream(p->fwd2d, s) != CUFFT_SUCCESS || cufftSetStream(p->inv2d, s) != CUFFT_SUCCESS ||
-      cufftSetStream(p->fftx, s) != CUFFT_SUCCESS)
-    return set_err(p, HSE_ERR_CUFFT, "cufftSetStream");
-  for (int c = 0; c < nin; ++c) {
-    cufftResult r = fft_forward(p, spec + c * g.buf_doubles);
-    ++p->n_fft;
-    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "forward FFT: %d", (int)r);
+  const bool df64 = sizeof(T) == 8 && q.fft == HSE_FFT_DF64;
+  const long long xs = (long long)g.Ny * g.pitch;
+  if (df64) {
+    HSE_TRY(fft64_forward(p, reinterpret_cast<double*>(spec), nin, g.buf_doubles, xs, s));
+    p->n_fft += nin;
+  } else {
+    if (cufftSetStream(p->fwd2d, s) != CUFFT_SUCCESS || cufftSetStream(p->inv2d, s) != CUFFT_SUCCESS ||
+        cufftSetStream(p->fftx, s) != CUFFT_SUCCESS)
+      return set_err(p, HSE_ERR_CUFFT, "cufftSetStream");
+    for (int c = 0; c < nin; ++c) {
+      cufftResult r = fft_forward(p, spec + c * g.buf_doubles);
+      ++p->n_fft;
+      if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "forward FFT: %d", (int)r);
+    }
   }
-  ScaleArgs<T> sa;
-  sa.buf = reinterpret_cast<typename Cplx<T>::type*>(spec);
-  sa.cstride = g.nh;
-  sa.Mt = q.Mt;
-  sa.mask = q.kernel_mask;
-  sa.h = q.h;
-  sa.tabB = reinterpret_cast<const T*>(p->tabB);
-  sa.tabH = reinterpret_cast<const T*>(p->tabH);
-  int k = 0;
-  sa.iS = sa.iT = sa.iW = sa.iD = -1;
-  if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
-  if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
-  if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
-  if (!free_space(q.kernel_mask)) sa.iD = k;
-  sa.nout = q.n_fft_out;
-  sa.n_inst = 1;
-  sa.istride = 0;
-  sa.xstride = (int64_t)g.Ny * (g.Nz / 2 + 1);
   stage_mark(p, HSE_STAGE_SCALE, s);
-  k_scale<T><<<blocks_for(g.nh, 256, 152 * 32), 256, 0, s>>>(sa);
-  ++p->n_launch;
-  HSE_CUDA(p, cudaGetLastError());
+  const int64_t planec = (int64_t)g.Ny * (g.Nz / 2 + 1);
+  if (df64) HSE_TRY(launch_scale<df>(p, spec, g.nh, 1, 0, planec, s));
+  else HSE_TRY(launch_scale<T>(p, spec, g.nh, 1, 0, planec, s));
   stage_mark(p, HSE_STAGE_IFFT, s);
-  for (int c = 0; c < q.n_fft_out; ++c) {
-    cufftResult r = fft_inverse(p, spec + c * g.buf_doubles);
-    ++p->n_fft;
-    if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "inverse FFT: %d", (int)r);
+  if (df64) {
+    HSE_TRY(fft64_inverse(p, reinterpret_cast<double*>(spec), q.n_fft_out, g.buf_doubles, xs, s));
+    p->n_fft += q.n_fft_out;
+  } else {
+    for (int c = 0; c < q.n_fft_out; ++c) {
+      cufftResult r = fft_inverse(p, spec + c * g.buf_doubles);
+      ++p->n_fft;
+      if (r != CUFFT_SUCCESS) return set_err(p, HSE_ERR_CUFFT, "inverse FFT: %d", (int)r);
+    }
   }
   stage_mark(p, HSE_STAGE_GATHER, s);
   if (n_tgt == 0) return HSE_OK;
@@ -840,6 +871,7 @@ static cufftHandle find_plan(const BatchFFT& f, int kind, int64_t batch, int64_t
 }
 
 hse_status batch_fft_prepare(hse_plan p, BatchFFT& f, int n_inst, char** work, int64_t* work_cap) {
+  if (p->prm.fft == HSE_FFT_DF64) return fft64_prepare(p);  // no cuFFT plans, no work area
   const GridDims& g = p->g;
   const bool mixed = p->prm.precision == HSE_MIXED;
   const long long nzh = g.Nz / 2 + 1;
@@ -942,31 +974,23 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nbuf, s));
   HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, plane * n_inst, plane * nbuf, g.pitch, s, n_inst, plane));
   stage_mark(p, HSE_STAGE_FFT, s);
-  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, true), spec, s));
+  const bool df64 = sizeof(T) == 8 && q.fft == HSE_FFT_DF64;
+  if (df64) {
+    HSE_TRY(fft64_forward(p, reinterpret_cast<double*>(spec), (int)nbuf, plane, plane * nbuf, s));
+    p->n_fft += (int)nbuf;
+  } else {
+    HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, true), spec, s));
+  }
   stage_mark(p, HSE_STAGE_SCALE, s);
-  ScaleArgs<T> sa;
-  sa.buf = reinterpret_cast<typename Cplx<T>::type*>(spec);
-  sa.cstride = planec * n_inst;
-  sa.istride = planec;
-  sa.xstride = planec * nbuf;
-  sa.n_inst = n_inst;
-  sa.Mt = q.Mt;
-  sa.mask = q.kernel_mask;
-  sa.h = q.h;
-  sa.tabB = reinterpret_cast<const T*>(p->tabB);
-  sa.tabH = reinterpret_cast<const T*>(p->tabH);
-  int k = 0;
-  sa.iS = sa.iT = sa.iW = sa.iD = -1;
-  if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }
-  if (q.kernel_mask & HSE_STRESSLET) { sa.iT = k; k += 6; }
-  if (q.kernel_mask & HSE_ROTLET) { sa.iW = k; k += 3; }
-  if (!free_space(q.kernel_mask)) sa.iD = k;
-  sa.nout = q.n_fft_out;
-  k_scale<T><<<blocks_for(g.nh * n_inst, 256, 152 * 32), 256, 0, s>>>(sa);
-  ++p->n_launch;
-  HSE_CUDA(p, cudaGetLastError());
+  if (df64) HSE_TRY(launch_scale<df>(p, spec, planec * n_inst, n_inst, planec, planec * nbuf, s));
+  else HSE_TRY(launch_scale<T>(p, spec, planec * n_inst, n_inst, planec, planec * nbuf, s));
   stage_mark(p, HSE_STAGE_IFFT, s);
-  HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, false), spec, s));
+  if (df64) {
+    HSE_TRY(fft64_inverse(p, reinterpret_cast<double*>(spec), q.n_fft_out * n_inst, plane, plane * nbuf, s));
+    p->n_fft += q.n_fft_out * n_inst;
+  } else {
+    HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, false), spec, s));
+  }
   stage_mark(p, HSE_STAGE_GATHER, s);
   GatherArgs<T> ga;
   ga.n_tgt = n_total;

@@ -113,6 +113,10 @@ struct hse_plan_s {
   // all (y, kz) lines (fftx, Z2Z both directions)
   cufftHandle fwd2d = 0, inv2d = 0, fftx = 0;
   bool have_fft = false;
+  // double-float transforms (prm.fft == HSE_FFT_DF64): twiddle tables
+  void* fft64 = nullptr;
+  int fft_mode = HSE_FFT_AUTO;  // requested; resolved into prm.fft when the grids are built
+  double tol = 0.0;  // tolerance the plan was created for (<= 0: explicit parameters)
   void* fft_work = nullptr;
   size_t fft_work_bytes = 0;
   hse::Workspace ws;
@@ -162,6 +166,14 @@ hse_status neighbor_counts(hse_plan p, int64_t n_src, int64_t n_tgt, const doubl
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
                          cudaStream_t s, cudaEvent_t gather_after = nullptr);
 hse_status spread_paper_grids(hse_plan p, int64_t n_src, double* grids, cudaStream_t s);
+// double-float zero-padded transforms of nb buffers, buffer b's real element
+// (x, y, z) at base + x * xs + b * bs + y * pitch + z (doubles); data at
+// x < Mt, y < Mt, z < 2 Mt (hse_fft64.cu)
+bool fft64_supported(int Nx, int Ny, int Nz);
+hse_status fft64_prepare(hse_plan p);
+void fft64_destroy(hse_plan p);
+hse_status fft64_forward(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s);
+hse_status fft64_inverse(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s);
 cudaError_t sort_keys_and_starts(int64_t n, int64_t ncells, int32_t* key_a, int32_t* val_a, int32_t* key_b,
                                  int32_t* val_b, int32_t* hist, int32_t* start_out, cudaStream_t s);
 hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of, double* out, cudaStream_t s);

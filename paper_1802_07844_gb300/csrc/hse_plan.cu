@@ -271,12 +271,66 @@ void free_grids(hse_plan p) {
     p->have_fft = false;
   }
   cudaFree(p->fft_work);
+  fft64_destroy(p);
   cudaFree(p->spec);
   cudaFree(p->tabB);
   cudaFree(p->tabH);
   p->fft_work = nullptr;
+  p->fft_work_bytes = 0;
   p->spec = p->tabB = p->tabH = nullptr;
   p->grid_ready = false;
+}
+
+// Transforms for the plan's grid.  Double-float transforms carry ~48-bit
+// arithmetic (rounding ~1e-14 of the data norm), so the automatic choice keeps
+// cuFFT double for tolerances below 1e-12; FP32 plans always use cuFFT single.
+constexpr double kDf64MinTol = 1e-12;
+static int resolve_fft(hse_plan p) {
+  const hse_params& q = p->prm;
+  if (q.precision != HSE_FP64) return HSE_FFT_CUFFT;
+  const bool ok = fft64_supported(p->g.Nx, p->g.Ny, p->g.Nz);
+  if (p->fft_mode == HSE_FFT_DF64) return ok ? HSE_FFT_DF64 : -1;
+  if (p->fft_mode == HSE_FFT_CUFFT) return HSE_FFT_CUFFT;
+  return ok && (p->tol <= 0.0 || p->tol >= kDf64MinTol) ? HSE_FFT_DF64 : HSE_FFT_CUFFT;
+}
+
+// cuFFT plans of the single-plan path (HSE_FFT_CUFFT, and every HSE_MIXED plan)
+static hse_status build_cufft(hse_plan p) {
+  if (p->have_fft) return HSE_OK;
+  const hse_params& q = p->prm;
+  const GridDims& g = p->g;
+  const bool mixed = q.precision == HSE_MIXED;
+  // cuFFT, in place: the input is zero outside x < Mt, y < Mt, z < 2Mt, so the
+  // forward transform is a 2-D (y,z) R2C over the Mt planes x < Mt followed by
+  // a 1-D transform along x over every (y, kz) line; the inverse runs the x
+  // transform first and the 2-D C2R only over the planes the gather reads.
+  const long long nzh = g.Nz / 2 + 1;
+  long long n2[2] = {g.Ny, g.Nz};
+  long long re[2] = {g.Ny, g.pitch}, ce[2] = {g.Ny, nzh};
+  long long nx[1] = {g.Nx}, xe[1] = {g.Nx};
+  size_t w1 = 0, w2 = 0, w3 = 0;
+  HSE_TRY(cufft_check(p, cufftCreate(&p->fwd2d), "cufftCreate"));
+  HSE_TRY(cufft_check(p, cufftCreate(&p->inv2d), "cufftCreate"));
+  HSE_TRY(cufft_check(p, cufftCreate(&p->fftx), "cufftCreate"));
+  p->have_fft = true;
+  cufftSetAutoAllocation(p->fwd2d, 0);
+  cufftSetAutoAllocation(p->inv2d, 0);
+  cufftSetAutoAllocation(p->fftx, 0);
+  const cufftType t_r2c = mixed ? CUFFT_R2C : CUFFT_D2Z, t_c2r = mixed ? CUFFT_C2R : CUFFT_Z2D;
+  const cufftType t_c2c = mixed ? CUFFT_C2C : CUFFT_Z2Z;
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fwd2d, 2, n2, re, 1, g.Ny * g.pitch, ce, 1, g.Ny * nzh, t_r2c,
+                                             q.Mt, &w1), "cufftMakePlanMany64 R2C (y,z)"));
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->inv2d, 2, n2, ce, 1, g.Ny * nzh, re, 1, g.Ny * g.pitch, t_c2r,
+                                             q.Mt, &w2), "cufftMakePlanMany64 C2R (y,z)"));
+  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fftx, 1, nx, xe, g.Ny * nzh, 1, xe, g.Ny * nzh, 1, t_c2c,
+                                             g.Ny * nzh, &w3), "cufftMakePlanMany64 C2C (x)"));
+  size_t wmax = w1 > w2 ? w1 : w2;
+  p->fft_work_bytes = wmax > w3 ? wmax : w3;
+  if (p->fft_work_bytes) HSE_CUDA(p, cudaMalloc(&p->fft_work, p->fft_work_bytes));
+  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fwd2d, p->fft_work), "cufftSetWorkArea"));
+  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->inv2d, p->fft_work), "cufftSetWorkArea"));
+  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fftx, p->fft_work), "cufftSetWorkArea"));
+  return HSE_OK;
 }
 
 hse_status build_grids(hse_plan p) {
@@ -320,36 +374,10 @@ hse_status build_grids(hse_plan p) {
       HSE_CUDA(p, e);
     }
   }
-  // cuFFT, in place: the input is zero outside x < Mt, y < Mt, z < 2Mt, so the
-  // forward transform is a 2-D (y,z) R2C over the Mt planes x < Mt followed by
-  // a 1-D transform along x over every (y, kz) line; the inverse runs the x
-  // transform first and the 2-D C2R only over the planes the gather reads.
-  const long long nzh = g.Nz / 2 + 1;
-  long long n2[2] = {g.Ny, g.Nz};
-  long long re[2] = {g.Ny, g.pitch}, ce[2] = {g.Ny, nzh};
-  long long nx[1] = {g.Nx}, xe[1] = {g.Nx};
-  size_t w1 = 0, w2 = 0, w3 = 0;
-  HSE_TRY(cufft_check(p, cufftCreate(&p->fwd2d), "cufftCreate"));
-  HSE_TRY(cufft_check(p, cufftCreate(&p->inv2d), "cufftCreate"));
-  HSE_TRY(cufft_check(p, cufftCreate(&p->fftx), "cufftCreate"));
-  p->have_fft = true;
-  cufftSetAutoAllocation(p->fwd2d, 0);
-  cufftSetAutoAllocation(p->inv2d, 0);
-  cufftSetAutoAllocation(p->fftx, 0);
-  const cufftType t_r2c = mixed ? CUFFT_R2C : CUFFT_D2Z, t_c2r = mixed ? CUFFT_C2R : CUFFT_Z2D;
-  const cufftType t_c2c = mixed ? CUFFT_C2C : CUFFT_Z2Z;
-  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fwd2d, 2, n2, re, 1, g.Ny * g.pitch, ce, 1, g.Ny * nzh, t_r2c,
-                                             q.Mt, &w1), "cufftMakePlanMany64 R2C (y,z)"));
-  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->inv2d, 2, n2, ce, 1, g.Ny * nzh, re, 1, g.Ny * g.pitch, t_c2r,
-                                             q.Mt, &w2), "cufftMakePlanMany64 C2R (y,z)"));
-  HSE_TRY(cufft_check(p, cufftMakePlanMany64(p->fftx, 1, nx, xe, g.Ny * nzh, 1, xe, g.Ny * nzh, 1, t_c2c,
-                                             g.Ny * nzh, &w3), "cufftMakePlanMany64 C2C (x)"));
-  size_t wmax = w1 > w2 ? w1 : w2;
-  p->fft_work_bytes = wmax > w3 ? wmax : w3;
-  if (p->fft_work_bytes) HSE_CUDA(p, cudaMalloc(&p->fft_work, p->fft_work_bytes));
-  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fwd2d, p->fft_work), "cufftSetWorkArea"));
-  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->inv2d, p->fft_work), "cufftSetWorkArea"));
-  HSE_TRY(cufft_check(p, cufftSetWorkArea(p->fftx, p->fft_work), "cufftSetWorkArea"));
+  q.fft = resolve_fft(p);
+  if (q.fft < 0) return set_err(p, HSE_ERR_UNSUPPORTED, "df64 FFT: grid %d x %d x %d", g.Nx, g.Ny, g.Nz);
+  if (q.fft == HSE_FFT_DF64) HSE_TRY(fft64_prepare(p));
+  else HSE_TRY(build_cufft(p));
   q.grid_bytes = spec_bytes + tab_elems * esz * (p->tabB ? 2 : 1) + p->fft_work_bytes;
   p->grid_ready = true;
   return HSE_OK;
@@ -525,6 +553,7 @@ extern "C" hse_status hse_plan_create(int kernel_mask, const double box[3], doub
   hse_params& q = p->prm;
   q.kernel_mask = kernel_mask;
   q.precision = precision;
+  p->tol = tol;
   for (int d = 0; d < 3; ++d) q.box[d] = box[d];
   q.L = std::fmax(box[0], std::fmax(box[1], box[2]));
   hse_status st = choose_params(p, xi, rc, P, tol);
@@ -567,6 +596,27 @@ extern "C" hse_status hse_plan_set_rc64(hse_plan p, double rc64) {
   if (!(rc64 >= 0.0) || p->prm.precision != HSE_FP64)
     return set_err(p, HSE_ERR_INVALID, "rc64 needs an HSE_FP64 plan and rc64 >= 0");
   p->prm.rc64 = rc64;
+  return HSE_OK;
+}
+
+extern "C" hse_status hse_plan_set_fft(hse_plan p, int mode) {
+  if (!p) return HSE_ERR_INVALID;
+  if (mode != HSE_FFT_AUTO && mode != HSE_FFT_CUFFT && mode != HSE_FFT_DF64)
+    return set_err(p, HSE_ERR_INVALID, "fft mode %d", mode);
+  if (mode == HSE_FFT_DF64 && p->prm.precision != HSE_FP64)
+    return set_err(p, HSE_ERR_INVALID, "HSE_FFT_DF64 needs an HSE_FP64 plan");
+  p->fft_mode = mode;
+  if (!p->grid_ready) return HSE_OK;
+  const int f = resolve_fft(p);
+  if (f < 0) {
+    p->fft_mode = HSE_FFT_AUTO;
+    return set_err(p, HSE_ERR_UNSUPPORTED, "df64 FFT: grid %d x %d x %d", p->g.Nx, p->g.Ny, p->g.Nz);
+  }
+  const size_t work_before = p->fft_work_bytes;
+  if (f == HSE_FFT_DF64) HSE_TRY(fft64_prepare(p));
+  else HSE_TRY(build_cufft(p));
+  p->prm.fft = f;
+  p->prm.grid_bytes += p->fft_work_bytes - work_before;  // a cuFFT work area made now
   return HSE_OK;
 }
 

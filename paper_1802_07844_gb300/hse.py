@@ -15,6 +15,7 @@ import os
 HSE_OK, HSE_ERR_INVALID, HSE_ERR_OOM, HSE_ERR_CUDA, HSE_ERR_CUFFT, HSE_ERR_TIMEOUT, HSE_ERR_UNSUPPORTED = range(7)
 HSE_STOKESLET, HSE_STRESSLET, HSE_ROTLET, HSE_FREE_SPACE = 1, 2, 4, 8
 HSE_FP64, HSE_MIXED = 0, 1
+HSE_FFT_AUTO, HSE_FFT_CUFFT, HSE_FFT_DF64 = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhse.so")
@@ -27,7 +28,7 @@ class hse_params(ctypes.Structure):
         ("P", ctypes.c_int),
         ("M", ctypes.c_int), ("Mt", ctypes.c_int), ("h", ctypes.c_double), ("eta", ctypes.c_double),
         ("ncell", ctypes.c_int * 3), ("n_fft_in", ctypes.c_int), ("n_fft_out", ctypes.c_int),
-        ("grid_bytes", ctypes.c_size_t),
+        ("fft", ctypes.c_int), ("grid_bytes", ctypes.c_size_t),
     ]
 
     def as_dict(self):
@@ -91,7 +92,7 @@ class HseError(RuntimeError):
 
 
 _lib = None
-_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
+_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_set_fft", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
           "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
@@ -113,6 +114,7 @@ def load(path: str = LIB_PATH):
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
     L.hse_plan_set_grid.argtypes = [vp, ctypes.c_int]
     L.hse_plan_set_rc64.argtypes = [vp, ctypes.c_double]
+    L.hse_plan_set_fft.argtypes = [vp, ctypes.c_int]
     L.hse_plan_get_params.argtypes = [vp, ctypes.POINTER(hse_params)]
     L.hse_eval.argtypes = [vp, i64, dp, dp, i64, dp, dp, vp]
     L.hse_eval_parts.argtypes = [vp, i64, dp, dp, i64, dp, dp, dp, vp]
@@ -177,6 +179,11 @@ def hse_plan_set_rc64(plan, rc64):
     """FP64 plans: pairs closer than rc64 in FP64, the shell [rc64, rc) in FP32
     (rc64 >= rc: FP64 throughout)."""
     _check(load().hse_plan_set_rc64(plan, float(rc64)), plan)
+
+
+def hse_plan_set_fft(plan, mode):
+    """Transforms of the Fourier part: HSE_FFT_AUTO, HSE_FFT_CUFFT or HSE_FFT_DF64."""
+    _check(load().hse_plan_set_fft(plan, int(mode)), plan)
 
 
 def hse_plan_set_grid(plan, M):
@@ -444,6 +451,10 @@ class Plan:
 
     def set_grid(self, M):
         hse_plan_set_grid(self.handle, M)
+        self.params = hse_plan_get_params(self.handle)
+
+    def set_fft(self, mode):
+        hse_plan_set_fft(self.handle, mode)
         self.params = hse_plan_get_params(self.handle)
 
     @staticmethod

@@ -1,0 +1,115 @@
+"""Double-float (df64) transforms of the FP64 Fourier part (Sec. 4 steps
+FFT - scale - IFFT) against cuFFT double on the same plan and inputs: every
+kernel mask, line lengths with radices 4, 2, 5 and 3 (including lengths not
+divisible by 4), the fallback to cuFFT for lengths with other prime factors,
+and the mode switch rules.  Both runs share the spread and the gather, so the
+comparison isolates the transforms and the scaling."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import KERNEL_S, KERNEL_T, KERNEL_W, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FREE = oracle.FREE_SPACE
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1802_07844_gb300 as p
+    return p
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def fourier_both(pkg, plan, pr):
+    src, st = dev(pr.src), dev(pr.strengths)
+    plan.set_fft(pkg.HSE_FFT_CUFFT)
+    assert plan.params["fft"] == pkg.HSE_FFT_CUFFT
+    _, ref = plan.eval_parts(src, st, real=False)
+    ref = host(ref)
+    plan.set_fft(pkg.HSE_FFT_DF64)
+    assert plan.params["fft"] == pkg.HSE_FFT_DF64
+    _, u = plan.eval_parts(src, st, real=False)
+    return host(u), ref
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W, KERNEL_S | KERNEL_T | KERNEL_W,
+                                  KERNEL_S | KERNEL_W | FREE])
+@pytest.mark.parametrize("M", [18, 33, 68])  # Mt = 30, 45, 80: lines 4.3.5, 2.5.3.3, 4.4.2.5 (x2 for z)
+def test_df64_matches_cufft(pkg, mask, M):
+    pr = problem(mask & 7, 3000, 1.0, "near_wall", 70 + M)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=6.0, rc=0.5, P=12, tol=0.0, M=M)
+    assert plan.params["fft"] == pkg.HSE_FFT_DF64  # explicit parameters: df64 by default
+    u, ref = fourier_both(pkg, plan, pr)
+    # ~48-bit arithmetic: the difference is rounding, far below any tolerance
+    assert rel(u, ref) < 1e-12
+    assert float(np.abs(u - ref).max() / np.abs(ref).max()) < 1e-12
+    plan.close()
+
+
+def test_df64_bench_shape(pkg):
+    # the benchmark's line length (Mt = 320: 640 = 4.4.4.2.5) at a reduced count
+    mask = KERNEL_S | KERNEL_W
+    pr = problem(mask, 20000, 1.0, "near_wall", 79)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=87.0, rc=0.0552, P=18, tol=0.0, M=302)
+    u, ref = fourier_both(pkg, plan, pr)
+    assert rel(u, ref) < 1e-12
+    plan.close()
+
+
+def test_df64_unsupported_length_falls_back(pkg):
+    # Mt = 28: lines of 56 = 8 x 7 have a factor the df64 transforms lack
+    plan = pkg.Plan(KERNEL_S, (1.0, 1.0, 1.0), xi=5.0, rc=0.5, P=12, tol=0.0, M=16)
+    assert plan.params["fft"] == pkg.HSE_FFT_CUFFT
+    with pytest.raises(pkg.HseError):
+        plan.set_fft(pkg.HSE_FFT_DF64)
+    assert plan.params["fft"] == pkg.HSE_FFT_CUFFT
+    pr = problem(KERNEL_S, 500, 1.0, "uniform", 80)
+    u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
+    assert np.isfinite(u).all()
+    plan.close()
+
+
+def test_df64_mode_rules(pkg):
+    # FP32 plans keep cuFFT single and refuse df64; tight tolerances keep cuFFT double
+    mixed = pkg.Plan(KERNEL_S, (1.0, 1.0, 1.0), xi=10.0, tol=1e-5, precision=pkg.HSE_MIXED)
+    assert mixed.params["fft"] == pkg.HSE_FFT_CUFFT
+    with pytest.raises(pkg.HseError):
+        mixed.set_fft(pkg.HSE_FFT_DF64)
+    mixed.close()
+    tight = pkg.Plan(KERNEL_W, (1.0, 1.0, 1.0), xi=10.0, tol=1e-13)
+    assert tight.params["fft"] == pkg.HSE_FFT_CUFFT
+    tight.close()
+    loose = pkg.Plan(KERNEL_W, (1.0, 1.0, 1.0), xi=10.0, tol=1e-8)
+    assert loose.params["fft"] == pkg.HSE_FFT_DF64
+    loose.set_fft(pkg.HSE_FFT_AUTO)
+    assert loose.params["fft"] == pkg.HSE_FFT_DF64
+    loose.close()
+
+
+def test_df64_full_eval_vs_oracle(pkg):
+    # whole evaluation with df64 transforms against the direct half-space sum
+    mask = KERNEL_S | KERNEL_T | KERNEL_W
+    pr = problem(mask, 600, 1.0, "near_wall", 81)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=10.0, tol=1e-9)
+    assert plan.params["fft"] == pkg.HSE_FFT_DF64
+    u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
+    ref = oracle.direct(mask, pr.src, pr.strengths)
+    assert rel(u, ref) < 1e-9
+    plan.close()
