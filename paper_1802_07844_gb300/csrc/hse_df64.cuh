@@ -66,6 +66,41 @@ __device__ __forceinline__ df operator*(df a, float b) {
 __device__ __forceinline__ df operator*(float b, df a) { return a * b; }
 __device__ __forceinline__ df operator*(df a, int i) { return a * (float)i; }
 
+// Unnormalised forms for intermediate results inside a computation: the pair
+// (s, e) still sums to the value with the same error bound, but |e| may exceed
+// ulp(s) / 2 by a few units.  Every df64 operation above accepts such inputs;
+// df_norm restores the invariant before a value is stored.
+__device__ __forceinline__ df df_add_raw(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return df(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_sub_raw(df a, df b) { return df_add_raw(a, -b); }
+__device__ __forceinline__ df df_mul_raw(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  return df(p, fmaf(a.lo, b.hi, e));
+}
+__device__ __forceinline__ df df_norm(df a) { return df_fast_two_sum(a.hi, a.lo); }
+
+// a b - c d with one rounding-error-free difference of the leading products
+// (16 FP32 operations against 25 for two products and a sum), unnormalised
+__device__ __forceinline__ df df_dot2_raw(df a, df b, df c, df d) {
+  const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+  const float e1 = fmaf(a.hi, b.hi, -p), e2 = fmaf(c.hi, d.hi, -q);
+  const float s = __fsub_rn(p, q);
+  const float bb = __fsub_rn(s, p);
+  float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(-q, bb));
+  e = __fadd_rn(e, __fsub_rn(e1, e2));
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  e = fmaf(-c.hi, d.lo, e);
+  e = fmaf(-c.lo, d.hi, e);
+  return df(s, e);
+}
+
 // complex df64, laid out like a complex double (16 bytes)
 struct __align__(16) cdf {
   df x, y;
@@ -84,6 +119,14 @@ __device__ __forceinline__ cdf operator*(cdf a, cdf b) {
 }
 __device__ __forceinline__ cdf operator*(df s, cdf a) { return cdf_make(s * a.x, s * a.y); }
 __device__ __forceinline__ cdf conj(cdf a) { return cdf_make(a.x, -a.y); }
+__device__ __forceinline__ cdf add_raw(cdf a, cdf b) { return cdf_make(df_add_raw(a.x, b.x), df_add_raw(a.y, b.y)); }
+__device__ __forceinline__ cdf sub_raw(cdf a, cdf b) { return cdf_make(df_sub_raw(a.x, b.x), df_sub_raw(a.y, b.y)); }
+__device__ __forceinline__ cdf scale_raw(df s, cdf a) { return cdf_make(df_mul_raw(s, a.x), df_mul_raw(s, a.y)); }
+// a w (w = wr + i wi), unnormalised
+__device__ __forceinline__ cdf mul_raw(cdf a, cdf w) {
+  return cdf_make(df_dot2_raw(a.x, w.x, a.y, w.y), df_dot2_raw(a.x, w.y, -a.y, w.x));
+}
+__device__ __forceinline__ cdf norm(cdf a) { return cdf_make(df_norm(a.x), df_norm(a.y)); }
 // multiply by -i (forward transforms) or +i (inverse)
 template <bool FWD>
 __device__ __forceinline__ cdf mul_mi(cdf a) {

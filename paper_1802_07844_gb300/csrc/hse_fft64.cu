@@ -16,9 +16,8 @@
 //
 // Each pass is a batched 1-D transform of lines.  A block holds LPB lines in
 // shared memory (element e of line l at e * LPB + l) and runs a mixed-radix
-// Stockham autosort transform over them (radices 4, 2, 5, 3), each thread
-// keeping its butterflies in registers across the barrier between the reads
-// and the writes of a pass.
+// Stockham autosort transform over them (radices 4, 2, 5, 3), alternating
+// between two shared buffers so that each radix pass needs one barrier.
 #include <cmath>
 #include <vector>
 
@@ -70,53 +69,65 @@ static bool make_steps(int N, FftSteps* st) {
 // threads per line: one radix-4 butterfly each when 4 | N, else one radix-2
 static int threads_per_line(int N) { return N % 4 == 0 ? N / 4 : N / 2; }
 
-// lines per block: a power of two, at most 512 threads and 16 lines
+// block shape: at most kFftThreads threads, kFftMinBlocks resident per SM
+// (register budget); compile-time tuning knobs
+#ifndef HSE_FFT64_THREADS
+#define HSE_FFT64_THREADS 512
+#endif
+#ifndef HSE_FFT64_MIN_BLOCKS
+#define HSE_FFT64_MIN_BLOCKS 2
+#endif
+constexpr int kFftThreads = HSE_FFT64_THREADS, kFftMinBlocks = HSE_FFT64_MIN_BLOCKS;
+
+// lines per block: a power of two, at most kFftThreads threads and 16 lines
 static int lines_per_block_log2(int N) {
   int tpl = threads_per_line(N), lsh = 0;
-  while (lsh < 4 && (tpl << (lsh + 1)) <= 512) ++lsh;
+  while (lsh < 4 && (tpl << (lsh + 1)) <= kFftThreads) ++lsh;
   return lsh;
 }
 
 // ------------------------------------------------------------- butterflies
+// In-register radix-R DFTs (forward: exp(-2 pi i j k / R)) on unnormalised
+// inputs; intermediate sums stay unnormalised and the outputs are normalised.
 template <bool FWD>
 __device__ __forceinline__ void dft2(cdf* v) {
   const cdf a = v[0], b = v[1];
-  v[0] = a + b;
-  v[1] = a - b;
+  v[0] = norm(add_raw(a, b));
+  v[1] = norm(sub_raw(a, b));
 }
 template <bool FWD>
 __device__ __forceinline__ void dft4(cdf* v) {
-  const cdf a0 = v[0] + v[2], a1 = v[0] - v[2];
-  const cdf b0 = v[1] + v[3], b1 = mul_mi<FWD>(v[1] - v[3]);
-  v[0] = a0 + b0;
-  v[2] = a0 - b0;
-  v[1] = a1 + b1;
-  v[3] = a1 - b1;
+  const cdf a0 = add_raw(v[0], v[2]), a1 = sub_raw(v[0], v[2]);
+  const cdf b0 = add_raw(v[1], v[3]), b1 = mul_mi<FWD>(sub_raw(v[1], v[3]));
+  v[0] = norm(add_raw(a0, b0));
+  v[2] = norm(sub_raw(a0, b0));
+  v[1] = norm(add_raw(a1, b1));
+  v[3] = norm(sub_raw(a1, b1));
 }
 template <bool FWD>
 __device__ __forceinline__ void dft3(cdf* v, const float* kc) {
   const df s3(kc[0], kc[1]);
-  const cdf t = v[1] + v[2];
-  const cdf a = v[0] - df(0.5f, 0.f) * t;
-  const cdf b = mul_mi<FWD>(s3 * (v[1] - v[2]));
-  v[0] = v[0] + t;
-  v[1] = a + b;
-  v[2] = a - b;
+  const cdf t = add_raw(v[1], v[2]);
+  const cdf a = sub_raw(v[0], scale_raw(df(0.5f, 0.f), t));
+  const cdf b = mul_mi<FWD>(scale_raw(s3, sub_raw(v[1], v[2])));
+  v[0] = norm(add_raw(v[0], t));
+  v[1] = norm(add_raw(a, b));
+  v[2] = norm(sub_raw(a, b));
 }
 template <bool FWD>
 __device__ __forceinline__ void dft5(cdf* v, const float* kc) {
   const df c1(kc[2], kc[3]), c2(kc[4], kc[5]), s1(kc[6], kc[7]), s2(kc[8], kc[9]);
-  const cdf t1 = v[1] + v[4], t2 = v[2] + v[3];
-  const cdf t3 = v[1] - v[4], t4 = v[2] - v[3];
-  const cdf a1 = v[0] + (c1 * t1 + c2 * t2);
-  const cdf a2 = v[0] + (c2 * t1 + c1 * t2);
-  const cdf b1 = mul_mi<FWD>(s1 * t3 + s2 * t4);
-  const cdf b2 = mul_mi<FWD>(s2 * t3 - s1 * t4);
-  v[0] = v[0] + (t1 + t2);
-  v[1] = a1 + b1;
-  v[4] = a1 - b1;
-  v[2] = a2 + b2;
-  v[3] = a2 - b2;
+  const cdf t1 = add_raw(v[1], v[4]), t2 = add_raw(v[2], v[3]);
+  const cdf t3 = sub_raw(v[1], v[4]), t4 = sub_raw(v[2], v[3]);
+  const cdf a1 = add_raw(v[0], add_raw(scale_raw(c1, t1), scale_raw(c2, t2)));
+  const cdf a2 = add_raw(v[0], add_raw(scale_raw(c2, t1), scale_raw(c1, t2)));
+  const cdf b1 = mul_mi<FWD>(add_raw(scale_raw(s1, t3), scale_raw(s2, t4)));
+  const cdf b2 = mul_mi<FWD>(sub_raw(scale_raw(s2, t3), scale_raw(s1, t4)));
+  v[0] = norm(add_raw(v[0], add_raw(t1, t2)));
+  v[1] = norm(add_raw(a1, b1));
+  v[4] = norm(sub_raw(a1, b1));
+  v[2] = norm(add_raw(a2, b2));
+  v[3] = norm(sub_raw(a2, b2));
 }
 
 template <bool FWD>
@@ -125,54 +136,43 @@ __device__ __forceinline__ cdf twiddle(const float4* __restrict__ tw, int idx) {
   return FWD ? w : conj(w);
 }
 
-// One Stockham pass (radix R, Ns = product of the earlier radices) over the
-// block's lines: butterfly j < N / R reads elements j + t N / R, multiplies
-// element t by w_N^{t (j mod Ns) N / (Ns R)}, transforms, and writes output t
-// to (j div Ns) Ns R + (j mod Ns) + t Ns.  A thread takes butterflies tj (and
-// tj + TPL) of line l: with TPL = N / 4 (or N / 2 when 4 does not divide N)
-// radices 2 and 3 need at most two butterflies per thread, 4 and 5 one.
+// One Stockham pass (radix R, Ns = product of the earlier radices) from src
+// to dst: butterfly j < N / R reads elements j + t N / R, multiplies element t
+// by w_N^{t (j mod Ns) N / (Ns R)}, transforms, and writes output t to
+// (j div Ns) Ns R + (j mod Ns) + t Ns.  Thread (l, tj) takes butterflies
+// tj, tj + TPL, ... of line l.
 template <int R, bool FWD>
-__device__ __forceinline__ void stockham_pass(float4* s, int N, int Ns, int step, unsigned magic, const float* kc,
-                                              int tpl, int lsh, int l, int tj, const float4* __restrict__ tw) {
-  constexpr int MB = R <= 3 ? 2 : 1;
+__device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, int N, int Ns, int step,
+                                              unsigned magic, const float* kc, int tpl, int lsh, int l, int tj,
+                                              const float4* __restrict__ tw) {
   const int nb = N / R;
-  cdf v[MB][R];
-  int dst[MB];
+  for (int j = tj; j < nb; j += tpl) {
+    const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, magic);
+    const int k = j - q * Ns;
+    cdf v[R];
 #pragma unroll
-  for (int m = 0; m < MB; ++m) {
-    const int j = tj + m * tpl;
-    dst[m] = -1;
-    if (j < nb) {
-      const int q = Ns == 1 ? j : (int)__umulhi((unsigned)j, magic);
-      const int k = j - q * Ns;
+    for (int t = 0; t < R; ++t) v[t] = ld_cdf(src + ((j + t * nb) << lsh) + l);
+    if (k != 0) {
 #pragma unroll
-      for (int t = 0; t < R; ++t) v[m][t] = ld_cdf(s + ((j + t * nb) << lsh) + l);
-      if (k != 0) {
-#pragma unroll
-        for (int t = 1; t < R; ++t) v[m][t] = v[m][t] * twiddle<FWD>(tw, t * k * step);
-      }
-      if (R == 2) dft2<FWD>(v[m]);
-      else if (R == 4) dft4<FWD>(v[m]);
-      else if (R == 3) dft3<FWD>(v[m], kc);
-      else dft5<FWD>(v[m], kc);
-      dst[m] = q * Ns * R + k;
+      for (int t = 1; t < R; ++t) v[t] = v[t] * twiddle<FWD>(tw, t * k * step);
     }
+    if (R == 2) dft2<FWD>(v);
+    else if (R == 4) dft4<FWD>(v);
+    else if (R == 3) dft3<FWD>(v, kc);
+    else dft5<FWD>(v, kc);
+    const int d = q * Ns * R + k;
+#pragma unroll
+    for (int t = 0; t < R; ++t) st_cdf(dst + ((d + t * Ns) << lsh) + l, v[t]);
   }
-  __syncthreads();
-#pragma unroll
-  for (int m = 0; m < MB; ++m)
-    if (dst[m] >= 0) {
-#pragma unroll
-      for (int t = 0; t < R; ++t) st_cdf(s + ((dst[m] + t * Ns) << lsh) + l, v[m][t]);
-    }
-  __syncthreads();
 }
 
-// all passes; the result is in natural order in s.  The schedule lives in
-// device memory (uniform loads) so that the pass loop indexes it freely.
+// All passes, alternating between the block's two shared buffers (a holds the
+// input); returns the buffer that holds the result, in natural order.  The
+// schedule lives in device memory (uniform loads) so the pass loop can index
+// it freely.
 template <bool FWD>
-__device__ __forceinline__ void transform_block(float4* s, const FftSteps* __restrict__ st, int lsh,
-                                                const float4* __restrict__ tw) {
+__device__ __forceinline__ float4* transform_block(float4* a, float4* b, const FftSteps* __restrict__ st, int lsh,
+                                                   const float4* __restrict__ tw) {
   const int tpl = blockDim.x >> lsh;
   const int l = threadIdx.x & ((1 << lsh) - 1), tj = threadIdx.x >> lsh;
   const int N = st->N, npass = st->npass;
@@ -181,12 +181,17 @@ __device__ __forceinline__ void transform_block(float4* s, const FftSteps* __res
     const int Ns = st->Ns[p], step = st->step[p];
     const unsigned magic = st->magic[p];
     switch (st->R[p]) {
-      case 4: stockham_pass<4, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
-      case 2: stockham_pass<2, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
-      case 5: stockham_pass<5, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
-      default: stockham_pass<3, FWD>(s, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      case 4: stockham_pass<4, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      case 2: stockham_pass<2, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      case 5: stockham_pass<5, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      default: stockham_pass<3, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
     }
+    __syncthreads();
+    float4* t = a;
+    a = b;
+    b = t;
   }
+  return a;
 }
 
 // ------------------------------------------------------------ line geometry
@@ -215,7 +220,7 @@ __global__ void k_twiddles(int N, float4* __restrict__ tw) {
 
 // ------------------------------------------------------------ C2C passes
 template <bool FWD>
-__global__ void __launch_bounds__(512, 1) k_fft_lines(float4* __restrict__ data, LineGeo g,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4* __restrict__ data, LineGeo g,
                                                       const FftSteps* __restrict__ st, int lsh,
                                                       const float4* __restrict__ tw) {
   extern __shared__ float4 sm[];
@@ -229,10 +234,10 @@ __global__ void __launch_bounds__(512, 1) k_fft_lines(float4* __restrict__ data,
       sm[i] = o >= 0 ? data[o + (long long)(i >> lsh) * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    transform_block<FWD>(sm, st, lsh, tw);
+    const float4* res = transform_block<FWD>(sm, sm + n, st, lsh, tw);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const long long o = start[i & (lpb - 1)];
-      if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = sm[i];
+      if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = res[i];
     }
     __syncthreads();
   }
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_lines(float4* __restrict__ data,
 // + i conj(w^k) (X_k - conj X_{N-k}), transforms back (unnormalised, like a
 // C2R transform) and writes the first nkeep doubles of the line.
 template <bool FWD>
-__global__ void __launch_bounds__(512, 1) k_fft_z(double* __restrict__ data, LineGeo g, const FftSteps* __restrict__ st,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __restrict__ data, LineGeo g, const FftSteps* __restrict__ st,
                                                   int lsh, const float4* __restrict__ tw,
                                                   const float4* __restrict__ tw2, int nkeep) {
   extern __shared__ float4 sm[];
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_z(double* __restrict__ data, Lin
       }
     }
     __syncthreads();
-    transform_block<FWD>(sm, st, lsh, tw);
+    const float4* res = transform_block<FWD>(sm, sm + (N << lsh), st, lsh, tw);
     for (int l = 0; l < lpb; ++l) {
       const long long o = start[l];
       if (o < 0) continue;
@@ -283,14 +288,14 @@ __global__ void __launch_bounds__(512, 1) k_fft_z(double* __restrict__ data, Lin
         float4* X = reinterpret_cast<float4*>(data + o);
         const df half(0.5f, 0.f);
         for (int k = threadIdx.x; k <= N; k += blockDim.x) {
-          const cdf zk = ld_cdf(sm + ((k == N ? 0 : k) << lsh) + l);
-          const cdf zn = conj(ld_cdf(sm + ((k == 0 ? 0 : N - k) << lsh) + l));
+          const cdf zk = ld_cdf(res + ((k == N ? 0 : k) << lsh) + l);
+          const cdf zn = conj(ld_cdf(res + ((k == 0 ? 0 : N - k) << lsh) + l));
           const cdf ev = half * (zk + zn), od = half * (zk - zn);
           st_cdf(X + k, ev + mul_mi<true>(ldg_cdf(tw2 + k) * od));
         }
       } else {
         for (int k = threadIdx.x; 2 * k < nkeep; k += blockDim.x) {
-          const cdf z = ld_cdf(sm + (k << lsh) + l);
+          const cdf z = ld_cdf(res + (k << lsh) + l);
           if (2 * k + 1 < nkeep)
             *reinterpret_cast<double2*>(data + o + 2 * k) = make_double2(z.x.to_double(), z.y.to_double());
           else
@@ -312,11 +317,11 @@ struct Fft64Tables {
 static Fft64Tables* tables(hse_plan p) { return reinterpret_cast<Fft64Tables*>(p->fft64); }
 
 // lengths whose schedule uses radices 2, 3, 4, 5 only and whose line fits
-// one block (threads_per_line <= 512)
+// one block (threads_per_line <= kFftThreads)
 bool fft64_supported(int Nx, int Ny, int Nz) {
   FftSteps a, b;
-  return Nx == Ny && Nz % 2 == 0 && make_steps(Nx, &a) && make_steps(Nz / 2, &b) && threads_per_line(Nx) <= 512 &&
-         threads_per_line(Nz / 2) <= 512;
+  return Nx == Ny && Nz % 2 == 0 && make_steps(Nx, &a) && make_steps(Nz / 2, &b) &&
+         threads_per_line(Nx) <= kFftThreads && threads_per_line(Nz / 2) <= kFftThreads;
 }
 
 hse_status fft64_prepare(hse_plan p) {
@@ -344,8 +349,8 @@ hse_status fft64_prepare(hse_plan p) {
   HSE_CUDA(p, cudaDeviceSynchronize());
   static bool attr = false;
   if (!attr) {
-    // a block holds (threads / TPL) lines of N points: at most 512 threads and
-    // TPL >= N / 4, so at most 2048 points, 32 KB
+    // a block holds two buffers of (threads / TPL) lines of N points: at most
+    // kFftThreads threads and TPL >= N / 4, so at most 2 x 16 KB x kFftThreads / 512
     const int cap = 64 * 1024;
     cudaFuncSetAttribute(k_fft_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_fft_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -375,7 +380,7 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
   const Fft64Tables* t = tables(p);
   const int lsh = lines_per_block_log2(t->sx.N);
   const unsigned threads = (unsigned)(threads_per_line(t->sx.N) << lsh);
-  const size_t shm = sizeof(float4) * ((size_t)t->sx.N << lsh);
+  const size_t shm = 2 * sizeof(float4) * ((size_t)t->sx.N << lsh);
   if (geo.nlines <= 0) return HSE_OK;
   float4* c = reinterpret_cast<float4*>(buf);
   if (fwd) k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw);
@@ -388,7 +393,7 @@ static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, i
   const Fft64Tables* t = tables(p);
   const int N = t->sz.N, lsh = lines_per_block_log2(N);
   const unsigned threads = (unsigned)(threads_per_line(N) << lsh);
-  const size_t shm = sizeof(float4) * ((size_t)N << lsh);
+  const size_t shm = 2 * sizeof(float4) * ((size_t)N << lsh);
   if (geo.nlines <= 0) return HSE_OK;
   const float4* tw = t->tw + t->sx.N;
   const float4* tw2 = tw + N;
