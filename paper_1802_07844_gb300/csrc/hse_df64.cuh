@@ -19,9 +19,9 @@
 
 namespace hse {
 
-struct df {
+struct __align__(8) df {
   float hi, lo;
-  __device__ __forceinline__ df() {}
+  df() = default;  // trivial: usable in __shared__ arrays
   __device__ __forceinline__ df(float h, float l) : hi(h), lo(l) {}
   // exact for integers of magnitude < 2^24
   __device__ __forceinline__ df(int i) : hi((float)i), lo(0.f) {}
@@ -32,6 +32,16 @@ struct df {
   }
   __device__ __forceinline__ double to_double() const { return (double)hi + (double)lo; }
 };
+
+// conversions between the grid element types (double, float, df)
+__device__ __forceinline__ float head32(double v) { return (float)v; }
+__device__ __forceinline__ float head32(float v) { return v; }
+__device__ __forceinline__ float head32(df v) { return v.hi; }
+__device__ __forceinline__ double to64(double v) { return v; }
+__device__ __forceinline__ double to64(float v) { return (double)v; }
+__device__ __forceinline__ double to64(df v) { return v.to_double(); }
+template <typename T> __device__ __forceinline__ T from32(float f) { return (T)f; }
+template <> __device__ __forceinline__ df from32<df>(float f) { return df(f, 0.f); }
 
 // s + e == a + b exactly, provided |a| >= |b| or a == 0
 __device__ __forceinline__ df df_fast_two_sum(float a, float b) {
@@ -65,6 +75,9 @@ __device__ __forceinline__ df operator*(df a, float b) {
 }
 __device__ __forceinline__ df operator*(float b, df a) { return a * b; }
 __device__ __forceinline__ df operator*(df a, int i) { return a * (float)i; }
+__device__ __forceinline__ df operator*(int i, df a) { return a * (float)i; }
+__device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
+__device__ __forceinline__ df& operator-=(df& a, df b) { return a = a - b; }
 
 // Unnormalised forms for intermediate results inside a computation: the pair
 // (s, e) still sums to the value with the same error bound, but |e| may exceed

@@ -8,11 +8,12 @@
 // double-float arithmetic on the 64x wider FP32 pipe; their rounding error
 // (~1e-14 of the data norm) is far below the tolerances the FP64 path serves.
 //
-// Storage: a complex df64 value occupies the 16 bytes of a complex double
-// ({re.hi, re.lo, im.hi, im.lo}), so the grids keep their layout.  The forward
-// z pass reads the spread's doubles and writes df64 half spectra in place;
-// every later pass, and the scaling, stays df64; the inverse z pass writes
-// doubles back for the gather.  Only those two passes convert.
+// Storage: the real grids hold df64 values (8 bytes, {hi, lo}) and a complex
+// df64 value occupies 16 bytes ({re.hi, re.lo, im.hi, im.lo}), so the grids
+// keep the layout of double grids.  The spread writes df64 values, the forward
+// z pass turns them into half spectra in place, every later pass and the
+// scaling stay df64, and the inverse z pass writes df64 values for the gather:
+// no pass converts to or from FP64.
 //
 // Each pass is a batched 1-D transform of lines.  A block holds LPB lines in
 // shared memory (element e of line l at e * LPB + l) and runs a mixed-radix
@@ -244,13 +245,13 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4
 }
 
 // ---------------------------------------------- real <-> half spectrum (z)
-// A real line of 2N doubles x (contiguous) is transformed as the N complex
+// A real line of 2N df64 values x (contiguous) is transformed as the N complex
 // values z_n = x_2n + i x_2n+1: with Z = DFT_N z, the half spectrum of x is
 // X_k = (Z_k + conj Z_{N-k}) / 2 - i w^k (Z_k - conj Z_{N-k}) / 2, k = 0..N,
 // w = exp(-2 pi i / 2N), written in place over the line (2N + 2 doubles hold
 // N + 1 complex df64 values).  The inverse forms Z_k = (X_k + conj X_{N-k})
 // + i conj(w^k) (X_k - conj X_{N-k}), transforms back (unnormalised, like a
-// C2R transform) and writes the first nkeep doubles of the line.
+// C2R transform) and writes the first nkeep values of the line.
 template <bool FWD>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __restrict__ data, LineGeo g, const FftSteps* __restrict__ st,
                                                   int lsh, const float4* __restrict__ tw,
@@ -267,8 +268,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
         cdf z = cdf_make(df(0.f, 0.f), df(0.f, 0.f));
         if (o >= 0) {
           if (FWD) {
-            const double2 x = *reinterpret_cast<const double2*>(data + o + 2 * k);
-            z = cdf_make(df(x.x), df(x.y));
+            z = ld_cdf(reinterpret_cast<const float4*>(data + o + 2 * k));  // x_2k, x_2k+1
           } else {
             const float4* X = reinterpret_cast<const float4*>(data + o);
             const cdf xk = ld_cdf(X + k), xn = conj(ld_cdf(X + N - k));
@@ -296,10 +296,8 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
       } else {
         for (int k = threadIdx.x; 2 * k < nkeep; k += blockDim.x) {
           const cdf z = ld_cdf(res + (k << lsh) + l);
-          if (2 * k + 1 < nkeep)
-            *reinterpret_cast<double2*>(data + o + 2 * k) = make_double2(z.x.to_double(), z.y.to_double());
-          else
-            data[o + 2 * k] = z.x.to_double();
+          if (2 * k + 1 < nkeep) st_cdf(reinterpret_cast<float4*>(data + o + 2 * k), z);
+          else *reinterpret_cast<float2*>(data + o + 2 * k) = make_float2(z.x.hi, z.x.lo);
         }
       }
     }
@@ -404,7 +402,7 @@ static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, i
 }
 
 // Geometry of the grids: buffer b's real element (x, y, z) at
-// x * xs + b * bs + y * pitch + z (doubles), nb buffers transformed together.
+// x * xs + b * bs + y * pitch + z (8-byte units), nb buffers transformed together.
 // Data occupy x < Mt, y < Mt, z < 2 Mt and the rest of the real grid is zero
 // on input.  As complex values the half spectrum (kx, ky, kz) of buffer b sits
 // at (kx * xs + b * bs) / 2 + ky * nzh + kz.
@@ -420,7 +418,7 @@ hse_status fft64_forward(hse_plan p, double* base, int nb, long long bs, long lo
                    true, s);
 }
 
-// Inverse (unnormalised): df64 half spectra -> doubles at x < Mt, y < Mt,
+// Inverse (unnormalised): df64 half spectra -> df64 values at x < Mt, y < Mt,
 // z < 2 Mt of each of the nb buffers (the rest is left undefined).
 hse_status fft64_inverse(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s) {
   const GridDims& g = p->g;

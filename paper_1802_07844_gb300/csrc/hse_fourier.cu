@@ -153,7 +153,7 @@ __global__ void k_prep(PrepArgs<T> a) {
     if (a.prep32) {  // FP32 copy of the record for the spread's small-weight part
       const T* o = a.prep + i * (int64_t)a.stride;
       float* o32 = a.prep32 + i * (int64_t)a.stride;
-      for (int t = 0; t < a.stride; ++t) o32[t] = (float)o[t];
+      for (int t = 0; t < a.stride; ++t) o32[t] = head32(o[t]);
     }
   }
 }
@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
     }
   if (px < a.Mt && py < a.Mt && pz < 2 * a.Mt) {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] += (T)acc32[c];
-    accD += (T)accD32;
+    for (int c = 0; c < NC; ++c) acc[c] += from32<T>(acc32[c]);
+    accD += from32<T>(accD32);
     T* dst = a.out + inst * a.is + px * a.xs + py * a.pitch + pz;
 #pragma unroll
     for (int c = 0; c < NC; ++c) dst[c * a.cs] = acc[c];
@@ -498,6 +498,14 @@ struct GatherArgs {
 
 constexpr int kGatherWarps = 4;
 
+// per-column sums of the gather are accumulated in FP64 (double, float grids)
+// or double-float (double-float grids)
+template <typename T> struct GAcc { typedef double type; };
+template <> struct GAcc<df> { typedef df type; };
+__device__ __forceinline__ double gacc(double v) { return v; }
+__device__ __forceinline__ double gacc(float v) { return (double)v; }
+__device__ __forceinline__ df gacc(df v) { return v; }
+
 // NF = 3: u = <T1> (free space).  NF = 4: u = <T1> - x3 <grad phi>, the
 // gradient taken through the window: <grad phi>(x) = h^3 sum_j grad_x W(x - x_j)
 // phi_j, grad_x W = -W' with W' the derivative with respect to the grid point.
@@ -544,10 +552,11 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
       }
     }
     __syncwarp();
-    // acc: <T1> (3), then the three window-derivative sums of phi
-    double acc[NF == 4 ? 6 : 3];
+    // acc: <T1> (3), then the three window-derivative sums of phi (FP64, or
+    // double-float for double-float grids)
+    typename GAcc<T>::type acc[NF == 4 ? 6 : 3];
 #pragma unroll
-    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c) acc[c] = 0.0;
+    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c) acc[c] = 0;
     for (int q = lane; q < P * P; q += 32) {
       int jj = q / P, kk = q - jj * P;
       T s[3] = {0, 0, 0}, s0 = 0, s1 = 0;
@@ -565,22 +574,25 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
       }
       const T wyz = wy[jj] * wz[kk];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] += (double)(wyz * s[c]);
+      for (int c = 0; c < 3; ++c) acc[c] += gacc(wyz * s[c]);
       if (NF == 4) {
-        acc[3] += (double)(wyz * s1);
-        acc[4] += (double)(dwy[jj] * wz[kk] * s0);
-        acc[5] += (double)(wy[jj] * dwz[kk] * s0);
+        acc[3] += gacc(wyz * s1);
+        acc[4] += gacc(dwy[jj] * wz[kk] * s0);
+        acc[5] += gacc(wy[jj] * dwz[kk] * s0);
       }
     }
+    double accd[NF == 4 ? 6 : 3];
 #pragma unroll
-    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c)
-      for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c) {
+      accd[c] = to64(acc[c]);
+      for (int off = 16; off > 0; off >>= 1) accd[c] += __shfl_xor_sync(0xffffffffu, accd[c], off);
+    }
     if (lane == 0) {
       for (int d = 0; d < 3; ++d) {
         // grad_x W = -W', so u = <T1> - x3 <grad phi> = h^3 (acc_T1 + x3 acc_W')
         double v;
-        if constexpr (NF == 4) v = a.h3 * (acc[d] + z * acc[3 + d]);
-        else v = a.h3 * acc[d];
+        if constexpr (NF == 4) v = a.h3 * (accd[d] + z * accd[3 + d]);
+        else v = a.h3 * accd[d];
         double* o = a.out + d * a.n_tgt + dst;
         *o = a.add ? *o + v : v;
       }
@@ -759,9 +771,11 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nin, s));
   HSE_TRY(spread_into<T>(p, n_src, p->comps, 0, spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
   stage_mark(p, HSE_STAGE_FFT, s);
-  const bool df64 = sizeof(T) == 8 && q.fft == HSE_FFT_DF64;
+  // double-float grids go with the double-float transforms; double and float
+  // grids with cuFFT
+  constexpr bool df64 = std::is_same<T, df>::value;
   const long long xs = (long long)g.Ny * g.pitch;
-  if (df64) {
+  if constexpr (df64) {
     HSE_TRY(fft64_forward(p, reinterpret_cast<double*>(spec), nin, g.buf_doubles, xs, s));
     p->n_fft += nin;
   } else {
@@ -776,10 +790,9 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   }
   stage_mark(p, HSE_STAGE_SCALE, s);
   const int64_t planec = (int64_t)g.Ny * (g.Nz / 2 + 1);
-  if (df64) HSE_TRY(launch_scale<df>(p, spec, g.nh, 1, 0, planec, s));
-  else HSE_TRY(launch_scale<T>(p, spec, g.nh, 1, 0, planec, s));
+  HSE_TRY(launch_scale<T>(p, spec, g.nh, 1, 0, planec, s));
   stage_mark(p, HSE_STAGE_IFFT, s);
-  if (df64) {
+  if constexpr (df64) {
     HSE_TRY(fft64_inverse(p, reinterpret_cast<double*>(spec), q.n_fft_out, g.buf_doubles, xs, s));
     p->n_fft += q.n_fft_out;
   } else {
@@ -974,18 +987,17 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nbuf, s));
   HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, plane * n_inst, plane * nbuf, g.pitch, s, n_inst, plane));
   stage_mark(p, HSE_STAGE_FFT, s);
-  const bool df64 = sizeof(T) == 8 && q.fft == HSE_FFT_DF64;
-  if (df64) {
+  constexpr bool df64 = std::is_same<T, df>::value;
+  if constexpr (df64) {
     HSE_TRY(fft64_forward(p, reinterpret_cast<double*>(spec), (int)nbuf, plane, plane * nbuf, s));
     p->n_fft += (int)nbuf;
   } else {
     HSE_TRY(run_schedule<T>(p, f, batch_schedule(g, nin, q.n_fft_out, n_inst, true), spec, s));
   }
   stage_mark(p, HSE_STAGE_SCALE, s);
-  if (df64) HSE_TRY(launch_scale<df>(p, spec, planec * n_inst, n_inst, planec, planec * nbuf, s));
-  else HSE_TRY(launch_scale<T>(p, spec, planec * n_inst, n_inst, planec, planec * nbuf, s));
+  HSE_TRY(launch_scale<T>(p, spec, planec * n_inst, n_inst, planec, planec * nbuf, s));
   stage_mark(p, HSE_STAGE_IFFT, s);
-  if (df64) {
+  if constexpr (df64) {
     HSE_TRY(fft64_inverse(p, reinterpret_cast<double*>(spec), q.n_fft_out * n_inst, plane, plane * nbuf, s));
     p->n_fft += q.n_fft_out * n_inst;
   } else {
@@ -1025,12 +1037,14 @@ hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const in
                                BatchFFT& f, double* out, cudaStream_t s) {
   if (p->prm.precision == HSE_MIXED)
     return fourier_space_batch_t<float>(p, n_total, n_inst, inst_of, spec, f, out, s);
+  if (p->prm.fft == HSE_FFT_DF64) return fourier_space_batch_t<df>(p, n_total, n_inst, inst_of, spec, f, out, s);
   return fourier_space_batch_t<double>(p, n_total, n_inst, inst_of, spec, f, out, s);
 }
 
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
                          cudaStream_t s, cudaEvent_t gather_after) {
   if (p->prm.precision == HSE_MIXED) return fourier_space_t<float>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
+  if (p->prm.fft == HSE_FFT_DF64) return fourier_space_t<df>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
   return fourier_space_t<double>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
 }
 
