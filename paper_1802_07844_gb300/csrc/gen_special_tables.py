@@ -2,14 +2,16 @@
 used by the real-space kernel.
 
 erfc(t) = exp(-t^2) * erfcx(t).  erfcx(t) = exp(t^2) erfc(t) is smooth and
-slowly varying on [0, 12); it is approximated on intervals of width 1/4 by the
-Chebyshev interpolant of degree 10 (nodes cos(pi (k + 1/2)/11)), rewritten as a
-polynomial in the local variable u = 8 (t - centre) in [-1, 1].  The values come
-from mpmath at 40 digits; the interpolation error is below 4e-16 relative.
+slowly varying on [0, 12); it is approximated on intervals of width 1/8 by the
+Chebyshev interpolant of degree 8 (nodes cos(pi (k + 1/2)/9)), rewritten as a
+polynomial in the local variable u = 16 (t - centre) in [-1, 1].  The values come
+from mpmath at 40 digits; the interpolation error is below 1e-15 relative.
 
-exp(-x) uses the Cody-Waite argument reduction x * log2(e) = n + f with ln 2 split
-into a head of 40 significant bits (so n * head is exact for |n| < 2^13) and a
-tail, then the Taylor polynomial of e^r to degree 13 on |r| <= ln(2)/2.
+exp(-x) uses Tang's table-driven reduction (P. T. P. Tang, ACM TOMS 15, 1989):
+-x = m ln2/64 + r with m = round(-x 64/ln2), |r| <= ln2/128, ln2/64 split into a
+head of 36 significant bits (m * head is exact for |m| < 2^17) and a tail; then
+e^{-x} = 2^n 2^{j/64} e^r with m = 64 n + j, 2^{j/64} from a 64-entry table and
+e^r from its Taylor polynomial of degree 5 (remainder < 4e-17 relative).
 
 Run: python gen_special_tables.py  (needs mpmath)
 """
@@ -18,9 +20,9 @@ import os
 import mpmath as mp
 
 mp.mp.dps = 40
-WIDTH = mp.mpf(1) / 4
-DEG = 10
-NINT = 48  # [0, 12)
+WIDTH = mp.mpf(1) / 8
+DEG = 8
+NINT = 96  # [0, 12)
 
 
 def erfcx(t):
@@ -38,8 +40,10 @@ def interval_coeffs(a, b):
 def main():
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "special_tables.inc")
     lines = ["// generated by gen_special_tables.py -- do not edit",
-             f"// erfcx on [0, {NINT}/4): {NINT} intervals of width 1/4, degree {DEG} in u = 8 (t - centre)",
+             f"// erfcx on [0, 12): {NINT} intervals of width 1/{int(1 / WIDTH)}, degree {DEG} in"
+             f" u = {int(2 / WIDTH)} (t - centre)",
              f"#define HSE_ERFCX_NINT {NINT}", f"#define HSE_ERFCX_DEG {DEG}",
+             f"#define HSE_ERFCX_INV_WIDTH {int(1 / WIDTH)}",
              "#define HSE_ERFCX_COEFS \\"]
     for i in range(NINT):
         a = WIDTH * i
@@ -47,12 +51,14 @@ def main():
         lines.append("    " + ", ".join(mp.nstr(x, 20, strip_zeros=False) for x in co) +
                      (", \\" if i < NINT - 1 else ""))
     ln2 = mp.log(2)
-    head = mp.mpf(float(mp.floor(ln2 * 2 ** 40))) / 2 ** 40
-    tail = ln2 - head
-    lines.append(f"constexpr double kLn2Head = {mp.nstr(head, 25)};")
-    lines.append(f"constexpr double kLn2Tail = {mp.nstr(tail, 25)};")
-    lines.append(f"constexpr double kLog2e = {mp.nstr(1 / ln2, 25)};")
-    lines.append("#define HSE_EXP_TAYLOR_COEFS " + ", ".join(mp.nstr(1 / mp.factorial(k), 25) for k in range(14)))
+    c = ln2 / 64
+    e = mp.floor(mp.log(c, 2))
+    head = mp.floor(c / mp.mpf(2) ** (e - 35)) * mp.mpf(2) ** (e - 35)  # 36 significant bits
+    lines.append(f"constexpr double kLn2By64Head = {mp.nstr(head, 25)};")
+    lines.append(f"constexpr double kLn2By64Tail = {mp.nstr(c - head, 25)};")
+    lines.append(f"constexpr double k64Log2e = {mp.nstr(64 / ln2, 25)};")
+    lines.append("#define HSE_EXP_TAYLOR5_COEFS " + ", ".join(mp.nstr(1 / mp.factorial(k), 25) for k in range(6)))
+    lines.append("#define HSE_EXP2_J64 " + ", ".join(mp.nstr(mp.mpf(2) ** (mp.mpf(j) / 64), 25) for j in range(64)))
     open(out, "w").write("\n".join(lines) + "\n")
     print("wrote", out)
 

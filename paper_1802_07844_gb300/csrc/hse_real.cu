@@ -20,9 +20,9 @@
 //   G_R: g0 = E_r, grad = -a1 r, grad grad = -a1 I + g2 r r, grad^3 with g2, g3.
 //
 // FP64 throughput (2 FMA/clk/SM on GB300) bounds this stage, so:
-//  * erfc(t) = exp(-t^2) erfcx(t), erfcx by degree-10 polynomials on intervals
-//    of width 1/4 (table from gen_special_tables.py), exp by Cody-Waite
-//    reduction and a degree-13 Taylor polynomial;
+//  * erfc(t) = exp(-t^2) erfcx(t), erfcx by degree-8 polynomials on intervals
+//    of width 1/8 (table from gen_special_tables.py), exp by Tang's
+//    table-driven reduction and a degree-5 Taylor polynomial;
 //  * candidates are screened in FP32 with a proven error margin; only those
 //    within the margin of r_c take the exact FP64 test, so the accepted set
 //    equals the FP64 rule ((dx*dx + dy*dy) + dz*dz < r_c^2, no contraction);
@@ -38,6 +38,7 @@
 namespace hse {
 
 __device__ const double d_erfcx_coef[HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1)] = {HSE_ERFCX_COEFS};
+__device__ const double d_exp2_j64[64] = {HSE_EXP2_J64};
 
 struct RealArgs {
   int64_t n_src, n_tgt;
@@ -73,32 +74,36 @@ __device__ __forceinline__ int cell_base(const RealArgs& a, int64_t sorted_idx) 
 enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2, Q_FAR = 4 };  // Q_FAR: flag on FREE / IMAGE
 constexpr int kWarpsPerBlock = 4;
 constexpr int kQueue = 64;
-constexpr int kTabN = HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1);
+constexpr int kErfcxN = HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1);
+constexpr int kTabN = kErfcxN + 64;  // erfcx intervals, then 2^{j/64}
 
-// e^{-x} for 0 <= x (Cody-Waite: x log2 e = n + f, e^{-x} = 2^-n e^r)
-__device__ __forceinline__ double exp_neg(double x) {
+// e^{-x} for 0 <= x (Tang's table-driven method, ACM TOMS 15, 1989):
+// -x = m ln2/64 + r, |r| <= ln2/128, m = 64 n + j, e^{-x} = 2^n 2^{j/64} e^r,
+// 2^{j/64} from the table t2 (shared memory), e^r from its degree-5 Taylor
+// polynomial; 10 FP64 operations.
+__device__ __forceinline__ double exp_neg(double x, const double* t2) {
   if (x > 700.0) return 0.0;
   const double magic = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low word
-  double y = -x;
-  double tn = fma(y, kLog2e, magic);
-  int n = __double2loint(tn);
-  double nd = tn - magic;
-  double r = fma(-nd, kLn2Head, y);
-  r = fma(-nd, kLn2Tail, r);
-  constexpr double C[14] = {HSE_EXP_TAYLOR_COEFS};
-  double p = C[13];
+  const double y = -x;
+  const double tn = fma(y, k64Log2e, magic);
+  const int m = __double2loint(tn);
+  const double md = tn - magic;
+  double r = fma(-md, kLn2By64Head, y);
+  r = fma(-md, kLn2By64Tail, r);
+  constexpr double C[6] = {HSE_EXP_TAYLOR5_COEFS};
+  double p = C[5];
 #pragma unroll
-  for (int k = 12; k >= 0; --k) p = fma(p, r, C[k]);
-  double scale = __hiloint2double((n + 1023) << 20, 0);
-  return p * scale;
+  for (int k = 4; k >= 0; --k) p = fma(p, r, C[k]);
+  const double v = t2[m & 63] * p;  // in [2^-1/128, 2^(1+1/128)): scaling by 2^n stays normal
+  return __hiloint2double(__double2hiint(v) + (int)((unsigned)(m >> 6) << 20), __double2loint(v));
 }
 
 // erfcx(t) = e^{t^2} erfc(t) on [0, 12) from the interval table in shared memory
 __device__ __forceinline__ double erfcx_tab(double t, float tf, const double* tab) {
-  int k = (int)(tf * 4.0f);
+  int k = (int)(tf * (float)HSE_ERFCX_INV_WIDTH);
   k = k < 0 ? 0 : (k > HSE_ERFCX_NINT - 1 ? HSE_ERFCX_NINT - 1 : k);
   const double* c = tab + k * (HSE_ERFCX_DEG + 1);
-  double u = fma(8.0, t, -(double)(2 * k + 1));
+  double u = fma(2.0 * HSE_ERFCX_INV_WIDTH, t, -(double)(2 * k + 1));
   double p = c[HSE_ERFCX_DEG];
 #pragma unroll
   for (int j = HSE_ERFCX_DEG - 1; j >= 0; --j) p = fma(p, u, c[j]);
@@ -115,9 +120,9 @@ __device__ __forceinline__ Radial<double> radial(double s, float sf, double xi, 
   Radial<double> R;
   double inv = rsqrt(s);
   double t = xi * s * inv;
-  double E = exp_neg(t * t);
+  double E = exp_neg(t * t, tab + kErfcxN);
   double ec;
-  if (t < 0.25 * HSE_ERFCX_NINT) ec = E * erfcx_tab(t, (float)xi * sqrtf(sf), tab);
+  if (t < (double)HSE_ERFCX_NINT / HSE_ERFCX_INV_WIDTH) ec = E * erfcx_tab(t, (float)xi * sqrtf(sf), tab);
   else ec = erfc(t);  // beyond the table: only reached when xi r_c > 12
   double i2 = inv * inv;
   R.c = (2.0 / kSqrtPi) * xi * E;
@@ -349,7 +354,7 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
 }
 
 __device__ __forceinline__ void load_table(double* tab) {
-  for (int i = threadIdx.x; i < kTabN; i += blockDim.x) tab[i] = d_erfcx_coef[i];
+  for (int i = threadIdx.x; i < kTabN; i += blockDim.x) tab[i] = i < kErfcxN ? d_erfcx_coef[i] : d_exp2_j64[i - kErfcxN];
   __syncthreads();
 }
 
