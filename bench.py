@@ -186,6 +186,8 @@ def run_ours(args, rank, world, local_rank):
     pr = replica_problem(rank, W["n"])
     if args.real_only:
         return run_real_only(args, pkg, torch, dev, W, pr)
+    if args.fourier_small:
+        return run_fourier_small(args, pkg, torch, dev, W)
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
     plan.set_timing(True)
     prm = plan.params
@@ -533,6 +535,34 @@ def run_real_only(args, pkg, torch, dev, W, pr):
             "ms_per_step": dt * 1e3}
 
 
+# Profiling aid: the Fourier half of the bench workload's kind at 1/8 of its
+# grid (Mt = 160) and the same particle density and support (P = 18), small
+# enough (3.7 GB of grids) for full ncu captures of the spread, transform,
+# scale and gather kernels.
+FOURIER_SMALL = dict(n=100000, xi=44.0, rc=0.11, P=18, M=142)
+
+
+def run_fourier_small(args, pkg, torch, dev, W):
+    F = dict(FOURIER_SMALL)
+    if args.n:
+        F["n"] = args.n
+    pr = replica_problem(0, F["n"])
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=F["xi"], rc=F["rc"], P=F["P"], tol=0.0, M=F["M"])
+    src = torch.from_numpy(pr.src).to(dev)
+    st = torch.from_numpy(pr.strengths).to(dev)
+    for _ in range(args.warmup):
+        plan.eval_parts(src, st, real=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.eval_parts(src, st, real=False)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    mt = plan.params["Mt"]
+    plan.close()
+    return {"profiling_run": "Fourier half only, small grid", "n": F["n"], "Mt": mt, "ms_per_step": dt * 1e3}
+
+
 # ---------------------------------------------------------- reference arm
 def run_reference(args):
     W = dict(WORKLOAD)
@@ -583,6 +613,8 @@ def main():
     ap.add_argument("--real-only", action="store_true",
                     help="profiling aid: plan without a grid, time only the real-space half")
     ap.add_argument("--mixed", action="store_true", help="with --real-only: the mixed-precision leg's plan")
+    ap.add_argument("--fourier-small", action="store_true",
+                    help="profiling aid: Fourier half only on a grid of Mt = 160 (100k sources)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -114,6 +114,16 @@ __device__ __forceinline__ df df_dot2_raw(df a, df b, df c, df d) {
   return df(s, e);
 }
 
+// multiply-accumulate acc + a b and the product a b in the grid element type:
+// FMA for double and float, an unnormalised product added with renormalisation
+// for df64 (products that only feed a sum need no renormalisation of their own)
+__device__ __forceinline__ double mac(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ __forceinline__ float mac(float acc, float a, float b) { return fmaf(a, b, acc); }
+__device__ __forceinline__ df mac(df acc, df a, df b) { return acc + df_mul_raw(a, b); }
+__device__ __forceinline__ double mulr(double a, double b) { return a * b; }
+__device__ __forceinline__ float mulr(float a, float b) { return a * b; }
+__device__ __forceinline__ df mulr(df a, df b) { return df_mul_raw(a, b); }
+
 // complex df64, laid out like a complex double (16 bytes)
 struct __align__(16) cdf {
   df x, y;

@@ -187,8 +187,10 @@ constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub
 // 4 (second derivatives).
 template <typename T, int NC, int DK>
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
-  __shared__ int list[256];
-  __shared__ int wcount[8];
+  // per-warp lists of the sources that reach the warp's sub-tile, in source
+  // order (bit 31: the FP32 small-weight record applies)
+  __shared__ int wlist[8][256];
+  __shared__ int wcount[8][8];  // [sub-tile b][warp w]: sources of warp w's batch that reach b
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int inst = blockIdx.z / a.nz_tiles, ztile = blockIdx.z - inst * a.nz_tiles;
   const int cbase = inst * a.ncells_inst;
@@ -219,47 +221,67 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   cell_range(by0, by0 + kTY - 1, a.ox, 1, cy0, cy1);
   cell_range(bz0, bz0 + kTZ - 1, a.oz, 2, cz0, cz1);
   const int nx = a.ncell[0], ny = a.ncell[1];
+  const unsigned below = (1u << lane) - 1;
   for (int cz = cz0; cz <= cz1; ++cz)
     for (int cy = cy0; cy <= cy1; ++cy) {
       int c0 = cbase + (cz * ny + cy) * nx + cx0;
       int s0 = a.cstart[c0], s1 = a.cstart[c0 + (cx1 - cx0) + 1];
       for (int base = s0; base < s1; base += 256) {
-        int j = base + tid;
-        bool hit = false;
+        // one thread per source: which of the 8 warp sub-tiles (2 x 4 x 4)
+        // its support reaches, and for which of them every weight is below
+        // the FP32 threshold (distance from the source to the sub-tile, less
+        // half a step for the FP32 position: if even the nearest point has
+        // weight below the threshold, so do all)
+        const int j = base + tid;
+        unsigned wm = 0, smask = 0;
         if (j < s1) {
-          int4 s = a.supp[j];
-          hit = s.x <= bx0 + kTX - 1 && s.x + P - 1 >= bx0 && s.y <= by0 + kTY - 1 && s.y + P - 1 >= by0 &&
-                s.z <= bz0 + kTZ - 1 && s.z + P - 1 >= bz0;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) wcount[w] = __popc(m);
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int ww = 0; ww < 8; ++ww) { off += ww < w ? wcount[ww] : 0; tot += wcount[ww]; }
-        if (hit) list[off + __popc(m & ((1u << lane) - 1))] = j;
-        __syncthreads();
-        for (int e = 0; e < tot; ++e) {
-          int jj = list[e];
-          int4 s = a.supp[jj];
-          bool warp_hit = s.x <= sx + 1 && s.x + P - 1 >= sx && s.y <= sy + 3 && s.y + P - 1 >= sy &&
-                          s.z <= sz + 3 && s.z + P - 1 >= sz;
-          if (!warp_hit) continue;
-          int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
-          bool small = false;
-          if constexpr (sizeof(T) == 8) {
-            if (split) {
-              // distance (grid steps) from the particle to the warp's 2 x 4 x 4
-              // points, less half a step for the FP32 position: if even the
-              // nearest point has weight below the threshold, so do all
-              const int64_t n = a.n_src;
-              const float gx = (a.spos32[jj] - oxf) * inv_h, gy = (a.spos32[n + jj] - oxf) * inv_h;
-              const float gz = (a.spos32[2 * n + jj] - ozf) * inv_h;
-              const float ex = fmaxf(0.f, fmaxf((float)sx - gx, gx - (float)(sx + 1)) - 0.5f);
-              const float ey = fmaxf(0.f, fmaxf((float)sy - gy, gy - (float)(sy + 3)) - 0.5f);
-              const float ez = fmaxf(0.f, fmaxf((float)sz - gz, gz - (float)(sz + 3)) - 0.5f);
-              small = a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr;
+          const int4 sp = a.supp[j];
+          float gx = 0.f, gy = 0.f, gz = 0.f;
+          if (split) {
+            const int64_t n = a.n_src;
+            gx = (a.spos32[j] - oxf) * inv_h;
+            gy = (a.spos32[n + j] - oxf) * inv_h;
+            gz = (a.spos32[2 * n + j] - ozf) * inv_h;
+          }
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const int tx = bx0 + 2 * (b & 1), ty = by0 + 4 * ((b >> 1) & 1), tz = bz0 + 4 * (b >> 2);
+            const bool hb = sp.x <= tx + 1 && sp.x + P - 1 >= tx && sp.y <= ty + 3 && sp.y + P - 1 >= ty &&
+                            sp.z <= tz + 3 && sp.z + P - 1 >= tz;
+            if (hb) {
+              wm |= 1u << b;
+              if (split) {
+                const float ex = fmaxf(0.f, fmaxf((float)tx - gx, gx - (float)(tx + 1)) - 0.5f);
+                const float ey = fmaxf(0.f, fmaxf((float)ty - gy, gy - (float)(ty + 3)) - 0.5f);
+                const float ez = fmaxf(0.f, fmaxf((float)tz - gz, gz - (float)(tz + 3)) - 0.5f);
+                if (a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr) smask |= 1u << b;
+              }
             }
           }
+        }
+        unsigned mb[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          mb[b] = __ballot_sync(0xffffffffu, (wm >> b) & 1u);
+          if (lane == 0) wcount[b][w] = __popc(mb[b]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+          if ((wm >> b) & 1u) {
+            int off = 0;
+            for (int ww = 0; ww < w; ++ww) off += wcount[b][ww];
+            wlist[b][off + __popc(mb[b] & below)] = j | (int)(((smask >> b) & 1u) << 31);
+          }
+        int tot = 0;
+        for (int ww = 0; ww < 8; ++ww) tot += wcount[w][ww];
+        __syncthreads();
+        for (int e = 0; e < tot; ++e) {
+          const int entry = wlist[w][e];
+          const int jj = entry & 0x7fffffff;
+          const bool small = entry < 0;
+          int4 s = a.supp[jj];
+          int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
           if (small) {
             if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
               const float* o = a.prep32 + (int64_t)jj * a.stride;
@@ -282,18 +304,22 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
           } else if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
             const T* o = a.prep + (int64_t)jj * a.stride;
             const T wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
-            const T wyz = wy * wz;
-            const T wv = wx * wyz;
+            const T wyz = mulr(wy, wz);
+            const T wv = mulr(wx, wyz);
             const T* cv = o + (NWIN + NXX) * P;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] += wv * cv[c];
+            for (int c = 0; c < NC; ++c) acc[c] = mac(acc[c], wv, cv[c]);
             if constexpr (DK != 0) {
               const T* xx = o + NWIN * P + dx;
               const T dwy = o[3 * P + dy], dwz = o[4 * P + dz];
-              accD += xx[0] * wyz + xx[P] * (dwy * wz) + xx[2 * P] * (wy * dwz);
+              accD = mac(accD, xx[0], wyz);
+              accD = mac(accD, xx[P], mulr(dwy, wz));
+              accD = mac(accD, xx[2 * P], mulr(wy, dwz));
               if constexpr ((DK & 4) != 0) {
                 const T ddwy = o[5 * P + dy], ddwz = o[6 * P + dz];
-                accD += xx[3 * P] * (ddwy * wz) + xx[4 * P] * (wy * ddwz) + xx[5 * P] * (dwy * dwz);
+                accD = mac(accD, xx[3 * P], mulr(ddwy, wz));
+                accD = mac(accD, xx[4 * P], mulr(wy, ddwz));
+                accD = mac(accD, xx[5 * P], mulr(dwy, dwz));
               }
             }
           }
@@ -565,20 +591,20 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
         const T wv = wx[ii];
         const T* pnt = col + (int64_t)ii * a.xs;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) s[c] += wv * pnt[c * a.bs];
+        for (int c = 0; c < 3; ++c) s[c] = mac(s[c], wv, pnt[c * a.bs]);
         if (NF == 4) {
           const T ph = pnt[3 * a.bs];
-          s0 += wv * ph;
-          s1 += dwx[ii] * ph;
+          s0 = mac(s0, wv, ph);
+          s1 = mac(s1, dwx[ii], ph);
         }
       }
-      const T wyz = wy[jj] * wz[kk];
+      const T wyz = mulr(wy[jj], wz[kk]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] += gacc(wyz * s[c]);
+      for (int c = 0; c < 3; ++c) acc[c] += gacc(mulr(wyz, s[c]));
       if (NF == 4) {
-        acc[3] += gacc(wyz * s1);
-        acc[4] += gacc(dwy[jj] * wz[kk] * s0);
-        acc[5] += gacc(wy[jj] * dwz[kk] * s0);
+        acc[3] += gacc(mulr(wyz, s1));
+        acc[4] += gacc(mulr(mulr(dwy[jj], wz[kk]), s0));
+        acc[5] += gacc(mulr(mulr(wy[jj], dwz[kk]), s0));
       }
     }
     double accd[NF == 4 ? 6 : 3];
