@@ -242,7 +242,9 @@ Chunk next_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const int* id
   const double plane_bytes = (double)p->g.buf_doubles / p->g.Nx * esz;
   cap = std::min<int64_t>(cap, std::max<int64_t>(1, (int64_t)(kMaxXStride / (plane_bytes * p->comps.n))));
   cap = std::min<int64_t>(cap, (int64_t(1) << 30) / ncells);
-  cap = std::min<int64_t>(cap, 65535 / ((2 * q.Mt + 7) / 8));  // spread grid: z blocks = instances x z tiles (8)
+  // spread grid: z blocks = instances x z tiles of 8 (up to 7 points of the
+  // first tile below z = 0 with double-float grids)
+  cap = std::min<int64_t>(cap, 65535 / ((2 * q.Mt + 14) / 8));
   const int64_t max_particles = int64_t(1) << 28;
   Chunk c{idx, 0, 0};
   while (c.m < remaining && c.m < cap) {

@@ -220,10 +220,13 @@ __global__ void k_twiddles(int N, float4* __restrict__ tw) {
 }
 
 // ------------------------------------------------------------ C2C passes
+// Elements e >= nload of a line are taken as zero (not read), and only
+// elements e < nstore are written back: the data region of a forward pass's
+// input and the part of an inverse pass's output that later steps read.
 template <bool FWD>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4* __restrict__ data, LineGeo g,
                                                       const FftSteps* __restrict__ st, int lsh,
-                                                      const float4* __restrict__ tw) {
+                                                      const float4* __restrict__ tw, int nload, int nstore) {
   extern __shared__ float4 sm[];
   __shared__ long long start[16];
   const int lpb = 1 << lsh, n = st->N << lsh;
@@ -232,11 +235,12 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const long long o = start[i & (lpb - 1)];
-      sm[i] = o >= 0 ? data[o + (long long)(i >> lsh) * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int e = i >> lsh;
+      sm[i] = o >= 0 && e < nload ? data[o + (long long)e * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     const float4* res = transform_block<FWD>(sm, sm + n, st, lsh, tw);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (nstore << lsh); i += blockDim.x) {
       const long long o = start[i & (lpb - 1)];
       if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = res[i];
     }
@@ -251,11 +255,12 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4
 // w = exp(-2 pi i / 2N), written in place over the line (2N + 2 doubles hold
 // N + 1 complex df64 values).  The inverse forms Z_k = (X_k + conj X_{N-k})
 // + i conj(w^k) (X_k - conj X_{N-k}), transforms back (unnormalised, like a
-// C2R transform) and writes the first nkeep values of the line.
+// C2R transform) and writes the first nkeep values of the line.  The forward
+// pass reads the first 2 nload real values only (the rest is zero).
 template <bool FWD>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __restrict__ data, LineGeo g, const FftSteps* __restrict__ st,
                                                   int lsh, const float4* __restrict__ tw,
-                                                  const float4* __restrict__ tw2, int nkeep) {
+                                                  const float4* __restrict__ tw2, int nkeep, int nload) {
   extern __shared__ float4 sm[];
   __shared__ long long start[16];
   const int lpb = 1 << lsh, N = st->N;
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
         cdf z = cdf_make(df(0.f, 0.f), df(0.f, 0.f));
         if (o >= 0) {
           if (FWD) {
-            z = ld_cdf(reinterpret_cast<const float4*>(data + o + 2 * k));  // x_2k, x_2k+1
+            if (k < nload) z = ld_cdf(reinterpret_cast<const float4*>(data + o + 2 * k));  // x_2k, x_2k+1
           } else {
             const float4* X = reinterpret_cast<const float4*>(data + o);
             const cdf xk = ld_cdf(X + k), xn = conj(ld_cdf(X + N - k));
@@ -374,20 +379,24 @@ static unsigned grid_for(long long nlines, int lsh) {
   return (unsigned)(blocks < cap ? blocks : cap);
 }
 
-static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fwd, cudaStream_t s) {
+static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fwd, int nload, int nstore,
+                            cudaStream_t s) {
   const Fft64Tables* t = tables(p);
   const int lsh = lines_per_block_log2(t->sx.N);
   const unsigned threads = (unsigned)(threads_per_line(t->sx.N) << lsh);
   const size_t shm = 2 * sizeof(float4) * ((size_t)t->sx.N << lsh);
   if (geo.nlines <= 0) return HSE_OK;
   float4* c = reinterpret_cast<float4*>(buf);
-  if (fwd) k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw);
-  else k_fft_lines<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw);
+  if (fwd)
+    k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw, nload, nstore);
+  else
+    k_fft_lines<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw, nload, nstore);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_fft_lines");
 }
 
-static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, int nkeep, cudaStream_t s) {
+static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, int nkeep, int nload,
+                        cudaStream_t s) {
   const Fft64Tables* t = tables(p);
   const int N = t->sz.N, lsh = lines_per_block_log2(N);
   const unsigned threads = (unsigned)(threads_per_line(N) << lsh);
@@ -395,27 +404,28 @@ static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, i
   if (geo.nlines <= 0) return HSE_OK;
   const float4* tw = t->tw + t->sx.N;
   const float4* tw2 = tw + N;
-  if (fwd) k_fft_z<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep);
-  else k_fft_z<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep);
+  if (fwd) k_fft_z<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep, nload);
+  else k_fft_z<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep, nload);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), fwd ? "k_fft_z<fwd>" : "k_fft_z<inv>");
 }
 
 // Geometry of the grids: buffer b's real element (x, y, z) at
 // x * xs + b * bs + y * pitch + z (8-byte units), nb buffers transformed together.
-// Data occupy x < Mt, y < Mt, z < 2 Mt and the rest of the real grid is zero
-// on input.  As complex values the half spectrum (kx, ky, kz) of buffer b sits
-// at (kx * xs + b * bs) / 2 + ky * nzh + kz.
+// Data occupy x < Mt, y < Mt, z < 2 Mt; the rest of the real grid is never
+// read (taken as zero), so it needs no clearing.  As complex values the half
+// spectrum (kx, ky, kz) of buffer b sits at (kx * xs + b * bs) / 2 + ky * nzh + kz.
 hse_status fft64_forward(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s) {
   const GridDims& g = p->g;
   const long long Mt = g.Mt, nzh = g.Nz / 2 + 1, pitch = g.pitch;
-  // z: lines (x < Mt, b, y < Mt)
-  HSE_TRY(run_z(p, base, LineGeo{Mt * nb * Mt, Mt, nb, pitch, bs, xs, 1}, true, 0, s));
-  // y: lines (x < Mt, b, kz), elements y
-  HSE_TRY(run_lines(p, base, LineGeo{Mt * nb * nzh, nzh, nb, 1, bs / 2, xs / 2, nzh}, true, s));
-  // x: lines (b, y, kz) of every buffer, elements x
+  const int N = (int)g.Nx, mt = (int)Mt;
+  // z: lines (x < Mt, b, y < Mt), data at z < 2 Mt (Mt complex pairs)
+  HSE_TRY(run_z(p, base, LineGeo{Mt * nb * Mt, Mt, nb, pitch, bs, xs, 1}, true, 0, mt, s));
+  // y: lines (x < Mt, b, kz), elements y (data at y < Mt)
+  HSE_TRY(run_lines(p, base, LineGeo{Mt * nb * nzh, nzh, nb, 1, bs / 2, xs / 2, nzh}, true, mt, N, s));
+  // x: lines (b, y, kz) of every buffer, elements x (data at x < Mt)
   return run_lines(p, base, LineGeo{(long long)nb * g.Ny * nzh, (long long)g.Ny * nzh, nb, 1, bs / 2, 0, xs / 2},
-                   true, s);
+                   true, mt, N, s);
 }
 
 // Inverse (unnormalised): df64 half spectra -> df64 values at x < Mt, y < Mt,
@@ -423,10 +433,13 @@ hse_status fft64_forward(hse_plan p, double* base, int nb, long long bs, long lo
 hse_status fft64_inverse(hse_plan p, double* base, int nb, long long bs, long long xs, cudaStream_t s) {
   const GridDims& g = p->g;
   const long long Mt = g.Mt, nzh = g.Nz / 2 + 1, pitch = g.pitch;
+  const int N = (int)g.Nx, mt = (int)Mt;
+  // x: every line, written back for x < Mt (the planes the later passes read)
   HSE_TRY(run_lines(p, base, LineGeo{(long long)nb * g.Ny * nzh, (long long)g.Ny * nzh, nb, 1, bs / 2, 0, xs / 2},
-                    false, s));
-  HSE_TRY(run_lines(p, base, LineGeo{Mt * nb * nzh, nzh, nb, 1, bs / 2, xs / 2, nzh}, false, s));
-  return run_z(p, base, LineGeo{Mt * nb * Mt, Mt, nb, pitch, bs, xs, 1}, false, (int)(2 * Mt), s);
+                    false, N, mt, s));
+  // y: the planes x < Mt, written back for y < Mt
+  HSE_TRY(run_lines(p, base, LineGeo{Mt * nb * nzh, nzh, nb, 1, bs / 2, xs / 2, nzh}, false, N, mt, s));
+  return run_z(p, base, LineGeo{Mt * nb * Mt, Mt, nb, pitch, bs, xs, 1}, false, (int)(2 * Mt), (int)(Mt), s);
 }
 
 }  // namespace hse

@@ -170,6 +170,7 @@ struct SpreadArgs {
   float ah2, lnthr;      // alpha h^2 (window exponent per squared grid step), ln(1/threshold)
   const int32_t* cstart;
   int stride, P, Mt, z0, nz_tiles;
+  int zlo;               // lowest z index any source support reaches (tiles below only write zeros)
   double h, ox, oz;
   double inv_cell[3];
   int ncell[3];
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   cell_range(bz0, bz0 + kTZ - 1, a.oz, 2, cz0, cz1);
   const int nx = a.ncell[0], ny = a.ncell[1];
   const unsigned below = (1u << lane) - 1;
+  if (bz0 + kTZ <= a.zlo) cz1 = cz0 - 1;  // no support reaches the tile: zeros only
   for (int cz = cz0; cz <= cz1; ++cz)
     for (int cy = cy0; cy <= cy1; ++cy) {
       int c0 = cbase + (cz * ny + cy) * nx + cx0;
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
         __syncthreads();
       }
     }
-  if (px < a.Mt && py < a.Mt && pz < 2 * a.Mt) {
+  if (px < a.Mt && py < a.Mt && pz >= 0 && pz < 2 * a.Mt) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] += from32<T>(acc32[c]);
     accD += from32<T>(accD32);
@@ -664,9 +666,13 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   return a;
 }
 
+// full_z: the spread's tiles cover z from 0 (not from the lowest z a support
+// reaches), so every point of the data region x, y < Mt, z < 2 Mt is written
+// (zero where no source reaches) and the grid needs no clearing beforehand.
 template <typename T>
 static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int paper, T* out, int64_t cstride,
-                              int64_t xs, int64_t pitch, cudaStream_t s, int n_inst = 1, int64_t istride = 0) {
+                              int64_t xs, int64_t pitch, cudaStream_t s, int n_inst = 1, int64_t istride = 0,
+                              bool full_z = false) {
   const hse_params& q = p->prm;
   PrepArgs<T> pa = prep_args<T>(p, n_src, paper, cs.n);
   if (n_src > 0) {
@@ -689,7 +695,11 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.stride = pa.stride;
   a.P = q.P;
   a.Mt = q.Mt;
-  a.z0 = p->zA0;
+  // full_z: tiles on the same z boundaries as from zA0, extended down to the
+  // first tile at or below 0 (the same warp sub-tiles, so the same FP32 /
+  // higher-precision split of the small weights as without full_z)
+  a.z0 = full_z ? p->zA0 - ((p->zA0 + kTZ - 1) / kTZ) * kTZ : p->zA0;
+  a.zlo = p->zA0;
   a.h = q.h;
   a.ox = pa.ox;
   a.oz = pa.oz;
@@ -700,7 +710,7 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.pitch = pitch;
   a.is = istride;
   a.ncells_inst = q.ncell[0] * q.ncell[1] * q.ncell[2];
-  int nzr = 2 * q.Mt - p->zA0;
+  int nzr = 2 * q.Mt - a.z0;
   a.nz_tiles = (nzr + kTZ - 1) / kTZ;
   dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, a.nz_tiles * n_inst);
   const int dk = paper ? 0 : deriv_kind(q.kernel_mask);
@@ -794,8 +804,13 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   const GridDims& g = p->g;
   const int nin = p->comps.n;
   T* spec = reinterpret_cast<T*>(p->spec);
-  HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nin, s));
-  HSE_TRY(spread_into<T>(p, n_src, p->comps, 0, spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s));
+  // cuFFT reads the whole padded grid (zeros outside the data region); the
+  // double-float transforms read only the data region, which the spread
+  // writes in full
+  constexpr bool full_z = std::is_same<T, df>::value;
+  if (!full_z) HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nin, s));
+  HSE_TRY(spread_into<T>(p, n_src, p->comps, 0, spec, g.buf_doubles, (int64_t)g.Ny * g.pitch, g.pitch, s, 1, 0,
+                         full_z));
   stage_mark(p, HSE_STAGE_FFT, s);
   // double-float grids go with the double-float transforms; double and float
   // grids with cuFFT
@@ -1010,8 +1025,10 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   T* spec = reinterpret_cast<T*>(specv);
   const int64_t nzh = g.Nz / 2 + 1, plane = (int64_t)g.Ny * g.pitch, planec = (int64_t)g.Ny * nzh;
   const int64_t nbuf = (int64_t)nin * n_inst;
-  HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nbuf, s));
-  HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, plane * n_inst, plane * nbuf, g.pitch, s, n_inst, plane));
+  constexpr bool full_z = std::is_same<T, df>::value;  // as in fourier_space_t
+  if (!full_z) HSE_CUDA(p, cudaMemsetAsync(spec, 0, sizeof(T) * g.buf_doubles * nbuf, s));
+  HSE_TRY(spread_into<T>(p, n_total, p->comps, 0, spec, plane * n_inst, plane * nbuf, g.pitch, s, n_inst, plane,
+                         full_z));
   stage_mark(p, HSE_STAGE_FFT, s);
   constexpr bool df64 = std::is_same<T, df>::value;
   if constexpr (df64) {
