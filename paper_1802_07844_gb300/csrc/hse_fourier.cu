@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   for (int c = 0; c < NC; ++c) { acc[c] = (T)0; acc32[c] = 0.f; }
   const bool split = sizeof(T) == 8 && a.prep32 != nullptr;
   const float inv_h = (float)(1.0 / a.h), oxf = (float)a.ox, ozf = (float)a.oz;
+  const float fbx = (float)bx0, fby = (float)by0, fbz = (float)bz0;  // tile origin (no per-source conversions)
   // positions whose support can reach this tile (one grid step of slack for clamping)
   auto cell_range = [&](int lo_idx, int hi_idx, double o, int d, int& c0, int& c1) {
     double lo = o + (lo_idx - P / 2 - 1) * a.h, hi = o + (hi_idx + P / 2 + 1) * a.h;
@@ -253,9 +254,11 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
             if (hb) {
               wm |= 1u << b;
               if (split) {
-                const float ex = fmaxf(0.f, fmaxf((float)tx - gx, gx - (float)(tx + 1)) - 0.5f);
-                const float ey = fmaxf(0.f, fmaxf((float)ty - gy, gy - (float)(ty + 3)) - 0.5f);
-                const float ez = fmaxf(0.f, fmaxf((float)tz - gz, gz - (float)(tz + 3)) - 0.5f);
+                const float fx = fbx + (float)(2 * (b & 1)), fy = fby + (float)(4 * ((b >> 1) & 1));
+                const float fz = fbz + (float)(4 * (b >> 2));
+                const float ex = fmaxf(0.f, fmaxf(fx - gx, gx - (fx + 1.f)) - 0.5f);
+                const float ey = fmaxf(0.f, fmaxf(fy - gy, gy - (fy + 3.f)) - 0.5f);
+                const float ez = fmaxf(0.f, fmaxf(fz - gz, gz - (fz + 3.f)) - 0.5f);
                 if (a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr) smask |= 1u << b;
               }
             }

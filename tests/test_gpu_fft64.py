@@ -113,3 +113,21 @@ def test_df64_full_eval_vs_oracle(pkg):
     ref = oracle.direct(mask, pr.src, pr.strengths)
     assert rel(u, ref) < 1e-9
     plan.close()
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S | KERNEL_W, KERNEL_T])
+def test_df64_at_the_tightest_automatic_tolerance(pkg, mask):
+    # tol = 1e-12 is the tightest tolerance the automatic rule serves with df64:
+    # the whole evaluation (df64 grids and transforms) must meet it against the
+    # direct half-space sum, as the cuFFT-double path does
+    pr = problem(mask, 1500, 1.0, "near_wall", 82)
+    ref = oracle.direct(mask, pr.src, pr.strengths)
+    src, st = dev(pr.src), dev(pr.strengths)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=8.0, tol=1e-12)
+    assert plan.params["fft"] == pkg.HSE_FFT_DF64
+    e_df = rel(host(plan.eval(src, st)), ref)
+    plan.set_fft(pkg.HSE_FFT_CUFFT)
+    e_cu = rel(host(plan.eval(src, st)), ref)
+    plan.close()
+    assert e_df < 1e-12 and e_cu < 1e-12
+    assert e_df < 2.0 * e_cu + 1e-14
