@@ -40,13 +40,16 @@ struct FftSteps {
   float kc[10];          // hi / lo of sin(2pi/3), cos(2pi/5), cos(4pi/5), sin(2pi/5), sin(4pi/5)
 };
 
-static bool make_steps(int N, FftSteps* st) {
-  if (N < 2 || N >= 65536) return false;
+// two_first: the first pass has radix 2 (used for inputs whose upper half is
+// zero: that pass reduces to a copy, done while loading)
+static bool make_steps(int N, FftSteps* st, bool two_first = false) {
+  if (N < 2 || N >= 65536 || (two_first && N % 2 != 0)) return false;
   FftSteps s{};
   s.N = N;
   int rem = N, Ns = 1;
   while (rem > 1) {
     int R = rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 5 == 0 ? 5 : rem % 3 == 0 ? 3 : 0;
+    if (two_first && s.npass == 0) R = 2;
     if (R == 0 || s.npass == kMaxPass) return false;
     s.R[s.npass] = R;
     s.Ns[s.npass] = Ns;
@@ -173,12 +176,12 @@ __device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, in
 // it freely.
 template <bool FWD>
 __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const FftSteps* __restrict__ st, int lsh,
-                                                   const float4* __restrict__ tw) {
+                                                   const float4* __restrict__ tw, int p0 = 0) {
   const int tpl = blockDim.x >> lsh;
   const int l = threadIdx.x & ((1 << lsh) - 1), tj = threadIdx.x >> lsh;
   const int N = st->N, npass = st->npass;
   const float* kc = st->kc;
-  for (int p = 0; p < npass; ++p) {
+  for (int p = p0; p < npass; ++p) {
     const int Ns = st->Ns[p], step = st->step[p];
     const unsigned magic = st->magic[p];
     switch (st->R[p]) {
@@ -233,13 +236,26 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4
   for (long long b0 = (long long)blockIdx.x * lpb; b0 < g.nlines; b0 += (long long)gridDim.x * lpb) {
     if (threadIdx.x < lpb) start[threadIdx.x] = b0 + threadIdx.x < g.nlines ? line_start(g, b0 + threadIdx.x) : -1;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const long long o = start[i & (lpb - 1)];
-      const int e = i >> lsh;
-      sm[i] = o >= 0 && e < nload ? data[o + (long long)e * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // half: the schedule starts with radix 2 and the input's upper half is zero,
+    // so that pass is a copy: element e < N/2 goes to positions 2e and 2e + 1
+    const bool half = nload * 2 == st->N && st->R[0] == 2;
+    if (half) {
+      for (int i = threadIdx.x; i < (nload << lsh); i += blockDim.x) {
+        const long long o = start[i & (lpb - 1)];
+        const int e = i >> lsh, l = i & (lpb - 1);
+        const float4 v = o >= 0 ? data[o + (long long)e * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
+        sm[((2 * e) << lsh) + l] = v;
+        sm[((2 * e + 1) << lsh) + l] = v;
+      }
+    } else {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const long long o = start[i & (lpb - 1)];
+        const int e = i >> lsh;
+        sm[i] = o >= 0 && e < nload ? data[o + (long long)e * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     __syncthreads();
-    const float4* res = transform_block<FWD>(sm, sm + n, st, lsh, tw);
+    const float4* res = transform_block<FWD>(sm, sm + n, st, lsh, tw, half ? 1 : 0);
     for (int i = threadIdx.x; i < (nstore << lsh); i += blockDim.x) {
       const long long o = start[i & (lpb - 1)];
       if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = res[i];
@@ -267,9 +283,12 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
   for (long long b0 = (long long)blockIdx.x * lpb; b0 < g.nlines; b0 += (long long)gridDim.x * lpb) {
     if (threadIdx.x < lpb) start[threadIdx.x] = b0 + threadIdx.x < g.nlines ? line_start(g, b0 + threadIdx.x) : -1;
     __syncthreads();
+    // forward with a zero upper half and a radix-2 first pass: that pass is a
+    // copy to positions 2k and 2k + 1, done here (as in k_fft_lines)
+    const bool half = FWD && nload * 2 == N && st->R[0] == 2;
     for (int l = 0; l < lpb; ++l) {
       const long long o = start[l];
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      for (int k = threadIdx.x; k < (half ? nload : N); k += blockDim.x) {
         cdf z = cdf_make(df(0.f, 0.f), df(0.f, 0.f));
         if (o >= 0) {
           if (FWD) {
@@ -281,11 +300,16 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
             z = (xk + xn) + mul_mi<false>(wk * (xk - xn));
           }
         }
-        st_cdf(sm + (k << lsh) + l, z);
+        if (half) {
+          st_cdf(sm + ((2 * k) << lsh) + l, z);
+          st_cdf(sm + ((2 * k + 1) << lsh) + l, z);
+        } else {
+          st_cdf(sm + (k << lsh) + l, z);
+        }
       }
     }
     __syncthreads();
-    const float4* res = transform_block<FWD>(sm, sm + (N << lsh), st, lsh, tw);
+    const float4* res = transform_block<FWD>(sm, sm + (N << lsh), st, lsh, tw, half ? 1 : 0);
     for (int l = 0; l < lpb; ++l) {
       const long long o = start[l];
       if (o < 0) continue;
@@ -313,7 +337,8 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
 // ------------------------------------------------------------------ driver
 struct Fft64Tables {
   FftSteps sx, sz;           // x / y lines (length Nx = Ny) and z half-lines (Nz / 2)
-  FftSteps* d_steps = nullptr;  // device copies {sx, sz}
+  FftSteps sxh, szh;         // the same with a radix-2 first pass (forward, zero upper half)
+  FftSteps* d_steps = nullptr;  // device copies {sx, sz, sxh, szh}
   float4* tw = nullptr;      // twiddles of lengths Nx, Nz / 2 and Nz, back to back
 };
 
@@ -335,6 +360,8 @@ hse_status fft64_prepare(hse_plan p) {
   Fft64Tables* t = new Fft64Tables();
   make_steps(g.Nx, &t->sx);
   make_steps(g.Nz / 2, &t->sz);
+  make_steps(g.Nx, &t->sxh, true);
+  make_steps(g.Nz / 2, &t->szh, true);
   const int n1 = g.Nx, nh = g.Nz / 2;
   cudaError_t e = cudaMalloc(&t->tw, sizeof(float4) * (n1 + nh + 2 * nh));
   if (e != cudaSuccess) {
@@ -342,9 +369,10 @@ hse_status fft64_prepare(hse_plan p) {
     return cuda_check(p, e, "cudaMalloc(df64 twiddles)");
   }
   p->fft64 = t;
-  HSE_CUDA(p, cudaMalloc(&t->d_steps, 2 * sizeof(FftSteps)));
-  HSE_CUDA(p, cudaMemcpy(t->d_steps, &t->sx, sizeof(FftSteps), cudaMemcpyHostToDevice));
-  HSE_CUDA(p, cudaMemcpy(t->d_steps + 1, &t->sz, sizeof(FftSteps), cudaMemcpyHostToDevice));
+  HSE_CUDA(p, cudaMalloc(&t->d_steps, 4 * sizeof(FftSteps)));
+  const FftSteps* hs[4] = {&t->sx, &t->sz, &t->sxh, &t->szh};
+  for (int i = 0; i < 4; ++i)
+    HSE_CUDA(p, cudaMemcpy(t->d_steps + i, hs[i], sizeof(FftSteps), cudaMemcpyHostToDevice));
   k_twiddles<<<(n1 + 255) / 256, 256>>>(n1, t->tw);
   k_twiddles<<<(nh + 255) / 256, 256>>>(nh, t->tw + n1);
   k_twiddles<<<(2 * nh + 255) / 256, 256>>>(2 * nh, t->tw + n1 + nh);
@@ -387,8 +415,9 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
   const size_t shm = 2 * sizeof(float4) * ((size_t)t->sx.N << lsh);
   if (geo.nlines <= 0) return HSE_OK;
   float4* c = reinterpret_cast<float4*>(buf);
-  if (fwd)
-    k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw, nload, nstore);
+  if (fwd)  // forward passes read a zero upper half: the radix-2-first schedule
+    k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps + 2, lsh, t->tw, nload,
+                                                                        nstore);
   else
     k_fft_lines<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw, nload, nstore);
   ++p->n_launch;
@@ -404,8 +433,12 @@ static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, i
   if (geo.nlines <= 0) return HSE_OK;
   const float4* tw = t->tw + t->sx.N;
   const float4* tw2 = tw + N;
-  if (fwd) k_fft_z<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep, nload);
-  else k_fft_z<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep, nload);
+  if (fwd)  // radix-2-first schedule, as for the forward line passes
+    k_fft_z<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 3, lsh, tw, tw2, nkeep,
+                                                                    nload);
+  else
+    k_fft_z<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(buf, geo, t->d_steps + 1, lsh, tw, tw2, nkeep,
+                                                                     nload);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), fwd ? "k_fft_z<fwd>" : "k_fft_z<inv>");
 }
