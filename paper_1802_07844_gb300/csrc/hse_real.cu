@@ -197,19 +197,26 @@ __device__ __forceinline__ void add_free(int mask, const Radial<T>& R, const T* 
 }
 
 // image contribution at a target of height x3 from source s of height h,
-// rt = x - y^I
+// rt = x - y^I.  The wall corrections' gradient is collected as
+// grad(phi) = ar r + gv (one coefficient of r shared by every kernel, plus the
+// strength-vector terms), which the final u -= x3 grad(phi) applies once.
 template <typename T>
 __device__ __forceinline__ void add_image(int mask, const Radial<T>& R, const T* r, T h, T x3, const Src<T>& s, T xi,
                                           T* u) {
   const T g1 = -R.a1, g2 = R.g2;
-  T phi = 0, gp[3] = {0, 0, 0};
+  T phi = 0, ar = 0, gv[3] = {0, 0, 0};
   if (mask & HSE_STOKESLET) {
+    // grad phi_S = 2 (-f3 g1 r - h (g1 fI + g2 r (r.fI)))
     T fI[3] = {s.f[0], s.f[1], -s.f[2]};
     T sa = R.er - R.c;
     T rf = r[0] * fI[0] + r[1] * fI[1] + r[2] * fI[2];
-    for (int i = 0; i < 3; ++i) u[i] -= sa * fI[i] + R.a1 * r[i] * rf;
-    phi += 2 * (-s.f[2] * R.er - h * g1 * rf);
-    for (int i = 0; i < 3; ++i) gp[i] += 2 * (-s.f[2] * g1 * r[i] - h * (g1 * fI[i] + g2 * r[i] * rf));
+    const T arf = R.a1 * rf;
+    for (int i = 0; i < 3; ++i) u[i] -= sa * fI[i] + arf * r[i];
+    const T hg1 = h * g1;
+    phi += 2 * (-s.f[2] * R.er - hg1 * rf);
+    ar -= 2 * (s.f[2] * g1 + h * g2 * rf);
+    const T cf = -2 * hg1;
+    for (int i = 0; i < 3; ++i) gv[i] += cf * fI[i];
   }
   if (mask & HSE_STRESSLET) {
     T gI[3] = {s.g[0], s.g[1], -s.g[2]}, qI[3] = {s.q[0], s.q[1], -s.q[2]};
@@ -218,13 +225,14 @@ __device__ __forceinline__ void add_image(int mask, const Radial<T>& R, const T*
     T rq = r[0] * qI[0] + r[1] * qI[1] + r[2] * qI[2];
     T gq = gI[0] * qI[0] + gI[1] * qI[1] + gI[2] * qI[2];
     for (int i = 0; i < 3; ++i) u[i] -= ta * r[i] * rg * rq + tb * (gI[i] * rq + qI[i] * rg + r[i] * gq);
-    // phi_T = 4 (gI.qI) d3G - 4 h gI.(grad grad G) qI
+    // phi_T = 4 (gI.qI) d3G - 4 h gI.(grad grad G) qI; its gradient
+    // 4 gq (g1 e3 + g2 r3 r) - 4 h (g2 (gq r + gI rq + qI rg) + g3 rg rq r)
     phi += 4 * gq * g1 * r[2] - 4 * h * (g1 * gq + g2 * rg * rq);
-    for (int i = 0; i < 3; ++i) {
-      T d3i = g1 * (i == 2 ? 1 : 0) + g2 * r[2] * r[i];
-      T t3 = g2 * (gq * r[i] + gI[i] * rq + qI[i] * rg) + R.g3 * rg * rq * r[i];
-      gp[i] += 4 * gq * d3i - 4 * h * t3;
-    }
+    ar += 4 * (gq * g2 * r[2] - h * (g2 * gq + R.g3 * rg * rq));
+    const T h4g2 = -4 * h * g2;
+    const T cg = h4g2 * rq, cq = h4g2 * rg;
+    for (int i = 0; i < 3; ++i) gv[i] += cg * gI[i] + cq * qI[i];
+    gv[2] += 4 * gq * g1;
   }
   if (mask & HSE_ROTLET) {
     T tI[3] = {s.tau[0], s.tau[1], -s.tau[2]};
@@ -232,14 +240,17 @@ __device__ __forceinline__ void add_image(int mask, const Radial<T>& R, const T*
     u[0] += wa * (tI[1] * r[2] - tI[2] * r[1]);
     u[1] += wa * (tI[2] * r[0] - tI[0] * r[2]);
     u[2] += wa * (tI[0] * r[1] - tI[1] * r[0]);
+    // grad phi_W = 4 (g1 v + g2 r (r.v)), v = (-tau2, tau1, 0)
     T v0 = -s.tau[1], v1 = s.tau[0];
     T rv = r[0] * v0 + r[1] * v1;
     phi += 4 * g1 * rv;
-    gp[0] += 4 * (g1 * v0 + g2 * r[0] * rv);
-    gp[1] += 4 * (g1 * v1 + g2 * r[1] * rv);
-    gp[2] += 4 * (g2 * r[2] * rv);
+    ar += 4 * g2 * rv;
+    const T g14 = 4 * g1;
+    gv[0] += g14 * v0;
+    gv[1] += g14 * v1;
   }
-  for (int i = 0; i < 3; ++i) u[i] -= x3 * gp[i];
+  const T xa = x3 * ar;
+  for (int i = 0; i < 3; ++i) u[i] -= xa * r[i] + x3 * gv[i];
   u[2] += phi;
 }
 
