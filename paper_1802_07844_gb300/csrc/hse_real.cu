@@ -178,15 +178,17 @@ __device__ __forceinline__ void add_free(int mask, const Radial<T>& R, const T* 
   if (mask & HSE_STOKESLET) {
     T sa = R.er - R.c;
     T rf = r[0] * s.f[0] + r[1] * s.f[1] + r[2] * s.f[2];
-    for (int i = 0; i < 3; ++i) u[i] += sa * s.f[i] + R.a1 * r[i] * rf;
+    const T arf = R.a1 * rf;
+    for (int i = 0; i < 3; ++i) u[i] += sa * s.f[i] + arf * r[i];
   }
   if (mask & HSE_STRESSLET) {
+    // ta r (r.g)(r.q) + tb (g (r.q) + q (r.g) + r (g.q)) as coefficients of r, g, q
     T ta = -2 * R.g2, tb = 2 * xi * xi * R.c;
     T rg = r[0] * s.g[0] + r[1] * s.g[1] + r[2] * s.g[2];
     T rq = r[0] * s.q[0] + r[1] * s.q[1] + r[2] * s.q[2];
     T gq = s.g[0] * s.q[0] + s.g[1] * s.q[1] + s.g[2] * s.q[2];
-    for (int i = 0; i < 3; ++i)
-      u[i] += sgn_odd * (ta * r[i] * rg * rq + tb * (s.g[i] * rq + s.q[i] * rg + r[i] * gq));
+    const T cr = sgn_odd * (ta * rg * rq + tb * gq), cg = sgn_odd * (tb * rq), cq = sgn_odd * (tb * rg);
+    for (int i = 0; i < 3; ++i) u[i] += cr * r[i] + cg * s.g[i] + cq * s.q[i];
   }
   if (mask & HSE_ROTLET) {
     T wa = sgn_odd * 2 * R.a1;
@@ -224,14 +226,15 @@ __device__ __forceinline__ void add_image(int mask, const Radial<T>& R, const T*
     T rg = r[0] * gI[0] + r[1] * gI[1] + r[2] * gI[2];
     T rq = r[0] * qI[0] + r[1] * qI[1] + r[2] * qI[2];
     T gq = gI[0] * qI[0] + gI[1] * qI[1] + gI[2] * qI[2];
-    for (int i = 0; i < 3; ++i) u[i] -= ta * r[i] * rg * rq + tb * (gI[i] * rq + qI[i] * rg + r[i] * gq);
+    const T cr = ta * rg * rq + tb * gq, cg = tb * rq, cq = tb * rg;
+    for (int i = 0; i < 3; ++i) u[i] -= cr * r[i] + cg * gI[i] + cq * qI[i];
     // phi_T = 4 (gI.qI) d3G - 4 h gI.(grad grad G) qI; its gradient
     // 4 gq (g1 e3 + g2 r3 r) - 4 h (g2 (gq r + gI rq + qI rg) + g3 rg rq r)
     phi += 4 * gq * g1 * r[2] - 4 * h * (g1 * gq + g2 * rg * rq);
     ar += 4 * (gq * g2 * r[2] - h * (g2 * gq + R.g3 * rg * rq));
     const T h4g2 = -4 * h * g2;
-    const T cg = h4g2 * rq, cq = h4g2 * rg;
-    for (int i = 0; i < 3; ++i) gv[i] += cg * gI[i] + cq * qI[i];
+    const T dg = h4g2 * rq, dq = h4g2 * rg;
+    for (int i = 0; i < 3; ++i) gv[i] += dg * gI[i] + dq * qI[i];
     gv[2] += 4 * gq * g1;
   }
   if (mask & HSE_ROTLET) {
