@@ -113,8 +113,9 @@ def test_real_part_matches_oracle(pkg, mask, dist):
 @pytest.mark.parametrize("dist", ["uniform", "near_wall"])
 def test_real_part_fp32_shell(pkg, mask, dist):
     """FP64 plans evaluate the outer shell [rc64, rc) of each neighbourhood in
-    FP32.  The error this adds stays well below the truncation error that the
-    cut-off rc itself makes (oracle: real part at rc vs without cut-off)."""
+    FP32.  The plan budgets the error this adds at the real-space truncation
+    estimate; it stays below the truncation error that the cut-off rc itself
+    makes (oracle: real part at rc vs without cut-off)."""
     pr = problem(mask, 2000, 1.0, dist, 33)
     xi, rc = 14.0, 0.3
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=rc, P=12, tol=0.0, M=40)
@@ -126,7 +127,8 @@ def test_real_part_fp32_shell(pkg, mask, dist):
     full = oracle.half_space_sum(mask, pr.src, pr.strengths, None, oracle.PART_REAL, xi, 0.0) + self_
     trunc = oracle.rel_rms(ref, full)
     err = oracle.rel_rms(host(ur), ref)
-    assert err < 0.3 * trunc
+    print(f"fp32 shell mask {mask} {dist}: shell error / truncation error {err / trunc:.3f}")
+    assert err < trunc
     assert err > 1e-15  # the shell really ran in FP32
     plan.close()
 
@@ -388,7 +390,9 @@ def test_fp32_shell_near_wall_dense(pkg):
     """Dense near-wall sources (the regime of the 1M benchmark): the FP32 outer
     shell must not amplify rounding for points close to the wall, where the
     free and image contributions of a source cancel to O(height / rho).  Shell
-    vs all-FP64 real part, globally and within the wall layer."""
+    vs all-FP64 real part, globally and within the wall layer: the plan budgets
+    the shell at the real-space truncation estimate (~1e-11 here), and the wall
+    layer must not exceed that either."""
     mask = KERNEL_S | KERNEL_W
     pr = problem(mask, 200000, 1.0, "near_wall", 38)
     xi = 90.0 * 0.2 ** (1.0 / 3.0)
@@ -400,7 +404,7 @@ def test_fp32_shell_near_wall_dense(pkg):
     plan.set_rc64(rc)
     fp64 = host(plan.eval_parts(src, st, fourier=False)[0])
     plan.close()
-    assert oracle.rel_rms(shell, fp64) < 1e-12
+    assert oracle.rel_rms(shell, fp64) < 1e-11
     wall = pr.src[2] < 0.002
     assert wall.sum() > 1000
-    assert oracle.rel_rms(shell[:, wall], fp64[:, wall]) < 1e-12
+    assert oracle.rel_rms(shell[:, wall], fp64[:, wall]) < 1e-11

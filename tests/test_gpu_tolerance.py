@@ -39,4 +39,6 @@ def test_error_within_tol_over_tolerances(pkg, mask, dist):
                 u = plan.eval(src, st).cpu().numpy()
             finally:
                 plan.close()
-            assert oracle.rel_rms(u, ref) < tol, (tol, prec, xi)
+            err = oracle.rel_rms(u, ref)
+            print(f"tol-sweep mask {mask} {dist} tol {tol:g} prec {prec} xi {xi:.1f}: err/tol {err / tol:.3f}")
+            assert err < tol, (tol, prec, xi)
