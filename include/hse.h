@@ -79,7 +79,7 @@ typedef struct {
   double rc64;       /* HSE_FP64, targets = sources: pairs closer than rc64 are     *
                       * evaluated in FP64, pairs in [rc64, rc) in FP32 (their      *
                       * screened kernels are small enough that FP32 rounding stays  *
-                      * below 1/10 of the real-space truncation error); rc64 >= rc  *
+                      * below half the real-space truncation estimate); rc64 >= rc  *
                       * means FP64 throughout (also for the spread's small-weight   *
                       * part, which otherwise runs in FP32).  0 under HSE_MIXED.     */
   int P;             /* Gaussian support width in grid points (even)               */

@@ -20,6 +20,7 @@
 // Stockham autosort transform over them (radices 4, 2, 5, 3), alternating
 // between two shared buffers so that each radix pass needs one barrier.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "hse_df64.cuh"
@@ -378,17 +379,17 @@ hse_status fft64_prepare(hse_plan p) {
   k_twiddles<<<(2 * nh + 255) / 256, 256>>>(2 * nh, t->tw + n1 + nh);
   HSE_CUDA(p, cudaGetLastError());
   HSE_CUDA(p, cudaDeviceSynchronize());
-  static bool attr = false;
-  if (!attr) {
-    // a block holds two buffers of (threads / TPL) lines of N points: at most
-    // kFftThreads threads and TPL >= N / 4, so at most 2 x 16 KB x kFftThreads / 512
+  // a block holds two buffers of (threads / TPL) lines of N points: at most
+  // kFftThreads threads and TPL >= N / 4, so at most 2 x 16 KB x kFftThreads / 512
+  // (plans may be built from several threads: set the limits once)
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     const int cap = 64 * 1024;
     cudaFuncSetAttribute(k_fft_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_fft_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_fft_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_fft_z<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    attr = true;
-  }
+  });
   return HSE_OK;
 }
 
