@@ -21,7 +21,6 @@
 // between two shared buffers so that each radix pass needs one barrier.
 #include <cmath>
 #include <mutex>
-#include <vector>
 
 #include "hse_df64.cuh"
 #include "hse_internal.cuh"
