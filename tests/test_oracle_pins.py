@@ -112,6 +112,36 @@ def test_blake_single_stokeslet():
         assert oracle.rel_rms(u, ub) < 1e-13
 
 
+def test_stokeslet_green_function_is_reciprocal():
+    """Lorentz reciprocity of Stokes flow with a no-slip wall: the half-space
+    stokeslet's Green's function satisfies G(x, y) = G(y, x)^T for any two
+    points above the wall (a transposed index or a wrong sign in the image
+    system breaks the symmetry)."""
+    eye = np.eye(3)
+    for trial in range(6):
+        x = np.array([RNG.uniform(0, 1), RNG.uniform(0, 1), RNG.uniform(0.005, 0.6)])
+        y = np.array([RNG.uniform(0, 1), RNG.uniform(0, 1), RNG.uniform(0.005, 0.6)])
+        gxy = np.stack([oracle.direct(KERNEL_S, y[:, None], eye[:, j:j + 1], x[:, None])[:, 0] for j in range(3)],
+                       axis=1)
+        gyx = np.stack([oracle.direct(KERNEL_S, x[:, None], eye[:, j:j + 1], y[:, None])[:, 0] for j in range(3)],
+                       axis=1)
+        assert np.abs(gxy - gyx.T).max() < 1e-13 * np.abs(gxy).max()
+
+
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_T | KERNEL_W])
+def test_invariant_under_shifts_parallel_to_the_wall(mask):
+    """The half-space sums depend on x - y in the wall's plane and on the
+    heights: shifting every source and target by (a1, a2, 0) leaves the
+    velocities unchanged (a term using an absolute coordinate where a
+    difference belongs breaks this)."""
+    pr = problem(mask, 40, 1.0, "near_wall", 93)
+    tg = _rand_targets(12, 0.0, 1.0)
+    u = oracle.direct(mask, pr.src, pr.strengths, tg)
+    shift = np.array([[0.37], [-0.21], [0.0]])
+    us = oracle.direct(mask, pr.src + shift, pr.strengths, tg + shift)
+    assert oracle.rel_rms(us, u) < 1e-13
+
+
 def test_rotlet_from_blake_dipole():
     """Half-space rotlet = antisymmetric force dipole of the half-space stokeslet:
     W8 tau = -(D(g,q) - D(q,g)) with tau = g x q (W8 tau = 2 tau x r / r^3)."""
