@@ -142,6 +142,26 @@ def test_invariant_under_shifts_parallel_to_the_wall(mask):
     assert oracle.rel_rms(us, u) < 1e-13
 
 
+@pytest.mark.parametrize("mask,degree", [(KERNEL_S, 1), (KERNEL_T, 2), (KERNEL_W, 2)])
+def test_homogeneity_under_scaling(mask, degree):
+    """Stokes flow has no length scale: with every position scaled by lam the
+    stokeslet field scales by lam^-1 and the stresslet and rotlet fields by
+    lam^-2 (their kernels have one more derivative), images and wall
+    corrections included; the Ewald parts obey the same law with xi -> xi/lam
+    (xi has units of inverse length).  A wrong power of r or a missing xi
+    factor in any term breaks it."""
+    pr = problem(mask, 30, 1.0, "near_wall", 94)
+    tg = _rand_targets(9, 0.0, 1.0)
+    lam, xi = 2.5, 7.0
+    u = oracle.direct(mask, pr.src, pr.strengths, tg)
+    us = oracle.direct(mask, lam * pr.src, pr.strengths, lam * tg)
+    assert oracle.rel_rms(us * lam ** degree, u) < 1e-13
+    for part in (oracle.PART_REAL, oracle.PART_SMOOTH):
+        a = oracle.half_space_sum(mask, pr.src, pr.strengths, tg, part, xi, 0.0)
+        b = oracle.half_space_sum(mask, lam * pr.src, pr.strengths, lam * tg, part, xi / lam, 0.0)
+        assert oracle.rel_rms(b * lam ** degree, a) < 1e-12, part
+
+
 def test_rotlet_from_blake_dipole():
     """Half-space rotlet = antisymmetric force dipole of the half-space stokeslet:
     W8 tau = -(D(g,q) - D(q,g)) with tau = g x q (W8 tau = 2 tau x r / r^3)."""
