@@ -239,6 +239,14 @@ hse_status hse_plan_set_timing(hse_plan plan, int enable);
  * caller's stream before the call's work ends; 0 (default): one after the
  * other on the caller's stream. */
 hse_status hse_plan_set_overlap(hse_plan plan, int enable);
+/* Cap the real-space kernel of targets = sources at blocks_per_sm resident
+ * blocks per multiprocessor (a persistent grid of blocks_per_sm x SM-count
+ * blocks; 0, the default: no cap).  Results are unchanged up to summation
+ * order.  With overlapped halves this leaves part of every SM's registers to
+ * the Fourier kernels, so the FP64-bound real space and the FP32-bound
+ * Fourier part share the SMs instead of running one after the other.
+ * HSE_ERR_INVALID for blocks_per_sm outside [0, 64]. */
+hse_status hse_plan_set_real_residency(hse_plan plan, int blocks_per_sm);
 
 /* Statistics of the last evaluation (synchronises on its last event when
  * timing is on).  out: host pointer. */
@@ -276,6 +284,8 @@ typedef struct {
   double targets_per_s;            /* completed targets / busy_s                         */
   int64_t plans_created, plans_evicted;
   size_t resident_bytes;           /* device bytes held by cached plans                  */
+  int64_t plan_hits;               /* requests admitted to a resident plan (cache hits)  */
+  double plan_build_s;             /* host time spent building plans (incl. prewarm)     */
 } hse_server_stats;
 
 /*
@@ -293,6 +303,18 @@ typedef struct {
 hse_status hse_server_create(const hse_server_config* cfg, hse_server* out);
 /* Queue a request; *ticket identifies it.  Never blocks on GPU work. */
 hse_status hse_server_submit(hse_server srv, const hse_request* req, uint64_t* ticket);
+/* Build, synchronously on the calling thread, the plan that a request like
+ * *req would use (only kernel_mask, precision, tol, box and n_src are read;
+ * no data), so that later requests with the same plan parameters find it
+ * resident instead of paying its set-up inside their latency.  HSE_OK when
+ * the plan is resident or already being built; HSE_ERR_OOM when it does not
+ * fit the memory budget next to the plans already held; the errors of
+ * hse_plan_create otherwise.  The calling thread's current device is kept. */
+hse_status hse_server_prewarm(hse_server srv, const hse_request* req);
+/* Parameters (xi, r_c, P, M, ...) of the plan that evaluated a finished
+ * request: HSE_OK, HSE_PENDING while it runs, HSE_ERR_INVALID for an unknown
+ * ticket or a request that failed before its plan existed.  out: host. */
+hse_status hse_server_request_params(hse_server srv, uint64_t ticket, hse_params* out);
 /* HSE_OK when finished, HSE_PENDING while queued or running, else the
  * request's error status. */
 hse_status hse_server_poll(hse_server srv, uint64_t ticket);
@@ -368,6 +390,10 @@ hse_status hse_batch_create(double tol, int precision, const double box[3], size
  * HSE_ERR_CUDA, HSE_ERR_CUFFT. */
 hse_status hse_batch_eval(hse_batch batch, int n_inst, const hse_instance* inst, void* cuda_stream);
 hse_status hse_batch_get_stats(hse_batch batch, hse_batch_stats* out);
+/* Parameters (xi, r_c, P, M, ...) of the group plan that evaluated instance i
+ * (0-based, in the order of the last hse_batch_eval call's array).
+ * HSE_ERR_INVALID when i was not evaluated by the last call.  out: host. */
+hse_status hse_batch_instance_params(hse_batch batch, int i, hse_params* out);
 /* Enable (1) or disable (0) CUDA-event timing of the stages of every chunk
  * (stage_ms of the stats; synchronises the stream once per chunk).  Timed
  * chunks are launched directly, not from graphs. */

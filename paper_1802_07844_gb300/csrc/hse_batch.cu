@@ -140,6 +140,7 @@ struct hse_batch_s {
   int* h_flag = nullptr;
   std::string err;
   hse_batch_stats st{};
+  std::vector<const Bucket*> inst_bucket;  // group whose plan evaluated each instance of the last call
 };
 
 namespace {
@@ -451,6 +452,7 @@ hse_status trial(hse_batch b, int mask, int lv, const hse_instance* inst, const 
   BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
   *t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / (double)c.n_tot;
   *covered = c.m;
+  for (int j = 0; j < c.m; ++j) b->inst_bucket[c.idx[j]] = k;  // these keep the trial's result
   return HSE_OK;
 }
 
@@ -542,6 +544,7 @@ extern "C" hse_status hse_batch_eval(hse_batch b, int n_inst, const hse_instance
   if (n_inst < 0 || (n_inst > 0 && !inst)) return berr(b, HSE_ERR_INVALID, "hse_batch_eval: bad instance array");
   b->err.clear();
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  b->inst_bucket.assign((size_t)n_inst, nullptr);
   std::map<std::pair<int, int>, std::vector<int>> groups;
   for (int i = 0; i < n_inst; ++i) {
     const hse_instance& I = inst[i];
@@ -562,7 +565,17 @@ extern "C" hse_status hse_batch_eval(hse_batch b, int n_inst, const hse_instance
   for (const Job& j : jobs) {
     WorkspaceLease lease(j.k->plan, &b->ws);
     BTRY(run_chunk(b, j.k, inst, j.c, s, true));
+    for (int i = 0; i < j.c.m; ++i) b->inst_bucket[j.c.idx[i]] = j.k;
   }
+  return HSE_OK;
+}
+
+extern "C" hse_status hse_batch_instance_params(hse_batch b, int i, hse_params* out) {
+  if (!b || !out) return HSE_ERR_INVALID;
+  if (i < 0 || i >= (int)b->inst_bucket.size() || !b->inst_bucket[i])
+    return berr(b, HSE_ERR_INVALID, "hse_batch_instance_params: instance " + std::to_string(i) +
+                                        " was not evaluated by the last call");
+  *out = b->inst_bucket[i]->plan->prm;
   return HSE_OK;
 }
 

@@ -157,6 +157,18 @@ extern "C" hse_status hse_plan_set_overlap(hse_plan p, int enable) {
   return HSE_OK;
 }
 
+extern "C" hse_status hse_plan_set_real_residency(hse_plan p, int blocks_per_sm) {
+  if (!p) return HSE_ERR_INVALID;
+  if (blocks_per_sm < 0 || blocks_per_sm > 64) return set_err(p, HSE_ERR_INVALID, "blocks_per_sm %d", blocks_per_sm);
+  if (p->n_sm == 0) {
+    int dev = 0;
+    HSE_CUDA(p, cudaGetDevice(&dev));
+    HSE_CUDA(p, cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  p->real_bps = blocks_per_sm;
+  return HSE_OK;
+}
+
 extern "C" hse_status hse_plan_set_timing(hse_plan p, int enable) {
   if (!p) return HSE_ERR_INVALID;
   if (enable && !p->timing) {

@@ -125,9 +125,11 @@ struct hse_plan_s {
   cudaEvent_t ev[HSE_N_STAGES + 1] = {};
   // concurrent halves (hse_plan_set_overlap): real space on a low-priority
   // stream, the Fourier part on a high-priority one, joined on the caller's.
-  // Off by default: on GB300 both halves are FP64-issue-bound and measured no
-  // faster together (1M near-wall S+W: 1106 vs 1109 ms).
   bool overlap = false;
+  // hse_plan_set_real_residency: at most this many real-space blocks per SM
+  // (a persistent grid of real_bps x n_sm blocks), 0 = no cap
+  int real_bps = 0;
+  int n_sm = 0;  // multiprocessors of the plan's device
   cudaStream_t s_real = nullptr, s_four = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_real = nullptr, ev_four = nullptr;
   cudaEvent_t ev_real_end = nullptr;  // timing: end of the real stage on its stream

@@ -770,6 +770,15 @@ static int warp_blocks(int64_t n_tgt) {
   return b < 1 ? 1 : (int)b;
 }
 
+// blocks of the symmetric kernel: one warp per target, grid-stride; with a
+// residency cap the grid is persistent (cap x SMs blocks), which leaves the
+// rest of each SM's registers to kernels running concurrently on other streams
+static int sym_blocks(hse_plan p, int64_t n_tgt) {
+  int b = warp_blocks(n_tgt);
+  if (p->real_bps > 0 && p->n_sm > 0 && b > p->real_bps * p->n_sm) b = p->real_bps * p->n_sm;
+  return b;
+}
+
 hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
                       cudaStream_t s) {
   if (n_tgt == 0) return HSE_OK;
@@ -782,15 +791,15 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
     a.out4 = p->ws.usort4;
     if (mixed) {
       HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
-      launch_real_sym<float>(a.mask, warp_blocks(n_tgt), a, s);
+      launch_real_sym<float>(a.mask, sym_blocks(p, n_tgt), a, s);
       if (!free_space(p->prm.kernel_mask)) {
-        k_close_images<<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
+        k_close_images<<<sym_blocks(p, n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
         ++p->n_launch;
       }
     } else {
       HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_tgt, s));
       if (shell32(p, a)) HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
-      launch_real_sym<double>(a.mask, warp_blocks(n_tgt), a, s);
+      launch_real_sym<double>(a.mask, sym_blocks(p, n_tgt), a, s);
     }
     HSE_CUDA(p, cudaGetLastError());
     int64_t b = (n_tgt + 255) / 256;

@@ -49,6 +49,8 @@ struct Record {
   hse_status status = (hse_status)HSE_PENDING;
   Clock::time_point t_submit, t_done;
   bool done = false;
+  bool have_params = false;
+  hse_params params{};  // parameters of the plan that evaluated the request
   std::string error;
 };
 
@@ -81,6 +83,8 @@ struct hse_server_s {
   // statistics
   std::vector<double> lat_ms;
   int64_t submitted = 0, completed = 0, failed = 0, targets_done = 0, plans_created = 0, plans_evicted = 0;
+  int64_t plan_hits = 0;     // admitted requests that found their plan resident
+  double plan_build_s = 0;   // host time spent building plans (requests and prewarm)
   bool have_first = false;
   Clock::time_point t_first, t_last;
 
@@ -146,6 +150,7 @@ struct hse_server_s {
       cv_work.wait(lk, [&] { return stop || pick(&t, &pi); });
       if (t == 0) return;  // stopping and nothing admitted
       Record& r = rec[t];
+      if (pi >= 0) ++plan_hits;
       if (pi < 0) {  // reserve memory and a pool slot, build outside the lock
         PlanEntry e;
         e.key = r.key;
@@ -163,13 +168,18 @@ struct hse_server_s {
       lk.unlock();
       hse_status st = HSE_OK;
       std::string err;
+      double build_s = 0.0;
       if (!plan) {
+        const Clock::time_point t0 = Clock::now();
         st = hse_plan_create(key.mask, key.box, key.xi, 0.0, 0, key.tol, key.precision, &plan);
+        build_s = std::chrono::duration<double>(Clock::now() - t0).count();
         if (st != HSE_OK) {
           plan = nullptr;
           err = std::string("plan: ") + hse_last_error(nullptr);
         }
       }
+      hse_params used{};
+      const bool have_params = plan && hse_plan_get_params(plan, &used) == HSE_OK;
       if (st == HSE_OK) {
         st = hse_eval(plan, req.n_src, req.src_xyz, req.strengths, req.n_tgt, req.tgt_xyz, req.vel, s);
         if (st != HSE_OK) err = std::string("eval: ") + hse_last_error(plan);
@@ -182,7 +192,10 @@ struct hse_server_s {
         }
       }
       lk.lock();
+      plan_build_s += build_s;
       rec[t].error = err;
+      rec[t].have_params = have_params;
+      rec[t].params = used;
       // the pool may have been compacted by evictions: find our busy entry by plan or reservation
       int idx = -1;
       for (size_t i = 0; i < pool.size(); ++i)
@@ -278,6 +291,74 @@ extern "C" hse_status hse_server_submit(hse_server srv, const hse_request* req, 
   return HSE_OK;
 }
 
+extern "C" hse_status hse_server_prewarm(hse_server srv, const hse_request* req) {
+  if (!srv || !req) return HSE_ERR_INVALID;
+  if (!hse::valid_mask(req->kernel_mask) || !(req->tol > 0.0) || req->n_src < 0 || !(req->box[0] > 0) ||
+      !(req->box[1] > 0) || !(req->box[2] > 0))
+    return set_err(nullptr, HSE_ERR_INVALID, "hse_server_prewarm: bad request");
+  PlanKey key;
+  key.mask = req->kernel_mask;
+  key.precision = req->precision;
+  key.tol = req->tol;
+  for (int d = 0; d < 3; ++d) key.box[d] = req->box[d];
+  key.xi = choose_xi(req->n_src, req->box);
+  size_t grid = 0;
+  HSE_TRY(hse::plan_estimate(key.mask, key.box, key.xi, key.tol, key.precision, &grid, nullptr, nullptr));
+  {
+    std::lock_guard<std::mutex> lk(srv->m);
+    if (srv->stop) return set_err(nullptr, HSE_ERR_INVALID, "server is stopping");
+    for (auto& e : srv->pool)
+      if (e.key == key) return HSE_OK;  // resident or being built
+    if (srv->resident + grid > srv->cfg.mem_budget_bytes)
+      return set_err(nullptr, HSE_ERR_OOM, "prewarm: plan of %zu bytes does not fit the budget", grid);
+    PlanEntry e;
+    e.key = key;
+    e.bytes = grid;
+    e.busy = true;  // reserved: no worker uses it until it is built
+    srv->pool.push_back(e);
+    srv->resident += grid;
+  }
+  int prev_dev = srv->device;
+  cudaGetDevice(&prev_dev);
+  cudaSetDevice(srv->device);
+  hse_plan plan = nullptr;
+  const Clock::time_point t0 = Clock::now();
+  hse_status st = hse_plan_create(key.mask, key.box, key.xi, 0.0, 0, key.tol, key.precision, &plan);
+  const double build_s = std::chrono::duration<double>(Clock::now() - t0).count();
+  cudaSetDevice(prev_dev);
+  std::lock_guard<std::mutex> lk(srv->m);
+  srv->plan_build_s += build_s;
+  for (size_t i = 0; i < srv->pool.size(); ++i) {
+    PlanEntry& e = srv->pool[i];
+    if (e.key == key && e.busy && e.plan == nullptr) {
+      if (st == HSE_OK) {
+        e.plan = plan;
+        e.busy = false;
+        e.last_used = ++srv->use_clock;
+        ++srv->plans_created;
+      } else {
+        srv->resident -= e.bytes;
+        srv->pool.erase(srv->pool.begin() + i);
+      }
+      break;
+    }
+  }
+  srv->cv_work.notify_all();
+  return st;
+}
+
+extern "C" hse_status hse_server_request_params(hse_server srv, uint64_t ticket, hse_params* out) {
+  if (!srv || !out) return HSE_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->m);
+  auto it = srv->rec.find(ticket);
+  if (it == srv->rec.end()) return HSE_ERR_INVALID;
+  if (!it->second.done) return (hse_status)HSE_PENDING;
+  if (!it->second.have_params) return set_err(nullptr, HSE_ERR_INVALID, "request %llu has no plan",
+                                              (unsigned long long)ticket);
+  *out = it->second.params;
+  return HSE_OK;
+}
+
 extern "C" hse_status hse_server_poll(hse_server srv, uint64_t ticket) {
   if (!srv) return HSE_ERR_INVALID;
   std::lock_guard<std::mutex> lk(srv->m);
@@ -315,6 +396,8 @@ extern "C" hse_status hse_server_get_stats(hse_server srv, hse_server_stats* out
   out->in_flight = srv->submitted - srv->completed - srv->failed;
   out->plans_created = srv->plans_created;
   out->plans_evicted = srv->plans_evicted;
+  out->plan_hits = srv->plan_hits;
+  out->plan_build_s = srv->plan_build_s;
   out->resident_bytes = srv->resident;
   std::vector<double> v = srv->lat_ms;
   if (!v.empty()) {
@@ -338,6 +421,8 @@ extern "C" hse_status hse_server_reset_stats(hse_server srv) {
   std::lock_guard<std::mutex> lk(srv->m);
   srv->lat_ms.clear();
   srv->completed = srv->failed = srv->targets_done = srv->submitted = 0;
+  srv->plan_hits = 0;
+  srv->plan_build_s = 0.0;
   for (auto& kv : srv->rec)
     if (!kv.second.done) ++srv->submitted;
   srv->have_first = false;

@@ -68,7 +68,7 @@ class hse_server_stats(ctypes.Structure):
                 ("in_flight", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("busy_s", ctypes.c_double), ("targets_per_s", ctypes.c_double),
                 ("plans_created", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
-                ("resident_bytes", ctypes.c_size_t)]
+                ("resident_bytes", ctypes.c_size_t), ("plan_hits", ctypes.c_int64), ("plan_build_s", ctypes.c_double)]
 
 
 class hse_instance(ctypes.Structure):
@@ -94,10 +94,11 @@ class HseError(RuntimeError):
 _lib = None
 _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_set_fft", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
-          "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_get_eval_stats", "hse_cell_list_noalloc",
+          "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_plan_set_real_residency", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
-          "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_batch_create",
-          "hse_batch_eval", "hse_batch_get_stats", "hse_batch_last_error", "hse_batch_destroy",
+          "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_server_prewarm",
+          "hse_server_request_params", "hse_batch_create",
+          "hse_batch_eval", "hse_batch_get_stats", "hse_batch_instance_params", "hse_batch_last_error", "hse_batch_destroy",
           "hse_batch_set_timing", "hse_batch_set_graphs")
 
 
@@ -124,6 +125,7 @@ def load(path: str = LIB_PATH):
     L.hse_plan_destroy.argtypes = [vp]
     L.hse_plan_set_timing.argtypes = [vp, ctypes.c_int]
     L.hse_plan_set_overlap.argtypes = [vp, ctypes.c_int]
+    L.hse_plan_set_real_residency.argtypes = [vp, ctypes.c_int]
     L.hse_server_create.argtypes = [ctypes.POINTER(hse_server_config), ctypes.POINTER(vp)]
     L.hse_server_submit.argtypes = [vp, ctypes.POINTER(hse_request), ctypes.POINTER(ctypes.c_uint64)]
     L.hse_server_poll.argtypes = [vp, ctypes.c_uint64]
@@ -131,12 +133,15 @@ def load(path: str = LIB_PATH):
     L.hse_server_get_stats.argtypes = [vp, ctypes.POINTER(hse_server_stats)]
     L.hse_server_reset_stats.argtypes = [vp]
     L.hse_server_destroy.argtypes = [vp]
+    L.hse_server_prewarm.argtypes = [vp, ctypes.POINTER(hse_request)]
+    L.hse_server_request_params.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hse_params)]
     L.hse_server_error_text.argtypes = [vp, ctypes.c_uint64]
     L.hse_server_error_text.restype = ctypes.c_char_p
     L.hse_batch_create.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                                    ctypes.c_int, ctypes.POINTER(vp)]
     L.hse_batch_eval.argtypes = [vp, ctypes.c_int, ctypes.POINTER(hse_instance), vp]
     L.hse_batch_get_stats.argtypes = [vp, ctypes.POINTER(hse_batch_stats)]
+    L.hse_batch_instance_params.argtypes = [vp, ctypes.c_int, ctypes.POINTER(hse_params)]
     L.hse_batch_last_error.argtypes = [vp]
     L.hse_batch_last_error.restype = ctypes.c_char_p
     L.hse_batch_destroy.argtypes = [vp]
@@ -230,6 +235,10 @@ def hse_plan_set_overlap(plan, enable):
     _check(load().hse_plan_set_overlap(plan, int(bool(enable))), plan)
 
 
+def hse_plan_set_real_residency(plan, blocks_per_sm):
+    _check(load().hse_plan_set_real_residency(plan, int(blocks_per_sm)), plan)
+
+
 def hse_get_eval_stats(plan) -> dict:
     st = hse_eval_stats()
     _check(load().hse_get_eval_stats(plan, ctypes.byref(st)), plan)
@@ -288,12 +297,17 @@ def hse_server_destroy(srv):
     _check(load().hse_server_destroy(srv))
 
 
-def server_xi(n, box=(1.0, 1.0, 1.0)):
-    """The xi a server picks for n sources (0.7 (N/V)^(1/3) on a sqrt(2) ladder)."""
-    import math
-    v = box[0] * box[1] * box[2]
-    xi = 0.7 * ((max(n, 1) / v) ** (1.0 / 3.0))
-    return 2.0 ** (round(2.0 * math.log2(xi)) / 2.0)
+def hse_server_prewarm(srv, req: hse_request):
+    _check(load().hse_server_prewarm(srv, ctypes.byref(req)))
+
+
+def hse_server_request_params(srv, ticket) -> dict:
+    """Parameters of the plan that evaluated a finished request."""
+    p = hse_params()
+    st = load().hse_server_request_params(srv, ticket, ctypes.byref(p))
+    if st != HSE_OK:
+        raise HseError(st, f"request {ticket}: no parameters")
+    return p.as_dict()
 
 
 class Server:
@@ -315,6 +329,14 @@ class Server:
         t = hse_server_submit(self.handle, req)
         self._keep[t] = (src, strengths, tgt, out)
         return t
+
+    def prewarm(self, kernel_mask, n_src, tol, precision=HSE_FP64, box=(1.0, 1.0, 1.0)):
+        req = hse_request(int(kernel_mask), int(precision), float(tol), (ctypes.c_double * 3)(*box), int(n_src),
+                          None, None, int(n_src), None, None)
+        hse_server_prewarm(self.handle, req)
+
+    def request_params(self, ticket):
+        return hse_server_request_params(self.handle, ticket)
 
     def poll(self, ticket):
         return hse_server_poll(self.handle, ticket)
@@ -374,6 +396,14 @@ def hse_batch_get_stats(batch) -> dict:
     return out
 
 
+def hse_batch_instance_params(batch, i) -> dict:
+    p = hse_params()
+    st = load().hse_batch_instance_params(batch, int(i), ctypes.byref(p))
+    if st != HSE_OK:
+        raise HseError(st, hse_batch_last_error(batch))
+    return p.as_dict()
+
+
 def hse_batch_set_timing(batch, enable):
     _check(load().hse_batch_set_timing(batch, 1 if enable else 0))
 
@@ -408,6 +438,9 @@ class Batch:
 
     def stats(self):
         return hse_batch_get_stats(self.handle)
+
+    def instance_params(self, i):
+        return hse_batch_instance_params(self.handle, i)
 
     def set_timing(self, enable=True):
         hse_batch_set_timing(self.handle, enable)
@@ -526,6 +559,9 @@ class Plan:
 
     def set_overlap(self, enable=True):
         hse_plan_set_overlap(self.handle, enable)
+
+    def set_real_residency(self, blocks_per_sm):
+        hse_plan_set_real_residency(self.handle, blocks_per_sm)
 
     def stats(self):
         return hse_get_eval_stats(self.handle)

@@ -37,10 +37,14 @@ def _to_dev(probs):
     return [(pr.mask, torch.from_numpy(pr.src).cuda(), torch.from_numpy(pr.strengths).cuda()) for pr in probs]
 
 
-def _alone(pkg, mask, src, st, tol, prec):
-    n = src.shape[1]
-    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=pkg.hse.server_xi(n), rc=0.0, P=0, tol=tol, precision=prec)
+def _alone(pkg, mask, src, st, tol, prec, used):
+    """The instance evaluated alone on a plan created as the batch creates its
+    group plans (xi of the group read back through the ABI; r_c, P, M from
+    tol), after checking that the plan's parameters are the group's."""
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=used["xi"], rc=0.0, P=0, tol=tol, precision=prec)
     try:
+        for k in ("xi", "rc", "P", "M", "Mt", "rc64", "eta"):
+            assert plan.params[k] == used[k], k
         return plan.eval(src, st).cpu().numpy()
     finally:
         plan.close()
@@ -65,6 +69,9 @@ def test_batch_equals_alone_and_oracle(pkg, prec, tol):
         outs = b.eval(items)
         torch.cuda.synchronize()
         stats = b.stats()
+        used = [b.instance_params(i) for i in range(len(items))]
+        with pytest.raises(pkg.hse.HseError):
+            b.instance_params(len(items))
     finally:
         b.close()
     assert stats["instances"] == len(probs)
@@ -74,7 +81,7 @@ def test_batch_equals_alone_and_oracle(pkg, prec, tol):
     for i, (pr, (mask, src, st), u) in enumerate(zip(probs, items, outs)):
         u = u.cpu().numpy()
         assert np.isfinite(u).all()
-        alone = _alone(pkg, mask, src, st, tol, prec)
+        alone = _alone(pkg, mask, src, st, tol, prec, used[i])
         # same plan parameters; only summation order differs (FP64 atomics, and
         # float4 atomics for the FP32 outer shell of the FP64 path): equal to
         # well within the tolerance

@@ -55,10 +55,15 @@ def _mix_equals_alone(pkg, srv):
     stats = srv.stats()
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert stats["plans_created"] + stats["plan_hits"] >= len(reqs)
     for t, pr, prec, tol, src, st in reqs:
         mixed = srv.result(t).cpu().numpy()
-        n = pr.src.shape[1]
-        plan = pkg.Plan(pr.mask, (1.0, 1.0, 1.0), xi=pkg.hse.server_xi(n), rc=0.0, P=0, tol=tol, precision=prec)
+        # the plan the server used, read back through the ABI; the same call
+        # the server makes (xi given, r_c, P, M from tol) gives the same plan
+        used = srv.request_params(t)
+        plan = pkg.Plan(pr.mask, (1.0, 1.0, 1.0), xi=used["xi"], rc=0.0, P=0, tol=tol, precision=prec)
+        for k in ("xi", "rc", "P", "M", "Mt", "rc64", "eta", "precision", "kernel_mask"):
+            assert plan.params[k] == used[k], k
         alone = plan.eval(src, st).cpu().numpy()
         plan.close()
         # same plan parameters: only the atomic summation order can differ
@@ -68,6 +73,33 @@ def _mix_equals_alone(pkg, srv):
         # reference fluctuate more than the error
         ref = oracle.direct(pr.mask, pr.src, pr.strengths)
         assert oracle.rel_rms(mixed, ref) < tol
+
+
+def test_prewarm_makes_the_first_request_a_cache_hit(pkg):
+    """A prewarmed plan is resident before the first request that needs it:
+    that request is admitted as a plan-cache hit, no plan is built inside its
+    latency, and its result equals the direct sum within tol."""
+    pr = problem(KERNEL_W, 4000, 1.0, "near_wall", 62)
+    src = torch.from_numpy(pr.src).cuda()
+    st = torch.from_numpy(pr.strengths).cuda()
+    srv = pkg.hse.Server(n_slots=2)
+    try:
+        srv.prewarm(KERNEL_W, 4000, 1e-8, pkg.HSE_FP64)
+        srv.prewarm(KERNEL_W, 4000, 1e-8, pkg.HSE_FP64)  # already resident: no second plan
+        s0 = srv.stats()
+        assert s0["plans_created"] == 1 and s0["plan_build_s"] > 0
+        srv.reset_stats()
+        t = srv.submit(KERNEL_W, src, st, 1e-8, pkg.HSE_FP64)
+        assert srv.wait(t, 300.0) == pkg.hse.HSE_OK
+        s1 = srv.stats()
+        assert s1["plan_hits"] == 1 and s1["plans_created"] == 1 and s1["plan_build_s"] == 0.0
+        ref = oracle.direct(KERNEL_W, pr.src, pr.strengths)
+        assert oracle.rel_rms(srv.result(t).cpu().numpy(), ref) < 1e-8
+        # an unknown ticket has no parameters
+        with pytest.raises(pkg.HseError):
+            srv.request_params(t + 1000)
+    finally:
+        srv.close()
 
 
 def test_bounded_wait_and_memory_admission(pkg):

@@ -31,7 +31,7 @@ def test_error_within_tol_over_tolerances(pkg, mask, dist):
     ref = oracle.direct(mask, pr.src, pr.strengths)
     src = torch.from_numpy(pr.src).cuda()
     st = torch.from_numpy(pr.strengths).cuda()
-    xi0 = pkg.hse.server_xi(3000)
+    xi0 = 2.0 ** 3.5  # near 0.7 N^(1/3) = 10.05 for N = 3000 in the unit box
     for tol, prec in ((1e-5, pkg.HSE_MIXED), (1e-5, pkg.HSE_FP64), (1e-8, pkg.HSE_FP64), (1e-10, pkg.HSE_FP64)):
         for xi in (xi0, 2 * xi0):
             plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=0.0, P=0, tol=tol, precision=prec)
