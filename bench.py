@@ -5,18 +5,29 @@ cell-list binning and sort, real-space sum, spreading, forward FFTs, k-space
 scaling, inverse FFTs and gather, for the workload
   stokeslet + rotlet, N = 1M sources = targets, x, y uniform in [0,1),
   z ~ Exponential(mean 0.05) truncated to (0,1], N(0,1) forces and torques,
-  FP64 path at relative RMS tolerance 1e-10 (plan set-up is not timed, Sec. 7).
+  FP64 plan at relative RMS tolerance 1e-10 (plan set-up is not timed, Sec. 7).
+The FP64 plan's arithmetic: real-space pairs closer than rc64 in FP64, the
+outer shell [rc64, r_c) in FP32, the Fourier part (grids, transforms, scaling)
+in double-float (~48-bit) arithmetic on the FP32 pipe.
 
 Prints one JSON line.  ``value`` is whole-job Mtargets/s with inputs resident
 on the device; ``e2e`` repeats the measurement with host inputs copied in and
-velocities copied out inside the timed region.  ``--impl reference`` times the
-FP64 CPU direct-sum oracle on a bounded target sample of the same workload.
-Multi-GPU: independent replicas (one per rank), weak scaling.
+velocities copied out inside the timed region.  After the timed region every
+leg's result is compared with the FP64 direct-sum oracle on a seeded sample of
+10k targets (the Sec. 6 relative RMS error); the oracle's time on that sample is
+the ``cpu_baseline``.  Further legs on the same workload: the plain FP64 form
+(every pair in FP64, cuFFT double, FP64 grids) at 1e-10, the FP64 plan and the
+mixed-precision plan at 1e-5; the N = 1000 and N = 100k workloads; batched small
+instances; a Poisson request stream through the serving runtime.
+``--impl reference`` times the FP64 CPU direct-sum oracle on a bounded target
+sample of the same workload.  Multi-GPU: independent replicas (one per rank),
+weak scaling.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -28,14 +39,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import KERNEL_S, KERNEL_W, problem  # noqa: E402
+from workloads import KERNEL_S, KERNEL_T, KERNEL_W, WORKLOADS, problem  # noqa: E402
 
 WORKLOAD = dict(
     name="hs_stokeslet_rotlet_n1m_nearwall",
     mask=KERNEL_S | KERNEL_W, n=1_000_000, dist="near_wall", index=2, tol=1e-10,
     # parameters checked against the FP64 oracle on a target sample (tests/test_gpu_parity.py):
     # xi r_c = 4.8, k_inf / xi = pi M / xi = 10.9, P = 18 give 3.0e-11 on 3000 targets (P = 16:
-    # 3.2e-10; xi = 90 with the same grid: 7.3e-11); Mt = 320 = 2^6 x 5 is a fast cuFFT size
+    # 3.2e-10; xi = 90 with the same grid: 7.3e-11); Mt = 320 = 2^6 x 5 is a fast transform size
     xi=87.0, rc=0.0552, P=18, M=302,
 )
 # mixed-precision (FP32 arithmetic) configuration of the same workload at tolerance 1e-5;
@@ -43,28 +54,32 @@ WORKLOAD = dict(
 # 2.9e-6 on 3000 targets (the plan's own rule at xi = 100 picks r_c 0.0367, P 14, M 306:
 # 4.4e-7 at 1.5x the time); Mt = 256 is a power of two, markedly faster in FP32 cuFFT
 MIXED = dict(tol=1e-5, xi=95.0, rc=0.035, P=12, M=244)
-METRIC = "Mtargets/s, N=1M stokeslet @1e-10 FP64 vs 1e-5 mixed; serve p50/p99 ms"
+# the smaller workloads: N = 1000 stokeslet at 1e-8, N = 100k stokeslet and
+# stresslet at 1e-10, uniform in the unit box; xi = 0.7 N^(1/3), r_c, P and M
+# chosen by the plan from tol
+CONFIG_LEGS = [("hs_stokeslet_n1000_uniform", 7.0), ("hs_stokeslet_n100k_uniform", 32.5),
+               ("hs_stresslet_n100k_uniform", 32.5)]
+ERR_SAMPLE = 10_000  # seeded targets of the 1M workload checked against the oracle
+METRIC = "Mtargets/s, N=1M stokeslet+rotlet @1e-10 FP64 vs 1e-5 mixed; serve p50/p99 ms"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP32 peak likewise: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# Algorithmic FP64 work of the real-space stage (stokeslet + rotlet), counted
-# from the written code (FMA = 2 flops): the radial part of a pair (distance,
-# reciprocal square root charged 4, exp by reduction + degree-13 polynomial,
-# erfcx by a degree-10 polynomial, the coefficients a1, g2) costs 82 flops and is
-# evaluated once per unordered pair; each direction then adds its contribution,
-# 37 flops for a free pair and 92 for an image pair with its wall corrections.
-# Pairs in the outer shell [rc64, rc) run the same formulas in FP32; they are
-# charged the same flops against the FP32 peak.
+# unit-count fallbacks when the pipe microbenchmark is unavailable:
+# 152 SMs x 2 FP64 FMA / 128 FP32 FMA per clock x 2 flop x 2.07 GHz
+FP64_UNIT_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic work of the real-space stage (stokeslet + rotlet), counted from
+# the written formulas (FMA = 2 flops): the radial part of a pair (distance,
+# reciprocal square root charged 4, exp by reduction + polynomial, erfcx by a
+# polynomial, the coefficients a1, g2) costs 82 flops and is evaluated once per
+# unordered pair; each direction then adds its contribution, 37 flops for a
+# free pair and 92 for an image pair with its wall corrections.
+FLOPS_RADIAL = 82
+FLOPS_FREE_DIR = 37
+FLOPS_IMAGE_DIR = 92
 # DRAM bytes of one k_real_sym<double, 5> launch per point, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum = 16.1 MB + 0 at N = 100k of
 # this workload); the kernel reads positions, strengths and cell lists about
 # once, so the figure is scaled by the number of points.
 REAL_TRAFFIC_BYTES_PER_POINT = 161.0
-FLOPS_RADIAL = 82
-FLOPS_FREE_DIR = 37
-FLOPS_IMAGE_DIR = 92
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -89,6 +104,97 @@ def whole_job_rate(points_per_rank: int, world: int, ms_max: float) -> float:
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------- roofline model
+def pair_flops(n_free: int, n_img: int, n_own: int) -> float:
+    """Real-space flops from ordered pair counts: each unordered free pair and
+    image pair once (radial part + both directions); a target's own image once
+    (radial part + one direction)."""
+    return ((n_free // 2) * (FLOPS_RADIAL + 2 * FLOPS_FREE_DIR)
+            + ((n_img - n_own) // 2) * (FLOPS_RADIAL + 2 * FLOPS_IMAGE_DIR) + n_own * (FLOPS_RADIAL + FLOPS_IMAGE_DIR))
+
+
+def fft_buffer_work(Mt: int, e: int):
+    """Algorithmic bytes and flops of one zero-padded 3-D transform of one
+    buffer, either direction, as three pruned 1-D passes (z lines of the data
+    region, y lines of the data planes, x lines of every (y, kz)): each pass
+    reads its input and writes its output once.  e = bytes of a real element.
+    Flops: 2.5 n log2 n per real line of length n, 5 n log2 n per complex line."""
+    c = 2 * e
+    nz = 2 * Mt + 1  # half-spectrum length of the padded z extent 4 Mt
+    z = Mt * Mt * 2 * Mt * e + Mt * Mt * nz * c
+    y = Mt * nz * Mt * c + Mt * nz * 2 * Mt * c
+    x = 2 * Mt * nz * Mt * c + 2 * Mt * nz * 2 * Mt * c
+    fl = (Mt * Mt * 2.5 * 4 * Mt * math.log2(4 * Mt) + Mt * nz * 5 * 2 * Mt * math.log2(2 * Mt)
+          + 2 * Mt * nz * 5 * 2 * Mt * math.log2(2 * Mt))
+    return z + y + x, fl
+
+
+def stage_model(kind: str, prm: dict, n: int, rows: int, pairs: dict):
+    """Per stage: (algorithmic HBM bytes, {pipe: flops}) of one evaluation.
+    kind: 'fp64' (FP64 pairs within rc64, FP32 shell, df64 Fourier part),
+    'plain' (every pair in FP64, FP64 grids, cuFFT double), 'mixed' (FP32).
+    pairs: flops of the FP64 and FP32 real-space pairs."""
+    Mt, P, nin, nout = prm["Mt"], prm["P"], prm["n_fft_in"], prm["n_fft_out"]
+    e = 4 if kind == "mixed" else 8
+    four = {"fp64": "df64", "plain": "fp64", "mixed": "fp32"}[kind]
+    grid = Mt * Mt * 2 * Mt * e  # data region of one real grid
+    nh = 2 * Mt * 2 * Mt * (2 * Mt + 1)
+    fb, ff = fft_buffer_work(Mt, e)
+    m = {
+        "check": (n * (3 + rows) * 8, {}),
+        # binning (positions in, key and index out), two radix passes over
+        # keys + indices, cell starts, the sorted copy of positions and
+        # strengths (FP64 and FP32 copies)
+        "cells": (n * (24 + 8) + 2 * n * 16 + 4 * n + n * (4 + 2 * (3 + rows) * 8 + (6 + rows) * 4), {}),
+        # sorted positions and strengths in, sums out and un-sorted
+        "real": (n * ((3 + rows) * 12 + 24 + 16 + 4 + 24 + 24), {k: v for k, v in pairs.items() if v}),
+        # per source its support's P^3 points x (one multiply-add per grid +
+        # the 3-D weight), the grids written once
+        "spread": (nin * grid + n * (3 + rows) * 8, {four: n * P ** 3 * (2 * nin + 2)}),
+        "fft": (nin * fb, {four: nin * ff}),
+        # all inputs read, T1 and phi written, two octant tables
+        "scale": ((nin + nout) * nh * 2 * e + 2 * (Mt + 1) ** 2 * (2 * Mt + 1) * e, {four: nh * (8 * nin + 8)}),
+        "ifft": (nout * fb, {four: nout * ff}),
+        # per target its support's P^3 points x (T1: 3, grad phi: 3 multiply-adds + weights)
+        "gather": (nout * grid + n * 3 * 8 * 2, {four: n * P ** 3 * 14}),
+    }
+    return m
+
+
+def stage_roofline(model: dict, stage_ms: dict, peaks: dict, ms_step: float):
+    """Each stage's roofline time max(bytes / BW, sum over pipes of flops /
+    peak) against its CUDA-event time, and the path fraction (sum of roofline
+    times over the measured step time)."""
+    out, t_roof = [], 0.0
+    for st, (byts, flops) in model.items():
+        t_mem = byts / (peaks["hbm_gbs"] * 1e9)
+        t_alu = sum(f / (peaks[p + "_tflops"] * 1e12) for p, f in flops.items())
+        t = max(t_mem, t_alu)
+        t_roof += t
+        ms = stage_ms.get(st, 0.0)
+        out.append({"stage": st, "ms": round(ms, 3), "bytes": int(byts),
+                    "flops": {p: float(f) for p, f in flops.items()},
+                    "bound": "hbm" if t_mem >= t_alu else "alu:" + "+".join(flops),
+                    "roofline_ms": round(t * 1e3, 3), "frac": round(t * 1e3 / ms, 3) if ms > 0 else None})
+    return out, t_roof * 1e3 / ms_step
+
+
+def pipe_peaks(pkg):
+    """Measured FP64 / FP32 / df64 throughput (TFLOP/s) and HBM GB/s."""
+    pk = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    out = {"hbm_gbs": pk.get("hbm_gbs", 6800.0),
+           "hbm_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"}
+    try:
+        m = pkg.hse.hse_measure_pipe_peaks()
+        out.update(fp64_tflops=m["fp64_tflops"], fp32_tflops=m["fp32_tflops"], df64_tflops=m["df64_tflops"],
+                   alu_source="hse_measure_pipe_peaks (multiply-add chains on every SM, best of 3)")
+    except Exception as ex:  # report the unit-count figures instead, and say so
+        out.update(fp64_tflops=FP64_UNIT_TFLOPS, fp32_tflops=FP32_UNIT_TFLOPS,
+                   df64_tflops=FP32_UNIT_TFLOPS / 7.5,
+                   alu_source=f"unit counts x 2.07 GHz (microbenchmark failed: {ex}); df64 = FP32 / 7.5")
+    return out
 
 
 # ----------------------------------------------------------------- clocks
@@ -171,6 +277,169 @@ def time_oracle(pr, mask, budget_s: float, start_targets: int = 16):
         k = int(min(n, max(2 * k, k * 0.5 * budget_s / max(dt, 1e-3))))
 
 
+def error_sample(n: int, k: int, seed: int = 1802078440 + 96) -> np.ndarray:
+    """Seeded sample of k target indices (sorted) out of n."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n, size=min(k, n), replace=False))
+
+
+def oracle_on_sample(pr, idx):
+    """FP64 direct half-space sum at the sampled targets (all sources) and its wall time."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src[:, idx])
+    return ref, time.perf_counter() - t0
+
+
+def rel_rms(u, ref) -> float:
+    """Relative RMS error over the checked targets (Sec. 6)."""
+    return float(np.sqrt(np.sum((u - ref) ** 2) / np.sum(ref ** 2)))
+
+
+# ------------------------------------------------------------- GPU legs
+def time_eval(torch, plan, src, st, vel, flush, stream, steps, warmup):
+    """Warm-up evaluations, then ``steps`` timed ones (CUDA events on the
+    launching stream, a write of 512 MB between steps evicts the 129 MB L2).
+    Returns (ms per step, mean stage ms, launches per step)."""
+    from paper_1802_07844_gb300.hse import STAGE_NAMES
+    for _ in range(warmup):
+        plan.eval(src, st, out=vel)
+    torch.cuda.synchronize()
+    stages = {k: [] for k in STAGE_NAMES}
+    launches = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.eval(src, st, out=vel)
+        ev[i][1].record(stream)
+        s = plan.stats()
+        launches += s["n_kernel_launches"]
+        for k, v in s["stage_ms"].items():
+            stages[k].append(v)
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+    return ms, {k: float(np.mean(v)) if v else 0.0 for k, v in stages.items()}, launches / steps
+
+
+def pair_counts(pkg, mask, src, z, rc):
+    """Ordered free and image pair counts within rc (exact, the real-space
+    kernel's own decision), and the number of targets whose own image lies
+    within rc, from a count-only plan."""
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=1.0 / rc, rc=rc, P=8, tol=0.0)
+    try:
+        a, b = plan.neighbor_counts(src)
+        nf, ni = int(a.sum().item()), int(b.sum().item())
+    finally:
+        plan.close()
+    return nf, ni, int(np.sum((z + z) * (z + z) < rc * rc))
+
+
+class PairCounter:
+    """Real-space pair counts of the rank's workload by cut-off (cached)."""
+
+    def __init__(self, pkg, mask, src, z):
+        self.pkg, self.mask, self.src, self.z, self.cache = pkg, mask, src, z, {}
+
+    def __call__(self, rc):
+        if rc not in self.cache:
+            self.cache[rc] = pair_counts(self.pkg, self.mask, self.src, self.z, rc)
+        return self.cache[rc]
+
+    def flops(self, kind, prm):
+        """Real-space flops by pipe for a plan's (rc, rc64) and arithmetic."""
+        rc, rc64 = prm["rc"], prm["rc64"]
+        total = pair_flops(*self(rc))
+        if kind == "mixed":
+            return {"fp32": total}
+        if kind == "plain" or not (0.0 < rc64 < rc):
+            return {"fp64": total}
+        w64 = pair_flops(*self(rc64))
+        return {"fp64": w64, "fp32": total - w64}
+
+
+ARITH = {
+    "fp64": "FP64 pairs within rc64, FP32 outer shell [rc64, r_c), double-float (~48-bit) spread, "
+            "transforms, scaling and gather on the FP32 pipe; FP64 sums",
+    "plain": "FP64 throughout: every pair in FP64, FP64 grids, cuFFT double transforms",
+    "mixed": "FP32 arithmetic (pairs, grids, cuFFT single); FP64 sums, close image pairs, self term, "
+             "tables built in FP64 and rounded once",
+}
+
+
+def run_leg(ctx, label, kind, p, tol):
+    """One further configuration of the bench workload: its own plan, warm-up,
+    timed steps, stage times and per-stage roofline; keeps the sampled result
+    for the oracle check."""
+    torch, pkg = ctx["torch"], ctx["pkg"]
+    args = ctx["args"]
+    prec = pkg.HSE_MIXED if kind == "mixed" else pkg.HSE_FP64
+    plan = pkg.Plan(ctx["mask"], (1.0, 1.0, 1.0), xi=p["xi"], rc=p["rc"], P=p["P"], tol=0.0, M=p["M"],
+                    precision=prec)
+    try:
+        if kind == "plain":
+            plan.set_rc64(p["rc"])
+            plan.set_fft(pkg.HSE_FFT_CUFFT)
+        plan.set_timing(True)
+        steps = max(1, min(args.steps, args.leg_steps))
+        ms, stages, launches = time_eval(torch, plan, ctx["src"], ctx["st"], ctx["vel"], ctx["flush"], ctx["stream"],
+                                         steps, max(3, min(args.warmup, 3)))
+        ctx["samples"][label] = ctx["vel"][:, ctx["idx_t"]].cpu().numpy()
+        prm = plan.params
+    finally:
+        plan.close()
+    ms_max = max_over_ranks(ms, ctx["world"], ctx["dev"])
+    n = ctx["n"]
+    model = stage_model(kind, prm, n, ctx["rows"], ctx["pairs"].flops(kind, prm))
+    st_list, path = stage_roofline(model, stages, ctx["peaks"], ms)
+    return {"value": whole_job_rate(n, ctx["world"], ms_max), "unit": "Mtargets/s", "ms_per_step": ms_max,
+            "steps": steps, "arithmetic": ARITH[kind], "tol": tol, "xi": prm["xi"], "rc": prm["rc"],
+            "rc64": prm["rc64"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
+            "fft": {0: "auto", 1: "cufft", 2: "df64"}.get(prm["fft"], prm["fft"]), "gpu_launches": launches,
+            "stage_ms": {k: round(v, 3) for k, v in stages.items()}, "path_roofline_frac": round(path, 3),
+            "stages_roofline": st_list}
+
+
+def run_config_legs(ctx):
+    """The N = 1000 and N = 100k workloads with plans chosen from tol: rate and
+    error against the oracle (all targets for N = 1000, a seeded sample of
+    4000 targets for N = 100k)."""
+    torch, pkg, args = ctx["torch"], ctx["pkg"], ctx["args"]
+    from workloads import workload
+    out = {}
+    for name, xi in CONFIG_LEGS:
+        w = WORKLOADS[name]
+        pr = workload(name)
+        n = pr.src.shape[1]
+        src = torch.from_numpy(pr.src).to(ctx["dev"])
+        st = torch.from_numpy(pr.strengths).to(ctx["dev"])
+        vel = torch.empty((3, n), dtype=torch.float64, device=ctx["dev"])
+        plan = pkg.Plan(w["mask"], (1.0, 1.0, 1.0), xi=xi, rc=0.0, P=0, tol=w["tol"])
+        try:
+            plan.set_timing(True)
+            steps = max(3, min(args.steps, 20))
+            ms, stages, launches = time_eval(torch, plan, src, st, vel, ctx["flush"], ctx["stream"], steps,
+                                             max(3, args.warmup))
+            u = vel.cpu().numpy()
+            prm = plan.params
+        finally:
+            plan.close()
+        rec = {"n": n, "kernel": {1: "stokeslet", 2: "stresslet"}[w["mask"]], "tol": w["tol"],
+               "value": n / (ms / 1e3) / 1e6, "unit": "Mtargets/s", "ms_per_step": ms, "steps": steps,
+               "arithmetic": ARITH["fp64"] if prm["fft"] == 2 else ARITH["plain"], "xi": prm["xi"], "rc": prm["rc"],
+               "rc64": prm["rc64"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"], "gpu_launches": launches,
+               "stage_ms": {k: round(v, 3) for k, v in stages.items()}}
+        if ctx["check"]:
+            idx = np.arange(n) if n <= 1000 else error_sample(n, 4000, seed=1802078440 + 95)
+            ref, dt = oracle_on_sample(pr, idx)
+            rec["err_rel_rms"] = rel_rms(u[:, idx], ref)
+            rec["err_sample"] = (f"all {n} targets" if len(idx) == n else f"{len(idx)} seeded targets") + \
+                " against the FP64 direct sum over all sources"
+        out[name] = rec
+        del src, st, vel
+    return out
+
+
 # ------------------------------------------------------------ main arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -188,31 +457,29 @@ def run_ours(args, rank, world, local_rank):
         return run_real_only(args, pkg, torch, dev, W, pr)
     if args.fourier_small:
         return run_fourier_small(args, pkg, torch, dev, W)
+    n = W["n"]
+    rows = pr.strengths.shape[0]
+    peaks = pipe_peaks(pkg)
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
+    if args.overlap:
+        plan.set_overlap(True)
+        plan.set_real_residency(args.real_residency)
     plan.set_timing(True)
     prm = plan.params
     src = torch.from_numpy(pr.src).to(dev)
     st = torch.from_numpy(pr.strengths).to(dev)
-    vel = torch.empty((3, W["n"]), dtype=torch.float64, device=dev)
+    vel = torch.empty((3, n), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)  # 512 MB > L2
     stream = torch.cuda.current_stream()
+    check = world == 1 and not args.no_check
+    idx = error_sample(n, ERR_SAMPLE)
+    idx_t = torch.from_numpy(idx).to(dev)
+    samples = {}
     for _ in range(args.warmup):
         plan.eval(src, st, out=vel)
     torch.cuda.synchronize()
-    # exact pair counts of the real-space stage (untimed); a target's own image
-    # counts once, every other pair is shared by its two targets
-    a, b = plan.neighbor_counts(src)
-    n_free, n_img = int(a.sum().item()), int(b.sum().item())
-    z = pr.src[2]
-    n_own = int(np.sum((z + z) * (z + z) < W["rc"] * W["rc"]))
-    # the same counts within rc64 (pairs evaluated in FP64), from a count-only plan
-    rc64 = prm["rc64"]
-    cplan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=W["xi"], rc=rc64, P=W["P"], tol=0.0)
-    a64, b64 = cplan.neighbor_counts(src)
-    n_free64, n_img64 = int(a64.sum().item()), int(b64.sum().item())
-    n_own64 = int(np.sum((z + z) * (z + z) < rc64 * rc64))
-    cplan.close()
-    del a, b, a64, b64
+    pairs = PairCounter(pkg, mask, src, pr.src[2])
+    real_flops = pairs.flops("fp64", prm)  # exact pair counts (untimed)
 
     def barrier():
         if world > 1:
@@ -220,6 +487,7 @@ def run_ours(args, rank, world, local_rank):
 
     stages = {k: [] for k in pkg.hse.STAGE_NAMES}
     launches = 0
+    overlapped = False
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
@@ -241,12 +509,13 @@ def run_ours(args, rank, world, local_rank):
     total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     ms_step = total_ms / args.steps
     ms_step_max = max_over_ranks(ms_step, world, dev)
-    value = whole_job_rate(W["n"], world, ms_step_max)
+    value = whole_job_rate(n, world, ms_step_max)
+    samples["fp64_1e-10"] = vel[:, idx_t].cpu().numpy()
 
     # end-to-end: pinned host inputs in, velocities out, inside the timed region
     h_src = torch.from_numpy(pr.src).pin_memory()
     h_st = torch.from_numpy(pr.strengths).pin_memory()
-    h_vel = torch.empty((3, W["n"]), dtype=torch.float64).pin_memory()
+    h_vel = torch.empty((3, n), dtype=torch.float64).pin_memory()
     d_src = torch.empty_like(src)
     d_st = torch.empty_like(st)
     e2e_steps = max(1, min(args.steps, 3))
@@ -266,50 +535,39 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
     e_ms /= e2e_steps
-    e2e_value = whole_job_rate(W["n"], world, max_over_ranks(e_ms, world, dev))
+    e2e_value = whole_job_rate(n, world, max_over_ranks(e_ms, world, dev))
     h2d = h_src.numel() * 8 + h_st.numel() * 8
     d2h = h_vel.numel() * 8
+    samples["e2e"] = h_vel.numpy()[:, idx]
+    plan.close()
+    del d_src, d_st
 
-    # roofline of the dominant kernel of this library
+    # roofline: every stage against its bound, and the dominant kernel
     avg = {k: float(np.mean(v)) if v else 0.0 for k, v in stages.items()}
-    own = {k: avg[k] for k in ("real", "spread", "scale", "gather")}
-    dom = max(own, key=own.get)
-    P, Mt, nc = prm["P"], prm["Mt"], prm["n_fft_in"]
-    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    if dom == "real":
-        def flops(nf, ni, no):
-            return ((nf // 2) * (FLOPS_RADIAL + 2 * FLOPS_FREE_DIR)
-                    + ((ni - no) // 2) * (FLOPS_RADIAL + 2 * FLOPS_IMAGE_DIR) + no * (FLOPS_RADIAL + FLOPS_IMAGE_DIR))
-        w64 = flops(n_free64, n_img64, n_own64)
-        w32 = flops(n_free, n_img, n_own) - w64
-        # FP64-equivalent rate: the FP32 shell flops weighted by the pipe ratio,
-        # so achieved / peak = (ideal time on both pipes) / measured time
-        work = w64 + w32 * FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS
-        roof = {"kernel": "k_real_sym", "bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 units x clock (152 SMs x 2 FMA/clk x 2.07 GHz); FP32 shell flops "
-                               "charged at FP64/FP32 = 1/64 (128 FP32 lanes/SM)",
-                "achieved": work / (avg["real"] / 1e3) / 1e12,
-                "work": {"free_pairs_ordered": n_free, "image_pairs_ordered": n_img, "own_images": n_own,
-                         "fp64_free_pairs_ordered": n_free64, "fp64_image_pairs_ordered": n_img64,
-                         "rc64": rc64, "flops_fp64": w64, "flops_fp32_shell": w32,
-                         "flops_radial": FLOPS_RADIAL, "flops_free_direction": FLOPS_FREE_DIR,
-                         "flops_image_direction": FLOPS_IMAGE_DIR}}
-    elif dom in ("spread", "gather"):
-        per = P ** 3 * (2 * nc + 2) if dom == "spread" else P ** 3 * 12
-        work = W["n"] * per
-        roof = {"kernel": "k_" + dom, "bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 units x clock", "achieved": work / (avg[dom] / 1e3) / 1e12}
-    else:
-        nh = (2 * Mt) * (2 * Mt) * (2 * Mt + 1)
-        byts = (nc + 6) * nh * 16 + nh * 8 * 2
-        roof = {"kernel": "k_scale", "bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs", "achieved": byts / (avg["scale"] / 1e3) / 1e9}
+    st_list, path = stage_roofline(stage_model("fp64", prm, n, rows, real_flops), avg, peaks, ms_step)
+    w64, w32 = real_flops.get("fp64", 0.0), real_flops.get("fp32", 0.0)
+    # FP64-equivalent rate: the FP32 shell's flops weighted by the pipe ratio,
+    # so achieved / peak = (ideal time on both pipes) / measured time
+    work = w64 + w32 * peaks["fp64_tflops"] / peaks["fp32_tflops"]
+    nf, ni, no = pairs(prm["rc"])
+    nf64, ni64, no64 = pairs(prm["rc64"])
+    roof = {"kernel": "k_real_sym", "bound": "alu", "unit": "TFLOP/s", "peak": peaks["fp64_tflops"],
+            "peak_source": "measured FP64 FMA throughput (" + peaks["alu_source"] + "); FP32 shell flops "
+                           "charged at the measured FP64/FP32 throughput ratio",
+            "achieved": work / (avg["real"] / 1e3) / 1e12,
+            "traffic": REAL_TRAFFIC_BYTES_PER_POINT * n,
+            "traffic_source": "ncu dram bytes of one launch at N = 100k, scaled by points",
+            "work": {"free_pairs_ordered": nf, "image_pairs_ordered": ni, "own_images": no,
+                     "fp64_free_pairs_ordered": nf64, "fp64_image_pairs_ordered": ni64, "rc64": prm["rc64"],
+                     "flops_fp64": w64, "flops_fp32_shell": w32, "flops_radial": FLOPS_RADIAL,
+                     "flops_free_direction": FLOPS_FREE_DIR, "flops_image_direction": FLOPS_IMAGE_DIR}}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = REAL_TRAFFIC_BYTES_PER_POINT * W["n"] if dom == "real" else None
-    if dom == "real":
-        roof["traffic_source"] = "ncu dram bytes of one launch at N = 100k, scaled by points"
     roof["stage_ms"] = {k: round(v, 3) for k, v in avg.items()}
+    roof["path_frac"] = round(path, 3)
+    roof["path_note"] = ("sum over stages of max(bytes / HBM, flops / pipe) over the measured step; pipes: "
+                         "FP64 pairs on FP64, shell on FP32, Fourier part df64 (2 flops per df64 multiply-add)")
+    roof["stages"] = st_list
+    roof["peaks"] = peaks
     if overlapped:
         roof["stage_ms_note"] = ("device time of each stage on its own stream: the real-space stage runs "
                                  "concurrently with spread..gather, so the stages overlap and their sum "
@@ -318,103 +576,99 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": W["name"], "n_sources": W["n"], "n_targets": W["n"], "kernels": "stokeslet+rotlet",
+        "vs_baseline": None, "dtype": "f64+f32+df64", "arithmetic": ARITH["fp64"], "data": "synthetic",
+        "config": {"workload": W["name"], "n_sources": n, "n_targets": n, "kernels": "stokeslet+rotlet",
                    "distribution": "x,y ~ U[0,1), z ~ TruncExp(0.05) on (0,1]", "tol": W["tol"],
-                   "precision": "fp64", "xi": prm["xi"], "rc": prm["rc"], "P": P, "M": prm["M"], "Mt": Mt,
-                   "fft_in": nc, "fft_out": prm["n_fft_out"], "parallelism": f"replicas x{world}",
-                   "l2": "512 MB buffer written between timed steps"},
+                   "precision": "HSE_FP64 plan: " + ARITH["fp64"], "xi": prm["xi"], "rc": prm["rc"],
+                   "rc64": prm["rc64"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
+                   "fft_in": prm["n_fft_in"], "fft_out": prm["n_fft_out"], "overlap": bool(args.overlap),
+                   "real_residency": args.real_residency if args.overlap else 0,
+                   "parallelism": f"replicas x{world}", "l2": "512 MB buffer written between timed steps"},
         "e2e": {"value": e2e_value, "unit": "Mtargets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "gpu_launches": launches,
         "clocks": clk,
     }
+    ctx = dict(torch=torch, pkg=pkg, args=args, dev=dev, world=world, mask=mask, n=n, rows=rows, src=src, st=st,
+               vel=vel, flush=flush, stream=stream, idx_t=idx_t, samples=samples, peaks=peaks, pairs=pairs,
+               check=check)
+    if not args.no_plain:
+        out["plain_fp64_1e-10"] = run_leg(ctx, "plain_fp64_1e-10", "plain", W, W["tol"])
     if not args.no_mixed:
-        out["mixed_1e-5"] = run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world)
-    if args.serve_requests > 0:
-        del flush
-        plan.close()
-        torch.cuda.empty_cache()
-        out["serve"] = run_serve(args, pkg, torch, dev)
+        out["mixed_1e-5"] = run_leg(ctx, "mixed_1e-5", "mixed", MIXED, MIXED["tol"])
+        out["fp64_1e-5"] = run_leg(ctx, "fp64_1e-5", "fp64", MIXED, MIXED["tol"])
+        out["plain_fp64_1e-5"] = run_leg(ctx, "plain_fp64_1e-5", "plain", MIXED, MIXED["tol"])
+    del src, st, vel
+    torch.cuda.empty_cache()
+    if check:
+        # the oracle on the sampled targets: every leg's error, and the CPU baseline
+        ref, t_or = oracle_on_sample(pr, idx)
+        errs = {k: rel_rms(u, ref) for k, u in samples.items()}
+        out["err_rel_rms"] = errs["fp64_1e-10"]
+        out["err_e2e_rel_rms"] = errs["e2e"]
+        out["err_sample"] = (f"{len(idx)} seeded targets of the {n}, FP64 direct half-space sum over all "
+                             f"{n} sources (relative RMS, Sec. 6)")
+        for k, v in errs.items():
+            if k in out:
+                out[k]["err_rel_rms"] = v
+        if rank == 0:
+            out["cpu_baseline"] = {"value": len(idx) / t_or / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(),
+                                   "kind": "oracle",
+                                   "sample": f"{len(idx)} seeded targets of the same workload against all {n} "
+                                             f"sources (FP64 direct half-space sum, OpenMP), {t_or:.1f} s"}
+    if args.config_legs:
+        out["configs"] = run_config_legs(ctx)
+    del flush
+    torch.cuda.empty_cache()
     if args.batch_instances > 0:
-        torch.cuda.empty_cache()
         out["batch"] = run_batch(args, pkg, torch, dev)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tps, k, dt = time_oracle(pr, mask, args.cpu_budget)
-        out["cpu_baseline"] = {"value": tps / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": f"{k} seeded targets of the same workload against all {W['n']} sources "
-                                         f"(FP64 direct half-space sum, OpenMP), {dt:.1f} s"}
-    plan.close()
+        torch.cuda.empty_cache()
+    if args.serve_requests > 0:
+        out["serve"] = run_serve(args, pkg, torch, dev)
     return out
-
-
-def run_mixed(args, pkg, torch, dev, pr, src, st, vel, flush, stream, world):
-    """The same workload through the FP32-arithmetic path at tolerance 1e-5."""
-    Mx = MIXED
-    plan = pkg.Plan(WORKLOAD["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=Mx["rc"], P=Mx["P"], tol=0.0, M=Mx["M"],
-                    precision=pkg.HSE_MIXED)
-    plan.set_timing(True)
-    for _ in range(args.warmup):
-        plan.eval(src, st, out=vel)
-    torch.cuda.synchronize()
-    stages = {k: [] for k in pkg.hse.STAGE_NAMES}
-    ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.eval(src, st, out=vel)
-        e1.record(stream)
-        s = plan.stats()
-        for k, v in s["stage_ms"].items():
-            stages[k].append(v)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-    ms /= args.steps
-    ms_max = max_over_ranks(ms, world, dev)
-    prm = plan.params
-    plan.close()
-    n = src.shape[1]
-    return {"value": whole_job_rate(n, world, ms_max), "unit": "Mtargets/s", "ms_per_step": ms_max,
-            "dtype": "f32 arithmetic (FP64 sums, close image pairs, tables)", "tol": Mx["tol"], "xi": prm["xi"],
-            "rc": prm["rc"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
-            "stage_ms": {k: round(float(np.mean(v)), 3) for k, v in stages.items()}}
 
 
 def run_serve(args, pkg, torch, dev):
     """Poisson stream of requests through the continuous-batching server:
     kernel uniform over stokeslet/stresslet/rotlet, N log-uniform in [1e3, 2e5],
     half uniform and half near-wall (TruncExp 0.05), tol 1e-10 (FP64) or 1e-5
-    (mixed) per request.  The offered load is 0.7 x the service capacity
-    measured on a closed-loop warm-up of the same request mix."""
-    from workloads import KERNEL_S, KERNEL_T, KERNEL_W, problem as mk
+    (mixed) per request.  The plans of the stream's parameter keys are built
+    before it starts (hse_server_prewarm); the offered load is 0.7 x the
+    service capacity measured on a closed-loop warm-up of the same request mix."""
+    from workloads import problem as mk
     rng = np.random.default_rng(1802078440 + 4)
     nreq = args.serve_requests
     kinds = [KERNEL_S, KERNEL_T, KERNEL_W]
-    reqs = []
+    reqs, probs = [], []
     for i in range(nreq):
         mask = kinds[int(rng.integers(3))]
         n = int(np.exp(rng.uniform(np.log(1e3), np.log(2e5))))
         dist = "uniform" if rng.uniform() < 0.5 else "near_wall"
         tol = 1e-10 if rng.uniform() < 0.5 else 1e-5
         pr = mk(mask, n, 1.0, dist, 4, sub=i)
+        probs.append(pr)
         reqs.append((mask, tol, torch.from_numpy(pr.src).to(dev), torch.from_numpy(pr.strengths).to(dev)))
     srv = pkg.hse.Server(n_slots=args.serve_slots)
     try:
-        return _serve_measure(srv, reqs, rng, pkg, args)
+        return _serve_measure(srv, reqs, probs, rng, pkg, torch, args)
     finally:
         srv.close()
 
 
-def _serve_measure(srv, reqs, rng, pkg, args):
+def _serve_measure(srv, reqs, probs, rng, pkg, torch, args):
     prec = lambda tol: pkg.HSE_MIXED if tol >= 1e-6 else pkg.HSE_FP64
+    t0 = time.perf_counter()
+    for m, tol, a, _ in reqs:
+        srv.prewarm(m, a.shape[1], tol, prec(tol))
+    prewarm_s = time.perf_counter() - t0
+    plans_prewarmed = srv.stats()["plans_created"]
 
     def closed_loop(batch):
         ts = [srv.submit(m, a, b, tol, prec(tol)) for m, tol, a, b in batch]
         for t in ts:
             srv.wait(t, 600.0)
 
-    # warm the plan cache and measure the service capacity (requests/s)
+    # measure the service capacity (requests/s) on the first requests
     warm = reqs[: min(len(reqs), 3 * args.serve_slots * 8)]
     closed_loop(warm)
     srv.reset_stats()
@@ -437,11 +691,53 @@ def _serve_measure(srv, reqs, rng, pkg, args):
         srv.wait(t, 600.0)
     st = srv.stats()
     n_tgt = sum(int(a.shape[1]) for _, _, a, _ in reqs)
-    return {"requests": len(reqs), "slots": args.serve_slots, "offered_load_req_per_s": lam,
-            "capacity_req_per_s": cap, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "throughput_req_per_s": st["completed"] / st["busy_s"] if st["busy_s"] else None,
-            "throughput_Mtargets_per_s": st["targets_per_s"] / 1e6, "targets": n_tgt, "failed": st["failed"],
-            "plans_created": st["plans_created"], "plans_evicted": st["plans_evicted"]}
+    out = {"requests": len(reqs), "slots": args.serve_slots, "offered_load_req_per_s": lam,
+           "capacity_req_per_s": cap, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+           "throughput_req_per_s": st["completed"] / st["busy_s"] if st["busy_s"] else None,
+           "throughput_Mtargets_per_s": st["targets_per_s"] / 1e6, "targets": n_tgt, "failed": st["failed"],
+           "plans_prewarmed": plans_prewarmed, "prewarm_s": prewarm_s,
+           "plans_created_during_stream": st["plans_created"] - plans_prewarmed,
+           "plan_cache_hit_rate": st["plan_hits"] / max(1, st["completed"] + st["failed"]),
+           "plan_build_s_during_stream": st["plan_build_s"], "plans_evicted": st["plans_evicted"]}
+    if args.no_check:
+        return out
+    import oracle
+    # per request: 64 seeded targets against the FP64 direct sum (all sources)
+    erng = np.random.default_rng(1802078440 + 94)
+    errs, over = [], 0
+    for t, pr, (m, tol, a, b) in zip(tickets, probs, reqs):
+        n = pr.src.shape[1]
+        idx = np.sort(erng.choice(n, size=min(64, n), replace=False))
+        ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src[:, idx])
+        u = srv.result(t)[:, torch.from_numpy(idx).to(a.device)].cpu().numpy()
+        e = rel_rms(u, ref)
+        errs.append(e / tol)
+        over += e > tol
+    out["err_64_targets_over_tol_median"] = float(np.median(errs))
+    out["err_64_targets_over_tol_max"] = float(np.max(errs))
+    out["requests_over_tol_on_64_targets"] = int(over)
+    out["err_64_targets_sample"] = ("64 seeded targets of every request, relative RMS against the FP64 direct sum, "
+                                    "divided by the request's tol (a sample norm of a heavy-tailed field: noisy)")
+    # the same request alone (a plan with the server's parameters, read back)
+    # against its result in the mix, for a seeded sample of requests
+    sel = sorted(erng.choice(len(reqs), size=min(48, len(reqs)), replace=False))
+    worst = 0.0
+    plans = {}
+    try:
+        for i in sel:
+            m, tol, a, b = reqs[i]
+            used = srv.request_params(tickets[i])
+            key = (m, tol, used["xi"])
+            if key not in plans:
+                plans[key] = pkg.Plan(m, (1.0, 1.0, 1.0), xi=used["xi"], rc=0.0, P=0, tol=tol, precision=prec(tol))
+            alone = plans[key].eval(a, b)
+            worst = max(worst, rel_rms(srv.result(tickets[i]).cpu().numpy(), alone.cpu().numpy()) / tol)
+    finally:
+        for p in plans.values():
+            p.close()
+    out["mix_vs_alone_over_tol_max"] = worst
+    out["mix_vs_alone_sample"] = f"{len(sel)} seeded requests, all targets, relative RMS / tol"
+    return out
 
 
 def run_batch(args, pkg, torch, dev):
@@ -449,7 +745,6 @@ def run_batch(args, pkg, torch, dev):
     log-uniform in [200, 2e4], uniform positions in the unit box, N(0,1)
     strengths, FP32 arithmetic at tol 1e-5, xi autotuned per group.  A step is
     one hse_batch_eval over all instances (inputs resident on the device)."""
-    from workloads import KERNEL_S, KERNEL_T, problem as mk
     import oracle
     n_inst = args.batch_instances
     rng = np.random.default_rng(1802078440 + 3)
@@ -457,7 +752,7 @@ def run_batch(args, pkg, torch, dev):
     for i in range(n_inst):
         mask = KERNEL_S if i % 2 == 0 else KERNEL_T
         n = int(np.exp(rng.uniform(np.log(200), np.log(2e4))))
-        probs.append(mk(mask, n, 1.0, "uniform", 3, sub=i))
+        probs.append(problem(mask, n, 1.0, "uniform", 3, sub=i))
     items = [(p.mask, torch.from_numpy(p.src).to(dev), torch.from_numpy(p.strengths).to(dev)) for p in probs]
     outs = [torch.empty((3, p.src.shape[1]), dtype=torch.float64, device=dev) for p in probs]
     n_tot = sum(p.src.shape[1] for p in probs)
@@ -481,9 +776,30 @@ def run_batch(args, pkg, torch, dev):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         s1 = b.stats()
+        used = [b.instance_params(i) for i in range(n_inst)]
     finally:
         b.close()
     ms_step = float(np.mean(ms))
+    groups = {}
+    for p, u in zip(probs, used):
+        key = (p.mask, u["xi"], u["P"], u["M"])
+        g = groups.setdefault(key, {"kernel": {1: "stokeslet", 2: "stresslet"}[p.mask], "xi": u["xi"],
+                                    "rc": u["rc"], "P": u["P"], "M": u["M"], "instances": 0, "n_min": 1 << 30,
+                                    "n_max": 0})
+        g["instances"] += 1
+        g["n_min"] = min(g["n_min"], p.src.shape[1])
+        g["n_max"] = max(g["n_max"], p.src.shape[1])
+    rec = {"instances": n_inst, "targets": n_tot, "value": n_tot / (ms_step / 1e3) / 1e6, "unit": "Mtargets/s",
+           "instances_per_s": n_inst / (ms_step / 1e3), "ms_per_step": ms_step,
+           "first_call_s": t_first, "tol": 1e-5, "arithmetic": ARITH["mixed"],
+           "chunks_per_step": (s1["chunks"] - s0["chunks"]) / max(1, args.steps),
+           "gpu_launches_per_step": (s1["kernel_launches"] - s0["kernel_launches"]) / max(1, args.steps),
+           "fft_execs_per_step": (s1["fft_execs"] - s0["fft_execs"]) / max(1, args.steps),
+           "plans": s1["plans"], "autotuned_groups": s1["autotuned_groups"],
+           "graph_launches_per_step": (s1["graph_launches"] - s0["graph_launches"]) / max(1, args.steps),
+           "groups": sorted(groups.values(), key=lambda g: (g["kernel"], g["xi"]))}
+    if args.no_check:
+        return rec
     # error against the FP64 direct sum: all targets of 32 seeded instances,
     # and 64 seeded targets of every instance
     erng = np.random.default_rng(1802078440 + 97)
@@ -498,20 +814,17 @@ def run_batch(args, pkg, torch, dev):
         idx = np.sort(erng.choice(n, size=min(64, n), replace=False))
         ref = oracle.direct(p.mask, p.src, p.strengths, p.src[:, idx])
         errs64.append(oracle.rel_rms(host[i][:, idx], ref))
-    steps = max(1, args.steps)
-    return {"instances": n_inst, "targets": n_tot, "value": n_tot / (ms_step / 1e3) / 1e6, "unit": "Mtargets/s",
-            "instances_per_s": n_inst / (ms_step / 1e3), "ms_per_step": ms_step,
-            "first_call_s": t_first, "tol": 1e-5, "dtype": "f32 arithmetic (FP64 sums, close image pairs, tables)",
-            "chunks_per_step": (s1["chunks"] - s0["chunks"]) / steps,
-            "gpu_launches_per_step": (s1["kernel_launches"] - s0["kernel_launches"]) / steps,
-            "fft_execs_per_step": (s1["fft_execs"] - s0["fft_execs"]) / steps,
-            "plans": s1["plans"], "autotuned_groups": s1["autotuned_groups"],
-            "err_vs_oracle_max": float(max(errs)),
-            "err_sample": f"{len(errs)} seeded instances, all their targets, FP64 direct sum",
-            "err_64_targets_median": float(np.median(errs64)), "err_64_targets_max": float(max(errs64)),
-            "err_64_targets_sample": "64 seeded targets of every instance (norm of a 64-target sample of a "
-                                     "heavy-tailed field: a noisy error estimate)",
-            "graph_launches_per_step": (s1["graph_launches"] - s0["graph_launches"]) / steps}
+    worst = int(np.argmax(errs64))
+    p = probs[worst]
+    full = oracle.rel_rms(host[worst], oracle.direct(p.mask, p.src, p.strengths))
+    rec.update({"err_vs_oracle_max": float(max(errs)),
+                "err_sample": f"{len(errs)} seeded instances, all their targets, FP64 direct sum",
+                "err_64_targets_median": float(np.median(errs64)), "err_64_targets_max": float(max(errs64)),
+                "err_64_targets_sample": "64 seeded targets of every instance (norm of a 64-target sample of a "
+                                         "heavy-tailed field: a noisy error estimate)",
+                "err_worst_64_instance_all_targets": full,
+                "instances_over_tol_on_64_targets": int(np.sum(np.array(errs64) > 1e-5))})
+    return rec
 
 
 def run_real_only(args, pkg, torch, dev, W, pr):
@@ -538,16 +851,19 @@ def run_real_only(args, pkg, torch, dev, W, pr):
 # Profiling aid: the Fourier half of the bench workload's kind at 1/8 of its
 # grid (Mt = 160) and the same particle density and support (P = 18), small
 # enough (3.7 GB of grids) for full ncu captures of the spread, transform,
-# scale and gather kernels.
+# scale and gather kernels.  --mixed: the mixed-precision leg's kind at the same
+# scale (P = 12, Mt = 128).
 FOURIER_SMALL = dict(n=100000, xi=44.0, rc=0.11, P=18, M=142)
+FOURIER_SMALL_MIXED = dict(n=100000, xi=47.5, rc=0.07, P=12, M=116)
 
 
 def run_fourier_small(args, pkg, torch, dev, W):
-    F = dict(FOURIER_SMALL)
+    F = dict(FOURIER_SMALL_MIXED if args.mixed else FOURIER_SMALL)
     if args.n:
         F["n"] = args.n
     pr = replica_problem(0, F["n"])
-    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=F["xi"], rc=F["rc"], P=F["P"], tol=0.0, M=F["M"])
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=F["xi"], rc=F["rc"], P=F["P"], tol=0.0, M=F["M"],
+                    precision=pkg.HSE_MIXED if args.mixed else pkg.HSE_FP64)
     src = torch.from_numpy(pr.src).to(dev)
     st = torch.from_numpy(pr.strengths).to(dev)
     for _ in range(args.warmup):
@@ -560,7 +876,8 @@ def run_fourier_small(args, pkg, torch, dev, W):
     dt = (time.perf_counter() - t0) / args.steps
     mt = plan.params["Mt"]
     plan.close()
-    return {"profiling_run": "Fourier half only, small grid", "n": F["n"], "Mt": mt, "ms_per_step": dt * 1e3}
+    return {"profiling_run": "Fourier half only, small grid" + (" (mixed precision)" if args.mixed else ""),
+            "n": F["n"], "Mt": mt, "ms_per_step": dt * 1e3}
 
 
 # ---------------------------------------------------------- reference arm
@@ -589,7 +906,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": W["name"], "n_sources": W["n"], "targets_per_step": k, "kernels": "stokeslet+rotlet",
-                   "tol": W["tol"], "precision": "fp64"},
+                   "tol": W["tol"], "precision": "fp64 (direct sum)"},
         "cpu_baseline": {"value": value, "unit": "Mtargets/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{k} seeded targets per step against all {W['n']} sources"},
         "e2e": {"value": value, "unit": "Mtargets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -603,16 +920,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=0, help="override the number of sources (smaller test runs)")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-arithmetic measurement")
-    ap.add_argument("--serve-requests", type=int, default=400, help="requests of the serving run (0: skip)")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle checks and the CPU baseline")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 1e-5 legs (mixed, FP64, plain FP64)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 leg at 1e-10")
+    ap.add_argument("--leg-steps", type=int, default=5, help="timed steps of each further leg (at most --steps)")
+    ap.add_argument("--config-legs", type=int, default=1, help="1: time the N = 1000 and N = 100k workloads")
+    ap.add_argument("--overlap", type=int, default=0,
+                    help="1: real-space and Fourier halves on two streams (hse_plan_set_overlap)")
+    ap.add_argument("--real-residency", type=int, default=0,
+                    help="with --overlap: real-space blocks per SM (hse_plan_set_real_residency)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving run (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--batch-instances", type=int, default=4096,
                     help="instances of the batched small-systems run (0: skip)")
     ap.add_argument("--real-only", action="store_true",
                     help="profiling aid: plan without a grid, time only the real-space half")
-    ap.add_argument("--mixed", action="store_true", help="with --real-only: the mixed-precision leg's plan")
+    ap.add_argument("--mixed", action="store_true",
+                    help="with --real-only / --fourier-small: the mixed-precision leg's kind of plan")
     ap.add_argument("--fourier-small", action="store_true",
                     help="profiling aid: Fourier half only on a grid of Mt = 160 (100k sources)")
     args = ap.parse_args()

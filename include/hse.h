@@ -58,8 +58,18 @@ typedef enum {
  * corrections (u = sum S8(r) f, T8(r)(g q), W8(r) tau); the box, the Ewald
  * split, the self term and every entry point are otherwise unchanged. */
 enum { HSE_STOKESLET = 1, HSE_STRESSLET = 2, HSE_ROTLET = 4, HSE_FREE_SPACE = 8 };
-/* arithmetic of the path: HSE_FP64 everywhere (for tolerances down to 1e-10),
- * HSE_MIXED: FP32 real space, spreading, FFT and gather (tolerances >= 1e-6) */
+/* arithmetic of the path.
+ * HSE_FP64 (any tolerance): real-space pairs closer than rc64 (hse_params) in
+ *   FP64 and the outer shell [rc64, r_c) in FP32, its rc64 chosen so that the
+ *   FP32 rounding stays below half the real-space truncation estimate; with
+ *   HSE_FFT_DF64 (the automatic choice for tol >= 1e-12 or explicit
+ *   parameters) the spread and gather grids, the zero-padded transforms and
+ *   the scaling run in double-float (~48-bit) arithmetic on the FP32 pipe;
+ *   sums, the self term and the combination in FP64.  hse_plan_set_rc64(plan,
+ *   rc) with hse_plan_set_fft(plan, HSE_FFT_CUFFT) gives FP64 throughout.
+ * HSE_MIXED (tol >= 1e-6): FP32 real-space pairs, spreading, cuFFT single
+ *   transforms, scaling and gather; FP64 sums, close image pairs of near-wall
+ *   targets, the self term and the tables' construction (rounded to FP32). */
 enum { HSE_FP64 = 0, HSE_MIXED = 1 };
 /* transforms of the Fourier part (hse_plan_set_fft): HSE_FFT_DF64 runs the
  * zero-padded FFTs and the scaling of HSE_FP64 plans in double-float (~48-bit)
@@ -434,6 +444,23 @@ hse_status hse_batch_destroy(hse_batch batch);
 #define HSE_NOALLOC_MAX_POINTS 262144
 hse_status hse_cell_list_noalloc(int64_t n, const double* pos, const double box[3], const int ncell[3],
                                  int32_t* cell_id, int32_t* perm, int32_t* cell_start, void* cuda_stream);
+
+/* Measured arithmetic throughput of the current device (dense multiply-add
+ * chains on every SM, best of three launches; synchronous, ~0.1 s).  The
+ * paper has no counterpart: these are the roofline denominators of the
+ * FP64-bound real-space pairs, the FP32 shell and mixed path, and the
+ * double-float (df64) Fourier part (one df64 multiply-add counted as 2 flops,
+ * the grid update of the spread and gather).  Allocates and frees a small
+ * device buffer.  Errors: HSE_ERR_INVALID (NULL out), HSE_ERR_OOM,
+ * HSE_ERR_CUDA. */
+typedef struct {
+  double fp64_tflops;   /* FP64 FMA, 2 flops each   */
+  double fp32_tflops;   /* FP32 FMA, 2 flops each   */
+  double df64_tflops;   /* df64 multiply-add, 2 flops each */
+  int n_sm;             /* multiprocessors          */
+  double sm_clock_mhz;  /* the device's reported maximum SM clock */
+} hse_pipe_peaks;
+hse_status hse_measure_pipe_peaks(hse_pipe_peaks* out);
 
 /* Release all device memory and cuFFT plans of the plan (synchronises). */
 hse_status hse_plan_destroy(hse_plan plan);

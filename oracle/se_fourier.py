@@ -115,8 +115,14 @@ def _sym(c6):
     return [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
 
 
-def fourier_part(mask, src, strengths, xi, L, M, P, tgt=None):
-    """u_F at the targets (targets = sources when ``tgt`` is None)."""
+def fourier_part(mask, src, strengths, xi, L, M, P, tgt=None, kmax=None):
+    """u_F at the targets (targets = sources when ``tgt`` is None).
+
+    kmax: optional wave-number cut-off(s) k_inf (Sec. 6): the scaled spectra
+    are zeroed wherever some |k_d| >= k_inf before the inverse transform,
+    i.e. the Fourier integral is truncated to the cube a grid of spacing
+    h = pi / k_inf resolves, while the discretisation (grid, window, P) stays
+    that of (M, P).  A sequence of cut-offs returns one result per cut-off."""
     src = np.ascontiguousarray(src, np.float64)
     h, Mt, eta = geometry(L, M, P, xi)
     if not (0.0 < eta < 1.0):
@@ -190,14 +196,16 @@ def fourier_part(mask, src, strengths, xi, L, M, P, tgt=None):
             phi += 4.0 * GF * 1j * (K[0] * C2[0] + K[1] * C2[1])
     T1[2] = T1[2] + phi
     T2 = [1j * K[j] * phi for j in range(3)]
-    fields = []
-    for F in T1 + T2:
-        F = np.where(nyq, 0.0, F)
-        fields.append(np.real(np.fft.ifftn(F))[:Mt, :Mt, :2 * Mt])
-    del T1, T2
-    # step 10: quadrature at the targets with the same truncated Gaussian
     tg = src if tgt is None else np.ascontiguousarray(tgt, np.float64)
-    return gather(fields, tg, xi, h, P, Mt, eta)
+    cuts = [None] if kmax is None else (list(kmax) if np.ndim(kmax) else [kmax])
+    results = []
+    for kc in cuts:
+        drop = nyq if kc is None else (nyq | (np.abs(K[0]) >= kc) | (np.abs(K[1]) >= kc) | (np.abs(K[2]) >= kc))
+        fields = [np.real(np.fft.ifftn(np.where(drop, 0.0, F)))[:Mt, :Mt, :2 * Mt] for F in T1 + T2]
+        # step 10: quadrature at the targets with the same truncated Gaussian
+        results.append(gather(fields, tg, xi, h, P, Mt, eta))
+    del T1, T2
+    return results if (kmax is not None and np.ndim(kmax)) else results[0]
 
 
 def _support(c, o, h, P, n):

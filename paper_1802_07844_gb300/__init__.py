@@ -5,7 +5,10 @@ for stokeslet, stresslet and rotlet sums above a no-slip wall: a real-space
 erfc-screened neighbour sum over sources and wall images, and a Fourier-space
 part (Gaussian spreading, zero-padded 3-D FFT, scaling by truncated kernels,
 inverse FFT, Gaussian quadrature), all in hand-written CUDA kernels behind the
-C ABI of ``include/hse.h`` (cuFFT for the transforms).
+C ABI of ``include/hse.h``.  FP64 plans run the real-space pairs within rc64 in
+FP64 (an outer shell in FP32) and the Fourier part in double-float arithmetic
+with the library's own zero-padded transforms (cuFFT double on request or
+below tol 1e-12); mixed-precision plans run FP32 arithmetic with cuFFT single.
 
 ``hse`` is the ctypes binding; ``build`` compiles the library in-tree.
 """

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhse.so")
-SOURCES = ["hse_plan.cu", "hse_cells.cu", "hse_real.cu", "hse_fourier.cu", "hse_eval.cu", "hse_noalloc.cu", "hse_server.cu", "hse_batch.cu", "hse_fft64.cu"]
+SOURCES = ["hse_plan.cu", "hse_cells.cu", "hse_real.cu", "hse_fourier.cu", "hse_eval.cu", "hse_noalloc.cu", "hse_server.cu", "hse_batch.cu", "hse_fft64.cu", "hse_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

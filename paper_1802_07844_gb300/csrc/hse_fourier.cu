@@ -1,22 +1,31 @@
 // hse_fourier.cu -- Fourier-space part of the half-space Spectral Ewald method
-// (Alg. 1, steps 5-10; Sec. 5.2).
+// (Alg. 1, steps 5-10; Sec. 5.2).  Grid element type T: double-float (df) for
+// FP64 plans on the transform path of hse_fft64.cu, double for FP64 plans on
+// cuFFT, float for mixed-precision plans.
 //
 //  prep    per source: support start (ix0, iy0, iz0), the 1-D Gaussian factors
 //          of the window (2 xi^2/(pi eta))^{3/2} exp(-2 xi^2 |x - z|^2 / eta)
-//          and the strength of every spread component;
+//          and their derivatives, folded with the strengths into the
+//          per-source arrays of every spread component;
 //  spread  owner-computes tiles: each thread owns one grid point and sums the
 //          windows of the cell-listed sources whose P^3 support covers it.
 //          Everything is accumulated at the SOURCE position: an image's window
 //          is the mirror (k -> 2 Mt - k) of its source's window, so
-//  mirror  forms C1 = A(k) +- A(2Mt - k) and the image-only corrections
-//          C(k) = A(2Mt - k) in place;
-//  FFT     zero-padded by 2 in every direction (cuFFT D2Z, in place);
-//  scale   per wave vector k: T1^ = K^_F C1^ + e3 phi^, T2^ = i k phi^ with
-//          phi^ = E H^R (Cs^ + i k.Cv^ + k.Ct^.k) (the merged harmonic
-//          corrections), stokeslet A^S = -(k^2 I - k k), stresslet A^T,
-//          rotlet A^W = -2 i eps k, tables including exp(-(1-eta)k^2/4xi^2);
-//  IFFT    cuFFT Z2D of the 6 fields T1, T2;
-//  gather  u_F(x) = h^3 sum over the P^3 support of W(x - x_j) (T1 - x3 T2).
+//  mirror  forms C1 = A(k) +- A(2Mt - k) and the image-only correction grid
+//          D(k) = A(2Mt - k) in place.  The wall corrections of every kernel
+//          are one harmonic potential whose source D = Cs W + Cv.grad W -
+//          Ct:grad grad W is spread through window derivatives (ik C^ and
+//          -k k C^ are the transforms of grad C and grad grad C);
+//  FFT     zero-padded by 2 in every direction: the pruned double-float
+//          transforms of hse_fft64.cu, or cuFFT D2Z / R2C, in place;
+//  scale   per wave vector k: T1^ = K^_F C1^ + e3 phi^ and phi^ = E H^R D^
+//          (the merged harmonic corrections), stokeslet A^S = -(k^2 I - k k),
+//          stresslet A^T, rotlet A^W = -2 i eps k, tables including
+//          exp(-(1-eta)k^2/4xi^2), written in place;
+//  IFFT    of the 4 fields T1 (3) and phi (hse_fft64.cu, or cuFFT Z2D / C2R);
+//  gather  u_F(x) = h^3 sum over the P^3 support of W(x - x_j) T1(x_j)
+//          - x3 h^3 sum of grad W(x - x_j) phi(x_j)  (grad phi through the
+//          window's gradient, so no T2 = i k phi^ grids are transformed).
 #include <algorithm>
 #include <type_traits>
 

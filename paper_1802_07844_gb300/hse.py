@@ -85,6 +85,11 @@ class hse_batch_stats(ctypes.Structure):
                 ("graphs_captured", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
 
 
+class hse_pipe_peaks(ctypes.Structure):
+    _fields_ = [("fp64_tflops", ctypes.c_double), ("fp32_tflops", ctypes.c_double), ("df64_tflops", ctypes.c_double),
+                ("n_sm", ctypes.c_int), ("sm_clock_mhz", ctypes.c_double)]
+
+
 class HseError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -99,7 +104,7 @@ _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan
           "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_server_prewarm",
           "hse_server_request_params", "hse_batch_create",
           "hse_batch_eval", "hse_batch_get_stats", "hse_batch_instance_params", "hse_batch_last_error", "hse_batch_destroy",
-          "hse_batch_set_timing", "hse_batch_set_graphs")
+          "hse_batch_set_timing", "hse_batch_set_graphs", "hse_measure_pipe_peaks")
 
 
 def load(path: str = LIB_PATH):
@@ -150,6 +155,7 @@ def load(path: str = LIB_PATH):
     L.hse_cell_list_noalloc.argtypes = [i64, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), dp, dp,
                                         dp, vp]
     L.hse_get_eval_stats.argtypes = [vp, ctypes.POINTER(hse_eval_stats)]
+    L.hse_measure_pipe_peaks.argtypes = [ctypes.POINTER(hse_pipe_peaks)]
     L.hse_status_string.argtypes = [ctypes.c_int]
     L.hse_status_string.restype = ctypes.c_char_p
     L.hse_last_error.argtypes = [vp]
@@ -245,6 +251,13 @@ def hse_get_eval_stats(plan) -> dict:
     return {"n_kernel_launches": st.n_kernel_launches, "n_fft_execs": st.n_fft_execs, "timing": bool(st.timing),
             "stage_ms": dict(zip(STAGE_NAMES, list(st.stage_ms))), "overlapped": bool(st.overlapped),
             "total_ms": st.total_ms}
+
+
+def hse_measure_pipe_peaks() -> dict:
+    """Measured FP64, FP32 and df64 multiply-add throughput (TFLOP/s) of the current device."""
+    p = hse_pipe_peaks()
+    _check(load().hse_measure_pipe_peaks(ctypes.byref(p)))
+    return {name: getattr(p, name) for name, _ in hse_pipe_peaks._fields_}
 
 
 HSE_NOALLOC_MAX_POINTS = 262144

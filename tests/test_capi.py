@@ -56,7 +56,7 @@ def test_library_has_no_oracle_dependency():
 
 # ------------------------------------------------------------ struct layouts
 _STRUCTS = ["hse_params", "hse_eval_stats", "hse_server_config", "hse_request", "hse_server_stats",
-            "hse_instance", "hse_batch_stats"]
+            "hse_instance", "hse_batch_stats", "hse_pipe_peaks"]
 
 
 def _header_fields(text, name):
