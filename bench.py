@@ -48,6 +48,12 @@ WORKLOAD = dict(
     # xi r_c = 4.8, k_inf / xi = pi M / xi = 10.9, P = 18 give 3.0e-11 on 3000 targets (P = 16:
     # 3.2e-10; xi = 90 with the same grid: 7.3e-11); Mt = 320 = 2^6 x 5 is a fast transform size
     xi=87.0, rc=0.0552, P=18, M=302,
+    # FP32 shell from rc64 = 0.032 (hse_plan_set_rc64): the plan's own rule (0.0365) holds the
+    # shell's FP32 rounding to half the real-space truncation ESTIMATE, which for this workload is
+    # ~10x the measured error; measured on 10k targets (RMS error / RMS velocity over all targets):
+    # rc64 0.0365 -> 1.2e-11, 0.030 -> 4.7e-11 (every pair in FP64: 1.2e-11 as well); the bench
+    # line reports the error of the run itself
+    rc64=0.032,
 )
 # mixed-precision (FP32 arithmetic) configuration of the same workload at tolerance 1e-5;
 # parameters checked against the FP64 oracle on a target sample (tests/test_gpu_parity.py):
@@ -292,8 +298,24 @@ def oracle_on_sample(pr, idx):
 
 
 def rel_rms(u, ref) -> float:
-    """Relative RMS error over the checked targets (Sec. 6)."""
+    """Relative RMS error over the checked targets, normalised by the RMS of
+    the reference at the same targets."""
     return float(np.sqrt(np.sum((u - ref) ** 2) / np.sum(ref ** 2)))
+
+
+def rel_rms_full(u, ref, mean_sq_all: float) -> float:
+    """The Sec. 6 error (RMS error over RMS velocity at all targets) estimated
+    from a target sample: the mean square error over the sampled targets
+    divided by the mean square velocity over ALL targets (taken from the
+    evaluated field, whose own error is far below its norm).  The velocity is
+    heavy-tailed (close pairs), so a sample's own norm fluctuates far more than
+    the error does; the error field is not."""
+    return float(np.sqrt(np.mean(np.sum((u - ref) ** 2, axis=0)) / mean_sq_all))
+
+
+def mean_sq(torch, u) -> float:
+    """Mean over targets of |u|^2 of a (3, n) device field (bench-side reduction)."""
+    return float((u * u).sum().item()) / u.shape[1]
 
 
 # ------------------------------------------------------------- GPU legs
@@ -384,7 +406,7 @@ def run_leg(ctx, label, kind, p, tol):
         steps = max(1, min(args.steps, args.leg_steps))
         ms, stages, launches = time_eval(torch, plan, ctx["src"], ctx["st"], ctx["vel"], ctx["flush"], ctx["stream"],
                                          steps, max(3, min(args.warmup, 3)))
-        ctx["samples"][label] = ctx["vel"][:, ctx["idx_t"]].cpu().numpy()
+        ctx["samples"][label] = (ctx["vel"][:, ctx["idx_t"]].cpu().numpy(), mean_sq(torch, ctx["vel"]))
         prm = plan.params
     finally:
         plan.close()
@@ -432,9 +454,9 @@ def run_config_legs(ctx):
         if ctx["check"]:
             idx = np.arange(n) if n <= 1000 else error_sample(n, 4000, seed=1802078440 + 95)
             ref, dt = oracle_on_sample(pr, idx)
-            rec["err_rel_rms"] = rel_rms(u[:, idx], ref)
+            rec["err_rel_rms"] = rel_rms_full(u[:, idx], ref, float(np.mean(np.sum(u ** 2, axis=0))))
             rec["err_sample"] = (f"all {n} targets" if len(idx) == n else f"{len(idx)} seeded targets") + \
-                " against the FP64 direct sum over all sources"
+                " against the FP64 direct sum over all sources (RMS error / RMS velocity over all targets)"
         out[name] = rec
         del src, st, vel
     return out
@@ -461,6 +483,8 @@ def run_ours(args, rank, world, local_rank):
     rows = pr.strengths.shape[0]
     peaks = pipe_peaks(pkg)
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
+    if W.get("rc64"):
+        plan.set_rc64(W["rc64"])
     if args.overlap:
         plan.set_overlap(True)
         plan.set_real_residency(args.real_residency)
@@ -510,7 +534,7 @@ def run_ours(args, rank, world, local_rank):
     ms_step = total_ms / args.steps
     ms_step_max = max_over_ranks(ms_step, world, dev)
     value = whole_job_rate(n, world, ms_step_max)
-    samples["fp64_1e-10"] = vel[:, idx_t].cpu().numpy()
+    samples["fp64_1e-10"] = (vel[:, idx_t].cpu().numpy(), mean_sq(torch, vel))
 
     # end-to-end: pinned host inputs in, velocities out, inside the timed region
     h_src = torch.from_numpy(pr.src).pin_memory()
@@ -538,7 +562,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = whole_job_rate(n, world, max_over_ranks(e_ms, world, dev))
     h2d = h_src.numel() * 8 + h_st.numel() * 8
     d2h = h_vel.numel() * 8
-    samples["e2e"] = h_vel.numpy()[:, idx]
+    samples["e2e"] = (h_vel.numpy()[:, idx], float(np.mean(np.sum(h_vel.numpy() ** 2, axis=0))))
     plan.close()
     del d_src, d_st
 
@@ -603,14 +627,18 @@ def run_ours(args, rank, world, local_rank):
     if check:
         # the oracle on the sampled targets: every leg's error, and the CPU baseline
         ref, t_or = oracle_on_sample(pr, idx)
-        errs = {k: rel_rms(u, ref) for k, u in samples.items()}
+        errs = {k: rel_rms_full(u, ref, msq) for k, (u, msq) in samples.items()}
+        errs_s = {k: rel_rms(u, ref) for k, (u, _) in samples.items()}
         out["err_rel_rms"] = errs["fp64_1e-10"]
+        out["err_rel_rms_sample_norm"] = errs_s["fp64_1e-10"]
         out["err_e2e_rel_rms"] = errs["e2e"]
-        out["err_sample"] = (f"{len(idx)} seeded targets of the {n}, FP64 direct half-space sum over all "
-                             f"{n} sources (relative RMS, Sec. 6)")
+        out["err_sample"] = (f"{len(idx)} seeded targets of the {n}, FP64 direct half-space sum over all {n} sources; "
+                             f"err_rel_rms = RMS error over the sample / RMS velocity over all {n} targets (Sec. 6), "
+                             f"err_rel_rms_sample_norm = the same with the sample's own RMS velocity")
         for k, v in errs.items():
             if k in out:
                 out[k]["err_rel_rms"] = v
+                out[k]["err_rel_rms_sample_norm"] = errs_s[k]
         if rank == 0:
             out["cpu_baseline"] = {"value": len(idx) / t_or / 1e6, "unit": "Mtargets/s", "cores": os.cpu_count(),
                                    "kind": "oracle",
@@ -709,15 +737,17 @@ def _serve_measure(srv, reqs, probs, rng, pkg, torch, args):
         n = pr.src.shape[1]
         idx = np.sort(erng.choice(n, size=min(64, n), replace=False))
         ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src[:, idx])
-        u = srv.result(t)[:, torch.from_numpy(idx).to(a.device)].cpu().numpy()
-        e = rel_rms(u, ref)
+        full = srv.result(t)
+        u = full[:, torch.from_numpy(idx).to(a.device)].cpu().numpy()
+        e = rel_rms_full(u, ref, mean_sq(torch, full))
         errs.append(e / tol)
         over += e > tol
     out["err_64_targets_over_tol_median"] = float(np.median(errs))
     out["err_64_targets_over_tol_max"] = float(np.max(errs))
     out["requests_over_tol_on_64_targets"] = int(over)
-    out["err_64_targets_sample"] = ("64 seeded targets of every request, relative RMS against the FP64 direct sum, "
-                                    "divided by the request's tol (a sample norm of a heavy-tailed field: noisy)")
+    out["err_64_targets_sample"] = ("64 seeded targets of every request against the FP64 direct sum: RMS error "
+                                    "over the 64 targets / RMS velocity over all of the request's targets, divided "
+                                    "by the request's tol")
     # the same request alone (a plan with the server's parameters, read back)
     # against its result in the mix, for a seeded sample of requests
     sel = sorted(erng.choice(len(reqs), size=min(48, len(reqs)), replace=False))
@@ -813,15 +843,15 @@ def run_batch(args, pkg, torch, dev):
         n = p.src.shape[1]
         idx = np.sort(erng.choice(n, size=min(64, n), replace=False))
         ref = oracle.direct(p.mask, p.src, p.strengths, p.src[:, idx])
-        errs64.append(oracle.rel_rms(host[i][:, idx], ref))
+        errs64.append(rel_rms_full(host[i][:, idx], ref, float(np.mean(np.sum(host[i] ** 2, axis=0)))))
     worst = int(np.argmax(errs64))
     p = probs[worst]
     full = oracle.rel_rms(host[worst], oracle.direct(p.mask, p.src, p.strengths))
     rec.update({"err_vs_oracle_max": float(max(errs)),
                 "err_sample": f"{len(errs)} seeded instances, all their targets, FP64 direct sum",
                 "err_64_targets_median": float(np.median(errs64)), "err_64_targets_max": float(max(errs64)),
-                "err_64_targets_sample": "64 seeded targets of every instance (norm of a 64-target sample of a "
-                                         "heavy-tailed field: a noisy error estimate)",
+                "err_64_targets_sample": "64 seeded targets of every instance: RMS error over the 64 targets / RMS "
+                                         "velocity over all of the instance's targets",
                 "err_worst_64_instance_all_targets": full,
                 "instances_over_tol_on_64_targets": int(np.sum(np.array(errs64) > 1e-5))})
     return rec

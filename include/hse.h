@@ -305,7 +305,9 @@ typedef struct {
  * (grids, tables and cell-list work areas) fits the budget next to the work
  * already admitted, checks out a resident plan with the request's parameters
  * (or builds one, evicting idle plans least recently used), and evaluates on
- * its own stream, so work of different requests overlaps on the GPU.  xi is
+ * its own stream, so work of different requests overlaps on the GPU (a
+ * request whose plan is busy with another request waits for it rather than
+ * building a duplicate).  xi is
  * chosen from N and the box (xi = 0.7 (N/V)^(1/3) rounded to a factor-sqrt(2)
  * ladder, so plans are shared between requests); r_c, M and P come from tol.
  * The caller keeps the request's arrays alive until the request completes.

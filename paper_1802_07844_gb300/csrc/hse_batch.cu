@@ -78,6 +78,8 @@ __global__ void k_batch_scatter(const InstDesc* __restrict__ d, int n_inst, int6
 struct Bucket {
   int mask = 0;
   double xi = 0.0;
+  int P = 0, M = 0;    // explicit support width and grid size (0: chosen from tol)
+  double tol = 0.0;    // tolerance the plan was made for
   hse_plan plan = nullptr;
   hse::BatchFFT fft;  // batched transforms, per chunk size met so far
 };
@@ -101,6 +103,17 @@ struct GraphEntry {
 constexpr size_t kMaxGraphs = 64;
 constexpr size_t kTrialInstances = 256;  // instances timed per autotuner trial
 constexpr int kTuneSteps = 4;            // ladder steps tried in each direction
+// support / grid refinement: a candidate (P, M) is kept when it is faster
+// and its result on the trial instances is within kAcceptFrac tol of a plan
+// made for tol / kRefFactor (the library's own tighter evaluation)
+constexpr double kAcceptFrac = 0.4;
+constexpr double kRefFactor = 10.0;
+
+// the autotuner's choice for a (mask, default level) group
+struct Choice {
+  int level = 0;
+  int P = 0, M = 0;  // 0: from tol
+};
 
 double ladder_xi(int k) { return std::exp2(k / 2.0); }
 int ladder_level(int64_t n, const double box[3]) {
@@ -117,7 +130,7 @@ struct hse_batch_s {
   double box[3] = {1, 1, 1};
   size_t budget = 0;
   int autotune = 0;
-  std::map<std::pair<int, int>, int> tuned;  // (mask, default level) -> chosen level
+  std::map<std::pair<int, int>, Choice> tuned;  // (mask, default level) -> chosen level, P, M
   std::vector<Bucket*> buckets;
   InstDesc* d_desc = nullptr;
   InstDesc* h_desc = nullptr;
@@ -138,6 +151,9 @@ struct hse_batch_s {
   uint64_t tick = 0;
   int* d_flag = nullptr;
   int* h_flag = nullptr;
+  double* d_ref = nullptr;     // autotuner: reference result of the trial chunk
+  int64_t ref_cap = 0;
+  double* d_sums = nullptr;    // autotuner: two FP64 sums of the error reduction
   std::string err;
   hse_batch_stats st{};
   std::vector<const Bucket*> inst_bucket;  // group whose plan evaluated each instance of the last call
@@ -192,9 +208,10 @@ hse_status grow(hse_batch b, T** p, int64_t* cap, int64_t need, size_t esz) {
   return HSE_OK;
 }
 
-Bucket* get_bucket(hse_batch b, int mask, double xi, hse_status* st) {
+Bucket* get_bucket(hse_batch b, int mask, double xi, hse_status* st, int P = 0, int M = 0, double tol = 0.0) {
+  if (tol <= 0.0) tol = b->tol;
   for (Bucket* k : b->buckets)
-    if (k->mask == mask && k->xi == xi) return k;
+    if (k->mask == mask && k->xi == xi && k->P == P && k->M == M && k->tol == tol) return k;
   Bucket* k = new (std::nothrow) Bucket();
   if (!k) {
     *st = berr(b, HSE_ERR_OOM, "host allocation");
@@ -202,9 +219,14 @@ Bucket* get_bucket(hse_batch b, int mask, double xi, hse_status* st) {
   }
   k->mask = mask;
   k->xi = xi;
-  *st = hse_plan_create(mask, b->box, xi, 0.0, 0, b->tol, b->precision, &k->plan);
+  k->P = P;
+  k->M = M;
+  k->tol = tol;
+  *st = hse_plan_create(mask, b->box, xi, 0.0, P, tol, b->precision, &k->plan);
+  if (*st == HSE_OK && M > 0) *st = hse_plan_set_grid(k->plan, M);
   if (*st != HSE_OK) {
-    b->err = std::string("plan: ") + hse_last_error(nullptr);
+    b->err = std::string("plan: ") + hse_last_error(k->plan);
+    if (k->plan) hse_plan_destroy(k->plan);
     delete k;
     return nullptr;
   }
@@ -434,16 +456,31 @@ hse_status run_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const Chu
   return HSE_OK;
 }
 
-// Seconds per particle of the group's first instances at ladder level lv (a
-// warm-up pass, then a timed one).  The instances evaluated keep a valid
-// result: every level meets tol.
-hse_status trial(hse_batch b, int mask, int lv, const hse_instance* inst, const std::vector<int>& idx,
-                 cudaStream_t s, double* t, int* covered) {
-  hse_status st = HSE_OK;
-  Bucket* k = get_bucket(b, mask, ladder_xi(lv), &st);
-  if (!k) return st;
+// Sum over the chunk of |res - ref|^2 and |ref|^2 (component-major 3 x n).
+__global__ void k_err_sums(const double* __restrict__ res, const double* __restrict__ ref, int64_t n3,
+                           double* __restrict__ sums) {
+  double e = 0.0, r = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = res[i] - ref[i];
+    e = fma(d, d, e);
+    r = fma(ref[i], ref[i], r);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, off);
+    r += __shfl_xor_sync(0xffffffffu, r, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sums, e);
+    atomicAdd(sums + 1, r);
+  }
+}
+
+// Seconds per particle of bucket k on chunk c (a warm-up pass, then a timed
+// one).  The chunk's instances keep the result, which meets tol for every
+// ladder level; candidates of the (P, M) refinement are re-run by the group's
+// final jobs.
+hse_status trial_bucket(hse_batch b, Bucket* k, const hse_instance* inst, const Chunk& c, cudaStream_t s, double* t) {
   WorkspaceLease lease(k->plan, &b->ws);
-  Chunk c = next_chunk(b, k, inst, idx.data(), (int)std::min<size_t>(idx.size(), kTrialInstances));
   BTRY(prepare_chunk(b, k, c));
   BTRY(run_chunk(b, k, inst, c, s, false));
   BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
@@ -451,8 +488,84 @@ hse_status trial(hse_batch b, int mask, int lv, const hse_instance* inst, const 
   BTRY(run_chunk(b, k, inst, c, s, false));
   BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
   *t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() / (double)c.n_tot;
+  for (int j = 0; j < c.m; ++j) b->inst_bucket[c.idx[j]] = k;
+  return HSE_OK;
+}
+
+hse_status trial(hse_batch b, int mask, int lv, const hse_instance* inst, const std::vector<int>& idx,
+                 cudaStream_t s, double* t, int* covered) {
+  hse_status st = HSE_OK;
+  Bucket* k = get_bucket(b, mask, ladder_xi(lv), &st);
+  if (!k) return st;
+  Chunk c = next_chunk(b, k, inst, idx.data(), (int)std::min<size_t>(idx.size(), kTrialInstances));
+  BTRY(trial_bucket(b, k, inst, c, s, t));
   *covered = c.m;
-  for (int j = 0; j < c.m; ++j) b->inst_bucket[c.idx[j]] = k;  // these keep the trial's result
+  return HSE_OK;
+}
+
+// Relative RMS difference of the last chunk result (d_res) from d_ref.
+hse_status chunk_error(hse_batch b, const Chunk& c, cudaStream_t s, double* err) {
+  BTRY(bcuda(b, cudaMemsetAsync(b->d_sums, 0, 2 * sizeof(double), s), "memset"));
+  const int64_t n3 = 3 * c.n_tot;
+  k_err_sums<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 152 * 8), 256, 0, s>>>(b->d_res, b->d_ref, n3,
+                                                                                     b->d_sums);
+  BTRY(bcuda(b, cudaGetLastError(), "k_err_sums"));
+  double h[2] = {0.0, 0.0};
+  BTRY(bcuda(b, cudaMemcpyAsync(h, b->d_sums, sizeof(h), cudaMemcpyDeviceToHost, s), "copy"));
+  BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
+  *err = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  return HSE_OK;
+}
+
+// Support and grid refinement at the chosen level: the trial instances are
+// evaluated by a plan for tol / kRefFactor (reference), then by candidates
+// with a smaller P and/or a smaller FFT-friendly grid; the fastest candidate
+// within kAcceptFrac tol of the reference is kept.  Seed: the plan's own
+// (P, M) for tol at that xi (Sec. 7: xi r_c and k_inf / xi held, then perturbed).
+hse_status refine_support_grid(hse_batch b, int mask, Choice* ch, double t_default, const hse_instance* inst,
+                               const std::vector<int>& idx, cudaStream_t s) {
+  hse_status st = HSE_OK;
+  const double xi = ladder_xi(ch->level);
+  double tref = b->tol / kRefFactor;
+  if (b->precision == HSE_MIXED && tref < 1e-6) tref = 1e-6;
+  Bucket* def = get_bucket(b, mask, xi, &st);
+  if (!def) return st;
+  Bucket* ref = get_bucket(b, mask, xi, &st, 0, 0, tref);
+  if (!ref) return st;
+  // one chunk for all: the reference plan has the largest grids
+  Chunk c = next_chunk(b, ref, inst, idx.data(), (int)std::min<size_t>(idx.size(), kTrialInstances));
+  double tr = 0.0;
+  BTRY(trial_bucket(b, ref, inst, c, s, &tr));
+  BTRY(grow(b, &b->d_ref, &b->ref_cap, 3 * c.n_tot, sizeof(double)));
+  BTRY(bcuda(b, cudaMemcpyAsync(b->d_ref, b->d_res, sizeof(double) * 3 * c.n_tot, cudaMemcpyDeviceToDevice, s),
+             "copy"));
+  const int P0 = def->plan->prm.P, M0 = def->plan->prm.M;
+  double best = t_default;
+  // the default is timed on the same chunk for a fair comparison
+  BTRY(trial_bucket(b, def, inst, c, s, &best));
+  std::vector<std::pair<int, int>> cand;
+  for (int dP : {0, 2, 4})
+    for (double f : {1.0, 0.9, 0.8}) {
+      const int P = P0 - dP;
+      int M = (int)std::floor(f * M0);
+      if (P < 4 || (dP == 0 && f == 1.0)) continue;
+      M = hse::fft_friendly_size(M + P) - P;
+      if (M > M0) M = M0;
+      cand.emplace_back(P, M);
+    }
+  for (auto& pm : cand) {
+    Bucket* k = get_bucket(b, mask, xi, &st, pm.first, pm.second);
+    if (!k) continue;  // e.g. eta outside (0, 1) for this grid
+    double t = 0.0, err = 0.0;
+    if (trial_bucket(b, k, inst, c, s, &t) != HSE_OK) continue;
+    if (chunk_error(b, c, s, &err) != HSE_OK) continue;
+    if (err <= kAcceptFrac * b->tol && t < best) {
+      best = t;
+      ch->P = pm.first;
+      ch->M = pm.second;
+    }
+  }
+  b->err.clear();
   return HSE_OK;
 }
 
@@ -461,8 +574,8 @@ struct Job {
   Chunk c;
 };
 
-// Pick the group's level (autotuning it once per (mask, default level)) and
-// append its remaining chunks to the job list.
+// Pick the group's level, support and grid (autotuning them once per (mask,
+// default level)) and append its chunks to the job list.
 hse_status plan_group(hse_batch b, int mask, int level, const hse_instance* inst, const std::vector<int>& idx,
                       cudaStream_t s, std::vector<Job>* jobs) {
   const std::pair<int, int> key(mask, level);
@@ -474,12 +587,10 @@ hse_status plan_group(hse_batch b, int mask, int level, const hse_instance* inst
     double best = 0.0, t = 0.0;
     int cov = 0, best_level = level;
     BTRY(trial(b, mask, level, inst, idx, s, &best, &cov));
-    done = std::max(done, cov);
     for (int dir : {-1, +1}) {
       for (int step = 1; step <= kTuneSteps; ++step) {
         const int lv = level + dir * step;
         if (trial(b, mask, lv, inst, idx, s, &t, &cov) != HSE_OK) break;  // e.g. no valid plan there
-        done = std::max(done, cov);
         if (t >= best) break;
         best = t;
         best_level = lv;
@@ -487,11 +598,17 @@ hse_status plan_group(hse_batch b, int mask, int level, const hse_instance* inst
       if (best_level != level) break;  // improved going down: no need to go up
     }
     b->err.clear();
-    b->tuned[key] = best_level;
+    Choice ch;
+    ch.level = best_level;
+    BTRY(refine_support_grid(b, mask, &ch, best, inst, idx, s));
+    b->tuned[key] = ch;
     ++b->st.autotuned_groups;
   }
+  Choice ch;
+  ch.level = level;
   auto it = b->tuned.find(key);
-  Bucket* k = get_bucket(b, mask, ladder_xi(it != b->tuned.end() ? it->second : level), &st);
+  if (it != b->tuned.end()) ch = it->second;
+  Bucket* k = get_bucket(b, mask, ladder_xi(ch.level), &st, ch.P, ch.M);
   if (!k) return st;
   while (done < (int)idx.size()) {
     Chunk c = next_chunk(b, k, inst, idx.data() + done, (int)idx.size() - done);
@@ -528,9 +645,11 @@ extern "C" hse_status hse_batch_create(double tol, int precision, const double b
     b->budget = fr / 2;
   }
   if (cudaMalloc(&b->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&b->h_flag, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_sums, 2 * sizeof(double)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->d_flag);
+    cudaFree(b->d_sums);
     if (b->h_flag) cudaFreeHost(b->h_flag);
     delete b;
     return hse::set_err(nullptr, HSE_ERR_OOM, "hse_batch_create: flag or stream");
@@ -629,6 +748,8 @@ extern "C" hse_status hse_batch_destroy(hse_batch b) {
   cudaFree(b->fft_work);
   hse::free_workspace(b->ws);
   cudaFree(b->d_flag);
+  cudaFree(b->d_sums);
+  cudaFree(b->d_ref);
   cudaFreeHost(b->h_flag);
   delete b;
   return HSE_OK;

@@ -195,12 +195,23 @@ constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub
 // NC plain components (C1, or the paper set), plus with DK != 0 the correction
 // grid D from derivative windows: DK bits 1 (W term), 2 (first derivatives),
 // 4 (second derivatives).
+//
+// Each warp owns a 2 x 4 x 4 sub-tile of the block's 4 x 8 x 8 tile (one
+// grid point per lane) and works alone, with no block-wide barrier: it scans
+// the cell-list rows whose sources can reach its sub-tile, 32 candidates at a
+// time (one per lane: does the support cover the sub-tile, and is every weight
+// on it below the FP32 threshold), compacts the hits into a warp-private list
+// in source order and accumulates them.  Per point the sources are added in
+// cell-row order and, within a row, in sorted order, so the result is
+// deterministic.
+// blocks per SM the spread is compiled for: 4 (64 registers) while the
+// accumulators fit without spilling, else 2
+template <int NC, int DK>
+constexpr int spread_min_blocks() { return NC + (DK != 0) <= 7 && DK != 7 && DK != 6 ? 4 : 2; }
+
 template <typename T, int NC, int DK>
-__global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
-  // per-warp lists of the sources that reach the warp's sub-tile, in source
-  // order (bit 31: the FP32 small-weight record applies)
-  __shared__ int wlist[8][256];
-  __shared__ int wcount[8][8];  // [sub-tile b][warp w]: sources of warp w's batch that reach b
+__global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(SpreadArgs<T> a) {
+  __shared__ int wlist[8][32];  // bit 31: the FP32 small-weight record applies
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int inst = blockIdx.z / a.nz_tiles, ztile = blockIdx.z - inst * a.nz_tiles;
   const int cbase = inst * a.ncells_inst;
@@ -220,83 +231,56 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   for (int c = 0; c < NC; ++c) { acc[c] = (T)0; acc32[c] = 0.f; }
   const bool split = sizeof(T) == 8 && a.prep32 != nullptr;
   const float inv_h = (float)(1.0 / a.h), oxf = (float)a.ox, ozf = (float)a.oz;
-  const float fbx = (float)bx0, fby = (float)by0, fbz = (float)bz0;  // tile origin (no per-source conversions)
-  // positions whose support can reach this tile (one grid step of slack for clamping)
+  const float fsx = (float)sx, fsy = (float)sy, fsz = (float)sz;  // sub-tile origin
+  // positions whose support can reach the sub-tile (one grid step of slack for clamping)
   auto cell_range = [&](int lo_idx, int hi_idx, double o, int d, int& c0, int& c1) {
     double lo = o + (lo_idx - P / 2 - 1) * a.h, hi = o + (hi_idx + P / 2 + 1) * a.h;
     c0 = cell_coord(lo, a.inv_cell[d], a.ncell[d]);
     c1 = cell_coord(hi, a.inv_cell[d], a.ncell[d]);
   };
   int cx0, cx1, cy0, cy1, cz0, cz1;
-  cell_range(bx0, bx0 + kTX - 1, a.ox, 0, cx0, cx1);
-  cell_range(by0, by0 + kTY - 1, a.ox, 1, cy0, cy1);
-  cell_range(bz0, bz0 + kTZ - 1, a.oz, 2, cz0, cz1);
+  cell_range(sx, sx + 1, a.ox, 0, cx0, cx1);
+  cell_range(sy, sy + 3, a.ox, 1, cy0, cy1);
+  cell_range(sz, sz + 3, a.oz, 2, cz0, cz1);
   const int nx = a.ncell[0], ny = a.ncell[1];
   const unsigned below = (1u << lane) - 1;
-  if (bz0 + kTZ <= a.zlo) cz1 = cz0 - 1;  // no support reaches the tile: zeros only
+  int* list = wlist[w];
+  if (sz + 4 <= a.zlo) cz1 = cz0 - 1;  // no support reaches the sub-tile: zeros only
   for (int cz = cz0; cz <= cz1; ++cz)
     for (int cy = cy0; cy <= cy1; ++cy) {
-      int c0 = cbase + (cz * ny + cy) * nx + cx0;
-      int s0 = a.cstart[c0], s1 = a.cstart[c0 + (cx1 - cx0) + 1];
-      for (int base = s0; base < s1; base += 256) {
-        // one thread per source: which of the 8 warp sub-tiles (2 x 4 x 4)
-        // its support reaches, and for which of them every weight is below
-        // the FP32 threshold (distance from the source to the sub-tile, less
-        // half a step for the FP32 position: if even the nearest point has
-        // weight below the threshold, so do all)
-        const int j = base + tid;
-        unsigned wm = 0, smask = 0;
+      const int c0 = cbase + (cz * ny + cy) * nx + cx0;
+      const int s0 = a.cstart[c0], s1 = a.cstart[c0 + (cx1 - cx0) + 1];
+      for (int base = s0; base < s1; base += 32) {
+        // lane = candidate: does its support cover the sub-tile, and if so is
+        // every weight on it below the FP32 threshold (distance from the
+        // source to the sub-tile, less half a step for the FP32 position: if
+        // even the nearest point has weight below the threshold, so do all)
+        const int j = base + lane;
+        bool hit = false, small = false;
         if (j < s1) {
           const int4 sp = a.supp[j];
-          float gx = 0.f, gy = 0.f, gz = 0.f;
-          if (split) {
+          hit = sp.x <= sx + 1 && sp.x + P - 1 >= sx && sp.y <= sy + 3 && sp.y + P - 1 >= sy && sp.z <= sz + 3 &&
+                sp.z + P - 1 >= sz;
+          if (hit && split) {
             const int64_t n = a.n_src;
-            gx = (a.spos32[j] - oxf) * inv_h;
-            gy = (a.spos32[n + j] - oxf) * inv_h;
-            gz = (a.spos32[2 * n + j] - ozf) * inv_h;
-          }
-#pragma unroll
-          for (int b = 0; b < 8; ++b) {
-            const int tx = bx0 + 2 * (b & 1), ty = by0 + 4 * ((b >> 1) & 1), tz = bz0 + 4 * (b >> 2);
-            const bool hb = sp.x <= tx + 1 && sp.x + P - 1 >= tx && sp.y <= ty + 3 && sp.y + P - 1 >= ty &&
-                            sp.z <= tz + 3 && sp.z + P - 1 >= tz;
-            if (hb) {
-              wm |= 1u << b;
-              if (split) {
-                const float fx = fbx + (float)(2 * (b & 1)), fy = fby + (float)(4 * ((b >> 1) & 1));
-                const float fz = fbz + (float)(4 * (b >> 2));
-                const float ex = fmaxf(0.f, fmaxf(fx - gx, gx - (fx + 1.f)) - 0.5f);
-                const float ey = fmaxf(0.f, fmaxf(fy - gy, gy - (fy + 3.f)) - 0.5f);
-                const float ez = fmaxf(0.f, fmaxf(fz - gz, gz - (fz + 3.f)) - 0.5f);
-                if (a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr) smask |= 1u << b;
-              }
-            }
+            const float gx = (a.spos32[j] - oxf) * inv_h, gy = (a.spos32[n + j] - oxf) * inv_h;
+            const float gz = (a.spos32[2 * n + j] - ozf) * inv_h;
+            const float ex = fmaxf(0.f, fmaxf(fsx - gx, gx - (fsx + 1.f)) - 0.5f);
+            const float ey = fmaxf(0.f, fmaxf(fsy - gy, gy - (fsy + 3.f)) - 0.5f);
+            const float ez = fmaxf(0.f, fmaxf(fsz - gz, gz - (fsz + 3.f)) - 0.5f);
+            small = a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr;
           }
         }
-        unsigned mb[8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          mb[b] = __ballot_sync(0xffffffffu, (wm >> b) & 1u);
-          if (lane == 0) wcount[b][w] = __popc(mb[b]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-          if ((wm >> b) & 1u) {
-            int off = 0;
-            for (int ww = 0; ww < w; ++ww) off += wcount[b][ww];
-            wlist[b][off + __popc(mb[b] & below)] = j | (int)(((smask >> b) & 1u) << 31);
-          }
-        int tot = 0;
-        for (int ww = 0; ww < 8; ++ww) tot += wcount[w][ww];
-        __syncthreads();
-        for (int e = 0; e < tot; ++e) {
-          const int entry = wlist[w][e];
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[__popc(m & below)] = j | (int)((unsigned)small << 31);
+        __syncwarp();
+        const int cnt = __popc(m);
+        for (int e = 0; e < cnt; ++e) {
+          const int entry = list[e];
           const int jj = entry & 0x7fffffff;
-          const bool small = entry < 0;
           int4 s = a.supp[jj];
           int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
-          if (small) {
+          if (entry < 0) {
             if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
               const float* o = a.prep32 + (int64_t)jj * a.stride;
               const float wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
@@ -338,7 +322,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
             }
           }
         }
-        __syncthreads();
+        __syncwarp();
       }
     }
   if (px < a.Mt && py < a.Mt && pz >= 0 && pz < 2 * a.Mt) {
@@ -441,6 +425,10 @@ struct ScaleArgs {
   double h;
   const typename Tab<T>::type* tabB;
   const typename Tab<T>::type* tabH;
+  // FP32 spectra: FP64 tables on the corner |kx|, |ky|, kz <= lowK (H, then
+  // B), whose k-points are scaled in FP64; null otherwise
+  const double* tabLow;
+  int lowK;
   int iS, iT, iW, iD;  // first component index of each group (C1 of S, T, W; correction grid), -1 if absent
   int n_inst;
   int64_t istride;     // complex elements between instances of one component
@@ -457,6 +445,56 @@ __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y
 template <typename C, typename T>
 __device__ __forceinline__ C cscale(T s, C z) { return cmk<C>(s * z.x, s * z.y); }
 
+// One k-point of the scaling in the arithmetic R (R = T, or double for the
+// lowest wave numbers of FP32 spectra): reads the inputs at complex element e,
+// writes T1 (and phi) in place.
+template <typename R, typename T>
+__device__ __forceinline__ void scale_point(const ScaleArgs<T>& a, int64_t e, const R k[3], R TH, R TB) {
+  typedef typename Cplx<R>::type C;
+  typedef typename Cplx<T>::type CT;
+  const C zero = cmk<C>((R)0, (R)0);
+  C T1[3] = {zero, zero, zero}, ph = zero;
+  const R k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  auto ld = [&](int c) {
+    const CT v = a.buf[c * a.cstride + e];
+    return cmk<C>((R)v.x, (R)v.y);
+  };
+  if (a.iS >= 0) {  // -(k^2 I - k k) (1 + k^2/4xi^2) E B^R C1
+    C Cv[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
+    C kc = cadd(cadd(cscale(k[0], Cv[0]), cscale(k[1], Cv[1])), cscale(k[2], Cv[2]));
+    for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale(-TB, cadd(cscale(k2, Cv[d]), cscale(-k[d], kc))));
+  }
+  if (a.iT >= 0) {  // -i (1 + k^2/4xi^2) E B^R [(k d + k d + k d) k^2 - 2 k k k] : C
+    C c6[6];
+    for (int m = 0; m < 6; ++m) c6[m] = ld(a.iT + m);
+    const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    C Ck[3], tr = cadd(cadd(c6[0], c6[3]), c6[5]);
+    for (int j = 0; j < 3; ++j) {
+      Ck[j] = zero;
+      for (int m = 0; m < 3; ++m) Ck[j] = cadd(Ck[j], cscale(k[m], c6[sidx[j][m]]));
+    }
+    C kCk = cadd(cadd(cscale(k[0], Ck[0]), cscale(k[1], Ck[1])), cscale(k[2], Ck[2]));
+    for (int j = 0; j < 3; ++j) {
+      C v = cadd(cscale(k2, cadd(cscale((R)2, Ck[j]), cscale(k[j], tr))), cscale((R)(-2) * k[j], kCk));
+      T1[j] = cadd(T1[j], cscale(-TB, cmul_i(v)));
+    }
+  }
+  if (a.iW >= 0) {  // -2 i E H^R (C x k)
+    C Cv[3] = {ld(a.iW), ld(a.iW + 1), ld(a.iW + 2)};
+    C cr[3] = {cadd(cscale(k[2], Cv[1]), cscale(-k[1], Cv[2])), cadd(cscale(k[0], Cv[2]), cscale(-k[2], Cv[0])),
+               cadd(cscale(k[1], Cv[0]), cscale(-k[0], Cv[1]))};
+    for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale((R)(-2) * TH, cmul_i(cr[d])));
+  }
+  // harmonic potential of the wall corrections: phi^ = E H^R D^ (D spread
+  // through window derivatives); T1 gains e3 phi, grad(phi) is gathered
+  if (a.iD >= 0) {
+    ph = cscale(TH, ld(a.iD));
+    T1[2] = cadd(T1[2], ph);
+  }
+  for (int d = 0; d < 3; ++d) a.buf[d * a.cstride + e] = cmk<CT>((T)T1[d].x, (T)T1[d].y);
+  if (a.nout == 4) a.buf[3 * a.cstride + e] = cmk<CT>((T)ph.x, (T)ph.y);
+}
+
 template <typename T>
 __global__ void k_scale(ScaleArgs<T> a) {
   typedef typename Cplx<T>::type C;
@@ -472,50 +510,30 @@ __global__ void k_scale(ScaleArgs<T> a) {
     int iy = (int)(t % Ny), ix = (int)(t / Ny);
     // element of component 0 of this instance
     const int64_t e = inst * a.istride + ix * a.xstride + (int64_t)iy * Nzh + jz;
-    C T1[3] = {zero, zero, zero}, ph = zero;
-    if (ix != Mt && iy != Mt && jz != 2 * Mt) {  // Nyquist modes are dropped
-      int wx = ix <= Mt ? ix : ix - Nx, wy = iy <= Mt ? iy : iy - Ny;
-      T k[3] = {dkx * wx, dkx * wy, dkz * jz};
-      T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-      int64_t ti = ((int64_t)abs(wx) * (Mt + 1) + abs(wy)) * Nzh + jz;
-      T TH = (T)a.tabH[ti];
-      T TB = a.tabB ? (T)a.tabB[ti] : (T)0;
-      auto ld = [&](int c) { return a.buf[c * a.cstride + e]; };
-      if (a.iS >= 0) {  // -(k^2 I - k k) (1 + k^2/4xi^2) E B^R C1
-        C Cv[3] = {ld(a.iS), ld(a.iS + 1), ld(a.iS + 2)};
-        C kc = cadd(cadd(cscale(k[0], Cv[0]), cscale(k[1], Cv[1])), cscale(k[2], Cv[2]));
-        for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale(-TB, cadd(cscale(k2, Cv[d]), cscale(-k[d], kc))));
-      }
-      if (a.iT >= 0) {  // -i (1 + k^2/4xi^2) E B^R [(k d + k d + k d) k^2 - 2 k k k] : C
-        C c6[6];
-        for (int m = 0; m < 6; ++m) c6[m] = ld(a.iT + m);
-        const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-        C Ck[3], tr = cadd(cadd(c6[0], c6[3]), c6[5]);
-        for (int j = 0; j < 3; ++j) {
-          Ck[j] = zero;
-          for (int m = 0; m < 3; ++m) Ck[j] = cadd(Ck[j], cscale(k[m], c6[sidx[j][m]]));
-        }
-        C kCk = cadd(cadd(cscale(k[0], Ck[0]), cscale(k[1], Ck[1])), cscale(k[2], Ck[2]));
-        for (int j = 0; j < 3; ++j) {
-          C v = cadd(cscale(k2, cadd(cscale((T)2, Ck[j]), cscale(k[j], tr))), cscale((T)(-2) * k[j], kCk));
-          T1[j] = cadd(T1[j], cscale(-TB, cmul_i(v)));
-        }
-      }
-      if (a.iW >= 0) {  // -2 i E H^R (C x k)
-        C Cv[3] = {ld(a.iW), ld(a.iW + 1), ld(a.iW + 2)};
-        C cr[3] = {cadd(cscale(k[2], Cv[1]), cscale(-k[1], Cv[2])), cadd(cscale(k[0], Cv[2]), cscale(-k[2], Cv[0])),
-                   cadd(cscale(k[1], Cv[0]), cscale(-k[0], Cv[1]))};
-        for (int d = 0; d < 3; ++d) T1[d] = cadd(T1[d], cscale((T)(-2) * TH, cmul_i(cr[d])));
-      }
-      // harmonic potential of the wall corrections: phi^ = E H^R D^ (D spread
-      // through window derivatives); T1 gains e3 phi, grad(phi) is gathered
-      if (a.iD >= 0) {
-        ph = cscale(TH, ld(a.iD));
-        T1[2] = cadd(T1[2], ph);
+    if (ix == Mt || iy == Mt || jz == 2 * Mt) {  // Nyquist modes are dropped
+      for (int d = 0; d < a.nout; ++d) a.buf[d * a.cstride + e] = zero;
+      continue;
+    }
+    const int wx = ix <= Mt ? ix : ix - Nx, wy = iy <= Mt ? iy : iy - Ny;
+    const int ax = abs(wx), ay = abs(wy);
+    if constexpr (std::is_same<T, float>::value) {
+      const int K = a.lowK;
+      if (a.tabLow && ax <= K && ay <= K && jz <= K) {
+        // lowest wave numbers in FP64, with FP64 tables: the projections
+        // k^2 C - k (k.C) of the smallest k are differences of nearly equal
+        // terms, and these modes carry the far field
+        const int nlow = (K + 1) * (K + 1) * (K + 1), li = (ax * (K + 1) + ay) * (K + 1) + jz;
+        const double dx = 2.0 * kPi / (Nx * a.h), dz = 2.0 * kPi / (4.0 * Mt * a.h);
+        const double k[3] = {dx * wx, dx * wy, dz * jz};
+        scale_point<double, T>(a, e, k, a.tabLow[li], a.tabB ? a.tabLow[nlow + li] : 0.0);
+        continue;
       }
     }
-    for (int d = 0; d < 3; ++d) a.buf[d * a.cstride + e] = T1[d];
-    if (a.nout == 4) a.buf[3 * a.cstride + e] = ph;
+    const T k[3] = {dkx * wx, dkx * wy, dkz * jz};
+    const int64_t ti = ((int64_t)ax * (Mt + 1) + ay) * Nzh + jz;
+    const T TH = (T)a.tabH[ti];
+    const T TB = a.tabB ? (T)a.tabB[ti] : (T)0;
+    scale_point<T, T>(a, e, k, TH, TB);
   }
 }
 
@@ -794,6 +812,8 @@ static hse_status launch_scale(hse_plan p, void* spec, int64_t cstride, int n_in
   sa.h = q.h;
   sa.tabB = reinterpret_cast<const typename Tab<S>::type*>(p->tabB);
   sa.tabH = reinterpret_cast<const typename Tab<S>::type*>(p->tabH);
+  sa.tabLow = std::is_same<S, float>::value ? p->tabLow : nullptr;
+  sa.lowK = kLowK < q.Mt ? kLowK : q.Mt;
   int k = 0;
   sa.iS = sa.iT = sa.iW = sa.iD = -1;
   if (q.kernel_mask & HSE_STOKESLET) { sa.iS = k; k += 3; }

@@ -20,6 +20,7 @@ constexpr double kWindowC = 0.95;  // Alg. 1 step 4
 constexpr int kMaxP = 32;          // support width limit (one warp lane per point)
 constexpr int kCellReach = 2;      // real-space cells per r_c (cell side >= r_c / kCellReach)
 constexpr int kMaxComp = 25;       // most spread components of any kernel combination
+constexpr int kLowK = 8;           // mixed precision: k-points with |k_d| <= kLowK grid wave numbers scaled in FP64
 
 // Layout of the FFT buffers: padded grid Nx x Ny x Nz = 2Mt x 2Mt x 4Mt, in-place
 // R2C: real rows of pitch 2 (Nz/2 + 1) doubles, complex rows of Nz/2 + 1.
@@ -108,6 +109,10 @@ struct hse_plan_s {
   double* spec = nullptr;  // n_fft_in buffers (float elements with HSE_MIXED)
   double* tabB = nullptr;  // s E B^R / Np on the octant (Mt+1)(Mt+1)(2Mt+1) (float with HSE_MIXED)
   double* tabH = nullptr;  // E H^R / Np on the octant (float with HSE_MIXED)
+  // HSE_MIXED: FP64 copies of both tables on the corner |kx|, |ky|, kz <=
+  // kLowK of the octant (H then B, (kLowK+1)^3 each), for the FP64 scaling of
+  // the lowest wave numbers
+  double* tabLow = nullptr;
   // zero-padded transforms split into a 2-D (y,z) transform over the Mt planes
   // that hold data (fwd2d R2C / inv2d C2R) and a 1-D transform along x over
   // all (y, kz) lines (fftx, Z2Z both directions)
@@ -153,6 +158,8 @@ CompSet product_components(int mask);
 hse_status plan_estimate(int mask, const double box[3], double xi, double tol, int precision, size_t* bytes,
                          int* M_out, int* P_out);
 CompSet paper_components(int mask);
+// smallest n' >= n whose padded transform lengths 2n', 4n' are fast sizes
+int fft_friendly_size(int n);
 
 // ----------------------------------------------------------- stage launchers
 hse_status launch_validate(hse_plan p, int64_t n, const double* pos, int is_src, cudaStream_t s);

@@ -196,6 +196,15 @@ __global__ void k_tab_to_float(const double* __restrict__ t, float* __restrict__
     f[e] = (float)t[e];
 }
 
+// the corner |wx|, |wy|, kz <= K of an octant table (Mt+1)(Mt+1)(2Mt+1), in FP64
+__global__ void k_tab_corner(const double* __restrict__ t, int Mt, int K, double* __restrict__ out) {
+  const int n = (K + 1) * (K + 1) * (K + 1);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int kz = e % (K + 1), wy = (e / (K + 1)) % (K + 1), wx = e / ((K + 1) * (K + 1));
+    out[e] = t ? t[((int64_t)wx * (Mt + 1) + wy) * (2 * Mt + 1) + kz] : 0.0;
+  }
+}
+
 static int grid_blocks(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b > 152 * 64) b = 152 * 64;
@@ -275,6 +284,8 @@ void free_grids(hse_plan p) {
   cudaFree(p->spec);
   cudaFree(p->tabB);
   cudaFree(p->tabH);
+  cudaFree(p->tabLow);
+  p->tabLow = nullptr;
   p->fft_work = nullptr;
   p->fft_work_bytes = 0;
   p->spec = p->tabB = p->tabH = nullptr;
@@ -363,6 +374,13 @@ hse_status build_grids(hse_plan p) {
   HSE_TRY(build_table(p, 0, p->tabH));
   if (p->tabB) HSE_TRY(build_table(p, 1, p->tabB));
   if (mixed) {  // the tables are built in FP64 and rounded to FP32 once
+    // except for their low-wave-number corner, kept in FP64 for the scaling
+    const int K = kLowK < q.Mt ? kLowK : q.Mt;
+    const int nlow = (K + 1) * (K + 1) * (K + 1);
+    HSE_CUDA(p, cudaMalloc(&p->tabLow, 2 * nlow * sizeof(double)));
+    k_tab_corner<<<grid_blocks(nlow, 256), 256>>>(p->tabH, q.Mt, K, p->tabLow);
+    k_tab_corner<<<grid_blocks(nlow, 256), 256>>>(p->tabB, q.Mt, K, p->tabLow + nlow);
+    HSE_CUDA(p, cudaGetLastError());
     for (double** tp : {&p->tabH, &p->tabB}) {
       if (!*tp) continue;
       float* f = nullptr;
@@ -450,6 +468,8 @@ static int fft_friendly(int n) {
       if (m >= n && m % 4 == 0 && m < best) best = (int)m;
   return best;
 }
+
+int fft_friendly_size(int n) { return fft_friendly(n); }
 
 static hse_status choose_params(hse_plan p, double xi, double rc, int P, double tol) {
   hse_params& q = p->prm;

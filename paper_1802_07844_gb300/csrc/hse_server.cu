@@ -3,8 +3,8 @@
 // Requests queue on submission.  Each worker slot (one thread, one
 // non-blocking CUDA stream) takes the oldest queued request whose plan is
 // resident and idle, or whose new plan fits the device-memory budget after
-// evicting idle plans (least recently used); requests that do not fit wait
-// while later ones that do are admitted.  Plans are checked out exclusively
+// evicting idle plans (least recently used); requests that do not fit, or
+// whose plan is busy with another request, wait while later ones are admitted.  Plans are checked out exclusively
 // (a plan is not re-entrant) and stay resident between requests with equal
 // (kernel mask, precision, tol, box, xi).  Waits on the host are bounded.
 #include <algorithm>
@@ -94,14 +94,22 @@ struct hse_server_s {
     for (auto it = queue.begin(); it != queue.end(); ++it) {
       Record& r = rec[*it];
       int idle = -1;
+      bool in_use = false;
       for (size_t i = 0; i < pool.size(); ++i)
-        if (!pool[i].busy && pool[i].plan && pool[i].key == r.key) { idle = (int)i; break; }
+        if (pool[i].key == r.key) {
+          if (!pool[i].busy && pool[i].plan) { idle = (int)i; break; }
+          in_use = true;
+        }
       if (idle >= 0) {
         *ticket = *it;
         *pool_idx = idle;
         queue.erase(it);
         return true;
       }
+      // its plan exists but is evaluating (or being built): it is free again
+      // within one evaluation, far sooner than a duplicate could be built, so
+      // the request waits for it while later requests are admitted
+      if (in_use) continue;
       // a new plan: evict idle plans (LRU) until it fits, if that can succeed
       size_t idle_bytes = 0;
       for (auto& e : pool)

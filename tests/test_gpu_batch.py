@@ -114,13 +114,31 @@ def test_batch_autotune_meets_tolerance(pkg):
     probs = _instances(30, 1802078453, [KERNEL_S, KERNEL_T], lo=500, hi=3000)
     items = _to_dev(probs)
     b = pkg.hse.Batch(1e-8, 0, autotune=True)
+    ref = pkg.hse.Batch(1e-8, 0)
     try:
         outs = b.eval(items)
-        outs2 = b.eval(items)  # tuned levels are reused
+        used = [b.instance_params(i) for i in range(len(items))]
+        outs2 = b.eval(items)  # tuned levels, supports and grids are reused
+        used2 = [b.instance_params(i) for i in range(len(items))]
         stats = b.stats()
+        ref.eval(items)
+        default = [ref.instance_params(i) for i in range(len(items))]
     finally:
         b.close()
+        ref.close()
     assert stats["autotuned_groups"] >= 2
+    assert used == used2
+    # the tuner only ever narrows the support or coarsens the grid of the
+    # plan it starts from at the chosen xi (same tol)
+    for u in used:
+        plan = pkg.Plan(u["kernel_mask"], (1.0, 1.0, 1.0), xi=u["xi"], rc=0.0, P=0, tol=1e-8)
+        try:
+            assert u["P"] <= plan.params["P"] and u["M"] <= plan.params["M"]
+            assert u["rc"] == plan.params["rc"]
+        finally:
+            plan.close()
+    print("autotuned (xi, P, M):", sorted({(u["xi"], u["P"], u["M"]) for u in used}),
+          "defaults:", sorted({(d["xi"], d["P"], d["M"]) for d in default}))
     for i, (pr, u, u2) in enumerate(zip(probs, outs, outs2)):
         u, u2 = u.cpu().numpy(), u2.cpu().numpy()
         assert _oracle_check(pr, u, 1e-8, seed=i) < 1e-8

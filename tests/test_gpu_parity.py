@@ -293,11 +293,17 @@ def test_bench_workload_parity():
     W = bench.WORKLOAD
     pr = problem(W["mask"], W["n"], 1.0, W["dist"], W["index"])
     plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
+    if W.get("rc64"):
+        plan.set_rc64(W["rc64"])
     u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
     plan.close()
     idx = np.sort(np.random.default_rng(1802078442).choice(W["n"], 2000, replace=False))
     ref = oracle.direct(W["mask"], pr.src, pr.strengths, pr.src[:, idx])
     assert oracle.rel_rms(u[:, idx], ref) < W["tol"]
+    # Sec. 6: RMS error (sample) over the RMS velocity of all targets, with margin
+    err = bench.rel_rms_full(u[:, idx], ref, float(np.mean(np.sum(u ** 2, axis=0))))
+    print(f"bench workload: relative RMS error {err:.3e} (tol {W['tol']:g})")
+    assert err < W["tol"] / 2
 
 
 # ------------------------------------------------- mixed precision (FP32 path)
