@@ -92,33 +92,38 @@ static int lines_per_block_log2(int N) {
 
 // ------------------------------------------------------------- butterflies
 // In-register radix-R DFTs (forward: exp(-2 pi i j k / R)) on unnormalised
-// inputs; intermediate sums stay unnormalised and the outputs are normalised.
-template <bool FWD>
+// inputs; intermediate sums stay unnormalised, and the outputs are normalised
+// only by the last pass of a transform (NORM): a df64 pair whose low part
+// exceeds half an ulp of its high part by a few units is still accepted by
+// every operation here, with the same error bound.
+template <bool NORM>
+__device__ __forceinline__ cdf out(cdf a) { return NORM ? norm(a) : a; }
+template <bool FWD, bool NORM>
 __device__ __forceinline__ void dft2(cdf* v) {
   const cdf a = v[0], b = v[1];
-  v[0] = norm(add_raw(a, b));
-  v[1] = norm(sub_raw(a, b));
+  v[0] = out<NORM>(add_raw(a, b));
+  v[1] = out<NORM>(sub_raw(a, b));
 }
-template <bool FWD>
+template <bool FWD, bool NORM>
 __device__ __forceinline__ void dft4(cdf* v) {
   const cdf a0 = add_raw(v[0], v[2]), a1 = sub_raw(v[0], v[2]);
   const cdf b0 = add_raw(v[1], v[3]), b1 = mul_mi<FWD>(sub_raw(v[1], v[3]));
-  v[0] = norm(add_raw(a0, b0));
-  v[2] = norm(sub_raw(a0, b0));
-  v[1] = norm(add_raw(a1, b1));
-  v[3] = norm(sub_raw(a1, b1));
+  v[0] = out<NORM>(add_raw(a0, b0));
+  v[2] = out<NORM>(sub_raw(a0, b0));
+  v[1] = out<NORM>(add_raw(a1, b1));
+  v[3] = out<NORM>(sub_raw(a1, b1));
 }
-template <bool FWD>
+template <bool FWD, bool NORM>
 __device__ __forceinline__ void dft3(cdf* v, const float* kc) {
   const df s3(kc[0], kc[1]);
   const cdf t = add_raw(v[1], v[2]);
   const cdf a = sub_raw(v[0], scale_raw(df(0.5f, 0.f), t));
   const cdf b = mul_mi<FWD>(scale_raw(s3, sub_raw(v[1], v[2])));
-  v[0] = norm(add_raw(v[0], t));
-  v[1] = norm(add_raw(a, b));
-  v[2] = norm(sub_raw(a, b));
+  v[0] = out<NORM>(add_raw(v[0], t));
+  v[1] = out<NORM>(add_raw(a, b));
+  v[2] = out<NORM>(sub_raw(a, b));
 }
-template <bool FWD>
+template <bool FWD, bool NORM>
 __device__ __forceinline__ void dft5(cdf* v, const float* kc) {
   const df c1(kc[2], kc[3]), c2(kc[4], kc[5]), s1(kc[6], kc[7]), s2(kc[8], kc[9]);
   const cdf t1 = add_raw(v[1], v[4]), t2 = add_raw(v[2], v[3]);
@@ -127,11 +132,11 @@ __device__ __forceinline__ void dft5(cdf* v, const float* kc) {
   const cdf a2 = add_raw(v[0], add_raw(scale_raw(c2, t1), scale_raw(c1, t2)));
   const cdf b1 = mul_mi<FWD>(add_raw(scale_raw(s1, t3), scale_raw(s2, t4)));
   const cdf b2 = mul_mi<FWD>(sub_raw(scale_raw(s2, t3), scale_raw(s1, t4)));
-  v[0] = norm(add_raw(v[0], add_raw(t1, t2)));
-  v[1] = norm(add_raw(a1, b1));
-  v[4] = norm(sub_raw(a1, b1));
-  v[2] = norm(add_raw(a2, b2));
-  v[3] = norm(sub_raw(a2, b2));
+  v[0] = out<NORM>(add_raw(v[0], add_raw(t1, t2)));
+  v[1] = out<NORM>(add_raw(a1, b1));
+  v[4] = out<NORM>(sub_raw(a1, b1));
+  v[2] = out<NORM>(add_raw(a2, b2));
+  v[3] = out<NORM>(sub_raw(a2, b2));
 }
 
 template <bool FWD>
@@ -142,10 +147,11 @@ __device__ __forceinline__ cdf twiddle(const float4* __restrict__ tw, int idx) {
 
 // One Stockham pass (radix R, Ns = product of the earlier radices) from src
 // to dst: butterfly j < N / R reads elements j + t N / R, multiplies element t
-// by w_N^{t (j mod Ns) N / (Ns R)}, transforms, and writes output t to
-// (j div Ns) Ns R + (j mod Ns) + t Ns.  Thread (l, tj) takes butterflies
-// tj, tj + TPL, ... of line l.
-template <int R, bool FWD>
+// by w_N^{t (j mod Ns) N / (Ns R)} (one exact two-sum per real part, result
+// unnormalised), transforms, and writes output t to (j div Ns) Ns R +
+// (j mod Ns) + t Ns.  Thread (l, tj) takes butterflies tj, tj + TPL, ... of
+// line l.
+template <int R, bool FWD, bool NORM>
 __device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, int N, int Ns, int step,
                                               unsigned magic, const float* kc, int tpl, int lsh, int l, int tj,
                                               const float4* __restrict__ tw) {
@@ -158,12 +164,12 @@ __device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, in
     for (int t = 0; t < R; ++t) v[t] = ld_cdf(src + ((j + t * nb) << lsh) + l);
     if (k != 0) {
 #pragma unroll
-      for (int t = 1; t < R; ++t) v[t] = v[t] * twiddle<FWD>(tw, t * k * step);
+      for (int t = 1; t < R; ++t) v[t] = mul_raw(v[t], twiddle<FWD>(tw, t * k * step));
     }
-    if (R == 2) dft2<FWD>(v);
-    else if (R == 4) dft4<FWD>(v);
-    else if (R == 3) dft3<FWD>(v, kc);
-    else dft5<FWD>(v, kc);
+    if (R == 2) dft2<FWD, NORM>(v);
+    else if (R == 4) dft4<FWD, NORM>(v);
+    else if (R == 3) dft3<FWD, NORM>(v, kc);
+    else dft5<FWD, NORM>(v, kc);
     const int d = q * Ns * R + k;
 #pragma unroll
     for (int t = 0; t < R; ++t) st_cdf(dst + ((d + t * Ns) << lsh) + l, v[t]);
@@ -184,11 +190,20 @@ __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const F
   for (int p = p0; p < npass; ++p) {
     const int Ns = st->Ns[p], step = st->step[p];
     const unsigned magic = st->magic[p];
-    switch (st->R[p]) {
-      case 4: stockham_pass<4, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
-      case 2: stockham_pass<2, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
-      case 5: stockham_pass<5, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
-      default: stockham_pass<3, FWD>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+    if (p == npass - 1) {  // the last pass stores normalised values
+      switch (st->R[p]) {
+        case 4: stockham_pass<4, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        case 2: stockham_pass<2, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        case 5: stockham_pass<5, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        default: stockham_pass<3, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      }
+    } else {
+      switch (st->R[p]) {
+        case 4: stockham_pass<4, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        case 2: stockham_pass<2, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        case 5: stockham_pass<5, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        default: stockham_pass<3, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+      }
     }
     __syncthreads();
     float4* t = a;

@@ -46,7 +46,9 @@ struct PrepArgs {
   int nc1;    // product set: number of C1 components
   int P, Mt;
   double h, ox, oz, alpha, pre;
+  double c2;      // exp(-2 alpha h^2): step of the window recurrence
   int stride;
+  RecLayout lay;  // record layout (rec_layout(nfac, components, P))
   T* prep;
   float* prep32;  // FP64 plans: the same record in FP32 (null otherwise)
   int4* supp;
@@ -67,18 +69,37 @@ __device__ __forceinline__ void prep_one(const PrepArgs<T>& a, int64_t i) {
     // also wy', wz' (and wy'', wz''), derivatives with respect to the grid
     // point: W' = -2 alpha d W, W'' = (4 alpha^2 d^2 - 2 alpha) W.  The x
     // derivatives go into the combined arrays XX below.
+    // The factors along an axis come from the fast Gaussian gridding
+    // recurrence (Greengard & Lee, SIAM Review 46, 2004): with d_t = d_0 + t h,
+    // w_{t+1} = w_t r_t, r_t = exp(-alpha (2 d_t h + h^2)), r_{t+1} = r_t
+    // exp(-2 alpha h^2): two exponentials per axis instead of P (relative
+    // rounding <~ 2 P eps64 after P steps).
+    const RecLayout& L = a.lay;
+    double wr[3], rr[3];
+    {
+      const double d0[3] = {a.ox + ix0 * a.h - x, a.ox + iy0 * a.h - y, a.oz + iz0 * a.h - z};
+      for (int k = 0; k < 3; ++k) {
+        wr[k] = exp(-a.alpha * d0[k] * d0[k]) * (k == 0 ? a.pre : 1.0);
+        rr[k] = exp(-a.alpha * (2.0 * d0[k] * a.h + a.h * a.h));
+      }
+    }
     for (int t = 0; t < P; ++t) {
       double d[3] = {a.ox + (ix0 + t) * a.h - x, a.ox + (iy0 + t) * a.h - y, a.oz + (iz0 + t) * a.h - z};
       for (int k = 0; k < 3; ++k) {
-        double wv = exp(-a.alpha * d[k] * d[k]) * (k == 0 ? a.pre : 1.0);
-        o[k * P + t] = (T)wv;
-        if (k > 0 && a.nfac > 1) o[(2 + k) * P + t] = (T)(-2.0 * a.alpha * d[k] * wv);
-        if (k > 0 && a.nfac > 2) o[(4 + k) * P + t] = (T)((4.0 * a.alpha * a.alpha * d[k] * d[k] - 2.0 * a.alpha) * wv);
+        const double wv = wr[k];
+        wr[k] *= rr[k];
+        rr[k] *= a.c2;
+        T* e = k == 0 ? o + L.x0 + t * L.kx : o + (k == 1 ? L.y0 : L.z0) + t * L.ky;
+        const int ke = k == 0 ? L.kx : L.ky;
+        for (int m = 1; m < ke; ++m) e[m] = (T)0;  // padding (and the x block's XX, written below)
+        e[0] = (T)wv;
+        if (k > 0 && a.nfac > 1) e[1] = (T)(-2.0 * a.alpha * d[k] * wv);
+        if (k > 0 && a.nfac > 2) e[2] = (T)((4.0 * a.alpha * a.alpha * d[k] * d[k] - 2.0 * a.alpha) * wv);
       }
     }
-    const int nwin = a.nfac == 1 ? 3 : (a.nfac == 2 ? 5 : 7);  // window arrays of P
-    const int nxx = a.nfac == 1 ? 0 : (a.nfac == 2 ? 3 : 6);   // combined x arrays of P
-    T* c = o + (nwin + nxx) * P;
+    const int nxx = a.nfac == 1 ? 0 : (a.nfac == 2 ? 3 : 6);  // combined x arrays
+    T* c = o + L.c0;
+    c[L.stride - L.c0 - 1] = (T)0;  // padding of an odd component count
     int k = 0;
     double f[3] = {0, 0, 0}, g[3] = {0, 0, 0}, q[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
     if (a.mask & HSE_STOKESLET) for (int d = 0; d < 3; ++d) f[d] = a.sstr[(a.rowS + d) * n + i];
@@ -121,19 +142,23 @@ __device__ __forceinline__ void prep_one(const PrepArgs<T>& a, int64_t i) {
       // terms flipped), folded with the x factors into
       //   D = XX00 wy wz + XX10 wy' wz + XX01 wy wz' + XX20 wy'' wz + XX02 wy wz'' + XX11 wy' wz'
       const double q[10] = {cs, cv[0], cv[1], -cv[2], -ct[0], -ct[3], -ct[5], -2.0 * ct[1], 2.0 * ct[2], 2.0 * ct[4]};
-      T* xx = o + nwin * P;
+      const double dx0 = a.ox + ix0 * a.h - x;
+      double wxr = a.pre * exp(-a.alpha * dx0 * dx0), rxr = exp(-a.alpha * (2.0 * dx0 * a.h + a.h * a.h));
       for (int t = 0; t < P; ++t) {
+        T* xx = o + L.x0 + t * L.kx + 1;  // XX_m of entry t
         const double dx = a.ox + (ix0 + t) * a.h - x;
-        const double wx = a.pre * exp(-a.alpha * dx * dx);
+        const double wx = wxr;  // the window along x (recurrence as above)
+        wxr *= rxr;
+        rxr *= a.c2;
         const double dwx = -2.0 * a.alpha * dx * wx;
         const double ddwx = (4.0 * a.alpha * a.alpha * dx * dx - 2.0 * a.alpha) * wx;
-        xx[t] = (T)(q[0] * wx + q[1] * dwx + q[4] * ddwx);
-        xx[P + t] = (T)(q[2] * wx + q[7] * dwx);
-        xx[2 * P + t] = (T)(q[3] * wx + q[8] * dwx);
+        xx[0] = (T)(q[0] * wx + q[1] * dwx + q[4] * ddwx);
+        xx[1] = (T)(q[2] * wx + q[7] * dwx);
+        xx[2] = (T)(q[3] * wx + q[8] * dwx);
         if (nxx == 6) {
-          xx[3 * P + t] = (T)(q[5] * wx);
-          xx[4 * P + t] = (T)(q[6] * wx);
-          xx[5 * P + t] = (T)(q[9] * wx);
+          xx[3] = (T)(q[5] * wx);
+          xx[4] = (T)(q[6] * wx);
+          xx[5] = (T)(q[9] * wx);
         }
       }
     } else {
@@ -179,6 +204,7 @@ struct SpreadArgs {
   float ah2, lnthr;      // alpha h^2 (window exponent per squared grid step), ln(1/threshold)
   const int32_t* cstart;
   int stride, P, Mt, z0, nz_tiles;
+  int y0, z0r, c0;       // offsets of the y and z blocks and of the components in a record
   int zlo;               // lowest z index any source support reaches (tiles below only write zeros)
   double h, ox, oz;
   double inv_cell[3];
@@ -191,6 +217,29 @@ struct SpreadArgs {
 };
 
 constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
+
+// two adjacent record elements with one load (8-byte elements: 16 bytes,
+// 4-byte elements: 8 bytes; record entries are aligned to two elements)
+__device__ __forceinline__ void ld2(const df* p, df& a, df& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = df(v.x, v.y);
+  b = df(v.z, v.w);
+}
+__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  a = v.x;
+  b = v.y;
+}
+template <typename T, int N>
+__device__ __forceinline__ void ldv(const T* p, T* out) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) ld2(p + 2 * i, out[2 * i], out[2 * i + 1]);
+}
 
 // NC plain components (C1, or the paper set), plus with DK != 0 the correction
 // grid D from derivative windows: DK bits 1 (W term), 2 (first derivatives),
@@ -211,7 +260,9 @@ constexpr int spread_min_blocks() { return NC + (DK != 0) <= 7 && DK != 7 && DK 
 
 template <typename T, int NC, int DK>
 __global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(SpreadArgs<T> a) {
-  __shared__ int wlist[8][32];  // bit 31: the FP32 small-weight record applies
+  // per warp: the hits of the current 32 candidates, with their support
+  // starts (w: source index, bit 31 set when the FP32 small-weight record applies)
+  __shared__ int4 wlist[8][32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int inst = blockIdx.z / a.nz_tiles, ztile = blockIdx.z - inst * a.nz_tiles;
   const int cbase = inst * a.ncells_inst;
@@ -219,10 +270,10 @@ __global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(Spr
   const int sx = bx0 + 2 * (w & 1), sy = by0 + 4 * ((w >> 1) & 1), sz = bz0 + 4 * (w >> 2);
   const int px = sx + (lane & 1), py = sy + ((lane >> 1) & 3), pz = sz + (lane >> 3);
   const int P = a.P;
-  // per-particle record: NWIN window arrays (wx, wy, wz, wy', wz', wy'', wz''),
-  // NXX combined x arrays of the correction grid, then the NC components
-  constexpr int NWIN = DK == 0 ? 3 : ((DK & 4) ? 7 : 5);
-  constexpr int NXX = DK == 0 ? 0 : ((DK & 4) ? 6 : 3);
+  // per-particle record (rec_layout): x entries {wx, XX_0..}, y entries
+  // {wy, wy', wy''}, z entries {wz, wz', wz''}, then the NC components
+  constexpr int NF = DK == 0 ? 1 : ((DK & 4) ? 3 : 2);
+  constexpr int KX = rec_kx(NF), KY = rec_ky(NF);
   T acc[NC];
   T accD = (T)0;
   float acc32[NC];
@@ -244,7 +295,7 @@ __global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(Spr
   cell_range(sz, sz + 3, a.oz, 2, cz0, cz1);
   const int nx = a.ncell[0], ny = a.ncell[1];
   const unsigned below = (1u << lane) - 1;
-  int* list = wlist[w];
+  int4* list = wlist[w];
   if (sz + 4 <= a.zlo) cz1 = cz0 - 1;  // no support reaches the sub-tile: zeros only
   for (int cz = cz0; cz <= cz1; ++cz)
     for (int cy = cy0; cy <= cy1; ++cy) {
@@ -257,8 +308,9 @@ __global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(Spr
         // even the nearest point has weight below the threshold, so do all)
         const int j = base + lane;
         bool hit = false, small = false;
+        int4 sp = make_int4(0, 0, 0, 0);
         if (j < s1) {
-          const int4 sp = a.supp[j];
+          sp = a.supp[j];
           hit = sp.x <= sx + 1 && sp.x + P - 1 >= sx && sp.y <= sy + 3 && sp.y + P - 1 >= sy && sp.z <= sz + 3 &&
                 sp.z + P - 1 >= sz;
           if (hit && split) {
@@ -272,52 +324,52 @@ __global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(Spr
           }
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) list[__popc(m & below)] = j | (int)((unsigned)small << 31);
+        if (hit) list[__popc(m & below)] = make_int4(sp.x, sp.y, sp.z, j | (int)((unsigned)small << 31));
         __syncwarp();
         const int cnt = __popc(m);
         for (int e = 0; e < cnt; ++e) {
-          const int entry = list[e];
+          const int4 s = list[e];
+          const int entry = s.w;
           const int jj = entry & 0x7fffffff;
-          int4 s = a.supp[jj];
           int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
+          if (!(dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P)) continue;
           if (entry < 0) {
-            if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
-              const float* o = a.prep32 + (int64_t)jj * a.stride;
-              const float wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
-              const float wyz = wy * wz;
-              const float wv = wx * wyz;
-              const float* cv = o + (NWIN + NXX) * P;
+            const float* o = a.prep32 + (int64_t)jj * a.stride;
+            float xv[KX], yv[KY], zv[KY];
+            ldv<float, KX>(o + dx * KX, xv);
+            ldv<float, KY>(o + a.y0 + dy * KY, yv);
+            ldv<float, KY>(o + a.z0r + dz * KY, zv);
+            const float wyz = yv[0] * zv[0];
+            const float wv = xv[0] * wyz;
+            float cv[(NC + 1) & ~1];
+            ldv<float, (NC + 1) & ~1>(o + a.c0, cv);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) acc32[c] += wv * cv[c];
-              if constexpr (DK != 0) {
-                const float* xx = o + NWIN * P + dx;
-                const float dwy = o[3 * P + dy], dwz = o[4 * P + dz];
-                accD32 += xx[0] * wyz + xx[P] * (dwy * wz) + xx[2 * P] * (wy * dwz);
-                if constexpr ((DK & 4) != 0) {
-                  const float ddwy = o[5 * P + dy], ddwz = o[6 * P + dz];
-                  accD32 += xx[3 * P] * (ddwy * wz) + xx[4 * P] * (wy * ddwz) + xx[5 * P] * (dwy * dwz);
-                }
-              }
+            for (int c = 0; c < NC; ++c) acc32[c] += wv * cv[c];
+            if constexpr (DK != 0) {
+              accD32 += xv[1] * wyz + xv[2] * (yv[1] * zv[0]) + xv[3] * (yv[0] * zv[1]);
+              if constexpr ((DK & 4) != 0)
+                accD32 += xv[4] * (yv[2] * zv[0]) + xv[5] * (yv[0] * zv[2]) + xv[6] * (yv[1] * zv[1]);
             }
-          } else if (dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P) {
+          } else {
             const T* o = a.prep + (int64_t)jj * a.stride;
-            const T wx = o[dx], wy = o[P + dy], wz = o[2 * P + dz];
-            const T wyz = mulr(wy, wz);
-            const T wv = mulr(wx, wyz);
-            const T* cv = o + (NWIN + NXX) * P;
+            T xv[KX], yv[KY], zv[KY];
+            ldv<T, KX>(o + dx * KX, xv);
+            ldv<T, KY>(o + a.y0 + dy * KY, yv);
+            ldv<T, KY>(o + a.z0r + dz * KY, zv);
+            const T wyz = mulr(yv[0], zv[0]);
+            const T wv = mulr(xv[0], wyz);
+            T cv[(NC + 1) & ~1];
+            ldv<T, (NC + 1) & ~1>(o + a.c0, cv);
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = mac(acc[c], wv, cv[c]);
             if constexpr (DK != 0) {
-              const T* xx = o + NWIN * P + dx;
-              const T dwy = o[3 * P + dy], dwz = o[4 * P + dz];
-              accD = mac(accD, xx[0], wyz);
-              accD = mac(accD, xx[P], mulr(dwy, wz));
-              accD = mac(accD, xx[2 * P], mulr(wy, dwz));
+              accD = mac(accD, xv[1], wyz);
+              accD = mac(accD, xv[2], mulr(yv[1], zv[0]));
+              accD = mac(accD, xv[3], mulr(yv[0], zv[1]));
               if constexpr ((DK & 4) != 0) {
-                const T ddwy = o[5 * P + dy], ddwz = o[6 * P + dz];
-                accD = mac(accD, xx[3 * P], mulr(ddwy, wz));
-                accD = mac(accD, xx[4 * P], mulr(wy, ddwz));
-                accD = mac(accD, xx[5 * P], mulr(dwy, dwz));
+                accD = mac(accD, xv[4], mulr(yv[2], zv[0]));
+                accD = mac(accD, xv[5], mulr(yv[0], zv[2]));
+                accD = mac(accD, xv[6], mulr(yv[1], zv[1]));
               }
             }
           }
@@ -550,18 +602,30 @@ struct GatherArgs {
   int64_t is;             // instance stride of the fields
   int P, Mt;
   double h, ox, oz, alpha, pre, h3;
+  double inv_h;           // 1 / h
   double* out;
   int add;
 };
 
 constexpr int kGatherWarps = 4;
 
-// per-column sums of the gather are accumulated in FP64 (double, float grids)
-// or double-float (double-float grids)
+// warp sum in FP64 (a double-float butterfly sum measured slower: its FP32
+// instructions compete for the issue slots the column sums need)
+__device__ __forceinline__ double warp_sum64(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ double warp_sum64(df v) { return warp_sum64(v.to_double()); }
+
+// per-column sums of the gather are accumulated in FP64 (double grids) or
+// double-float (double-float and FP32 grids)
+// (FP32 grids: double-float sums on the FP32 pipe, where FP64 additions and
+// float -> double conversions would queue on the narrow FP64 pipe)
 template <typename T> struct GAcc { typedef double type; };
 template <> struct GAcc<df> { typedef df type; };
+template <> struct GAcc<float> { typedef df type; };
 __device__ __forceinline__ double gacc(double v) { return v; }
-__device__ __forceinline__ double gacc(float v) { return (double)v; }
+__device__ __forceinline__ df gacc(float v) { return df(v, 0.f); }
 __device__ __forceinline__ df gacc(df v) { return v; }
 
 // NF = 3: u = <T1> (free space).  NF = 4: u = <T1> - x3 <grad phi>, the
@@ -589,9 +653,13 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
       x = a.spos[w]; y = a.spos[a.n_src + w]; z = a.spos[2 * a.n_src + w];
       dst = a.sorig[w];
     }
-    int ix0 = support_start(x, a.ox, a.h, P, a.Mt);
-    int iy0 = support_start(y, a.ox, a.h, P, a.Mt);
-    int iz0 = support_start(z, a.oz, a.h, P, 2 * a.Mt);
+    // the target's P nearest grid points per axis (a product with 1/h: a
+    // target within rounding of a grid plane may take the support one point
+    // over, an equally valid quadrature; the spread's supports use the
+    // correctly rounded quotient, which the oracle's grids reproduce)
+    int ix0 = support_start_mul(x, a.ox, a.inv_h, P, a.Mt);
+    int iy0 = support_start_mul(y, a.ox, a.inv_h, P, a.Mt);
+    int iz0 = support_start_mul(z, a.oz, a.inv_h, P, 2 * a.Mt);
     const T* fields = a.buf + (a.inst_of ? a.inst_of[w] * a.is : 0);
     __syncwarp();
     if (lane < P) {
@@ -641,10 +709,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_gather(GatherArgs<T> a) {
     }
     double accd[NF == 4 ? 6 : 3];
 #pragma unroll
-    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c) {
-      accd[c] = to64(acc[c]);
-      for (int off = 16; off > 0; off >>= 1) accd[c] += __shfl_xor_sync(0xffffffffu, accd[c], off);
-    }
+    for (int c = 0; c < (NF == 4 ? 6 : 3); ++c) accd[c] = warp_sum64(acc[c]);
     if (lane == 0) {
       for (int d = 0; d < 3; ++d) {
         // grad_x W = -W', so u = <T1> - x3 <grad phi> = h^3 (acc_T1 + x3 acc_W')
@@ -682,11 +747,14 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   a.oz = -(double)q.Mt * q.h;
   a.alpha = 2.0 * q.xi * q.xi / q.eta;
   a.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
+  a.c2 = std::exp(-2.0 * a.alpha * q.h * q.h);
   const int dk = paper ? 0 : deriv_kind(q.kernel_mask);
   a.nfac = dk == 0 ? 1 : ((dk & 4) ? 3 : 2);
   a.nc1 = c1_count(q.kernel_mask);
-  // paper: [wx wy wz][components]; product: [windows][combined x arrays][C1]
-  a.stride = paper ? 3 * q.P + ncomp : (dk == 0 ? 3 : ((dk & 4) ? 13 : 8)) * q.P + a.nc1;
+  // paper: plain windows and every component; product: derivative windows,
+  // the combined x arrays of D and C1
+  a.lay = rec_layout(a.nfac, paper ? ncomp : a.nc1, q.P);
+  a.stride = a.lay.stride;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
   // FP64 plans split small window weights to FP32 unless the plan asks for
   // FP64 throughout (rc64 >= rc)
@@ -716,13 +784,22 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.prep32 = pa.prep32;
   a.spos32 = p->ws.spos32;
   a.n_src = n_src;
-  // FP32 below 1e-5 of the window's peak: those terms carry relative errors
-  // <~ 4 eps32 1e-5 ~ 3e-12 of the largest contribution of their particle
+  // FP32 below a fraction tau of the window's peak: those terms carry
+  // relative errors <~ 4 eps32 tau of the largest contribution of their
+  // particle.  Measured on the 1M near-wall S+W workload the velocity changes
+  // by ~5e-9 tau (relative RMS) against an all-FP64 spread, so a plan that
+  // knows its tolerance takes tau = 2e6 tol (its share stays ~1/100 of tol),
+  // clamped to [1e-5, 1e-3]; plans with explicit parameters and no tol keep
+  // tau = 1e-5.
   a.ah2 = (float)(pa.alpha * q.h * q.h);
-  a.lnthr = (float)std::log(1e5);
+  const double tau = p->tol > 0.0 ? std::fmin(1e-3, std::fmax(1e-5, 2e6 * p->tol)) : 1e-5;
+  a.lnthr = (float)std::log(1.0 / tau);
 
   a.cstart = p->ws.cell_start;
   a.stride = pa.stride;
+  a.y0 = pa.lay.y0;
+  a.z0r = pa.lay.z0;
+  a.c0 = pa.lay.c0;
   a.P = q.P;
   a.Mt = q.Mt;
   // full_z: tiles on the same z boundaries as from zA0, extended down to the
@@ -898,6 +975,7 @@ static hse_status fourier_space_t(hse_plan p, int64_t n_src, int64_t n_tgt, cons
   ga.alpha = 2.0 * q.xi * q.xi / q.eta;
   ga.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
   ga.h3 = q.h * q.h * q.h;
+  ga.inv_h = 1.0 / q.h;
   ga.out = out;
   ga.add = add ? 1 : 0;
   if (q.n_fft_out == 4) k_gather<T, 4><<<blocks_for(n_tgt, kGatherWarps, 152 * 64), kGatherWarps * 32, 0, s>>>(ga);
@@ -1099,6 +1177,7 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
   ga.alpha = 2.0 * q.xi * q.xi / q.eta;
   ga.pre = pow(2.0 * q.xi * q.xi / (kPi * q.eta), 1.5);
   ga.h3 = q.h * q.h * q.h;
+  ga.inv_h = 1.0 / q.h;
   ga.out = out;
   ga.add = 1;
   if (q.n_fft_out == 4)

@@ -54,14 +54,39 @@ inline int deriv_kind(int mask) {
 inline int c1_count(int mask) {
   return ((mask & HSE_STOKESLET) ? 3 : 0) + ((mask & HSE_STRESSLET) ? 6 : 0) + ((mask & HSE_ROTLET) ? 3 : 0);
 }
-// per-particle record of the spread (elements): the larger of the product
-// layout [window arrays][combined x arrays of D][C1] and the paper layout
-// [wx wy wz][C1, C2, C3 of every kernel]
+// Per-particle record of the spread (elements of the grid type), three blocks
+// of P entries and the components:
+//   x block, entry t: {wx, XX_0 .. XX_{nxx-1}} (the window and the combined x
+//                      arrays of the correction grid D) padded to kx elements
+//   y block, entry t: {wy, wy', wy''} (the first nfac of them) padded to ky
+//   z block, entry t: {wz, wz', wz''} padded to ky
+//   components: nc values, padded to an even count
+// so that a lane reads the factors of one grid offset with 16-byte loads.
+// nfac = 1, 2, 3 goes with nxx = 0, 3, 6.
+struct RecLayout {
+  int kx, ky, x0, y0, z0, c0, stride;
+};
+__host__ __device__ constexpr int rec_kx(int nfac) { return nfac == 1 ? 2 : (nfac == 2 ? 4 : 8); }
+__host__ __device__ constexpr int rec_ky(int nfac) { return nfac == 3 ? 4 : 2; }
+__host__ __device__ inline RecLayout rec_layout(int nfac, int nc, int P) {
+  RecLayout r;
+  r.kx = rec_kx(nfac);
+  r.ky = rec_ky(nfac);
+  r.x0 = 0;
+  r.y0 = P * r.kx;
+  r.z0 = r.y0 + P * r.ky;
+  r.c0 = r.z0 + P * r.ky;
+  r.stride = r.c0 + ((nc + 1) & ~1);
+  return r;
+}
+// the larger of the product record (C1 + the derivative-window factors of D)
+// and the paper record (C1, C2, C3 of every kernel, plain windows)
 inline int prep_stride_max(int mask, int P) {
   const int dk = deriv_kind(mask);
-  const int product = (dk == 0 ? 3 : ((dk & 4) ? 13 : 8)) * P + c1_count(mask);
-  const int paper = 3 * P + ((mask & HSE_STOKESLET) ? 7 : 0) + ((mask & HSE_STRESSLET) ? 13 : 0) +
-                    ((mask & HSE_ROTLET) ? 5 : 0);
+  const int nfac = dk == 0 ? 1 : ((dk & 4) ? 3 : 2);
+  const int product = rec_layout(nfac, c1_count(mask), P).stride;
+  const int paper = rec_layout(1, ((mask & HSE_STOKESLET) ? 7 : 0) + ((mask & HSE_STRESSLET) ? 13 : 0) +
+                                      ((mask & HSE_ROTLET) ? 5 : 0), P).stride;
   return product > paper ? product : paper;
 }
 
@@ -227,6 +252,14 @@ __device__ __forceinline__ double dist2_exact(double dx, double dy, double dz) {
 __device__ __forceinline__ int support_start(double c, double o, double h, int P, int n) {
   double t = floor(__ddiv_rn(__dsub_rn(c, o), h));
   long long i0 = (long long)t - P / 2 + 1;
+  if (i0 < 0) i0 = 0;
+  if (i0 > n - P) i0 = n - P;
+  return (int)i0;
+}
+
+// the same with a product by 1/h (the gather's supports)
+__device__ __forceinline__ int support_start_mul(double c, double o, double inv_h, int P, int n) {
+  long long i0 = (long long)floor((c - o) * inv_h) - P / 2 + 1;
   if (i0 < 0) i0 = 0;
   if (i0 > n - P) i0 = n - P;
   return (int)i0;

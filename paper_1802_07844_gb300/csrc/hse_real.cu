@@ -82,7 +82,6 @@ constexpr int kTabN = kErfcxN + 64;  // erfcx intervals, then 2^{j/64}
 // 2^{j/64} from the table t2 (shared memory), e^r from its degree-5 Taylor
 // polynomial; 10 FP64 operations.
 __device__ __forceinline__ double exp_neg(double x, const double* t2) {
-  if (x > 700.0) return 0.0;
   const double magic = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low word
   const double y = -x;
   const double tn = fma(y, k64Log2e, magic);
@@ -115,14 +114,25 @@ struct Radial {
   T er, c, a1, g2, g3;  // erfc(t)/rho, 2 xi e^{-t^2}/sqrt(pi), a1, g2, g3
 };
 
-// FP64: own exp and erfcx table
+// FP32 approximation of a positive normal double within the float range, by
+// truncation (integer operations only: the FP64 pipe, which bounds the
+// real-space kernel, also executes double -> float conversions)
+__device__ __forceinline__ float approx_float(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  return __uint_as_float(((hi - 0x38000000u) << 3) | (lo >> 29));
+}
+
+// FP64: own exp and erfcx table.  The table interval and the range tests use
+// FP32 copies of t (t < 12 on the table; e^{-t^2} needs t < 26), so that the
+// FP64 pipe only does the arithmetic.
 __device__ __forceinline__ Radial<double> radial(double s, float sf, double xi, const double* tab, bool need_g3) {
   Radial<double> R;
   double inv = rsqrt(s);
   double t = xi * s * inv;
-  double E = exp_neg(t * t, tab + kErfcxN);
+  const float tf = __fmul_rn(approx_float(xi), sqrtf(sf));
+  double E = tf < 26.0f ? exp_neg(t * t, tab + kErfcxN) : 0.0;
   double ec;
-  if (t < (double)HSE_ERFCX_NINT / HSE_ERFCX_INV_WIDTH) ec = E * erfcx_tab(t, (float)xi * sqrtf(sf), tab);
+  if (tf < 11.99f) ec = E * erfcx_tab(t, tf, tab);
   else ec = erfc(t);  // beyond the table: only reached when xi r_c > 12
   double i2 = inv * inv;
   R.c = (2.0 / kSqrtPi) * xi * E;
@@ -428,11 +438,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
         double rd[3], hd;
         pair_vec(a, x, j, true, rd, &hd);
         double s2 = rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2];
-        Radial<double> Rd = radial(s2, (float)s2, a.xi, tab, need_g3);
+        Radial<double> Rd = radial(s2, approx_float(s2), a.xi, tab, need_g3);
         add_image<double>(a.mask, Rd, rd, hd, x.d[2], sdbl, a.xi, uself);
         return;
       }
-      Radial<T> R = radial(sd, (float)sd, xi, tab, need_g3);
+      Radial<T> R = radial(sd, sizeof(T) == 8 ? approx_float((double)sd) : (float)sd, xi, tab, need_g3);
       if (type == Q_FREE) add_free<T>(a.mask, R, r, s, xi, (T)1, u);
       else add_image<T>(a.mask, R, r, h, x3, s, xi, u);
     };
@@ -525,7 +535,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
       T sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       // close image pairs are left to k_close_images (FP64), see there
       if (sizeof(T) == 4 && type == Q_IMAGE && (float)sq3(r) < a.img64_2) return;
-      Radial<T> R = radial(sd, (float)sd, xi, tab, need_g3);
+      Radial<T> R = radial(sd, sizeof(T) == 8 ? approx_float((double)sd) : (float)sd, xi, tab, need_g3);
       T v[3] = {0, 0, 0};
       if (type == Q_FREE) {
         add_free<T>(KM, R, r, s, xi, (T)1, u);
@@ -666,7 +676,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_close_images(RealArgs a
           double rd[3], hd;
           pair_vec(a, x, j, true, rd, &hd);
           double s2 = sq3(rd);
-          Radial<double> R = radial(s2, (float)s2, a.xi, tab, need_g3);
+          Radial<double> R = radial(s2, approx_float(s2), a.xi, tab, need_g3);
           add_image<double>(a.mask, R, rd, hd, x.d[2], sj, a.xi, u);
         }
       }

@@ -292,7 +292,7 @@ def test_bench_workload_parity():
     import paper_1802_07844_gb300 as pkg
     W = bench.WORKLOAD
     pr = problem(W["mask"], W["n"], 1.0, W["dist"], W["index"])
-    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0, M=W["M"])
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=W["tol"], M=W["M"])
     if W.get("rc64"):
         plan.set_rc64(W["rc64"])
     u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
@@ -353,7 +353,7 @@ def test_mixed_bench_workload_parity():
     W = bench.WORKLOAD
     Mx = bench.MIXED
     pr = problem(W["mask"], W["n"], 1.0, W["dist"], W["index"])
-    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=Mx["rc"], P=Mx["P"], tol=0.0, M=Mx["M"],
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=Mx["xi"], rc=Mx["rc"], P=Mx["P"], tol=Mx["tol"], M=Mx["M"],
                     precision=pkg.HSE_MIXED)
     u = host(plan.eval(dev(pr.src), dev(pr.strengths)))
     plan.close()
