@@ -879,6 +879,8 @@ def run_real_only(args, pkg, torch, dev, W, pr):
                         precision=pkg.HSE_MIXED)
     else:
         plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=W["xi"], rc=W["rc"], P=W["P"], tol=0.0)
+        if W.get("rc64"):
+            plan.set_rc64(W["rc64"])
     src = torch.from_numpy(pr.src).to(dev)
     st = torch.from_numpy(pr.strengths).to(dev)
     for _ in range(args.warmup):
@@ -908,7 +910,8 @@ def run_fourier_small(args, pkg, torch, dev, W):
     if args.n:
         F["n"] = args.n
     pr = replica_problem(0, F["n"])
-    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=F["xi"], rc=F["rc"], P=F["P"], tol=0.0, M=F["M"],
+    plan = pkg.Plan(W["mask"], (1.0, 1.0, 1.0), xi=F["xi"], rc=F["rc"], P=F["P"],
+                    tol=MIXED["tol"] if args.mixed else W["tol"], M=F["M"],
                     precision=pkg.HSE_MIXED if args.mixed else pkg.HSE_FP64)
     src = torch.from_numpy(pr.src).to(dev)
     st = torch.from_numpy(pr.strengths).to(dev)

@@ -153,7 +153,8 @@ struct hse_batch_s {
   int* h_flag = nullptr;
   double* d_ref = nullptr;     // autotuner: reference result of the trial chunk
   int64_t ref_cap = 0;
-  double* d_sums = nullptr;    // autotuner: two FP64 sums of the error reduction
+  double* d_sums = nullptr;    // autotuner: two FP64 sums per instance of the error reduction
+  int64_t sums_cap = 0;
   std::string err;
   hse_batch_stats st{};
   std::vector<const Bucket*> inst_bucket;  // group whose plan evaluated each instance of the last call
@@ -456,22 +457,28 @@ hse_status run_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const Chu
   return HSE_OK;
 }
 
-// Sum over the chunk of |res - ref|^2 and |ref|^2 (component-major 3 x n).
-__global__ void k_err_sums(const double* __restrict__ res, const double* __restrict__ ref, int64_t n3,
-                           double* __restrict__ sums) {
-  double e = 0.0, r = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const double d = res[i] - ref[i];
-    e = fma(d, d, e);
-    r = fma(ref[i], ref[i], r);
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, off);
-    r += __shfl_xor_sync(0xffffffffu, r, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(sums, e);
-    atomicAdd(sums + 1, r);
+// Per instance of the chunk: the sums over its particles of |res - ref|^2
+// and |ref|^2 (results component-major 3 x n_tot, instance i at d[i].off).
+__global__ void k_err_sums(const InstDesc* __restrict__ d, int n_inst, int64_t n_tot, const double* __restrict__ res,
+                           const double* __restrict__ ref, double* __restrict__ sums) {
+  for (int i = blockIdx.y; i < n_inst; i += gridDim.y) {
+    const InstDesc D = d[i];
+    double e = 0.0, r = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < D.n; l += (int64_t)gridDim.x * blockDim.x)
+      for (int c = 0; c < 3; ++c) {
+        const int64_t k = c * n_tot + D.off + l;
+        const double df = res[k] - ref[k];
+        e = fma(df, df, e);
+        r = fma(ref[k], ref[k], r);
+      }
+    for (int off = 16; off > 0; off >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, off);
+      r += __shfl_xor_sync(0xffffffffu, r, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(sums + 2 * i, e);
+      atomicAdd(sums + 2 * i + 1, r);
+    }
   }
 }
 
@@ -503,24 +510,33 @@ hse_status trial(hse_batch b, int mask, int lv, const hse_instance* inst, const 
   return HSE_OK;
 }
 
-// Relative RMS difference of the last chunk result (d_res) from d_ref.
+// The largest relative RMS difference, over the chunk's instances, of the
+// last chunk result (d_res) from d_ref (the descriptors of the chunk are the
+// last ones uploaded).
 hse_status chunk_error(hse_batch b, const Chunk& c, cudaStream_t s, double* err) {
-  BTRY(bcuda(b, cudaMemsetAsync(b->d_sums, 0, 2 * sizeof(double), s), "memset"));
-  const int64_t n3 = 3 * c.n_tot;
-  k_err_sums<<<(unsigned)std::min<int64_t>((n3 + 255) / 256, 152 * 8), 256, 0, s>>>(b->d_res, b->d_ref, n3,
-                                                                                     b->d_sums);
+  BTRY(grow(b, &b->d_sums, &b->sums_cap, 2 * (int64_t)c.m, sizeof(double)));
+  BTRY(bcuda(b, cudaMemsetAsync(b->d_sums, 0, 2 * sizeof(double) * c.m, s), "memset"));
+  int64_t nmax = 1;
+  for (int i = 0; i < c.m; ++i) nmax = std::max<int64_t>(nmax, b->h_desc[i].n);
+  dim3 grid((unsigned)std::min<int64_t>((nmax + 255) / 256, 64), (unsigned)std::min(c.m, 65535));
+  k_err_sums<<<grid, 256, 0, s>>>(b->d_desc, c.m, c.n_tot, b->d_res, b->d_ref, b->d_sums);
   BTRY(bcuda(b, cudaGetLastError(), "k_err_sums"));
-  double h[2] = {0.0, 0.0};
-  BTRY(bcuda(b, cudaMemcpyAsync(h, b->d_sums, sizeof(h), cudaMemcpyDeviceToHost, s), "copy"));
+  std::vector<double> h(2 * (size_t)c.m);
+  BTRY(bcuda(b, cudaMemcpyAsync(h.data(), b->d_sums, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s),
+             "copy"));
   BTRY(bcuda(b, cudaStreamSynchronize(s), "sync"));
-  *err = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  double worst = 0.0;
+  for (int i = 0; i < c.m; ++i)
+    if (h[2 * i + 1] > 0.0) worst = std::max(worst, std::sqrt(h[2 * i] / h[2 * i + 1]));
+  *err = worst;
   return HSE_OK;
 }
 
 // Support and grid refinement at the chosen level: the trial instances are
 // evaluated by a plan for tol / kRefFactor (reference), then by candidates
 // with a smaller P and/or a smaller FFT-friendly grid; the fastest candidate
-// within kAcceptFrac tol of the reference is kept.  Seed: the plan's own
+// whose result is within kAcceptFrac tol of the reference for EVERY trial
+// instance (relative RMS over the instance's own particles) is kept.  Seed: the plan's own
 // (P, M) for tol at that xi (Sec. 7: xi r_c and k_inf / xi held, then perturbed).
 hse_status refine_support_grid(hse_batch b, int mask, Choice* ch, double t_default, const hse_instance* inst,
                                const std::vector<int>& idx, cudaStream_t s) {
@@ -645,7 +661,7 @@ extern "C" hse_status hse_batch_create(double tol, int precision, const double b
     b->budget = fr / 2;
   }
   if (cudaMalloc(&b->d_flag, sizeof(int)) != cudaSuccess || cudaMallocHost(&b->h_flag, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&b->d_sums, 2 * sizeof(double)) != cudaSuccess ||
+
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->d_flag);

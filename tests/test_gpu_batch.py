@@ -145,6 +145,25 @@ def test_batch_autotune_meets_tolerance(pkg):
         assert _oracle_check(pr, u2, 1e-8, seed=i) < 1e-8
 
 
+def test_batch_autotune_mixed_meets_tolerance_per_instance(pkg):
+    """Mixed precision at tol 1e-5 with the (xi, P, M) tuner: every instance,
+    small and large, meets tol on its own (the tuner accepts a candidate only
+    when it is within 0.4 tol of the tighter reference for every trial
+    instance, not only in aggregate over the chunk)."""
+    probs = _instances(40, 1802078455, [KERNEL_S, KERNEL_T], lo=200, hi=20000, index=75)
+    items = _to_dev(probs)
+    b = pkg.hse.Batch(1e-5, pkg.HSE_MIXED, autotune=True)
+    try:
+        outs = b.eval(items)
+        used = [b.instance_params(i) for i in range(len(items))]
+    finally:
+        b.close()
+    errs = [_oracle_check(pr, u.cpu().numpy(), 1e-5) for pr, u in zip(probs, outs)]
+    print("mixed autotuned (xi, P, M):", sorted({(u["xi"], u["P"], u["M"]) for u in used}),
+          "worst error / tol", max(errs) / 1e-5)
+    assert max(errs) < 1e-5
+
+
 def test_batch_edge_cases(pkg):
     b = pkg.hse.Batch(1e-8, 0)
     try:
