@@ -773,9 +773,11 @@ def _serve_measure(srv, reqs, probs, rng, pkg, torch, args):
         for i in sel:
             m, tol, a, b = reqs[i]
             used = srv.request_params(tickets[i])
-            key = (m, tol, used["xi"])
+            key = (m, tol, used["xi"], used["fft"])
             if key not in plans:
                 plans[key] = pkg.Plan(m, (1.0, 1.0, 1.0), xi=used["xi"], rc=0.0, P=0, tol=tol, precision=prec(tol))
+                if plans[key].params["fft"] != used["fft"]:
+                    plans[key].set_fft(used["fft"])  # the server's double-float Fourier part of mixed plans
             alone = plans[key].eval(a, b)
             worst = max(worst, rel_rms(srv.result(tickets[i]).cpu().numpy(), alone.cpu().numpy()) / tol)
     finally:

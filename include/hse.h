@@ -72,10 +72,15 @@ enum { HSE_STOKESLET = 1, HSE_STRESSLET = 2, HSE_ROTLET = 4, HSE_FREE_SPACE = 8 
  *   targets, the self term and the tables' construction (rounded to FP32). */
 enum { HSE_FP64 = 0, HSE_MIXED = 1 };
 /* transforms of the Fourier part (hse_plan_set_fft): HSE_FFT_DF64 runs the
- * zero-padded FFTs and the scaling of HSE_FP64 plans in double-float (~48-bit)
- * arithmetic on the FP32 pipe, HSE_FFT_CUFFT in cuFFT double (HSE_MIXED plans:
- * cuFFT single); HSE_FFT_AUTO picks HSE_FFT_DF64 for HSE_FP64 plans with
- * tol >= 1e-12 or explicit parameters, HSE_FFT_CUFFT otherwise. */
+ * grids, zero-padded FFTs and scaling in double-float (~48-bit) arithmetic on
+ * the FP32 pipe, HSE_FFT_CUFFT in cuFFT double (HSE_MIXED plans: FP32 grids
+ * and cuFFT single); HSE_FFT_AUTO picks HSE_FFT_DF64 for HSE_FP64 plans with
+ * tol >= 1e-12 or explicit parameters, HSE_FFT_CUFFT otherwise.  An HSE_MIXED
+ * plan with HSE_FFT_DF64 keeps FP32 real space and runs a double-float Fourier
+ * part: for the half-space stokeslet with sources spread through the box the
+ * FP32 Fourier part loses ~2.5e-8 sqrt(N) of the velocity (FP32 rounding at
+ * low wave numbers, where the image system cancels the long-range field and
+ * the kernel scales by ~1/k^2), which the double-float part avoids. */
 enum { HSE_FFT_AUTO = 0, HSE_FFT_CUFFT = 1, HSE_FFT_DF64 = 2 };
 
 /* Parameters of a plan, as chosen or given (Alg. 1 notation). */
@@ -140,9 +145,10 @@ hse_status hse_plan_set_rc64(hse_plan plan, double rc64);
 
 /* Choose the transforms of the Fourier part (HSE_FFT_AUTO, HSE_FFT_CUFFT or
  * HSE_FFT_DF64; hse_params.fft reports the choice).  Builds what the choice
- * needs when the grids exist (synchronous).  HSE_ERR_INVALID for an unknown
- * mode or HSE_FFT_DF64 on an HSE_MIXED plan; HSE_ERR_UNSUPPORTED when the grid
- * has a length with a prime factor other than 2, 3, 5. */
+ * needs when the grids exist (synchronous; an HSE_MIXED plan rebuilds its
+ * grids and tables, whose element changes between FP32 and double-float).
+ * HSE_ERR_INVALID for an unknown mode; HSE_ERR_UNSUPPORTED when the grid has
+ * a length with a prime factor other than 2, 3, 5. */
 hse_status hse_plan_set_fft(hse_plan plan, int mode);
 
 /*
@@ -307,7 +313,10 @@ typedef struct {
  * (or builds one, evicting idle plans least recently used), and evaluates on
  * its own stream, so work of different requests overlaps on the GPU (a
  * request whose plan is busy with another request waits for it rather than
- * building a duplicate).  xi is
+ * building a duplicate).  An HSE_MIXED request with the stokeslet bit (half
+ * space) whose modelled FP32 rounding of the Fourier part, 2.5e-8 sqrt(n_src)
+ * of the velocity, exceeds tol/3 runs its Fourier part in double-float (see
+ * HSE_FFT_DF64; hse_server_request_params reports fft).  xi is
  * chosen from N and the box (xi = 0.7 (N/V)^(1/3) rounded to a factor-sqrt(2)
  * ladder, so plans are shared between requests); r_c, M and P come from tol.
  * The caller keeps the request's arrays alive until the request completes.

@@ -756,9 +756,9 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   a.lay = rec_layout(a.nfac, paper ? ncomp : a.nc1, q.P);
   a.stride = a.lay.stride;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
-  // FP64 plans split small window weights to FP32 unless the plan asks for
-  // FP64 throughout (rc64 >= rc)
-  const bool split = sizeof(T) == 8 && !paper && q.precision == HSE_FP64 && q.rc64 < q.rc;
+  // 8-byte grids split small window weights to FP32 unless an FP64 plan asks
+  // for FP64 throughout (rc64 >= rc)
+  const bool split = sizeof(T) == 8 && !paper && (q.precision == HSE_MIXED || q.rc64 < q.rc);
   a.prep32 = split ? p->ws.prep32 : nullptr;
   a.supp = reinterpret_cast<int4*>(p->ws.supp);
   return a;
@@ -1189,16 +1189,18 @@ static hse_status fourier_space_batch_t(hse_plan p, int64_t n_total, int n_inst,
 
 hse_status fourier_space_batch(hse_plan p, int64_t n_total, int n_inst, const int32_t* inst_of, void* spec,
                                BatchFFT& f, double* out, cudaStream_t s) {
+  // double-float grids first: FP64 plans, and HSE_MIXED plans asked for a
+  // double-float Fourier part
+  if (p->prm.fft == HSE_FFT_DF64) return fourier_space_batch_t<df>(p, n_total, n_inst, inst_of, spec, f, out, s);
   if (p->prm.precision == HSE_MIXED)
     return fourier_space_batch_t<float>(p, n_total, n_inst, inst_of, spec, f, out, s);
-  if (p->prm.fft == HSE_FFT_DF64) return fourier_space_batch_t<df>(p, n_total, n_inst, inst_of, spec, f, out, s);
   return fourier_space_batch_t<double>(p, n_total, n_inst, inst_of, spec, f, out, s);
 }
 
 hse_status fourier_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add,
                          cudaStream_t s, cudaEvent_t gather_after) {
-  if (p->prm.precision == HSE_MIXED) return fourier_space_t<float>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
   if (p->prm.fft == HSE_FFT_DF64) return fourier_space_t<df>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
+  if (p->prm.precision == HSE_MIXED) return fourier_space_t<float>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
   return fourier_space_t<double>(p, n_src, n_tgt, tgt, out, add, s, gather_after);
 }
 

@@ -181,7 +181,8 @@ void free_workspace(hse_plan p);
 void free_workspace(Workspace& w);
 CompSet product_components(int mask);
 hse_status plan_estimate(int mask, const double box[3], double xi, double tol, int precision, size_t* bytes,
-                         int* M_out, int* P_out);
+                         int* M_out, int* P_out,
+                         int df64_fourier = 0);
 CompSet paper_components(int mask);
 // smallest n' >= n whose padded transform lengths 2n', 4n' are fast sizes
 int fft_friendly_size(int n);

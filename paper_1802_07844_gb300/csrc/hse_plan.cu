@@ -296,10 +296,12 @@ void free_grids(hse_plan p) {
 // arithmetic (rounding ~1e-14 of the data norm), so the automatic choice keeps
 // cuFFT double for tolerances below 1e-12; FP32 plans always use cuFFT single.
 constexpr double kDf64MinTol = 1e-12;
+// HSE_MIXED plans take cuFFT single unless HSE_FFT_DF64 is asked for (FP32
+// real space with a double-float Fourier part).
 static int resolve_fft(hse_plan p) {
   const hse_params& q = p->prm;
-  if (q.precision != HSE_FP64) return HSE_FFT_CUFFT;
   const bool ok = fft64_supported(p->g.Nx, p->g.Ny, p->g.Nz);
+  if (q.precision != HSE_FP64) return p->fft_mode == HSE_FFT_DF64 ? (ok ? HSE_FFT_DF64 : -1) : HSE_FFT_CUFFT;
   if (p->fft_mode == HSE_FFT_DF64) return ok ? HSE_FFT_DF64 : -1;
   if (p->fft_mode == HSE_FFT_CUFFT) return HSE_FFT_CUFFT;
   return ok && (p->tol <= 0.0 || p->tol >= kDf64MinTol) ? HSE_FFT_DF64 : HSE_FFT_CUFFT;
@@ -364,7 +366,11 @@ hse_status build_grids(hse_plan p) {
   p->comps = product_components(q.kernel_mask);
   q.n_fft_in = p->comps.n;
   q.n_fft_out = free_space(q.kernel_mask) ? 3 : 4;  // T1 (and phi with a wall)
-  const bool mixed = q.precision == HSE_MIXED;
+  q.fft = resolve_fft(p);
+  if (q.fft < 0) return set_err(p, HSE_ERR_UNSUPPORTED, "df64 FFT: grid %d x %d x %d", g.Nx, g.Ny, g.Nz);
+  // FP32 grids and tables: HSE_MIXED plans on cuFFT single; double-float or
+  // FP64 grids otherwise (8-byte elements)
+  const bool mixed = q.precision == HSE_MIXED && q.fft != HSE_FFT_DF64;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   size_t tab_elems = (size_t)(q.Mt + 1) * (q.Mt + 1) * (2 * q.Mt + 1);
   size_t spec_bytes = (size_t)g.buf_doubles * esz * q.n_fft_in;
@@ -392,8 +398,6 @@ hse_status build_grids(hse_plan p) {
       HSE_CUDA(p, e);
     }
   }
-  q.fft = resolve_fft(p);
-  if (q.fft < 0) return set_err(p, HSE_ERR_UNSUPPORTED, "df64 FFT: grid %d x %d x %d", g.Nx, g.Ny, g.Nz);
   if (q.fft == HSE_FFT_DF64) HSE_TRY(fft64_prepare(p));
   else HSE_TRY(build_cufft(p));
   q.grid_bytes = spec_bytes + tab_elems * esz * (p->tabB ? 2 : 1) + p->fft_work_bytes;
@@ -538,7 +542,7 @@ static hse_status choose_params(hse_plan p, double xi, double rc, int P, double 
 // Device bytes a plan with these settings will hold (grids, tables, an FFT
 // work area of one buffer), without creating it.  Host-only.
 hse_status plan_estimate(int mask, const double box[3], double xi, double tol, int precision, size_t* bytes,
-                         int* M_out, int* P_out) {
+                         int* M_out, int* P_out, int df64_fourier) {
   hse_plan_s tmp;
   hse_params& q = tmp.prm;
   q.kernel_mask = mask;
@@ -547,7 +551,7 @@ hse_status plan_estimate(int mask, const double box[3], double xi, double tol, i
   q.L = std::fmax(box[0], std::fmax(box[1], box[2]));
   HSE_TRY(choose_params(&tmp, xi, 0.0, 0, tol));
   int Mt = q.M + q.P;
-  size_t esz = precision == HSE_MIXED ? 4 : 8;
+  size_t esz = precision == HSE_MIXED && !df64_fourier ? 4 : 8;
   size_t buf = (size_t)(2 * Mt) * (2 * Mt) * (2 * (2 * Mt + 1)) * esz;
   size_t tab = (size_t)(Mt + 1) * (Mt + 1) * (2 * Mt + 1) * esz;
   int ncomp = product_components(mask).n;
@@ -629,10 +633,20 @@ extern "C" hse_status hse_plan_set_fft(hse_plan p, int mode) {
   if (!p) return HSE_ERR_INVALID;
   if (mode != HSE_FFT_AUTO && mode != HSE_FFT_CUFFT && mode != HSE_FFT_DF64)
     return set_err(p, HSE_ERR_INVALID, "fft mode %d", mode);
-  if (mode == HSE_FFT_DF64 && p->prm.precision != HSE_FP64)
-    return set_err(p, HSE_ERR_INVALID, "HSE_FFT_DF64 needs an HSE_FP64 plan");
+  const int old_mode = p->fft_mode;
   p->fft_mode = mode;
   if (!p->grid_ready) return HSE_OK;
+  if (p->prm.precision == HSE_MIXED) {
+    // the grid element changes between FP32 (cuFFT single) and double-float:
+    // rebuild grids and tables
+    const int f = resolve_fft(p);
+    if (f < 0) {
+      p->fft_mode = old_mode;
+      return set_err(p, HSE_ERR_UNSUPPORTED, "df64 FFT: grid %d x %d x %d", p->g.Nx, p->g.Ny, p->g.Nz);
+    }
+    if (f != p->prm.fft) return build_grids(p);
+    return HSE_OK;
+  }
   const int f = resolve_fft(p);
   if (f < 0) {
     p->fft_mode = HSE_FFT_AUTO;

@@ -28,9 +28,10 @@ using Clock = std::chrono::steady_clock;
 struct PlanKey {
   int mask, precision;
   double tol, box[3], xi;
+  int df64_fourier = 0;  // HSE_MIXED: double-float Fourier part (see choose_df64_fourier)
   bool operator==(const PlanKey& o) const {
     return mask == o.mask && precision == o.precision && tol == o.tol && box[0] == o.box[0] &&
-           box[1] == o.box[1] && box[2] == o.box[2] && xi == o.xi;
+           box[1] == o.box[1] && box[2] == o.box[2] && xi == o.xi && df64_fourier == o.df64_fourier;
   }
 };
 
@@ -64,6 +65,29 @@ double choose_xi(int64_t n, const double box[3]) {
 }
 
 size_t workspace_bytes(int64_t n) { return (size_t)(n > 1024 ? n : 1024) * 640; }
+
+// HSE_MIXED half-space stokeslet requests: the FP32 rounding of the Fourier
+// part is amplified where the wall's image system cancels the long-range field
+// (low wave numbers, scaled by ~1/k^2), measured at ~2.5e-8 sqrt(N) of the
+// velocity for sources spread through the box; when that exceeds a third of
+// tol the request runs its Fourier part in double-float (the real space stays
+// FP32).
+bool choose_df64_fourier(int mask, int precision, double tol, int64_t n) {
+  if (precision != HSE_MIXED || !(mask & HSE_STOKESLET) || hse::free_space(mask)) return false;
+  return 2.5e-8 * std::sqrt((double)(n > 1 ? n : 1)) > tol / 3.0;
+}
+
+hse_status create_plan(const PlanKey& key, hse_plan* plan) {
+  hse_status st = hse_plan_create(key.mask, key.box, key.xi, 0.0, 0, key.tol, key.precision, plan);
+  if (st == HSE_OK && key.df64_fourier) {
+    st = hse_plan_set_fft(*plan, HSE_FFT_DF64);
+    if (st != HSE_OK) {
+      hse_plan_destroy(*plan);
+      *plan = nullptr;
+    }
+  }
+  return st;
+}
 
 }  // namespace
 
@@ -179,7 +203,7 @@ struct hse_server_s {
       double build_s = 0.0;
       if (!plan) {
         const Clock::time_point t0 = Clock::now();
-        st = hse_plan_create(key.mask, key.box, key.xi, 0.0, 0, key.tol, key.precision, &plan);
+        st = create_plan(key, &plan);
         build_s = std::chrono::duration<double>(Clock::now() - t0).count();
         if (st != HSE_OK) {
           plan = nullptr;
@@ -275,9 +299,10 @@ extern "C" hse_status hse_server_submit(hse_server srv, const hse_request* req, 
   r.key.tol = req->tol;
   for (int d = 0; d < 3; ++d) r.key.box[d] = req->box[d];
   r.key.xi = choose_xi(req->n_src, req->box);
+  r.key.df64_fourier = choose_df64_fourier(r.key.mask, r.key.precision, r.key.tol, req->n_src) ? 1 : 0;
   size_t grid = 0;
   hse_status st = hse::plan_estimate(r.key.mask, r.key.box, r.key.xi, r.key.tol, r.key.precision, &grid, nullptr,
-                                     nullptr);
+                                     nullptr, r.key.df64_fourier);
   if (st != HSE_OK) return st;
   r.est_bytes = grid + workspace_bytes(req->n_src);
   std::lock_guard<std::mutex> lk(srv->m);
@@ -310,8 +335,10 @@ extern "C" hse_status hse_server_prewarm(hse_server srv, const hse_request* req)
   key.tol = req->tol;
   for (int d = 0; d < 3; ++d) key.box[d] = req->box[d];
   key.xi = choose_xi(req->n_src, req->box);
+  key.df64_fourier = choose_df64_fourier(key.mask, key.precision, key.tol, req->n_src) ? 1 : 0;
   size_t grid = 0;
-  HSE_TRY(hse::plan_estimate(key.mask, key.box, key.xi, key.tol, key.precision, &grid, nullptr, nullptr));
+  HSE_TRY(hse::plan_estimate(key.mask, key.box, key.xi, key.tol, key.precision, &grid, nullptr, nullptr,
+                             key.df64_fourier));
   {
     std::lock_guard<std::mutex> lk(srv->m);
     if (srv->stop) return set_err(nullptr, HSE_ERR_INVALID, "server is stopping");
@@ -331,7 +358,7 @@ extern "C" hse_status hse_server_prewarm(hse_server srv, const hse_request* req)
   cudaSetDevice(srv->device);
   hse_plan plan = nullptr;
   const Clock::time_point t0 = Clock::now();
-  hse_status st = hse_plan_create(key.mask, key.box, key.xi, 0.0, 0, key.tol, key.precision, &plan);
+  hse_status st = create_plan(key, &plan);
   const double build_s = std::chrono::duration<double>(Clock::now() - t0).count();
   cudaSetDevice(prev_dev);
   std::lock_guard<std::mutex> lk(srv->m);

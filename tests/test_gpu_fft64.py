@@ -87,11 +87,16 @@ def test_df64_unsupported_length_falls_back(pkg):
 
 
 def test_df64_mode_rules(pkg):
-    # FP32 plans keep cuFFT single and refuse df64; tight tolerances keep cuFFT double
+    # FP32 plans take cuFFT single unless a double-float Fourier part is asked
+    # for; tight tolerances keep cuFFT double
     mixed = pkg.Plan(KERNEL_S, (1.0, 1.0, 1.0), xi=10.0, tol=1e-5, precision=pkg.HSE_MIXED)
     assert mixed.params["fft"] == pkg.HSE_FFT_CUFFT
-    with pytest.raises(pkg.HseError):
-        mixed.set_fft(pkg.HSE_FFT_DF64)
+    b32 = mixed.params["grid_bytes"]
+    mixed.set_fft(pkg.HSE_FFT_DF64)
+    assert mixed.params["fft"] == pkg.HSE_FFT_DF64
+    assert mixed.params["grid_bytes"] > 1.5 * b32  # 8-byte grids and tables
+    mixed.set_fft(pkg.HSE_FFT_CUFFT)
+    assert mixed.params["fft"] == pkg.HSE_FFT_CUFFT
     mixed.close()
     tight = pkg.Plan(KERNEL_W, (1.0, 1.0, 1.0), xi=10.0, tol=1e-13)
     assert tight.params["fft"] == pkg.HSE_FFT_CUFFT
@@ -131,3 +136,37 @@ def test_df64_at_the_tightest_automatic_tolerance(pkg, mask):
     plan.close()
     assert e_df < 1e-12 and e_cu < 1e-12
     assert e_df < 2.0 * e_cu + 1e-14
+
+
+def test_mixed_plan_with_double_float_fourier_part(pkg):
+    """Half-space stokeslets spread through the box: with FP32 grids the
+    Fourier part loses ~2.5e-8 sqrt(N) of the velocity (FP32 rounding at low
+    wave numbers, where the image system cancels the long-range field and the
+    kernel scales by ~1/k^2).  An HSE_MIXED plan with HSE_FFT_DF64 keeps FP32
+    real space and matches the FP64 plan's Fourier part far more closely, and
+    the whole evaluation meets tol against the direct sum."""
+    n = 60000
+    pr = problem(KERNEL_S, n, 1.0, "uniform", 83)
+    src, st = dev(pr.src), dev(pr.strengths)
+    m = pkg.Plan(KERNEL_S, (1.0, 1.0, 1.0), xi=28.0, tol=1e-5, precision=pkg.HSE_MIXED)
+    prm = m.params
+    d = pkg.Plan(KERNEL_S, (1.0, 1.0, 1.0), xi=prm["xi"], rc=prm["rc"], P=prm["P"], tol=0.0, M=prm["M"])
+    try:
+        _, f64 = d.eval_parts(src, st)
+        u64 = host(d.eval(src, st))
+        _, f32 = m.eval_parts(src, st)
+        m.set_fft(pkg.HSE_FFT_DF64)
+        _, fdf = m.eval_parts(src, st)
+        u = host(m.eval(src, st))
+    finally:
+        m.close()
+        d.close()
+    urms = np.sqrt(np.mean(np.sum(u64 ** 2, axis=0)))
+    e32 = np.sqrt(np.mean(np.sum((host(f32) - host(f64)) ** 2, axis=0))) / urms
+    edf = np.sqrt(np.mean(np.sum((host(fdf) - host(f64)) ** 2, axis=0))) / urms
+    print(f"Fourier part vs FP64, relative to |u|: FP32 grids {e32:.2e}, double-float grids {edf:.2e}")
+    assert edf < 1e-8 and edf < e32 / 100
+    idx = np.sort(np.random.default_rng(7).choice(n, 1500, replace=False))
+    ref = oracle.direct(KERNEL_S, pr.src, pr.strengths, pr.src[:, idx])
+    err = np.sqrt(np.mean(np.sum((u[:, idx] - ref) ** 2, axis=0))) / urms
+    assert err < 1e-5

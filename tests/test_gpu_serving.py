@@ -102,6 +102,33 @@ def test_prewarm_makes_the_first_request_a_cache_hit(pkg):
         srv.close()
 
 
+def test_mixed_stokeslet_requests_take_a_double_float_fourier_part_when_large(pkg):
+    """HSE_MIXED half-space stokeslet requests whose modelled FP32 rounding of
+    the Fourier part (2.5e-8 sqrt(N)) exceeds tol/3 run their Fourier part in
+    double-float; small ones, and other kernels, keep FP32 grids."""
+    srv = pkg.hse.Server(n_slots=2)
+    try:
+        tickets = []
+        for mask, n in ((KERNEL_S, 30000), (KERNEL_S, 4000), (KERNEL_W, 30000)):
+            pr = problem(mask, n, 1.0, "uniform", 63, sub=n)
+            src = torch.from_numpy(pr.src).cuda()
+            st = torch.from_numpy(pr.strengths).cuda()
+            tickets.append((srv.submit(mask, src, st, 1e-5, pkg.HSE_MIXED), pr, src, st))
+        ffts = []
+        for t, pr, _, _ in tickets:
+            assert srv.wait(t, 300.0) == pkg.hse.HSE_OK
+            ffts.append(srv.request_params(t)["fft"])
+            n = pr.src.shape[1]
+            idx = np.sort(np.random.default_rng(3).choice(n, min(n, 800), replace=False))
+            ref = oracle.direct(pr.mask, pr.src, pr.strengths, pr.src[:, idx])
+            u = srv.result(t).cpu().numpy()
+            err = np.sqrt(np.mean(np.sum((u[:, idx] - ref) ** 2, axis=0)) / np.mean(np.sum(u ** 2, axis=0)))
+            assert err < 1e-5
+        assert ffts == [pkg.HSE_FFT_DF64, pkg.HSE_FFT_CUFFT, pkg.HSE_FFT_CUFFT]
+    finally:
+        srv.close()
+
+
 def test_bounded_wait_and_memory_admission(pkg):
     pr = problem(KERNEL_S, 200_000, 1.0, "uniform", 61)
     src = torch.from_numpy(pr.src).cuda()
