@@ -58,7 +58,7 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   HSE_CUDA(p, cudaMalloc(&w.spos32lo, sizeof(float) * 3 * cap));
   HSE_CUDA(p, cudaMalloc(&w.sstr32, sizeof(float) * 12 * cap));
   HSE_CUDA(p, cudaMalloc(&w.usort, sizeof(double) * 3 * cap));
-  HSE_CUDA(p, cudaMalloc(&w.usort4, sizeof(float4) * cap));
+  HSE_CUDA(p, cudaMalloc(&w.usort4, sizeof(float4) * 2 * cap));  // partner sums, then their rounding errors
   HSE_CUDA(p, cudaMalloc(&w.sstr, sizeof(double) * 12 * cap));
   HSE_CUDA(p, cudaMalloc(&w.prep, sizeof(double) * (size_t)stride * cap));
   HSE_CUDA(p, cudaMalloc(&w.prep32, sizeof(float) * (size_t)stride * cap));

@@ -250,16 +250,21 @@ __device__ __forceinline__ void ldv(const T* p, T* out) {
 // the cell-list rows whose sources can reach its sub-tile, 32 candidates at a
 // time (one per lane: does the support cover the sub-tile, and is every weight
 // on it below the FP32 threshold), compacts the hits into a warp-private list
-// in source order and accumulates them.  Per point the sources are added in
-// cell-row order and, within a row, in sorted order, so the result is
-// deterministic.
-// blocks per SM the spread is compiled for: 4 (64 registers) while the
-// accumulators fit without spilling, else 2
-template <int NC, int DK>
-constexpr int spread_min_blocks() { return NC + (DK != 0) <= 7 && DK != 7 && DK != 6 ? 4 : 2; }
+// (FP32 small-weight hits from the front, the others from the back, each in
+// source order) and accumulates them into separate FP32 and full-precision
+// sums.  Per point and class the sources are added in cell-row order and,
+// within a row, in sorted order, so the result is deterministic.
+// blocks per SM the spread is compiled for, while the accumulators fit without
+// spilling (else 2): FP32 4 (64 registers); 8-byte elements 3 (80 registers:
+// measured on the N = 1M near-wall S+W workload, 41.3 ms against 44.2 ms at 4
+// blocks, where the unrolled loop spills)
+template <typename T, int NC, int DK>
+constexpr int spread_min_blocks() {
+  return NC + (DK != 0) <= 7 && DK != 7 && DK != 6 ? (sizeof(T) == 4 ? 4 : 3) : 2;
+}
 
 template <typename T, int NC, int DK>
-__global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(SpreadArgs<T> a) {
+__global__ void __launch_bounds__(256, spread_min_blocks<T, NC, DK>()) k_spread(SpreadArgs<T> a) {
   // per warp: the hits of the current 32 candidates, with their support
   // starts (w: source index, bit 31 set when the FP32 small-weight record applies)
   __shared__ int4 wlist[8][32];
@@ -323,54 +328,73 @@ __global__ void __launch_bounds__(256, spread_min_blocks<NC, DK>()) k_spread(Spr
             small = a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr;
           }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) list[__popc(m & below)] = make_int4(sp.x, sp.y, sp.z, j | (int)((unsigned)small << 31));
+        // FP32 small-weight hits fill the list from the front, the others from
+        // the back, each class in source order (fixed per point: deterministic
+        // sums)
+        const unsigned ms = __ballot_sync(0xffffffffu, hit && small);
+        const unsigned mb = __ballot_sync(0xffffffffu, hit && !small);
+        if (hit) list[small ? __popc(ms & below) : 31 - __popc(mb & below)] = make_int4(sp.x, sp.y, sp.z, j);
         __syncwarp();
-        const int cnt = __popc(m);
-        for (int e = 0; e < cnt; ++e) {
+        const int ns = __popc(ms), nb = __popc(mb);
+        // Branch-free bodies (a lane outside the source's support reads
+        // clamped entries and adds zero weights), unrolled so that the next
+        // source's record loads are in flight while this one accumulates.
+#pragma unroll 2
+        for (int e = 0; e < ns; ++e) {
           const int4 s = list[e];
-          const int entry = s.w;
-          const int jj = entry & 0x7fffffff;
           int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
-          if (!(dx >= 0 && dx < P && dy >= 0 && dy < P && dz >= 0 && dz < P)) continue;
-          if (entry < 0) {
-            const float* o = a.prep32 + (int64_t)jj * a.stride;
-            float xv[KX], yv[KY], zv[KY];
-            ldv<float, KX>(o + dx * KX, xv);
-            ldv<float, KY>(o + a.y0 + dy * KY, yv);
-            ldv<float, KY>(o + a.z0r + dz * KY, zv);
-            const float wyz = yv[0] * zv[0];
-            const float wv = xv[0] * wyz;
-            float cv[(NC + 1) & ~1];
-            ldv<float, (NC + 1) & ~1>(o + a.c0, cv);
+          const bool in = (unsigned)dx < (unsigned)P && (unsigned)dy < (unsigned)P && (unsigned)dz < (unsigned)P;
+          dx = min(max(dx, 0), P - 1);
+          dy = min(max(dy, 0), P - 1);
+          dz = min(max(dz, 0), P - 1);
+          const float* o = a.prep32 + (int64_t)s.w * a.stride;
+          float xv[KX], yv[KY], zv[KY];
+          ldv<float, KX>(o + dx * KX, xv);
+          ldv<float, KY>(o + a.y0 + dy * KY, yv);
+          ldv<float, KY>(o + a.z0r + dz * KY, zv);
+          float cv[(NC + 1) & ~1];
+          ldv<float, (NC + 1) & ~1>(o + a.c0, cv);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc32[c] += wv * cv[c];
-            if constexpr (DK != 0) {
-              accD32 += xv[1] * wyz + xv[2] * (yv[1] * zv[0]) + xv[3] * (yv[0] * zv[1]);
-              if constexpr ((DK & 4) != 0)
-                accD32 += xv[4] * (yv[2] * zv[0]) + xv[5] * (yv[0] * zv[2]) + xv[6] * (yv[1] * zv[1]);
-            }
-          } else {
-            const T* o = a.prep + (int64_t)jj * a.stride;
-            T xv[KX], yv[KY], zv[KY];
-            ldv<T, KX>(o + dx * KX, xv);
-            ldv<T, KY>(o + a.y0 + dy * KY, yv);
-            ldv<T, KY>(o + a.z0r + dz * KY, zv);
-            const T wyz = mulr(yv[0], zv[0]);
-            const T wv = mulr(xv[0], wyz);
-            T cv[(NC + 1) & ~1];
-            ldv<T, (NC + 1) & ~1>(o + a.c0, cv);
+          for (int k = 0; k < KX; ++k) xv[k] = in ? xv[k] : 0.f;
+          const float wyz = yv[0] * zv[0];
+          const float wv = xv[0] * wyz;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = mac(acc[c], wv, cv[c]);
-            if constexpr (DK != 0) {
-              accD = mac(accD, xv[1], wyz);
-              accD = mac(accD, xv[2], mulr(yv[1], zv[0]));
-              accD = mac(accD, xv[3], mulr(yv[0], zv[1]));
-              if constexpr ((DK & 4) != 0) {
-                accD = mac(accD, xv[4], mulr(yv[2], zv[0]));
-                accD = mac(accD, xv[5], mulr(yv[0], zv[2]));
-                accD = mac(accD, xv[6], mulr(yv[1], zv[1]));
-              }
+          for (int c = 0; c < NC; ++c) acc32[c] += wv * cv[c];
+          if constexpr (DK != 0) {
+            accD32 += xv[1] * wyz + xv[2] * (yv[1] * zv[0]) + xv[3] * (yv[0] * zv[1]);
+            if constexpr ((DK & 4) != 0)
+              accD32 += xv[4] * (yv[2] * zv[0]) + xv[5] * (yv[0] * zv[2]) + xv[6] * (yv[1] * zv[1]);
+          }
+        }
+#pragma unroll 2
+        for (int e = 0; e < nb; ++e) {
+          const int4 s = list[31 - e];
+          int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
+          const bool in = (unsigned)dx < (unsigned)P && (unsigned)dy < (unsigned)P && (unsigned)dz < (unsigned)P;
+          dx = min(max(dx, 0), P - 1);
+          dy = min(max(dy, 0), P - 1);
+          dz = min(max(dz, 0), P - 1);
+          const T* o = a.prep + (int64_t)s.w * a.stride;
+          T xv[KX], yv[KY], zv[KY];
+          ldv<T, KX>(o + dx * KX, xv);
+          ldv<T, KY>(o + a.y0 + dy * KY, yv);
+          ldv<T, KY>(o + a.z0r + dz * KY, zv);
+          T cv[(NC + 1) & ~1];
+          ldv<T, (NC + 1) & ~1>(o + a.c0, cv);
+#pragma unroll
+          for (int k = 0; k < KX; ++k) xv[k] = in ? xv[k] : (T)0;
+          const T wyz = mulr(yv[0], zv[0]);
+          const T wv = mulr(xv[0], wyz);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = mac(acc[c], wv, cv[c]);
+          if constexpr (DK != 0) {
+            accD = mac(accD, xv[1], wyz);
+            accD = mac(accD, xv[2], mulr(yv[1], zv[0]));
+            accD = mac(accD, xv[3], mulr(yv[0], zv[1]));
+            if constexpr ((DK & 4) != 0) {
+              accD = mac(accD, xv[4], mulr(yv[2], zv[0]));
+              accD = mac(accD, xv[5], mulr(yv[0], zv[2]));
+              accD = mac(accD, xv[6], mulr(yv[1], zv[1]));
             }
           }
         }
@@ -788,11 +812,21 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   // relative errors <~ 4 eps32 tau of the largest contribution of their
   // particle.  Measured on the 1M near-wall S+W workload the velocity changes
   // by ~5e-9 tau (relative RMS) against an all-FP64 spread, so a plan that
-  // knows its tolerance takes tau = 2e6 tol (its share stays ~1/100 of tol),
-  // clamped to [1e-5, 1e-3]; plans with explicit parameters and no tol keep
-  // tau = 1e-5.
+  // knows its tolerance takes tau = 2e6 tol (its share stays ~1/100 of tol).
+  // Stokeslets spread through the box are worse: their rounding noise is
+  // white, and the low wave numbers, where the image system cancels the
+  // long-range field, scale it by ~1/k^2, so the Fourier part changes by
+  // ~1.6e-9 tau sqrt(N) (uniform sources, N = 79k-135k at tau = 2e-4:
+  // 0.9e-10-1.2e-10); stokeslet plans cap tau at tol / (1.6e-8 sqrt(N)) per
+  // instance, which keeps that share below tol / 10.  tau stays within
+  // [1e-5, 1e-3]; plans with explicit parameters and no tol keep tau = 1e-5.
   a.ah2 = (float)(pa.alpha * q.h * q.h);
-  const double tau = p->tol > 0.0 ? std::fmin(1e-3, std::fmax(1e-5, 2e6 * p->tol)) : 1e-5;
+  double tau = p->tol > 0.0 ? 2e6 * p->tol : 1e-5;
+  if (p->tol > 0.0 && (q.kernel_mask & HSE_STOKESLET) && n_src > 0) {
+    const double n_per = (double)n_src / (n_inst > 0 ? n_inst : 1);
+    tau = std::fmin(tau, p->tol / (1.6e-8 * std::sqrt(n_per)));
+  }
+  tau = std::fmin(1e-3, std::fmax(1e-5, tau));
   a.lnthr = (float)std::log(1.0 / tau);
 
   a.cstart = p->ws.cell_start;

@@ -494,16 +494,17 @@ static hse_status choose_params(hse_plan p, double xi, double rc, int P, double 
   // pair is ~ kappa eps32 |K_R(rho)| |c|; summed over the shell [rc64, rc) it
   // behaves like kappa eps32 times the truncation estimate evaluated at rc64
   // (the same sum, started at rc64), so rc64 is where that estimate reaches
-  // kShellShare / (kappa eps32) times its value at rc (kappa = 16, eps32 = 2^-24):
-  // the shell gets half the error share of the real-space truncation estimate
-  // (itself at most tol/3).  Measured against all-FP64 pairs: at a share of 1
-  // the stokeslet near the wall reached 1.2x its actual truncation error
-  // (xi = 14, r_c = 0.3, N = 2000), the other kernels 0.2-0.6x; at 0.5 the
-  // N = 1M near-wall S+W workload at tol 1e-10 keeps the shell at a few 1e-12.
-  constexpr double kShellShare = 0.5;
+  // kShellShare / (kappa eps32) times its value at rc (eps32 = 2^-24): the
+  // shell gets half the error share of the real-space truncation estimate
+  // (itself at most tol/3).  kappa = 4: the shell carries the Gaussian's
+  // exponent in double-float and compensates its sums, ~1e-7 per term;
+  // measured against all-FP64 pairs on the N = 1M near-wall S+W workload
+  // (xi = 87, r_c = 0.0552) the shell adds 2.4e-12 at rc64 = 0.032 and
+  // 1.5e-11 at 0.028, and the plain FP32 form 8x more.
+  constexpr double kShellShare = 0.5, kShellKappa = 4.0;
   q.rc64 = 0.0;
   if (q.precision == HSE_FP64) {
-    const double target = est_real(mask, xi, rc, L) * (kShellShare / (16.0 * std::ldexp(1.0, -24)));
+    const double target = est_real(mask, xi, rc, L) * (kShellShare / (kShellKappa * std::ldexp(1.0, -24)));
     const double lo = 1.5 / xi;  // never FP32 for xi rho < 1.5
     if (lo >= rc) q.rc64 = rc;
     else if (est_real(mask, xi, lo, L) <= target) q.rc64 = lo;

@@ -52,6 +52,7 @@ struct RealArgs {
   const double* tgt;       // explicit targets (3 x n_tgt) or null (targets = sources)
   double* out;             // 3 x n_tgt in caller order (symmetric kernel: sorted order)
   float4* out4;            // symmetric FP32 kernel: partner sums in sorted order
+  float4* out4lo;          // FP64 kernel's FP32 shell: rounding errors of the out4 sums (null: none)
   int add;                 // accumulate into out (asymmetric kernel)
   int mask, rowS, rowT, rowW;
   double xi, rc2, rc;
@@ -153,6 +154,50 @@ __device__ __forceinline__ Radial<float> radial(float s, float, float xi, const 
   float i2 = inv * inv;
   R.c = (float)(2.0 / kSqrtPi) * xi * E;
   R.er = ec * inv;
+  R.a1 = (R.er + R.c) * i2;
+  R.g2 = i2 * fmaf(3.0f, R.a1, 2.0f * xi * xi * R.c);
+  R.g3 = need_g3 ? -i2 * fmaf(5.0f, R.g2, 4.0f * xi * xi * xi * xi * R.c) : 0.0f;
+  return R;
+}
+
+// s + e == a + b exactly (Knuth's two-sum; no ordering of |a|, |b| needed)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Radial coefficients of an outer-shell pair of an FP64 plan, in FP32 but with
+// the Gaussian's exponent carried to ~44 bits.  e^{-t^2} and erfc(t) change by
+// 2 t^2 times the relative error of rho^2 (t = xi rho, 2 t^2 ~ 15 at the
+// shell's inner edge), so the plain FP32 form above loses ~1.5e-6 per term;
+// here rho^2 = sum_d (dh_d + dl_d)^2 is formed with exact products and sums,
+// t^2 = xi^2 rho^2 = zh + zl with the product's error kept, e^{-t^2} =
+// e^{-zh} (1 - zl), and erfc(t) = e^{-t^2} erfcx(t), where erfcx varies slowly
+// (its relative error stays that of t).  ~1e-7 per term.
+__device__ __forceinline__ Radial<float> radial_shell(const float* dh, const float* dl, float xi, float xi2h,
+                                                      float xi2l, bool need_g3) {
+  float p[3], q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    p[d] = __fmul_rn(dh[d], dh[d]);
+    q[d] = fmaf(dh[d], dh[d], -p[d]);
+  }
+  float s1, e1, sh, e2;
+  two_sum(p[0], p[1], s1, e1);
+  two_sum(s1, p[2], sh, e2);
+  const float cross = fmaf(dh[0], dl[0], fmaf(dh[1], dl[1], __fmul_rn(dh[2], dl[2])));
+  const float sl = __fadd_rn(__fadd_rn(e1, e2), fmaf(2.0f, cross, __fadd_rn(q[0], __fadd_rn(q[1], q[2]))));
+  const float zh = __fmul_rn(xi2h, sh);
+  const float zl = __fadd_rn(fmaf(xi2h, sh, -zh), fmaf(xi2h, sl, __fmul_rn(xi2l, sh)));
+  const float E = __fmul_rn(expf(-zh), __fsub_rn(1.0f, zl));
+  const float s = __fadd_rn(sh, sl);
+  const float inv = rsqrtf(s);
+  const float t = xi * s * inv;
+  Radial<float> R;
+  const float i2 = inv * inv;
+  R.c = (float)(2.0 / kSqrtPi) * xi * E;
+  R.er = E * erfcxf(t) * inv;
   R.a1 = (R.er + R.c) * i2;
   R.g2 = i2 * fmaf(3.0f, R.a1, 2.0f * xi * xi * R.c);
   R.g3 = need_g3 ? -i2 * fmaf(5.0f, R.g2, 4.0f * xi * xi * xi * xi * R.c) : 0.0f;
@@ -293,6 +338,25 @@ __device__ __forceinline__ void pair_vec(const RealArgs& a, const TgtPos& x, int
   r[0] = (x.h[0] - H[j]) + (x.l[0] - L[j]);
   r[1] = (x.h[1] - H[n + j]) + (x.l[1] - L[n + j]);
   r[2] = img ? (x.h[2] + H[2 * n + j]) + (x.l[2] + L[2 * n + j]) : (x.h[2] - H[2 * n + j]) + (x.l[2] - L[2 * n + j]);
+  *h = H[2 * n + j] + L[2 * n + j];
+}
+// The same separation as head + tail per component with the heads' difference
+// split exactly (two-sum): r_d = dh_d + dl_d to ~2^-24 of the tails, so that
+// the shell's distance^2 keeps ~44 bits; r (FP32) is their rounded sum.
+__device__ __forceinline__ void pair_vec_split(const RealArgs& a, const TgtPos& x, int64_t j, bool img, float* dh,
+                                               float* dl, float* r, float* h) {
+  const int64_t n = a.n_src;
+  const float* H = a.spos32;
+  const float* L = a.spos32lo;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const bool sum = img && d == 2;
+    const float yh = H[d * n + j], yl = L[d * n + j];
+    float e;
+    two_sum(x.h[d], sum ? yh : -yh, dh[d], e);
+    dl[d] = __fadd_rn(e, sum ? __fadd_rn(x.l[d], yl) : __fsub_rn(x.l[d], yl));
+    r[d] = __fadd_rn(dh[d], dl[d]);
+  }
   *h = H[2 * n + j] + L[2 * n + j];
 }
 
@@ -500,7 +564,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
   const bool need_g3 = KM & HSE_STRESSLET;
   const T xi = (T)a.xi;
   const float xi32 = (float)a.xi;
+  const float xi2h = (float)(a.xi * a.xi), xi2l = (float)(a.xi * a.xi - (double)xi2h);
   const T* str = strengths_of<T>(a);
+  // Compensated FP32 partner sums of the shell: a source receives thousands of
+  // float4 atomics, whose rounding would grow with their number.  atomicAdd
+  // returns the old value, so the rounding error of each add is recovered
+  // exactly by a two-sum (the atomic rounds to nearest) and added to out4lo.
+  // The two-sum of a lane's last atomic is taken at its next shell batch, so
+  // the atomic's round trip overlaps the scan.
+  float4 pend_old = make_float4(0.f, 0.f, 0.f, 0.f), pend_v = pend_old;
+  int64_t pend_j = -1;
+  auto flush_pending = [&]() {
+    if (pend_j >= 0) {
+      float s0, e0, e1, e2;
+      two_sum(pend_old.x, pend_v.x, s0, e0);
+      two_sum(pend_old.y, pend_v.y, s0, e1);
+      two_sum(pend_old.z, pend_v.z, s0, e2);
+      atomicAdd(a.out4lo + pend_j, make_float4(e0, e1, e2, 0.f));
+      pend_j = -1;
+    }
+  };
   for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < n; w += nwarps) {
     TgtPos x;
     for (int d = 0; d < 3; ++d) {
@@ -513,7 +596,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
     Src<T> sp;
     load_src<T, KM>(a, str, w, sp);
     T u[3] = {0, 0, 0};
-    float uf[3] = {0.f, 0.f, 0.f};  // FP32 shell pairs
+    float uf[3] = {0.f, 0.f, 0.f}, ufl[3] = {0.f, 0.f, 0.f};  // FP32 shell pairs, compensated
     double uself[3] = {0.0, 0.0, 0.0};
     if (lane == 0 && (KM & HSE_STOKESLET))
       for (int i = 0; i < 3; ++i) uself[i] = -4.0 * a.xi / kSqrtPi * a.sstr[(a.rowS + i) * n + w];
@@ -555,22 +638,33 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
       Src<float> s, spf;
       load_src<float, KM>(a, a.sstr32, j, s);
       load_src<float, KM>(a, a.sstr32, w, spf);
-      float r[3], h;
-      pair_vec(a, x, j, type == Q_IMAGE, r, &h);
-      float sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      Radial<float> R = radial(sd, sd, xi32, nullptr, need_g3);
-      float v[3] = {0.f, 0.f, 0.f};
+      float r[3], dh[3], dl[3], h;
+      pair_vec_split(a, x, j, type == Q_IMAGE, dh, dl, r, &h);
+      Radial<float> R = radial_shell(dh, dl, xi32, xi2h, xi2l, need_g3);
+      float v[3] = {0.f, 0.f, 0.f}, t[3] = {0.f, 0.f, 0.f};
       if (type == Q_FREE) {
-        add_free<float>(KM, R, r, s, xi32, 1.f, uf);
+        add_free<float>(KM, R, r, s, xi32, 1.f, t);
         add_free<float>(KM, R, r, spf, xi32, -1.f, v);
       } else {
-        add_image<float>(KM, R, r, h, x3f, s, xi32, uf);
+        add_image<float>(KM, R, r, h, x3f, s, xi32, t);
         if (j != w) {
           float rp[3] = {-r[0], -r[1], r[2]};
           add_image<float>(KM, R, rp, x3f, h, spf, xi32, v);
         }
       }
-      if (type == Q_FREE || j != w) atomicAdd(a.out4 + j, make_float4(v[0], v[1], v[2], 0.f));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float s_, e_;
+        two_sum(uf[i], t[i], s_, e_);
+        uf[i] = s_;
+        ufl[i] += e_;
+      }
+      flush_pending();
+      if (type == Q_FREE || j != w) {
+        pend_v = make_float4(v[0], v[1], v[2], 0.f);
+        pend_old = atomicAdd(a.out4 + j, pend_v);
+        pend_j = j;
+      }
     };
     float xf[3] = {x.h[0], x.h[1], x.h[2]};
     for_candidates(a, x.d, xf, w, lane, (int)w + 1, (int)w, cell_base(a, w), [&](bool hit, int j, int type) {
@@ -608,7 +702,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
     __syncwarp();
     double ud[3];
     for (int i = 0; i < 3; ++i) {
-      ud[i] = (double)u[i] + (double)uf[i] + uself[i];
+      ud[i] = (double)u[i] + ((double)uf[i] + (double)ufl[i]) + uself[i];
       for (int off = 16; off > 0; off >>= 1) ud[i] += __shfl_xor_sync(0xffffffffu, ud[i], off);
     }
     if (lane == 0) {
@@ -618,17 +712,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
         for (int i = 0; i < 3; ++i) atomicAdd(a.out + i * n + w, ud[i]);
     }
   }
+  if constexpr (sizeof(T) == 8) flush_pending();
 }
 
 // caller order: out[orig(i)] = sorted[i] (+ the FP32 partner sums, if any)
 __global__ void k_unsort(int64_t n, const int32_t* __restrict__ sorig, const double* __restrict__ us,
-                         const float4* __restrict__ us4, double* __restrict__ out) {
+                         const float4* __restrict__ us4, const float4* __restrict__ us4lo, double* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t o = sorig[i];
-    float4 p = us4 ? us4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    out[o] = us[i] + (double)p.x;
-    out[n + o] = us[n + i] + (double)p.y;
-    out[2 * n + o] = us[2 * n + i] + (double)p.z;
+    const float4 p = us4 ? us4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 q = us4lo ? us4lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    out[o] = us[i] + ((double)p.x + (double)q.x);
+    out[n + o] = us[n + i] + ((double)p.y + (double)q.y);
+    out[2 * n + o] = us[2 * n + i] + ((double)p.z + (double)q.z);
   }
 }
 
@@ -720,7 +816,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_counts(RealArgs a, int3
 // (rounding of each coordinate to FP32, of the difference, of the squares and
 // sums).  Four times that bound around r_c^2 is sent to the FP64 test.
 static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tgt, double* out, bool add) {
-  RealArgs a;
+  RealArgs a{};
   a.n_src = n_src;
   a.n_tgt = n_tgt;
   a.spos = p->ws.spos;
@@ -808,13 +904,16 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
       }
     } else {
       HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_tgt, s));
-      if (shell32(p, a)) HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_tgt, s));
+      if (shell32(p, a)) {
+        a.out4lo = a.out4 + n_tgt;
+        HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * 2 * n_tgt, s));
+      }
       launch_real_sym<double>(a.mask, sym_blocks(p, n_tgt), a, s);
     }
     HSE_CUDA(p, cudaGetLastError());
     int64_t b = (n_tgt + 255) / 256;
     k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(
-        n_tgt, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, out);
+        n_tgt, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, a.out4lo, out);
     ++p->n_launch;
   } else {
     if (mixed) k_real<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);
@@ -845,14 +944,17 @@ hse_status real_space_batch(hse_plan p, int64_t n_total, const int32_t* inst_of,
     }
   } else {
     HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_total, s));
-    if (shell32(p, a)) HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * n_total, s));
+    if (shell32(p, a)) {
+      a.out4lo = a.out4 + n_total;
+      HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * 2 * n_total, s));
+    }
     launch_real_sym<double>(a.mask, warp_blocks(n_total), a, s);
     ++p->n_launch;
   }
   HSE_CUDA(p, cudaGetLastError());
   int64_t b = (n_total + 255) / 256;
   k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(
-      n_total, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, out);
+      n_total, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, a.out4lo, out);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "real_space_batch");
 }
