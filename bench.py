@@ -831,10 +831,10 @@ def run_batch(args, pkg, torch, dev):
     ms_step = float(np.mean(ms))
     groups = {}
     for p, u in zip(probs, used):
-        key = (p.mask, u["xi"], u["P"], u["M"])
+        key = (p.mask, u["xi"], u["P"], u["M"], tuple(u["spread_tile"]))
         g = groups.setdefault(key, {"kernel": {1: "stokeslet", 2: "stresslet"}[p.mask], "xi": u["xi"],
-                                    "rc": u["rc"], "P": u["P"], "M": u["M"], "instances": 0, "n_min": 1 << 30,
-                                    "n_max": 0})
+                                    "rc": u["rc"], "P": u["P"], "M": u["M"], "spread_tile": list(u["spread_tile"]),
+                                    "instances": 0, "n_min": 1 << 30, "n_max": 0})
         g["instances"] += 1
         g["n_min"] = min(g["n_min"], p.src.shape[1])
         g["n_max"] = max(g["n_max"], p.src.shape[1])

@@ -107,6 +107,8 @@ typedef struct {
   int n_fft_out;     /* number of inverse FFTs per evaluation (6)                  */
   int fft;           /* transforms: HSE_FFT_DF64 or HSE_FFT_CUFFT (see hse_plan_set_fft) */
   size_t grid_bytes; /* device bytes held by grids and tables                      */
+  int spread_tile[3];/* grid points along x, y, z that one warp of the spread owns   *
+                      * (one per lane; product 32), see hse_plan_set_spread_tile   */
 } hse_params;
 
 /*
@@ -263,6 +265,16 @@ hse_status hse_plan_set_overlap(hse_plan plan, int enable);
  * Fourier part share the SMs instead of running one after the other.
  * HSE_ERR_INVALID for blocks_per_sm outside [0, 64]. */
 hse_status hse_plan_set_real_residency(hse_plan plan, int blocks_per_sm);
+
+/* Shape of the grid tile one warp of the spread owns (Alg. 1 step 5: each
+ * lane sums the windows of the sources covering its grid point): wx x wy x wz
+ * points along x, y, z, each 1, 2, 4, 8 or 16 with wx wy wz = 32; a block of
+ * 8 warps owns 2wx x 2wy x 2wz points.  The default 2 x 4 x 4 suits large
+ * grids; the batch autotuner (hse_batch_create) picks the shape per group of
+ * instances.  Results change only by the rounding of the FP32 small-weight
+ * part of the spread (which weights take it depends on the tile), far below
+ * the plan's tolerance.  HSE_ERR_INVALID for any other shape. */
+hse_status hse_plan_set_spread_tile(hse_plan plan, int wx, int wy, int wz);
 
 /* Statistics of the last evaluation (synchronises on its last event when
  * timing is on).  out: host pointer. */

@@ -75,10 +75,16 @@ __global__ void k_batch_scatter(const InstDesc* __restrict__ d, int n_inst, int6
   }
 }
 
+// spread tiles the autotuner tries (warp sub-tile along x, y, z; the first is
+// the plans' default)
+constexpr int kTiles[][3] = {{2, 4, 4}, {4, 4, 2}, {2, 2, 8}, {4, 2, 4}};
+constexpr int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
+
 struct Bucket {
   int mask = 0;
   double xi = 0.0;
   int P = 0, M = 0;    // explicit support width and grid size (0: chosen from tol)
+  int tile = 0;        // spread tile (index into kTiles)
   double tol = 0.0;    // tolerance the plan was made for
   hse_plan plan = nullptr;
   hse::BatchFFT fft;  // batched transforms, per chunk size met so far
@@ -108,11 +114,13 @@ constexpr int kTuneSteps = 4;            // ladder steps tried in each direction
 // made for tol / kRefFactor (the library's own tighter evaluation)
 constexpr double kAcceptFrac = 0.4;
 constexpr double kRefFactor = 10.0;
+constexpr double kTileMargin = 0.97;
 
 // the autotuner's choice for a (mask, default level) group
 struct Choice {
   int level = 0;
   int P = 0, M = 0;  // 0: from tol
+  int tile = 0;      // index into kTiles
 };
 
 double ladder_xi(int k) { return std::exp2(k / 2.0); }
@@ -209,10 +217,11 @@ hse_status grow(hse_batch b, T** p, int64_t* cap, int64_t need, size_t esz) {
   return HSE_OK;
 }
 
-Bucket* get_bucket(hse_batch b, int mask, double xi, hse_status* st, int P = 0, int M = 0, double tol = 0.0) {
+Bucket* get_bucket(hse_batch b, int mask, double xi, hse_status* st, int P = 0, int M = 0, double tol = 0.0,
+                   int tile = 0) {
   if (tol <= 0.0) tol = b->tol;
   for (Bucket* k : b->buckets)
-    if (k->mask == mask && k->xi == xi && k->P == P && k->M == M && k->tol == tol) return k;
+    if (k->mask == mask && k->xi == xi && k->P == P && k->M == M && k->tol == tol && k->tile == tile) return k;
   Bucket* k = new (std::nothrow) Bucket();
   if (!k) {
     *st = berr(b, HSE_ERR_OOM, "host allocation");
@@ -223,8 +232,11 @@ Bucket* get_bucket(hse_batch b, int mask, double xi, hse_status* st, int P = 0, 
   k->P = P;
   k->M = M;
   k->tol = tol;
+  k->tile = tile;
   *st = hse_plan_create(mask, b->box, xi, 0.0, P, tol, b->precision, &k->plan);
   if (*st == HSE_OK && M > 0) *st = hse_plan_set_grid(k->plan, M);
+  if (*st == HSE_OK && tile > 0)
+    *st = hse_plan_set_spread_tile(k->plan, kTiles[tile][0], kTiles[tile][1], kTiles[tile][2]);
   if (*st != HSE_OK) {
     b->err = std::string("plan: ") + hse_last_error(k->plan);
     if (k->plan) hse_plan_destroy(k->plan);
@@ -268,7 +280,8 @@ Chunk next_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const int* id
   cap = std::min<int64_t>(cap, (int64_t(1) << 30) / ncells);
   // spread grid: z blocks = instances x z tiles of 8 (up to 7 points of the
   // first tile below z = 0 with double-float grids)
-  cap = std::min<int64_t>(cap, 65535 / ((2 * q.Mt + 14) / 8));
+  const int tz = 2 * q.spread_tile[2];  // z extent of a spread block
+  cap = std::min<int64_t>(cap, 65535 / ((2 * q.Mt + 2 * tz - 2) / tz));
   const int64_t max_particles = int64_t(1) << 28;
   Chunk c{idx, 0, 0};
   while (c.m < remaining && c.m < cap) {
@@ -581,6 +594,25 @@ hse_status refine_support_grid(hse_batch b, int mask, Choice* ch, double t_defau
       ch->M = pm.second;
     }
   }
+  // spread tile at the chosen (P, M): the sub-tile shape sets how many lanes
+  // of a warp fall outside a source's support and how many blocks cover a
+  // small grid's edges.  A shape replaces the default only when it is faster
+  // by kTileMargin (one timed pass per trial: the margin keeps timing noise
+  // from picking a shape)
+  best *= kTileMargin;
+  for (int tile = 1; tile < kNumTiles; ++tile) {
+    Bucket* k = get_bucket(b, mask, xi, &st, ch->P, ch->M, 0.0, tile);
+    if (!k) continue;
+    const int tz = 2 * kTiles[tile][2], mt = k->plan->prm.Mt;
+    if ((int64_t)((2 * mt + 2 * tz - 2) / tz) * c.m > 65535) continue;  // the trial chunk's z blocks
+    double t = 0.0, err = 0.0;
+    if (trial_bucket(b, k, inst, c, s, &t) != HSE_OK) continue;
+    if (chunk_error(b, c, s, &err) != HSE_OK) continue;
+    if (err <= kAcceptFrac * b->tol && t < best) {
+      best = t;
+      ch->tile = tile;
+    }
+  }
   b->err.clear();
   return HSE_OK;
 }
@@ -624,7 +656,7 @@ hse_status plan_group(hse_batch b, int mask, int level, const hse_instance* inst
   ch.level = level;
   auto it = b->tuned.find(key);
   if (it != b->tuned.end()) ch = it->second;
-  Bucket* k = get_bucket(b, mask, ladder_xi(ch.level), &st, ch.P, ch.M);
+  Bucket* k = get_bucket(b, mask, ladder_xi(ch.level), &st, ch.P, ch.M, 0.0, ch.tile);
   if (!k) return st;
   while (done < (int)idx.size()) {
     Chunk c = next_chunk(b, k, inst, idx.data() + done, (int)idx.size() - done);

@@ -214,9 +214,9 @@ struct SpreadArgs {
   int64_t is;            // batched instances: instance stride of out (blockIdx.z = inst * nz_tiles + tile)
   int ncells_inst;       // cells per instance in the cell list
   int64_t n_src;         // sorted particles (rows of spos32)
+  int wl[3];             // log2 of the warp sub-tile along x, y, z (hse_params.spread_tile)
 };
 
-constexpr int kTX = 4, kTY = 8, kTZ = 8;  // block tile; warps own 2 x 4 x 4 sub-tiles
 
 // two adjacent record elements with one load (8-byte elements: 16 bytes,
 // 4-byte elements: 8 bytes; record entries are aligned to two elements)
@@ -245,8 +245,9 @@ __device__ __forceinline__ void ldv(const T* p, T* out) {
 // grid D from derivative windows: DK bits 1 (W term), 2 (first derivatives),
 // 4 (second derivatives).
 //
-// Each warp owns a 2 x 4 x 4 sub-tile of the block's 4 x 8 x 8 tile (one
-// grid point per lane) and works alone, with no block-wide barrier: it scans
+// Each warp owns a wx x wy x wz sub-tile (one grid point per lane; 2 x 4 x 4
+// unless the plan sets another shape) of the block's 2wx x 2wy x 2wz tile (8
+// warps, 2 per dimension) and works alone, with no block-wide barrier: it scans
 // the cell-list rows whose sources can reach its sub-tile, 32 candidates at a
 // time (one per lane: does the support cover the sub-tile, and is every weight
 // on it below the FP32 threshold), compacts the hits into a warp-private list
@@ -271,9 +272,11 @@ __global__ void __launch_bounds__(256, spread_min_blocks<T, NC, DK>()) k_spread(
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int inst = blockIdx.z / a.nz_tiles, ztile = blockIdx.z - inst * a.nz_tiles;
   const int cbase = inst * a.ncells_inst;
-  const int bx0 = kTX * blockIdx.x, by0 = kTY * blockIdx.y, bz0 = a.z0 + kTZ * ztile;
-  const int sx = bx0 + 2 * (w & 1), sy = by0 + 4 * ((w >> 1) & 1), sz = bz0 + 4 * (w >> 2);
-  const int px = sx + (lane & 1), py = sy + ((lane >> 1) & 3), pz = sz + (lane >> 3);
+  const int lx = a.wl[0], ly = a.wl[1], lz = a.wl[2];
+  const int wx = 1 << lx, wy = 1 << ly, wz = 1 << lz;  // warp sub-tile
+  const int bx0 = (2 * wx) * blockIdx.x, by0 = (2 * wy) * blockIdx.y, bz0 = a.z0 + (2 * wz) * ztile;
+  const int sx = bx0 + wx * (w & 1), sy = by0 + wy * ((w >> 1) & 1), sz = bz0 + wz * (w >> 2);
+  const int px = sx + (lane & (wx - 1)), py = sy + ((lane >> lx) & (wy - 1)), pz = sz + (lane >> (lx + ly));
   const int P = a.P;
   // per-particle record (rec_layout): x entries {wx, XX_0..}, y entries
   // {wy, wy', wy''}, z entries {wz, wz', wz''}, then the NC components
@@ -295,13 +298,13 @@ __global__ void __launch_bounds__(256, spread_min_blocks<T, NC, DK>()) k_spread(
     c1 = cell_coord(hi, a.inv_cell[d], a.ncell[d]);
   };
   int cx0, cx1, cy0, cy1, cz0, cz1;
-  cell_range(sx, sx + 1, a.ox, 0, cx0, cx1);
-  cell_range(sy, sy + 3, a.ox, 1, cy0, cy1);
-  cell_range(sz, sz + 3, a.oz, 2, cz0, cz1);
+  cell_range(sx, sx + wx - 1, a.ox, 0, cx0, cx1);
+  cell_range(sy, sy + wy - 1, a.ox, 1, cy0, cy1);
+  cell_range(sz, sz + wz - 1, a.oz, 2, cz0, cz1);
   const int nx = a.ncell[0], ny = a.ncell[1];
   const unsigned below = (1u << lane) - 1;
   int4* list = wlist[w];
-  if (sz + 4 <= a.zlo) cz1 = cz0 - 1;  // no support reaches the sub-tile: zeros only
+  if (sz + wz <= a.zlo) cz1 = cz0 - 1;  // no support reaches the sub-tile: zeros only
   for (int cz = cz0; cz <= cz1; ++cz)
     for (int cy = cy0; cy <= cy1; ++cy) {
       const int c0 = cbase + (cz * ny + cy) * nx + cx0;
@@ -316,15 +319,15 @@ __global__ void __launch_bounds__(256, spread_min_blocks<T, NC, DK>()) k_spread(
         int4 sp = make_int4(0, 0, 0, 0);
         if (j < s1) {
           sp = a.supp[j];
-          hit = sp.x <= sx + 1 && sp.x + P - 1 >= sx && sp.y <= sy + 3 && sp.y + P - 1 >= sy && sp.z <= sz + 3 &&
-                sp.z + P - 1 >= sz;
+          hit = sp.x <= sx + wx - 1 && sp.x + P - 1 >= sx && sp.y <= sy + wy - 1 && sp.y + P - 1 >= sy &&
+                sp.z <= sz + wz - 1 && sp.z + P - 1 >= sz;
           if (hit && split) {
             const int64_t n = a.n_src;
             const float gx = (a.spos32[j] - oxf) * inv_h, gy = (a.spos32[n + j] - oxf) * inv_h;
             const float gz = (a.spos32[2 * n + j] - ozf) * inv_h;
-            const float ex = fmaxf(0.f, fmaxf(fsx - gx, gx - (fsx + 1.f)) - 0.5f);
-            const float ey = fmaxf(0.f, fmaxf(fsy - gy, gy - (fsy + 3.f)) - 0.5f);
-            const float ez = fmaxf(0.f, fmaxf(fsz - gz, gz - (fsz + 3.f)) - 0.5f);
+            const float ex = fmaxf(0.f, fmaxf(fsx - gx, gx - (fsx + (float)(wx - 1))) - 0.5f);
+            const float ey = fmaxf(0.f, fmaxf(fsy - gy, gy - (fsy + (float)(wy - 1))) - 0.5f);
+            const float ez = fmaxf(0.f, fmaxf(fsz - gz, gz - (fsz + (float)(wz - 1))) - 0.5f);
             small = a.ah2 * (ex * ex + ey * ey + ez * ez) >= a.lnthr;
           }
         }
@@ -839,7 +842,13 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   // full_z: tiles on the same z boundaries as from zA0, extended down to the
   // first tile at or below 0 (the same warp sub-tiles, so the same FP32 /
   // higher-precision split of the small weights as without full_z)
-  a.z0 = full_z ? p->zA0 - ((p->zA0 + kTZ - 1) / kTZ) * kTZ : p->zA0;
+  const int tx = 2 * q.spread_tile[0], ty = 2 * q.spread_tile[1], tz = 2 * q.spread_tile[2];  // block tile
+  for (int d = 0; d < 3; ++d) {
+    int l = 0;
+    while ((1 << l) < q.spread_tile[d]) ++l;
+    a.wl[d] = l;
+  }
+  a.z0 = full_z ? p->zA0 - ((p->zA0 + tz - 1) / tz) * tz : p->zA0;
   a.zlo = p->zA0;
   a.h = q.h;
   a.ox = pa.ox;
@@ -852,8 +861,8 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.is = istride;
   a.ncells_inst = q.ncell[0] * q.ncell[1] * q.ncell[2];
   int nzr = 2 * q.Mt - a.z0;
-  a.nz_tiles = (nzr + kTZ - 1) / kTZ;
-  dim3 grid((q.Mt + kTX - 1) / kTX, (q.Mt + kTY - 1) / kTY, a.nz_tiles * n_inst);
+  a.nz_tiles = (nzr + tz - 1) / tz;
+  dim3 grid((q.Mt + tx - 1) / tx, (q.Mt + ty - 1) / ty, a.nz_tiles * n_inst);
   const int dk = paper ? 0 : deriv_kind(q.kernel_mask);
   const int nplain = dk ? cs.n - 1 : cs.n;  // the product set's last component is D
   if (!launch_spread<T>(nplain, dk, a, grid, s))

@@ -584,6 +584,9 @@ extern "C" hse_status hse_plan_create(int kernel_mask, const double box[3], doub
   hse_params& q = p->prm;
   q.kernel_mask = kernel_mask;
   q.precision = precision;
+  q.spread_tile[0] = 2;
+  q.spread_tile[1] = 4;
+  q.spread_tile[2] = 4;
   p->tol = tol;
   for (int d = 0; d < 3; ++d) q.box[d] = box[d];
   q.L = std::fmax(box[0], std::fmax(box[1], box[2]));
@@ -658,6 +661,17 @@ extern "C" hse_status hse_plan_set_fft(hse_plan p, int mode) {
   else HSE_TRY(build_cufft(p));
   p->prm.fft = f;
   p->prm.grid_bytes += p->fft_work_bytes - work_before;  // a cuFFT work area made now
+  return HSE_OK;
+}
+
+extern "C" hse_status hse_plan_set_spread_tile(hse_plan p, int wx, int wy, int wz) {
+  if (!p) return HSE_ERR_INVALID;
+  auto pow2 = [](int v) { return v >= 1 && v <= 16 && (v & (v - 1)) == 0; };
+  if (!pow2(wx) || !pow2(wy) || !pow2(wz) || wx * wy * wz != 32)
+    return set_err(p, HSE_ERR_INVALID, "spread tile %d x %d x %d (powers of two up to 16, product 32)", wx, wy, wz);
+  p->prm.spread_tile[0] = wx;
+  p->prm.spread_tile[1] = wy;
+  p->prm.spread_tile[2] = wz;
   return HSE_OK;
 }
 

@@ -76,7 +76,7 @@ enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2, Q_FAR = 4 };  // Q_FAR: flag on FREE
 constexpr int kWarpsPerBlock = 4;
 constexpr int kQueue = 64;
 constexpr int kErfcxN = HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1);
-constexpr int kTabN = kErfcxN + 64;  // erfcx intervals, then 2^{j/64}
+constexpr int kTabN = kErfcxN + 64 + HSE_ERFCX_NINT;  // erfcx intervals, 2^{j/64}, interval centres
 
 // e^{-x} for 0 <= x (Tang's table-driven method, ACM TOMS 15, 1989):
 // -x = m ln2/64 + r, |r| <= ln2/128, m = 64 n + j, e^{-x} = 2^n 2^{j/64} e^r,
@@ -103,7 +103,9 @@ __device__ __forceinline__ double erfcx_tab(double t, float tf, const double* ta
   int k = (int)(tf * (float)HSE_ERFCX_INV_WIDTH);
   k = k < 0 ? 0 : (k > HSE_ERFCX_NINT - 1 ? HSE_ERFCX_NINT - 1 : k);
   const double* c = tab + k * (HSE_ERFCX_DEG + 1);
-  double u = fma(2.0 * HSE_ERFCX_INV_WIDTH, t, -(double)(2 * k + 1));
+  // centre 2k + 1 of the interval in units of half its width, from the table
+  // (an int -> double conversion would take an FP64 instruction)
+  double u = fma(2.0 * HSE_ERFCX_INV_WIDTH, t, -tab[kErfcxN + 64 + k]);
   double p = c[HSE_ERFCX_DEG];
 #pragma unroll
   for (int j = HSE_ERFCX_DEG - 1; j >= 0; --j) p = fma(p, u, c[j]);
@@ -226,90 +228,115 @@ __device__ __forceinline__ void load_src(const RealArgs& a, const T* str, int64_
 
 // free-space contribution of source s at r = x - y (sgn_odd = -1 gives the
 // contribution at the source's position from the target's strengths when the
-// roles are swapped: S is even in r, T and W odd)
+// roles are swapped: S is even in r, T and W odd).  Written as chains of
+// multiply-adds into u: the FP64 pipe bounds the real-space kernel, and an
+// unfused product and sum take two of its instructions.
 template <typename T>
 __device__ __forceinline__ void add_free(int mask, const Radial<T>& R, const T* r, const Src<T>& s, T xi, T sgn_odd,
                                          T* u) {
   if (mask & HSE_STOKESLET) {
-    T sa = R.er - R.c;
-    T rf = r[0] * s.f[0] + r[1] * s.f[1] + r[2] * s.f[2];
+    // (er - c) f + a1 r (r.f)
+    const T sa = R.er - R.c;
+    const T rf = fma(r[2], s.f[2], fma(r[1], s.f[1], r[0] * s.f[0]));
     const T arf = R.a1 * rf;
-    for (int i = 0; i < 3; ++i) u[i] += sa * s.f[i] + arf * r[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[i] = fma(arf, r[i], fma(sa, s.f[i], u[i]));
   }
   if (mask & HSE_STRESSLET) {
-    // ta r (r.g)(r.q) + tb (g (r.q) + q (r.g) + r (g.q)) as coefficients of r, g, q
-    T ta = -2 * R.g2, tb = 2 * xi * xi * R.c;
-    T rg = r[0] * s.g[0] + r[1] * s.g[1] + r[2] * s.g[2];
-    T rq = r[0] * s.q[0] + r[1] * s.q[1] + r[2] * s.q[2];
-    T gq = s.g[0] * s.q[0] + s.g[1] * s.q[1] + s.g[2] * s.q[2];
-    const T cr = sgn_odd * (ta * rg * rq + tb * gq), cg = sgn_odd * (tb * rq), cq = sgn_odd * (tb * rg);
-    for (int i = 0; i < 3; ++i) u[i] += cr * r[i] + cg * s.g[i] + cq * s.q[i];
+    // ta r (r.g)(r.q) + tb (g (r.q) + q (r.g) + r (g.q)), ta = -2 g2, tb = 2 xi^2 c,
+    // as coefficients of r, g, q
+    const T tb = (sgn_odd * 2 * xi * xi) * R.c;
+    const T rg = fma(r[2], s.g[2], fma(r[1], s.g[1], r[0] * s.g[0]));
+    const T rq = fma(r[2], s.q[2], fma(r[1], s.q[1], r[0] * s.q[0]));
+    const T gq = fma(s.g[2], s.q[2], fma(s.g[1], s.q[1], s.g[0] * s.q[0]));
+    const T cr = fma((sgn_odd * -2) * R.g2 * rg, rq, tb * gq), cg = tb * rq, cq = tb * rg;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[i] = fma(cr, r[i], fma(cg, s.g[i], fma(cq, s.q[i], u[i])));
   }
   if (mask & HSE_ROTLET) {
-    T wa = sgn_odd * 2 * R.a1;
-    u[0] += wa * (s.tau[1] * r[2] - s.tau[2] * r[1]);
-    u[1] += wa * (s.tau[2] * r[0] - s.tau[0] * r[2]);
-    u[2] += wa * (s.tau[0] * r[1] - s.tau[1] * r[0]);
+    // 2 a1 tau x r
+    const T wa = (sgn_odd * 2) * R.a1;
+    const T w0 = wa * s.tau[0], w1 = wa * s.tau[1], w2 = wa * s.tau[2];
+    u[0] = fma(w1, r[2], fma(-w2, r[1], u[0]));
+    u[1] = fma(w2, r[0], fma(-w0, r[2], u[1]));
+    u[2] = fma(w0, r[1], fma(-w1, r[0], u[2]));
   }
 }
 
 // image contribution at a target of height x3 from source s of height h,
 // rt = x - y^I.  The wall corrections' gradient is collected as
 // grad(phi) = ar r + gv (one coefficient of r shared by every kernel, plus the
-// strength-vector terms), which the final u -= x3 grad(phi) applies once.
+// strength-vector terms), which the final u -= x3 grad(phi) applies once;
+// phi, ar and gv are accumulated at half their values (the kernels'
+// corrections carry factors 2 and 4) and doubled once.
 template <typename T>
 __device__ __forceinline__ void add_image(int mask, const Radial<T>& R, const T* r, T h, T x3, const Src<T>& s, T xi,
                                           T* u) {
-  const T g1 = -R.a1, g2 = R.g2;
-  T phi = 0, ar = 0, gv[3] = {0, 0, 0};
+  const T a1 = R.a1, g2 = R.g2;  // g1 = -a1 (gradient coefficient of G_R)
+  T phi = 0, ar = 0, gv0 = 0, gv1 = 0, gv2 = 0;  // halves
   if (mask & HSE_STOKESLET) {
-    // grad phi_S = 2 (-f3 g1 r - h (g1 fI + g2 r (r.fI)))
-    T fI[3] = {s.f[0], s.f[1], -s.f[2]};
-    T sa = R.er - R.c;
-    T rf = r[0] * fI[0] + r[1] * fI[1] + r[2] * fI[2];
-    const T arf = R.a1 * rf;
-    for (int i = 0; i < 3; ++i) u[i] -= sa * fI[i] + arf * r[i];
-    const T hg1 = h * g1;
-    phi += 2 * (-s.f[2] * R.er - hg1 * rf);
-    ar -= 2 * (s.f[2] * g1 + h * g2 * rf);
-    const T cf = -2 * hg1;
-    for (int i = 0; i < 3; ++i) gv[i] += cf * fI[i];
+    // -S^R(rt) f^I, f^I = (f1, f2, -f3)
+    const T sa = R.er - R.c;
+    const T rf = fma(-r[2], s.f[2], fma(r[1], s.f[1], r[0] * s.f[0]));  // rt . f^I
+    const T arf = a1 * rf;
+    u[0] = fma(-arf, r[0], fma(-sa, s.f[0], u[0]));
+    u[1] = fma(-arf, r[1], fma(-sa, s.f[1], u[1]));
+    u[2] = fma(-arf, r[2], fma(sa, s.f[2], u[2]));
+    // phi_S = 2 (-f3 G_R - h grad G_R . f^I) = 2 (h a1 rf - f3 er),
+    // grad phi_S = 2 (f3 a1 r + h a1 f^I - h g2 rf r)
+    const T ha = h * a1;
+    phi = fma(ha, rf, -(s.f[2] * R.er));
+    ar = fma(-(h * g2), rf, s.f[2] * a1);
+    gv0 = ha * s.f[0];
+    gv1 = ha * s.f[1];
+    gv2 = -ha * s.f[2];
   }
   if (mask & HSE_STRESSLET) {
-    T gI[3] = {s.g[0], s.g[1], -s.g[2]}, qI[3] = {s.q[0], s.q[1], -s.q[2]};
-    T ta = -2 * R.g2, tb = 2 * xi * xi * R.c;
-    T rg = r[0] * gI[0] + r[1] * gI[1] + r[2] * gI[2];
-    T rq = r[0] * qI[0] + r[1] * qI[1] + r[2] * qI[2];
-    T gq = gI[0] * qI[0] + gI[1] * qI[1] + gI[2] * qI[2];
-    const T cr = ta * rg * rq + tb * gq, cg = tb * rq, cq = tb * rg;
-    for (int i = 0; i < 3; ++i) u[i] -= cr * r[i] + cg * gI[i] + cq * qI[i];
-    // phi_T = 4 (gI.qI) d3G - 4 h gI.(grad grad G) qI; its gradient
-    // 4 gq (g1 e3 + g2 r3 r) - 4 h (g2 (gq r + gI rq + qI rg) + g3 rg rq r)
-    phi += 4 * gq * g1 * r[2] - 4 * h * (g1 * gq + g2 * rg * rq);
-    ar += 4 * (gq * g2 * r[2] - h * (g2 * gq + R.g3 * rg * rq));
-    const T h4g2 = -4 * h * g2;
-    const T dg = h4g2 * rq, dq = h4g2 * rg;
-    for (int i = 0; i < 3; ++i) gv[i] += dg * gI[i] + dq * qI[i];
-    gv[2] += 4 * gq * g1;
+    // -T^R(rt)(g^I q^I)
+    const T tb = (2 * xi * xi) * R.c;
+    const T gI2 = -s.g[2], qI2 = -s.q[2];
+    const T rg = fma(r[2], gI2, fma(r[1], s.g[1], r[0] * s.g[0]));
+    const T rq = fma(r[2], qI2, fma(r[1], s.q[1], r[0] * s.q[0]));
+    const T gq = fma(gI2, qI2, fma(s.g[1], s.q[1], s.g[0] * s.q[0]));
+    const T g2rg = g2 * rg;
+    const T cr = fma(-2 * g2rg, rq, tb * gq), cg = tb * rq, cq = tb * rg;
+    u[0] = fma(-cr, r[0], fma(-cg, s.g[0], fma(-cq, s.q[0], u[0])));
+    u[1] = fma(-cr, r[1], fma(-cg, s.g[1], fma(-cq, s.q[1], u[1])));
+    u[2] = fma(-cr, r[2], fma(-cg, gI2, fma(-cq, qI2, u[2])));
+    // phi_T = 4 (gI.qI) d3 G_R - 4 h gI.(grad grad G_R) qI; halves:
+    //   phi/2 = -2 gq a1 r3 - 2 h (g2 rg rq - a1 gq)
+    //   (grad phi)/2 = 2 gq (g2 r3 r - a1 e3) - 2 h (g2 (gq r + gI rq + qI rg) + g3 rg rq r)
+    const T gq2 = gq + gq, h2 = h + h;
+    const T ga = gq2 * a1;
+    phi = fma(-ga, r[2], fma(-h2, fma(g2rg, rq, -a1 * gq), phi));
+    ar = fma(gq2 * g2, r[2], fma(-h2, fma(g2, gq, R.g3 * rg * rq), ar));
+    const T hg = -h2 * g2;
+    const T dg = hg * rq, dq = hg * rg;
+    gv0 = fma(dg, s.g[0], fma(dq, s.q[0], gv0));
+    gv1 = fma(dg, s.g[1], fma(dq, s.q[1], gv1));
+    gv2 = fma(dg, gI2, fma(dq, qI2, gv2 - ga));
   }
   if (mask & HSE_ROTLET) {
-    T tI[3] = {s.tau[0], s.tau[1], -s.tau[2]};
-    T wa = 2 * R.a1;
-    u[0] += wa * (tI[1] * r[2] - tI[2] * r[1]);
-    u[1] += wa * (tI[2] * r[0] - tI[0] * r[2]);
-    u[2] += wa * (tI[0] * r[1] - tI[1] * r[0]);
-    // grad phi_W = 4 (g1 v + g2 r (r.v)), v = (-tau2, tau1, 0)
-    T v0 = -s.tau[1], v1 = s.tau[0];
-    T rv = r[0] * v0 + r[1] * v1;
-    phi += 4 * g1 * rv;
-    ar += 4 * g2 * rv;
-    const T g14 = 4 * g1;
-    gv[0] += g14 * v0;
-    gv[1] += g14 * v1;
+    // +W^R(rt) tau^I = 2 a1 tau^I x rt, tau^I = (tau1, tau2, -tau3)
+    const T wa = 2 * a1;
+    const T w0 = wa * s.tau[0], w1 = wa * s.tau[1], w2 = -wa * s.tau[2];
+    u[0] = fma(w1, r[2], fma(-w2, r[1], u[0]));
+    u[1] = fma(w2, r[0], fma(-w0, r[2], u[1]));
+    u[2] = fma(w0, r[1], fma(-w1, r[0], u[2]));
+    // phi_W = 4 g1 (rt.v), grad phi_W = 4 (g1 v + g2 rt (rt.v)), v = (-tau2, tau1, 0);
+    // halves: -wa rv, wa... : g1 v / 2 * 4 = -wa v
+    const T rv = fma(r[1], s.tau[0], -r[0] * s.tau[1]);
+    phi = fma(-wa, rv, phi);
+    ar = fma(g2 + g2, rv, ar);
+    gv0 += w1;   // -wa v0 = wa tau2
+    gv1 -= w0;   // -wa v1 = -wa tau1
   }
-  const T xa = x3 * ar;
-  for (int i = 0; i < 3; ++i) u[i] -= xa * r[i] + x3 * gv[i];
-  u[2] += phi;
+  // u -= x3 grad(phi) = x3 (ar r + gv); u3 += phi (both from their halves)
+  const T xd = x3 + x3;
+  const T xa = xd * ar;
+  u[0] = fma(-xa, r[0], fma(-xd, gv0, u[0]));
+  u[1] = fma(-xa, r[1], fma(-xd, gv1, u[1]));
+  u[2] = fma(-xa, r[2], fma(-xd, gv2, u[2] + (phi + phi)));
 }
 
 // Target position in the arithmetic type of the pair evaluation.  FP32 keeps
@@ -442,7 +469,8 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
 }
 
 __device__ __forceinline__ void load_table(double* tab) {
-  for (int i = threadIdx.x; i < kTabN; i += blockDim.x) tab[i] = i < kErfcxN ? d_erfcx_coef[i] : d_exp2_j64[i - kErfcxN];
+  for (int i = threadIdx.x; i < kTabN; i += blockDim.x)
+    tab[i] = i < kErfcxN ? d_erfcx_coef[i] : i < kErfcxN + 64 ? d_exp2_j64[i - kErfcxN] : (double)(2 * (i - kErfcxN - 64) + 1);
   __syncthreads();
 }
 
@@ -550,8 +578,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
 // distance^2 >= far2) are queued separately and evaluated in FP32 -- their
 // screened kernels are small, so FP32 rounding stays far below the truncation
 // error -- with the partner's share sent by one float4 atomic into a.out4.
+// Resident blocks per SM the FP64 symmetric kernel is compiled for: 4 (128
+// registers) where the pair arithmetic fits without spilling, which keeps 16
+// warps per SM issuing to the FP64 pipe; the stokeslet + stresslet masks need
+// more registers (3 blocks, up to 170).
 template <typename T, int KM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_sym(RealArgs a) {
+constexpr int real_min_blocks() {
+  return sizeof(T) == 8 ? (KM != 3 && KM != 7 ? 4 : 3) : 1;
+}
+
+template <typename T, int KM>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>()) k_real_sym(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
   __shared__ int queue_far[kWarpsPerBlock][kQueue];
   __shared__ double tab[kTabN];

@@ -28,7 +28,7 @@ class hse_params(ctypes.Structure):
         ("P", ctypes.c_int),
         ("M", ctypes.c_int), ("Mt", ctypes.c_int), ("h", ctypes.c_double), ("eta", ctypes.c_double),
         ("ncell", ctypes.c_int * 3), ("n_fft_in", ctypes.c_int), ("n_fft_out", ctypes.c_int),
-        ("fft", ctypes.c_int), ("grid_bytes", ctypes.c_size_t),
+        ("fft", ctypes.c_int), ("grid_bytes", ctypes.c_size_t), ("spread_tile", ctypes.c_int * 3),
     ]
 
     def as_dict(self):
@@ -99,7 +99,7 @@ class HseError(RuntimeError):
 _lib = None
 _NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_set_fft", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
-          "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_plan_set_real_residency", "hse_get_eval_stats", "hse_cell_list_noalloc",
+          "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_plan_set_real_residency", "hse_plan_set_spread_tile", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
           "hse_server_reset_stats", "hse_server_destroy", "hse_server_error_text", "hse_server_prewarm",
           "hse_server_request_params", "hse_batch_create",
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH):
     L.hse_plan_set_timing.argtypes = [vp, ctypes.c_int]
     L.hse_plan_set_overlap.argtypes = [vp, ctypes.c_int]
     L.hse_plan_set_real_residency.argtypes = [vp, ctypes.c_int]
+    L.hse_plan_set_spread_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hse_server_create.argtypes = [ctypes.POINTER(hse_server_config), ctypes.POINTER(vp)]
     L.hse_server_submit.argtypes = [vp, ctypes.POINTER(hse_request), ctypes.POINTER(ctypes.c_uint64)]
     L.hse_server_poll.argtypes = [vp, ctypes.c_uint64]
@@ -243,6 +244,10 @@ def hse_plan_set_overlap(plan, enable):
 
 def hse_plan_set_real_residency(plan, blocks_per_sm):
     _check(load().hse_plan_set_real_residency(plan, int(blocks_per_sm)), plan)
+
+
+def hse_plan_set_spread_tile(plan, wx, wy, wz):
+    _check(load().hse_plan_set_spread_tile(plan, int(wx), int(wy), int(wz)), plan)
 
 
 def hse_get_eval_stats(plan) -> dict:
@@ -575,6 +580,10 @@ class Plan:
 
     def set_real_residency(self, blocks_per_sm):
         hse_plan_set_real_residency(self.handle, blocks_per_sm)
+
+    def set_spread_tile(self, wx, wy, wz):
+        hse_plan_set_spread_tile(self.handle, wx, wy, wz)
+        self.params = hse_plan_get_params(self.handle)
 
     def stats(self):
         return hse_get_eval_stats(self.handle)

@@ -137,7 +137,11 @@ def test_batch_autotune_meets_tolerance(pkg):
             assert u["rc"] == plan.params["rc"]
         finally:
             plan.close()
-    print("autotuned (xi, P, M):", sorted({(u["xi"], u["P"], u["M"]) for u in used}),
+    # the spread tile is one of the shapes the tuner tries; the untuned batch keeps the default
+    tiles = {(2, 4, 4), (4, 4, 2), (2, 2, 8), (4, 2, 4)}
+    assert all(tuple(u["spread_tile"]) in tiles for u in used)
+    assert all(tuple(d["spread_tile"]) == (2, 4, 4) for d in default)
+    print("autotuned (xi, P, M, tile):", sorted({(u["xi"], u["P"], u["M"], tuple(u["spread_tile"])) for u in used}),
           "defaults:", sorted({(d["xi"], d["P"], d["M"]) for d in default}))
     for i, (pr, u, u2) in enumerate(zip(probs, outs, outs2)):
         u, u2 = u.cpu().numpy(), u2.cpu().numpy()
@@ -159,7 +163,8 @@ def test_batch_autotune_mixed_meets_tolerance_per_instance(pkg):
     finally:
         b.close()
     errs = [_oracle_check(pr, u.cpu().numpy(), 1e-5) for pr, u in zip(probs, outs)]
-    print("mixed autotuned (xi, P, M):", sorted({(u["xi"], u["P"], u["M"]) for u in used}),
+    print("mixed autotuned (xi, P, M, tile):",
+          sorted({(u["xi"], u["P"], u["M"], tuple(u["spread_tile"])) for u in used}),
           "worst error / tol", max(errs) / 1e-5)
     assert max(errs) < 1e-5
 

@@ -94,6 +94,50 @@ def test_spread_grids_match_oracle(pkg, mask):
     plan.close()
 
 
+TILES = [(2, 4, 4), (4, 4, 2), (2, 2, 8), (4, 2, 4), (1, 4, 8), (8, 4, 1), (16, 2, 1), (1, 2, 16)]
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_spread_grids_any_tile(pkg, tile):
+    """Every warp sub-tile shape of the spread gives the oracle's grids (the
+    shape only moves work between lanes and blocks); M = 17 leaves ragged
+    edges for every shape."""
+    mask = KERNEL_S | KERNEL_T | KERNEL_W
+    pr = problem(mask, 150, 1.0, "near_wall", 33)
+    xi, M, P = 5.0, 17, 12
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=xi, rc=0.6, P=P, tol=0.0, M=M)
+    plan.set_spread_tile(*tile)
+    assert tuple(plan.params["spread_tile"]) == tile
+    g = host(plan.spread_grids(dev(pr.src), dev(pr.strengths)))
+    h, Mt, _ = se.geometry(1.0, M, P, xi)
+    ref = oracle.spread(mask, pr.src, pr.strengths, xi, h, P, Mt)
+    assert rel_max(g, ref) < 1e-13
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_eval_any_tile_equals_default(pkg, prec):
+    """A full evaluation with another spread tile equals the default-tile one
+    up to the rounding of the FP32 small-weight part; invalid shapes are
+    rejected."""
+    mask = KERNEL_S | KERNEL_W
+    pr = problem(mask, 20000, 1.0, "near_wall", 38)
+    mixed = prec == "mixed"
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=30.0, rc=0.0, P=0, tol=1e-5 if mixed else 1e-10,
+                    precision=pkg.HSE_MIXED if mixed else pkg.HSE_FP64)
+    src, st = dev(pr.src), dev(pr.strengths)
+    base = host(plan.eval(src, st))
+    for tile in [(4, 4, 2), (2, 2, 8), (8, 2, 2)]:
+        plan.set_spread_tile(*tile)
+        u = host(plan.eval(src, st))
+        assert oracle.rel_rms(u, base) < (1e-6 if mixed else 1e-12)
+    for bad in [(3, 4, 4), (2, 4, 8), (32, 1, 1), (0, 8, 4), (2, 4, -4)]:
+        with pytest.raises(pkg.HseError):
+            plan.set_spread_tile(*bad)
+    assert tuple(plan.params["spread_tile"]) == (8, 2, 2)
+    plan.close()
+
+
 # ------------------------------------------------------- real space (Sec. 5.1)
 @pytest.mark.parametrize("mask", MASKS)
 @pytest.mark.parametrize("dist", ["uniform", "near_wall"])
