@@ -57,6 +57,8 @@ struct RealArgs {
   int mask, rowS, rowT, rowW;
   double xi, rc2, rc;
   float rc2_lo, rc2_hi;    // FP32 screening thresholds
+  float cull2;             // rows of cells farther than sqrt(cull2) (> r_c by a safety margin) are skipped
+  float cell_side[3];      // L_d / ncell_d
   float img64_2;           // FP32 path: image pairs closer than this (squared) are evaluated in FP64
   float far2;              // FP64 symmetric kernel: pairs with FP32 distance^2 >= far2 take the
                            // FP32 evaluation (0: none)
@@ -128,7 +130,8 @@ __device__ __forceinline__ float approx_float(double v) {
 // FP64: own exp and erfcx table.  The table interval and the range tests use
 // FP32 copies of t (t < 12 on the table; e^{-t^2} needs t < 26), so that the
 // FP64 pipe only does the arithmetic.
-__device__ __forceinline__ Radial<double> radial(double s, float sf, double xi, const double* tab, bool need_g3) {
+__device__ __forceinline__ Radial<double> radial(double s, float sf, double xi, const double* tab, const float*,
+                                                 bool need_g3) {
   Radial<double> R;
   double inv = rsqrt(s);
   double t = xi * s * inv;
@@ -146,13 +149,29 @@ __device__ __forceinline__ Radial<double> radial(double s, float sf, double xi, 
   return R;
 }
 
-// FP32 (mixed precision): the FP32 pipe is ~60x the FP64 one on GB300
-__device__ __forceinline__ Radial<float> radial(float s, float, float xi, const double*, bool need_g3) {
+// erfcx(t) in FP32 from the float copy of the interval table (t in [0, 12));
+// t - c_k is exact (c_k = (2k + 1)/16 has few bits and lies within a factor 2
+// of t), so u carries only t's own rounding
+__device__ __forceinline__ float erfcx_tab32(float t, const float* tab) {
+  int k = (int)(t * (float)HSE_ERFCX_INV_WIDTH);
+  k = k < 0 ? 0 : (k > HSE_ERFCX_NINT - 1 ? HSE_ERFCX_NINT - 1 : k);
+  const float* c = tab + k * (HSE_ERFCX_DEG + 1);
+  const float u = (t - (float)(2 * k + 1) * (0.5f / HSE_ERFCX_INV_WIDTH)) * (2.0f * HSE_ERFCX_INV_WIDTH);
+  float p = c[HSE_ERFCX_DEG];
+#pragma unroll
+  for (int j = HSE_ERFCX_DEG - 1; j >= 0; --j) p = fmaf(p, u, c[j]);
+  return p;
+}
+
+// FP32 (mixed precision): the FP32 pipe is ~60x the FP64 one on GB300;
+// erfc(t) = e^{-t^2} erfcx(t) with erfcx from the FP32 table tab32
+__device__ __forceinline__ Radial<float> radial(float s, float, float xi, const double*, const float* tab32,
+                                                bool need_g3) {
   Radial<float> R;
   float inv = rsqrtf(s);
   float t = xi * s * inv;
   float E = expf(-t * t);
-  float ec = erfcf(t);
+  float ec = t < 11.99f ? E * erfcx_tab32(t, tab32) : erfcf(t);
   float i2 = inv * inv;
   R.c = (float)(2.0 / kSqrtPi) * xi * E;
   R.er = ec * inv;
@@ -178,7 +197,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // e^{-zh} (1 - zl), and erfc(t) = e^{-t^2} erfcx(t), where erfcx varies slowly
 // (its relative error stays that of t).  ~1e-7 per term.
 __device__ __forceinline__ Radial<float> radial_shell(const float* dh, const float* dl, float xi, float xi2h,
-                                                      float xi2l, bool need_g3) {
+                                                      float xi2l, bool need_g3, const float* tab32) {
   float p[3], q[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -199,7 +218,7 @@ __device__ __forceinline__ Radial<float> radial_shell(const float* dh, const flo
   Radial<float> R;
   const float i2 = inv * inv;
   R.c = (float)(2.0 / kSqrtPi) * xi * E;
-  R.er = E * erfcxf(t) * inv;
+  R.er = E * erfcx_tab32(t, tab32) * inv;
   R.a1 = (R.er + R.c) * i2;
   R.g2 = i2 * fmaf(3.0f, R.a1, 2.0f * xi * xi * R.c);
   R.g3 = need_g3 ? -i2 * fmaf(5.0f, R.g2, 4.0f * xi * xi * xi * xi * R.c) : 0.0f;
@@ -419,10 +438,32 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
     int z0 = pass == 0 ? (cz > R - 1 ? cz - R : 0) : 0;
     int z1 = pass == 0 ? (cz < nz - R ? cz + R : nz - 1) : czi_hi;
     int jmin = pass == 0 ? free_min : img_min;
-    for (int iz = z0; iz <= z1; ++iz)
+    for (int iz = z0; iz <= z1; ++iz) {
+      // rows of cells whose box lies beyond the cut-off are skipped, and each
+      // row's end cells likewise (box distances in FP32 against a cut-off
+      // widened by 1e-5 L, so no pair within r_c is lost); the image pass
+      // measures to the mirrored layer
+      const float zl = (float)iz * a.cell_side[2], zh = zl + a.cell_side[2];
+      const float dzc = pass == 0 ? fmaxf(0.f, fmaxf(zl - xf[2], xf[2] - zh)) : xf[2] + zl;
+      const float rz = a.cull2 - dzc * dzc;
+      if (!(rz > 0.f)) continue;
       for (int iy = (cy > R - 1 ? cy - R : 0); iy <= (cy < ny - R ? cy + R : ny - 1); ++iy) {
+        const float yl = (float)iy * a.cell_side[1], yh = yl + a.cell_side[1];
+        const float dyc = fmaxf(0.f, fmaxf(yl - xf[1], xf[1] - yh));
+        const float rem = rz - dyc * dyc;
+        if (!(rem > 0.f)) continue;
         // x-neighbours are contiguous in the cell numbering
         int xa = cx > R - 1 ? cx - R : 0, xb = cx < nx - R ? cx + R : nx - 1;
+        while (xa < xb) {
+          const float d = xf[0] - (float)(xa + 1) * a.cell_side[0];
+          if (d > 0.f && d * d >= rem) ++xa;
+          else break;
+        }
+        while (xb > xa) {
+          const float d = (float)xb * a.cell_side[0] - xf[0];
+          if (d > 0.f && d * d >= rem) --xb;
+          else break;
+        }
         int c0 = base + (iz * ny + iy) * nx + xa;
         int s0 = a.cstart[c0], s1 = a.cstart[c0 + (xb - xa) + 1];
         if (s0 < jmin) s0 = jmin;
@@ -465,6 +506,7 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
           visit(hit, j, type);
         }
       }
+    }
   }
 }
 
@@ -481,6 +523,8 @@ template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
   __shared__ double tab[kTabN];
+  __shared__ float tab32[kErfcxN];  // erfcx table in FP32 (FP32 pairs)
+  for (int i = threadIdx.x; i < kErfcxN; i += blockDim.x) tab32[i] = (float)d_erfcx_coef[i];
   load_table(tab);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* qu = queue[wib];
@@ -530,11 +574,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
         double rd[3], hd;
         pair_vec(a, x, j, true, rd, &hd);
         double s2 = rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2];
-        Radial<double> Rd = radial(s2, approx_float(s2), a.xi, tab, need_g3);
+        Radial<double> Rd = radial(s2, approx_float(s2), a.xi, tab, tab32, need_g3);
         add_image<double>(a.mask, Rd, rd, hd, x.d[2], sdbl, a.xi, uself);
         return;
       }
-      Radial<T> R = radial(sd, sizeof(T) == 8 ? approx_float((double)sd) : (float)sd, xi, tab, need_g3);
+      Radial<T> R = radial(sd, sizeof(T) == 8 ? approx_float((double)sd) : (float)sd, xi, tab, tab32, need_g3);
       if (type == Q_FREE) add_free<T>(a.mask, R, r, s, xi, (T)1, u);
       else add_image<T>(a.mask, R, r, h, x3, s, xi, u);
     };
@@ -580,11 +624,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
 // error -- with the partner's share sent by one float4 atomic into a.out4.
 // Resident blocks per SM the FP64 symmetric kernel is compiled for: 4 (128
 // registers) where the pair arithmetic fits without spilling, which keeps 16
-// warps per SM issuing to the FP64 pipe; the stokeslet + stresslet masks need
+// warps per SM issuing to the FP64 pipe; the masks with two strength tensors need
 // more registers (3 blocks, up to 170).
 template <typename T, int KM>
 constexpr int real_min_blocks() {
-  return sizeof(T) == 8 ? (KM != 3 && KM != 7 ? 4 : 3) : 1;
+  return sizeof(T) == 8 ? (KM != 3 && KM != 6 && KM != 7 ? 4 : 3) : 1;
 }
 
 template <typename T, int KM>
@@ -592,6 +636,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>())
   __shared__ int queue[kWarpsPerBlock][kQueue];
   __shared__ int queue_far[kWarpsPerBlock][kQueue];
   __shared__ double tab[kTabN];
+  __shared__ float tab32[kErfcxN];  // erfcx table in FP32 (shell and FP32 pairs)
+  for (int i = threadIdx.x; i < kErfcxN; i += blockDim.x) tab32[i] = (float)d_erfcx_coef[i];
   load_table(tab);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* qu = queue[wib];
@@ -655,7 +701,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>())
       T sd = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       // close image pairs are left to k_close_images (FP64), see there
       if (sizeof(T) == 4 && type == Q_IMAGE && (float)sq3(r) < a.img64_2) return;
-      Radial<T> R = radial(sd, sizeof(T) == 8 ? approx_float((double)sd) : (float)sd, xi, tab, need_g3);
+      Radial<T> R = radial(sd, sizeof(T) == 8 ? approx_float((double)sd) : (float)sd, xi, tab, tab32, need_g3);
       T v[3] = {0, 0, 0};
       if (type == Q_FREE) {
         add_free<T>(KM, R, r, s, xi, (T)1, u);
@@ -677,7 +723,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>())
       load_src<float, KM>(a, a.sstr32, w, spf);
       float r[3], dh[3], dl[3], h;
       pair_vec_split(a, x, j, type == Q_IMAGE, dh, dl, r, &h);
-      Radial<float> R = radial_shell(dh, dl, xi32, xi2h, xi2l, need_g3);
+      Radial<float> R = radial_shell(dh, dl, xi32, xi2h, xi2l, need_g3, tab32);
       float v[3] = {0.f, 0.f, 0.f}, t[3] = {0.f, 0.f, 0.f};
       if (type == Q_FREE) {
         add_free<float>(KM, R, r, s, xi32, 1.f, t);
@@ -809,7 +855,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_close_images(RealArgs a
           double rd[3], hd;
           pair_vec(a, x, j, true, rd, &hd);
           double s2 = sq3(rd);
-          Radial<double> R = radial(s2, approx_float(s2), a.xi, tab, need_g3);
+          Radial<double> R = radial(s2, approx_float(s2), a.xi, tab, nullptr, need_g3);
           add_image<double>(a.mask, R, rd, hd, x.d[2], sj, a.xi, u);
         }
       }
@@ -877,6 +923,11 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   double m = 4.0 * (2.0 * std::sqrt(3.0) * rc * delta + 3.0 * delta * delta + std::ldexp(1.0, -21) * rc * rc);
   a.rc2_lo = (float)std::fmax(0.0, a.rc2 - m) * (1.0f - 1e-6f);
   a.rc2_hi = (float)(a.rc2 + m) * (1.0f + 1e-6f);
+  // cell rows are culled by an FP32 box distance: target and cell bounds are
+  // rounded to FP32 (~3e-7 L), far inside the 1e-5 L margin
+  const double rcull = rc + 1e-5 * lmax;
+  a.cull2 = (float)(rcull * rcull);
+  for (int d = 0; d < 3; ++d) a.cell_side[d] = (float)(p->prm.box[d] / p->prm.ncell[d]);
   a.img64_2 = (float)(a.rc2 / 256.0);
   a.far2 = 0.0f;
   for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = p->prm.ncell[d]; }
