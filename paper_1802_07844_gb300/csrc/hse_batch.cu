@@ -269,7 +269,7 @@ Chunk next_chunk(hse_batch b, Bucket* k, const hse_instance* inst, const int* id
   const hse_params& q = p->prm;
   const size_t esz = b->precision == HSE_MIXED ? 4 : 8;
   const double per_inst = (double)p->g.buf_doubles * esz * p->comps.n;
-  const double per_part = 320.0 + 8.0 * hse::prep_stride_max(q.kernel_mask, q.P) + 8.0 * p->n_rows;
+  const double per_part = 320.0 + 8.0 * hse::prep_stride_max(q.kernel_mask, q.P, q.spread_tile) + 8.0 * p->n_rows;
   const int64_t ncells = (int64_t)q.ncell[0] * q.ncell[1] * q.ncell[2];
   int64_t cap = 4096;
   // the x lines of the slab-major grids have a stride of nc * C planes; past a

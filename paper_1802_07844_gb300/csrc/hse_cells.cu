@@ -32,7 +32,7 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   }
   // grow-only: a workspace sized for a wider spread record or more particles
   // serves narrower / fewer ones too
-  int stride = prep_stride_max(p->prm.kernel_mask, p->prm.P);
+  int stride = prep_stride_max(p->prm.kernel_mask, p->prm.P, p->prm.spread_tile);
   if (n <= w.cap && stride <= w.prep_stride) return HSE_OK;
   int64_t cap = n < 1024 ? 1024 : n;
   if (cap < w.cap) cap = w.cap;

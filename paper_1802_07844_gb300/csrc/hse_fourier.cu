@@ -75,6 +75,15 @@ __device__ __forceinline__ void prep_one(const PrepArgs<T>& a, int64_t i) {
     // exp(-2 alpha h^2): two exponentials per axis instead of P (relative
     // rounding <~ 2 P eps64 after P steps).
     const RecLayout& L = a.lay;
+    {  // zero entries around the x, y and z blocks
+      const int pad[3] = {L.px, L.py, L.pz}, base[3] = {L.x0, L.y0, L.z0}, ke[3] = {L.kx, L.ky, L.ky};
+      for (int k = 0; k < 3; ++k)
+        for (int t = 0; t < pad[k]; ++t)
+          for (int m = 0; m < ke[k]; ++m) {
+            o[base[k] + t * ke[k] + m] = (T)0;
+            o[base[k] + (P + pad[k] + t) * ke[k] + m] = (T)0;
+          }
+    }
     double wr[3], rr[3];
     {
       const double d0[3] = {a.ox + ix0 * a.h - x, a.ox + iy0 * a.h - y, a.oz + iz0 * a.h - z};
@@ -89,7 +98,7 @@ __device__ __forceinline__ void prep_one(const PrepArgs<T>& a, int64_t i) {
         const double wv = wr[k];
         wr[k] *= rr[k];
         rr[k] *= a.c2;
-        T* e = k == 0 ? o + L.x0 + t * L.kx : o + (k == 1 ? L.y0 : L.z0) + t * L.ky;
+        T* e = k == 0 ? o + L.x0 + (t + L.px) * L.kx : (k == 1 ? o + L.y0 + (t + L.py) * L.ky : o + L.z0 + (t + L.pz) * L.ky);
         const int ke = k == 0 ? L.kx : L.ky;
         for (int m = 1; m < ke; ++m) e[m] = (T)0;  // padding (and the x block's XX, written below)
         e[0] = (T)wv;
@@ -145,7 +154,7 @@ __device__ __forceinline__ void prep_one(const PrepArgs<T>& a, int64_t i) {
       const double dx0 = a.ox + ix0 * a.h - x;
       double wxr = a.pre * exp(-a.alpha * dx0 * dx0), rxr = exp(-a.alpha * (2.0 * dx0 * a.h + a.h * a.h));
       for (int t = 0; t < P; ++t) {
-        T* xx = o + L.x0 + t * L.kx + 1;  // XX_m of entry t
+        T* xx = o + L.x0 + (t + L.px) * L.kx + 1;  // XX_m of entry t
         const double dx = a.ox + (ix0 + t) * a.h - x;
         const double wx = wxr;  // the window along x (recurrence as above)
         wxr *= rxr;
@@ -205,6 +214,7 @@ struct SpreadArgs {
   const int32_t* cstart;
   int stride, P, Mt, z0, nz_tiles;
   int y0, z0r, c0;       // offsets of the y and z blocks and of the components in a record
+  int pad[3];            // zero entries before each block (warp sub-tile - 1)
   int zlo;               // lowest z index any source support reaches (tiles below only write zeros)
   double h, ox, oz;
   double inv_cell[3];
@@ -339,26 +349,21 @@ __global__ void __launch_bounds__(256, spread_min_blocks<T, NC, DK>()) k_spread(
         if (hit) list[small ? __popc(ms & below) : 31 - __popc(mb & below)] = make_int4(sp.x, sp.y, sp.z, j);
         __syncwarp();
         const int ns = __popc(ms), nb = __popc(mb);
-        // Branch-free bodies (a lane outside the source's support reads
-        // clamped entries and adds zero weights), unrolled so that the next
-        // source's record loads are in flight while this one accumulates.
+        // Branch-free bodies (a lane outside the source's support reads the
+        // record's zero pads), unrolled so that the next source's record
+        // loads are in flight while this one accumulates.
 #pragma unroll 2
         for (int e = 0; e < ns; ++e) {
           const int4 s = list[e];
-          int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
-          const bool in = (unsigned)dx < (unsigned)P && (unsigned)dy < (unsigned)P && (unsigned)dz < (unsigned)P;
-          dx = min(max(dx, 0), P - 1);
-          dy = min(max(dy, 0), P - 1);
-          dz = min(max(dz, 0), P - 1);
+          // entry of the lane's grid point in the source's padded blocks (the
+          // pads hold zeros for points outside the support)
           const float* o = a.prep32 + (int64_t)s.w * a.stride;
           float xv[KX], yv[KY], zv[KY];
-          ldv<float, KX>(o + dx * KX, xv);
-          ldv<float, KY>(o + a.y0 + dy * KY, yv);
-          ldv<float, KY>(o + a.z0r + dz * KY, zv);
+          ldv<float, KX>(o + (px - s.x + a.pad[0]) * KX, xv);
+          ldv<float, KY>(o + a.y0 + (py - s.y + a.pad[1]) * KY, yv);
+          ldv<float, KY>(o + a.z0r + (pz - s.z + a.pad[2]) * KY, zv);
           float cv[(NC + 1) & ~1];
           ldv<float, (NC + 1) & ~1>(o + a.c0, cv);
-#pragma unroll
-          for (int k = 0; k < KX; ++k) xv[k] = in ? xv[k] : 0.f;
           const float wyz = yv[0] * zv[0];
           const float wv = xv[0] * wyz;
 #pragma unroll
@@ -372,20 +377,13 @@ __global__ void __launch_bounds__(256, spread_min_blocks<T, NC, DK>()) k_spread(
 #pragma unroll 2
         for (int e = 0; e < nb; ++e) {
           const int4 s = list[31 - e];
-          int dx = px - s.x, dy = py - s.y, dz = pz - s.z;
-          const bool in = (unsigned)dx < (unsigned)P && (unsigned)dy < (unsigned)P && (unsigned)dz < (unsigned)P;
-          dx = min(max(dx, 0), P - 1);
-          dy = min(max(dy, 0), P - 1);
-          dz = min(max(dz, 0), P - 1);
           const T* o = a.prep + (int64_t)s.w * a.stride;
           T xv[KX], yv[KY], zv[KY];
-          ldv<T, KX>(o + dx * KX, xv);
-          ldv<T, KY>(o + a.y0 + dy * KY, yv);
-          ldv<T, KY>(o + a.z0r + dz * KY, zv);
+          ldv<T, KX>(o + (px - s.x + a.pad[0]) * KX, xv);
+          ldv<T, KY>(o + a.y0 + (py - s.y + a.pad[1]) * KY, yv);
+          ldv<T, KY>(o + a.z0r + (pz - s.z + a.pad[2]) * KY, zv);
           T cv[(NC + 1) & ~1];
           ldv<T, (NC + 1) & ~1>(o + a.c0, cv);
-#pragma unroll
-          for (int k = 0; k < KX; ++k) xv[k] = in ? xv[k] : (T)0;
           const T wyz = mulr(yv[0], zv[0]);
           const T wv = mulr(xv[0], wyz);
 #pragma unroll
@@ -780,7 +778,7 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   a.nc1 = c1_count(q.kernel_mask);
   // paper: plain windows and every component; product: derivative windows,
   // the combined x arrays of D and C1
-  a.lay = rec_layout(a.nfac, paper ? ncomp : a.nc1, q.P);
+  a.lay = rec_layout(a.nfac, paper ? ncomp : a.nc1, q.P, q.spread_tile);
   a.stride = a.lay.stride;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
   // 8-byte grids split small window weights to FP32 unless an FP64 plan asks
@@ -837,6 +835,9 @@ static hse_status spread_into(hse_plan p, int64_t n_src, const CompSet& cs, int 
   a.y0 = pa.lay.y0;
   a.z0r = pa.lay.z0;
   a.c0 = pa.lay.c0;
+  a.pad[0] = pa.lay.px;
+  a.pad[1] = pa.lay.py;
+  a.pad[2] = pa.lay.pz;
   a.P = q.P;
   a.Mt = q.Mt;
   // full_z: tiles on the same z boundaries as from zA0, extended down to the

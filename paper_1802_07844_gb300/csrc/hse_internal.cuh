@@ -65,28 +65,36 @@ inline int c1_count(int mask) {
 // nfac = 1, 2, 3 goes with nxx = 0, 3, 6.
 struct RecLayout {
   int kx, ky, x0, y0, z0, c0, stride;
+  int px, py, pz;  // zero entries before and after the x, y, z blocks
 };
 __host__ __device__ constexpr int rec_kx(int nfac) { return nfac == 1 ? 2 : (nfac == 2 ? 4 : 8); }
 __host__ __device__ constexpr int rec_ky(int nfac) { return nfac == 3 ? 4 : 2; }
-__host__ __device__ inline RecLayout rec_layout(int nfac, int nc, int P) {
+// tile: the spread's warp sub-tile (hse_params.spread_tile).  Each block
+// carries tile_d - 1 zero entries on both sides, so a lane whose grid point
+// lies outside a source's support (at most tile_d - 1 points before or after
+// it) reads zero weights: the spread needs no range test and no clamping.
+__host__ __device__ inline RecLayout rec_layout(int nfac, int nc, int P, const int tile[3]) {
   RecLayout r;
   r.kx = rec_kx(nfac);
   r.ky = rec_ky(nfac);
+  r.px = tile[0] - 1;
+  r.py = tile[1] - 1;
+  r.pz = tile[2] - 1;
   r.x0 = 0;
-  r.y0 = P * r.kx;
-  r.z0 = r.y0 + P * r.ky;
-  r.c0 = r.z0 + P * r.ky;
+  r.y0 = (P + 2 * r.px) * r.kx;
+  r.z0 = r.y0 + (P + 2 * r.py) * r.ky;
+  r.c0 = r.z0 + (P + 2 * r.pz) * r.ky;
   r.stride = r.c0 + ((nc + 1) & ~1);
   return r;
 }
 // the larger of the product record (C1 + the derivative-window factors of D)
 // and the paper record (C1, C2, C3 of every kernel, plain windows)
-inline int prep_stride_max(int mask, int P) {
+inline int prep_stride_max(int mask, int P, const int tile[3]) {
   const int dk = deriv_kind(mask);
   const int nfac = dk == 0 ? 1 : ((dk & 4) ? 3 : 2);
-  const int product = rec_layout(nfac, c1_count(mask), P).stride;
+  const int product = rec_layout(nfac, c1_count(mask), P, tile).stride;
   const int paper = rec_layout(1, ((mask & HSE_STOKESLET) ? 7 : 0) + ((mask & HSE_STRESSLET) ? 13 : 0) +
-                                      ((mask & HSE_ROTLET) ? 5 : 0), P).stride;
+                                      ((mask & HSE_ROTLET) ? 5 : 0), P, tile).stride;
   return product > paper ? product : paper;
 }
 
