@@ -18,7 +18,10 @@
 // Each pass is a batched 1-D transform of lines.  A block holds LPB lines in
 // shared memory (element e of line l at e * LPB + l) and runs a mixed-radix
 // Stockham autosort transform over them (radices 4, 2, 5, 3), alternating
-// between two shared buffers so that each radix pass needs one barrier.
+// between two shared buffers so that each radix pass needs one barrier; the
+// twiddle table sits in shared memory, and the line passes queue the next
+// line set's loads (cp.async) into a third buffer before transforming the
+// current one.
 #include <cmath>
 #include <mutex>
 
@@ -141,7 +144,7 @@ __device__ __forceinline__ void dft5(cdf* v, const float* kc) {
 
 template <bool FWD>
 __device__ __forceinline__ cdf twiddle(const float4* __restrict__ tw, int idx) {
-  const cdf w = ldg_cdf(tw + idx);
+  const cdf w = ld_cdf(tw + idx);  // shared-memory copy of the table
   return FWD ? w : conj(w);
 }
 
@@ -237,46 +240,94 @@ __global__ void k_twiddles(int N, float4* __restrict__ tw) {
   }
 }
 
+// Asynchronous 16-byte copies global -> shared (the next line set is loaded
+// while the current one is transformed)
+__device__ __forceinline__ void cp_async16(float4* dst, const float4* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Queue the loads of one line set (starts s[]) into the shared buffer dst.
+// half: element e < N/2 goes to positions 2e and 2e + 1 (the radix-2 first
+// pass of an input whose upper half is zero is a copy); otherwise elements
+// e >= nload are zero.  Lines beyond the last (start -1) are zero.
+__device__ __forceinline__ void queue_set(const float4* data, const LineGeo& g, const long long* s, float4* dst,
+                                          int lsh, int N, int nload, bool half) {
+  const int lpb = 1 << lsh;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (half) {
+    for (int i = threadIdx.x; i < (nload << lsh); i += blockDim.x) {
+      const long long o = s[i & (lpb - 1)];
+      const int e = i >> lsh, l = i & (lpb - 1);
+      float4* d0 = dst + ((2 * e) << lsh) + l;
+      if (o >= 0) {
+        const float4* src = data + o + (long long)e * g.es;
+        cp_async16(d0, src);
+        cp_async16(d0 + lpb, src);
+      } else {
+        d0[0] = zero;
+        d0[lpb] = zero;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < (N << lsh); i += blockDim.x) {
+      const long long o = s[i & (lpb - 1)];
+      const int e = i >> lsh;
+      if (o >= 0 && e < nload) cp_async16(dst + i, data + o + (long long)e * g.es);
+      else dst[i] = zero;
+    }
+  }
+  cp_async_commit();
+}
+
 // ------------------------------------------------------------ C2C passes
 // Elements e >= nload of a line are taken as zero (not read), and only
 // elements e < nstore are written back: the data region of a forward pass's
 // input and the part of an inverse pass's output that later steps read.
+// A block loops over line sets with three shared buffers: the set being
+// transformed, its scratch buffer, and the next set, whose loads are queued
+// (cp.async) before the current set's passes run.
 template <bool FWD>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4* __restrict__ data, LineGeo g,
                                                       const FftSteps* __restrict__ st, int lsh,
                                                       const float4* __restrict__ tw, int nload, int nstore) {
   extern __shared__ float4 sm[];
-  __shared__ long long start[16];
-  const int lpb = 1 << lsh, n = st->N << lsh;
-  for (long long b0 = (long long)blockIdx.x * lpb; b0 < g.nlines; b0 += (long long)gridDim.x * lpb) {
-    if (threadIdx.x < lpb) start[threadIdx.x] = b0 + threadIdx.x < g.nlines ? line_start(g, b0 + threadIdx.x) : -1;
-    __syncthreads();
-    // half: the schedule starts with radix 2 and the input's upper half is zero,
-    // so that pass is a copy: element e < N/2 goes to positions 2e and 2e + 1
-    const bool half = nload * 2 == st->N && st->R[0] == 2;
-    if (half) {
-      for (int i = threadIdx.x; i < (nload << lsh); i += blockDim.x) {
-        const long long o = start[i & (lpb - 1)];
-        const int e = i >> lsh, l = i & (lpb - 1);
-        const float4 v = o >= 0 ? data[o + (long long)e * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
-        sm[((2 * e) << lsh) + l] = v;
-        sm[((2 * e + 1) << lsh) + l] = v;
-      }
-    } else {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const long long o = start[i & (lpb - 1)];
-        const int e = i >> lsh;
-        sm[i] = o >= 0 && e < nload ? data[o + (long long)e * g.es] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    __syncthreads();
-    const float4* res = transform_block<FWD>(sm, sm + n, st, lsh, tw, half ? 1 : 0);
+  __shared__ long long start[3][16];  // line starts of three consecutive sets (one being written)
+  const int lpb = 1 << lsh, N = st->N, n = N << lsh;
+  float4* stw = sm + 3 * n;  // twiddles in shared memory (read by every pass)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) stw[i] = __ldg(tw + i);
+  const bool half = nload * 2 == N && st->R[0] == 2;
+  const long long step = (long long)gridDim.x * lpb;
+  long long b0 = (long long)blockIdx.x * lpb;
+  if (b0 >= g.nlines) return;
+  auto set_starts = [&](long long b, long long* s) {
+    if (threadIdx.x < lpb) s[threadIdx.x] = b + threadIdx.x < g.nlines ? line_start(g, b + threadIdx.x) : -1;
+  };
+  set_starts(b0, start[0]);
+  __syncthreads();
+  int cur = 0, nxt = 2;  // buffer of the current set, buffer the next set is loaded into
+  queue_set(data, g, start[0], sm + cur * n, lsh, N, nload, half);
+  for (int it = 0; b0 < g.nlines; b0 += step, ++it) {
+    const long long* sc = start[it % 3];
+    long long* sn = start[(it + 1) % 3];
+    const long long b1 = b0 + step;
+    if (b1 < g.nlines) set_starts(b1, sn);
+    cp_async_wait_all();
+    __syncthreads();  // the current set has landed; the last set's stores have read their buffer
+    const int scr = 3 - cur - nxt;
+    if (b1 < g.nlines) queue_set(data, g, sn, sm + nxt * n, lsh, N, nload, half);
+    const float4* res = transform_block<FWD>(sm + cur * n, sm + scr * n, st, lsh, stw, half ? 1 : 0);
     for (int i = threadIdx.x; i < (nstore << lsh); i += blockDim.x) {
-      const long long o = start[i & (lpb - 1)];
+      const long long o = sc[i & (lpb - 1)];
       if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = res[i];
     }
-    __syncthreads();
+    const int used = res == sm + cur * n ? cur : scr;  // free after the next barrier
+    cur = nxt;
+    nxt = used;
   }
+  cp_async_wait_all();
 }
 
 // ---------------------------------------------- real <-> half spectrum (z)
@@ -295,6 +346,8 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
   extern __shared__ float4 sm[];
   __shared__ long long start[16];
   const int lpb = 1 << lsh, N = st->N;
+  float4* stw = sm + 2 * (N << lsh);  // twiddles in shared memory (read by every pass)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) stw[i] = __ldg(tw + i);
   for (long long b0 = (long long)blockIdx.x * lpb; b0 < g.nlines; b0 += (long long)gridDim.x * lpb) {
     if (threadIdx.x < lpb) start[threadIdx.x] = b0 + threadIdx.x < g.nlines ? line_start(g, b0 + threadIdx.x) : -1;
     __syncthreads();
@@ -324,7 +377,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
       }
     }
     __syncthreads();
-    const float4* res = transform_block<FWD>(sm, sm + (N << lsh), st, lsh, tw, half ? 1 : 0);
+    const float4* res = transform_block<FWD>(sm, sm + (N << lsh), st, lsh, stw, half ? 1 : 0);
     for (int l = 0; l < lpb; ++l) {
       const long long o = start[l];
       if (o < 0) continue;
@@ -393,12 +446,12 @@ hse_status fft64_prepare(hse_plan p) {
   k_twiddles<<<(2 * nh + 255) / 256, 256>>>(2 * nh, t->tw + n1 + nh);
   HSE_CUDA(p, cudaGetLastError());
   HSE_CUDA(p, cudaDeviceSynchronize());
-  // a block holds two buffers of (threads / TPL) lines of N points: at most
-  // kFftThreads threads and TPL >= N / 4, so at most 2 x 16 KB x kFftThreads / 512
-  // (plans may be built from several threads: set the limits once)
+  // a block holds up to three buffers of (threads / TPL) lines of N points (at
+  // most kFftThreads threads and TPL >= N / 4: 32 KB each for 512 threads) and
+  // the N twiddles (plans may be built from several threads: set the limits once)
   static std::once_flag attr;
   std::call_once(attr, [] {
-    const int cap = 64 * 1024;
+    const int cap = 160 * 1024;  // up to three line buffers (<= 96 KB) and the twiddles (<= 32 KB)
     cudaFuncSetAttribute(k_fft_lines<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_fft_lines<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     cudaFuncSetAttribute(k_fft_z<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -427,7 +480,7 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
   const Fft64Tables* t = tables(p);
   const int lsh = lines_per_block_log2(t->sx.N);
   const unsigned threads = (unsigned)(threads_per_line(t->sx.N) << lsh);
-  const size_t shm = 2 * sizeof(float4) * ((size_t)t->sx.N << lsh);
+  const size_t shm = sizeof(float4) * (3 * ((size_t)t->sx.N << lsh) + t->sx.N);  // three line buffers, twiddles
   if (geo.nlines <= 0) return HSE_OK;
   float4* c = reinterpret_cast<float4*>(buf);
   if (fwd)  // forward passes read a zero upper half: the radix-2-first schedule
@@ -444,7 +497,7 @@ static hse_status run_z(hse_plan p, double* buf, const LineGeo& geo, bool fwd, i
   const Fft64Tables* t = tables(p);
   const int N = t->sz.N, lsh = lines_per_block_log2(N);
   const unsigned threads = (unsigned)(threads_per_line(N) << lsh);
-  const size_t shm = 2 * sizeof(float4) * ((size_t)N << lsh);
+  const size_t shm = sizeof(float4) * (2 * ((size_t)N << lsh) + N);  // two line buffers, twiddles
   if (geo.nlines <= 0) return HSE_OK;
   const float4* tw = t->tw + t->sx.N;
   const float4* tw2 = tw + N;
