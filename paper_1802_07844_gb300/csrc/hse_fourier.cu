@@ -492,7 +492,7 @@ template <> struct Cplx<double> { typedef double2 type; };
 template <> struct Cplx<float> { typedef float2 type; };
 template <> struct Cplx<df> { typedef cdf type; };
 template <typename T> struct Tab { typedef T type; };
-template <> struct Tab<df> { typedef double type; };
+template <> struct Tab<df> { typedef df type; };  // float-pair copies of the FP64 tables
 
 template <typename T>
 struct ScaleArgs {
@@ -931,8 +931,9 @@ static hse_status launch_scale(hse_plan p, void* spec, int64_t cstride, int n_in
   sa.Mt = q.Mt;
   sa.mask = q.kernel_mask;
   sa.h = q.h;
-  sa.tabB = reinterpret_cast<const typename Tab<S>::type*>(p->tabB);
-  sa.tabH = reinterpret_cast<const typename Tab<S>::type*>(p->tabH);
+  constexpr bool dft = std::is_same<S, df>::value;
+  sa.tabB = reinterpret_cast<const typename Tab<S>::type*>(dft ? p->tabB_df : p->tabB);
+  sa.tabH = reinterpret_cast<const typename Tab<S>::type*>(dft ? p->tabH_df : p->tabH);
   sa.tabLow = std::is_same<S, float>::value ? p->tabLow : nullptr;
   sa.lowK = kLowK < q.Mt ? kLowK : q.Mt;
   int k = 0;

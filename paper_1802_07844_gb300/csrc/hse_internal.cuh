@@ -146,6 +146,10 @@ struct hse_plan_s {
   // kLowK of the octant (H then B, (kLowK+1)^3 each), for the FP64 scaling of
   // the lowest wave numbers
   double* tabLow = nullptr;
+  // double-float grids: the two tables again as float pairs {hi, lo} (8 bytes
+  // each), so that the scaling splits no FP64 value per k-point
+  double* tabB_df = nullptr;
+  double* tabH_df = nullptr;
   // zero-padded transforms split into a 2-D (y,z) transform over the Mt planes
   // that hold data (fwd2d R2C / inv2d C2R) and a 1-D transform along x over
   // all (y, kz) lines (fftx, Z2Z both directions)

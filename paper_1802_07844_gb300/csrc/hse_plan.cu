@@ -190,6 +190,15 @@ __global__ void k_tab_finish(double* __restrict__ tab, int Mt, double h, double 
   }
 }
 
+// double -> float pair {hi, lo} of every table value (double-float grids)
+__global__ void k_tab_to_df(const double* __restrict__ t, float2* __restrict__ f, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = t[i];
+    const float hi = __double2float_rn(v);
+    f[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
 // FP64 table -> FP32 copy (mixed precision)
 __global__ void k_tab_to_float(const double* __restrict__ t, float* __restrict__ f, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -285,11 +294,32 @@ void free_grids(hse_plan p) {
   cudaFree(p->tabB);
   cudaFree(p->tabH);
   cudaFree(p->tabLow);
-  p->tabLow = nullptr;
+  cudaFree(p->tabB_df);
+  cudaFree(p->tabH_df);
+  p->tabLow = p->tabB_df = p->tabH_df = nullptr;
   p->fft_work = nullptr;
   p->fft_work_bytes = 0;
   p->spec = p->tabB = p->tabH = nullptr;
   p->grid_ready = false;
+}
+
+// Float-pair copies of the tables for double-float grids (made once, with
+// the df64 transforms)
+static hse_status prepare_df_tables(hse_plan p) {
+  if (p->tabH_df) return HSE_OK;
+  const int Mt = p->prm.Mt;
+  const int64_t n = (int64_t)(Mt + 1) * (Mt + 1) * (2 * Mt + 1);
+  for (int k = 0; k < 2; ++k) {
+    double* src = k == 0 ? p->tabH : p->tabB;
+    double** dst = k == 0 ? &p->tabH_df : &p->tabB_df;
+    if (!src) continue;
+    HSE_CUDA(p, cudaMalloc(dst, n * sizeof(double)));
+    k_tab_to_df<<<grid_blocks(n, 256), 256>>>(src, reinterpret_cast<float2*>(*dst), n);
+    HSE_CUDA(p, cudaGetLastError());
+  }
+  HSE_CUDA(p, cudaDeviceSynchronize());
+  p->prm.grid_bytes += (size_t)n * sizeof(double) * (p->tabB ? 2 : 1);
+  return HSE_OK;
 }
 
 // Transforms for the plan's grid.  Double-float transforms carry ~48-bit
@@ -401,6 +431,7 @@ hse_status build_grids(hse_plan p) {
   if (q.fft == HSE_FFT_DF64) HSE_TRY(fft64_prepare(p));
   else HSE_TRY(build_cufft(p));
   q.grid_bytes = spec_bytes + tab_elems * esz * (p->tabB ? 2 : 1) + p->fft_work_bytes;
+  if (q.fft == HSE_FFT_DF64) HSE_TRY(prepare_df_tables(p));
   p->grid_ready = true;
   return HSE_OK;
 }
@@ -661,6 +692,7 @@ extern "C" hse_status hse_plan_set_fft(hse_plan p, int mode) {
   else HSE_TRY(build_cufft(p));
   p->prm.fft = f;
   p->prm.grid_bytes += p->fft_work_bytes - work_before;  // a cuFFT work area made now
+  if (f == HSE_FFT_DF64) HSE_TRY(prepare_df_tables(p));
   return HSE_OK;
 }
 
