@@ -21,7 +21,9 @@
 // between two shared buffers so that each radix pass needs one barrier; the
 // twiddle table sits in shared memory, and the line passes queue the next
 // line set's loads (cp.async) into a third buffer before transforming the
-// current one.
+// current one, and store the outputs of their last radix pass straight to
+// global memory (inverse passes whose first half is kept end with a radix-2
+// pass that forms only that half).
 #include <cmath>
 #include <mutex>
 
@@ -45,14 +47,22 @@ struct FftSteps {
 
 // two_first: the first pass has radix 2 (used for inputs whose upper half is
 // zero: that pass reduces to a copy, done while loading)
-static bool make_steps(int N, FftSteps* st, bool two_first = false) {
-  if (N < 2 || N >= 65536 || (two_first && N % 2 != 0)) return false;
+// two_last: the last pass has radix 2 (used for inverse lines of which only
+// the first half is kept: that pass then computes one output per butterfly)
+static bool make_steps(int N, FftSteps* st, bool two_first = false, bool two_last = false) {
+  if (N < 2 || N >= 65536 || ((two_first || two_last) && N % 2 != 0) || (two_first && two_last && N % 4 != 0))
+    return false;
   FftSteps s{};
   s.N = N;
   int rem = N, Ns = 1;
   while (rem > 1) {
     int R = rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 5 == 0 ? 5 : rem % 3 == 0 ? 3 : 0;
     if (two_first && s.npass == 0) R = 2;
+    if (two_last) {  // keep one factor 2 for the end
+      if (rem == 2) R = 2;
+      else if (R == 4 && (rem / 4) % 2 != 0) R = (rem / 2) % 2 == 0 ? 2 : (rem % 5 == 0 ? 5 : (rem % 3 == 0 ? 3 : 2));
+      else if (R == 2 && rem != 2 && (rem / 2) % 2 != 0) R = rem % 5 == 0 ? 5 : (rem % 3 == 0 ? 3 : 0);
+    }
     if (R == 0 || s.npass == kMaxPass) return false;
     s.R[s.npass] = R;
     s.Ns[s.npass] = Ns;
@@ -185,12 +195,13 @@ __device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, in
 // it freely.
 template <bool FWD>
 __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const FftSteps* __restrict__ st, int lsh,
-                                                   const float4* __restrict__ tw, int p0 = 0) {
+                                                   const float4* __restrict__ tw, int p0 = 0, int p_end = -1) {
   const int tpl = blockDim.x >> lsh;
   const int l = threadIdx.x & ((1 << lsh) - 1), tj = threadIdx.x >> lsh;
   const int N = st->N, npass = st->npass;
   const float* kc = st->kc;
-  for (int p = p0; p < npass; ++p) {
+  if (p_end < 0) p_end = npass;
+  for (int p = p0; p < p_end; ++p) {
     const int Ns = st->Ns[p], step = st->step[p];
     const unsigned magic = st->magic[p];
     if (p == npass - 1) {  // the last pass stores normalised values
@@ -214,6 +225,44 @@ __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const F
     b = t;
   }
   return a;
+}
+
+// The last Stockham pass of a line set (Ns = N / R: butterfly j takes
+// elements j + t N/R and writes output t to element j + t N/R) with its
+// normalised outputs stored straight to the line in global memory (elements
+// e < nstore; start s[l] of line l, stride es), not to shared memory.  With
+// R = 2 and nstore = N/2 only the first output of each butterfly is formed.
+template <int R, bool FWD>
+__device__ __forceinline__ void last_pass_store(const float4* src, float4* __restrict__ data, const long long* s,
+                                                long long es, int N, int step, const float* kc, int lsh, int nstore,
+                                                const float4* __restrict__ tw) {
+  const int tpl = blockDim.x >> lsh;
+  const int l = threadIdx.x & ((1 << lsh) - 1), tj = threadIdx.x >> lsh;
+  const long long o = s[l];
+  if (o < 0) return;
+  const int nb = N / R;
+  for (int j = tj; j < nb; j += tpl) {
+    cdf v[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[t] = ld_cdf(src + ((j + t * nb) << lsh) + l);
+    if (j != 0) {
+#pragma unroll
+      for (int t = 1; t < R; ++t) v[t] = mul_raw(v[t], twiddle<FWD>(tw, t * j * step));
+    }
+    if (R == 2 && 2 * nstore == N) {
+      st_cdf(data + o + (long long)j * es, norm(add_raw(v[0], v[1])));
+      continue;
+    }
+    if (R == 2) dft2<FWD, true>(v);
+    else if (R == 4) dft4<FWD, true>(v);
+    else if (R == 3) dft3<FWD, true>(v, kc);
+    else dft5<FWD, true>(v, kc);
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int e = j + t * nb;
+      if (e < nstore) st_cdf(data + o + (long long)e * es, v[t]);
+    }
+  }
 }
 
 // ------------------------------------------------------------ line geometry
@@ -318,12 +367,25 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4
     __syncthreads();  // the current set has landed; the last set's stores have read their buffer
     const int scr = 3 - cur - nxt;
     if (b1 < g.nlines) queue_set(data, g, sn, sm + nxt * n, lsh, N, nload, half);
-    const float4* res = transform_block<FWD>(sm + cur * n, sm + scr * n, st, lsh, stw, half ? 1 : 0);
-    for (int i = threadIdx.x; i < (nstore << lsh); i += blockDim.x) {
-      const long long o = sc[i & (lpb - 1)];
-      if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = res[i];
+    // all passes but the last in shared memory; the last one stores to global
+    const int p0 = half ? 1 : 0, pl = st->npass - 1;
+    if (pl >= p0) {
+      const float4* res = transform_block<FWD>(sm + cur * n, sm + scr * n, st, lsh, stw, p0, pl);
+      const int step = st->step[pl];
+      switch (st->R[pl]) {
+        case 4: last_pass_store<4, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
+        case 2: last_pass_store<2, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
+        case 5: last_pass_store<5, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
+        default: last_pass_store<3, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
+      }
+    } else {  // the whole transform was the load's radix-2 copy
+      const float4* res = sm + cur * n;
+      for (int i = threadIdx.x; i < (nstore << lsh); i += blockDim.x) {
+        const long long o = sc[i & (lpb - 1)];
+        if (o >= 0) data[o + (long long)(i >> lsh) * g.es] = res[i];
+      }
     }
-    const int used = res == sm + cur * n ? cur : scr;  // free after the next barrier
+    const int used = cur;  // both of this set's buffers are free after the next barrier
     cur = nxt;
     nxt = used;
   }
@@ -406,7 +468,8 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_z(double* __
 struct Fft64Tables {
   FftSteps sx, sz;           // x / y lines (length Nx = Ny) and z half-lines (Nz / 2)
   FftSteps sxh, szh;         // the same with a radix-2 first pass (forward, zero upper half)
-  FftSteps* d_steps = nullptr;  // device copies {sx, sz, sxh, szh}
+  FftSteps sxl;              // x / y lines with a radix-2 last pass (inverse, first half kept)
+  FftSteps* d_steps = nullptr;  // device copies {sx, sz, sxh, szh, sxl}
   float4* tw = nullptr;      // twiddles of lengths Nx, Nz / 2 and Nz, back to back
 };
 
@@ -430,6 +493,7 @@ hse_status fft64_prepare(hse_plan p) {
   make_steps(g.Nz / 2, &t->sz);
   make_steps(g.Nx, &t->sxh, true);
   make_steps(g.Nz / 2, &t->szh, true);
+  if (!make_steps(g.Nx, &t->sxl, false, true)) t->sxl = t->sx;
   const int n1 = g.Nx, nh = g.Nz / 2;
   cudaError_t e = cudaMalloc(&t->tw, sizeof(float4) * (n1 + nh + 2 * nh));
   if (e != cudaSuccess) {
@@ -437,9 +501,9 @@ hse_status fft64_prepare(hse_plan p) {
     return cuda_check(p, e, "cudaMalloc(df64 twiddles)");
   }
   p->fft64 = t;
-  HSE_CUDA(p, cudaMalloc(&t->d_steps, 4 * sizeof(FftSteps)));
-  const FftSteps* hs[4] = {&t->sx, &t->sz, &t->sxh, &t->szh};
-  for (int i = 0; i < 4; ++i)
+  HSE_CUDA(p, cudaMalloc(&t->d_steps, 5 * sizeof(FftSteps)));
+  const FftSteps* hs[5] = {&t->sx, &t->sz, &t->sxh, &t->szh, &t->sxl};
+  for (int i = 0; i < 5; ++i)
     HSE_CUDA(p, cudaMemcpy(t->d_steps + i, hs[i], sizeof(FftSteps), cudaMemcpyHostToDevice));
   k_twiddles<<<(n1 + 255) / 256, 256>>>(n1, t->tw);
   k_twiddles<<<(nh + 255) / 256, 256>>>(nh, t->tw + n1);
@@ -487,7 +551,9 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
     k_fft_lines<true><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps + 2, lsh, t->tw, nload,
                                                                         nstore);
   else
-    k_fft_lines<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(c, geo, t->d_steps, lsh, t->tw, nload, nstore);
+    // inverse keeping the first half: the radix-2-last schedule
+    k_fft_lines<false><<<grid_for(geo.nlines, lsh), threads, shm, s>>>(
+        c, geo, t->d_steps + (2 * nstore == t->sx.N ? 4 : 0), lsh, t->tw, nload, nstore);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_fft_lines");
 }
