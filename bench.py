@@ -84,10 +84,10 @@ FLOPS_RADIAL = 82
 FLOPS_FREE_DIR = 37
 FLOPS_IMAGE_DIR = 92
 # DRAM bytes of one k_real_sym<double, 5> launch per point, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum = 16.1 MB + 0 at N = 100k of
-# this workload); the kernel reads positions, strengths and cell lists about
-# once, so the figure is scaled by the number of points.
-REAL_TRAFFIC_BYTES_PER_POINT = 161.0
+# (dram__bytes_read.sum + dram__bytes_write.sum = 17.8 MB + 0 at N = 100k of
+# this workload, rc64 = 0.026); the kernel reads positions, strengths and cell
+# lists about once, so the figure is scaled by the number of points.
+REAL_TRAFFIC_BYTES_PER_POINT = 178.0
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
