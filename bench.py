@@ -62,6 +62,11 @@ WORKLOAD = dict(
 # 2.9e-6 on 3000 targets (the plan's own rule at xi = 100 picks r_c 0.0367, P 14, M 306:
 # 4.4e-7 at 1.5x the time); Mt = 256 is a power of two, markedly faster in FP32 cuFFT
 MIXED = dict(tol=1e-5, xi=95.0, rc=0.035, P=12, M=244)
+# lower edge of the double-float band of the `df64_band_1e-10` leg (hse_plan_set_rcmid): every pair
+# of the 1M workload at FP64-level accuracy without the FP32 shell; measured against all pairs in
+# FP64 the band moves the real part by 6.5e-13 of the velocity at 0.004 (1.2e-13 at 0.01) and takes
+# the real stage from 540 to 230 ms
+BAND_RCMID = 0.004
 # the smaller workloads: N = 1000 stokeslet at 1e-8, N = 100k stokeslet and
 # stresslet at 1e-10, uniform in the unit box; xi = 0.7 N^(1/3), r_c, P and M
 # chosen by the plan from tol
@@ -146,7 +151,7 @@ def stage_model(kind: str, prm: dict, n: int, rows: int, pairs: dict):
     pairs: flops of the FP64 and FP32 real-space pairs."""
     Mt, P, nin, nout = prm["Mt"], prm["P"], prm["n_fft_in"], prm["n_fft_out"]
     e = 4 if kind == "mixed" else 8
-    four = {"fp64": "df64", "plain": "fp64", "mixed": "fp32"}[kind]
+    four = {"fp64": "df64", "band": "df64", "plain": "fp64", "mixed": "fp32"}[kind]
     grid = Mt * Mt * 2 * Mt * e  # data region of one real grid
     nh = 2 * Mt * 2 * Mt * (2 * Mt + 1)
     fb, ff = fft_buffer_work(Mt, e)
@@ -376,6 +381,9 @@ class PairCounter:
         total = pair_flops(*self(rc))
         if kind == "mixed":
             return {"fp32": total}
+        if kind == "band":  # FP64 below rcmid, double-float beyond (near-wall pairs counted as df64)
+            w64 = pair_flops(*self(prm["rcmid"]))
+            return {"fp64": w64, "df64": total - w64}
         if kind == "plain" or not (0.0 < rc64 < rc):
             return {"fp64": total}
         w64 = pair_flops(*self(rc64))
@@ -386,6 +394,8 @@ ARITH = {
     "fp64": "FP64 pairs within rc64, FP32 outer shell [rc64, r_c), double-float (~48-bit) spread, "
             "transforms, scaling and gather on the FP32 pipe; FP64 sums",
     "plain": "FP64 throughout: every pair in FP64, FP64 grids, cuFFT double transforms",
+    "band": "FP64 pairs closer than rcmid, double-float pairs [rcmid, r_c) on the FP32 pipe (no FP32 shell), "
+            "double-float Fourier part; FP64 sums",
     "mixed": "FP32 arithmetic (pairs, grids, cuFFT single); FP64 sums, close image pairs, self term, "
              "tables built in FP64 and rounded once",
 }
@@ -404,6 +414,9 @@ def run_leg(ctx, label, kind, p, tol):
         if kind == "plain":
             plan.set_rc64(p["rc"])
             plan.set_fft(pkg.HSE_FFT_CUFFT)
+        if kind == "band":  # every pair at FP64-level accuracy: no FP32 shell
+            plan.set_rc64(p["rc"])
+            plan.set_rcmid(BAND_RCMID)
         plan.set_timing(True)
         steps = max(1, min(args.steps, args.leg_steps))
         ms, stages, launches = time_eval(torch, plan, ctx["src"], ctx["st"], ctx["vel"], ctx["flush"], ctx["stream"],
@@ -418,7 +431,7 @@ def run_leg(ctx, label, kind, p, tol):
     st_list, path = stage_roofline(model, stages, ctx["peaks"], ms)
     return {"value": whole_job_rate(n, ctx["world"], ms_max), "unit": "Mtargets/s", "ms_per_step": ms_max,
             "steps": steps, "arithmetic": ARITH[kind], "tol": tol, "xi": prm["xi"], "rc": prm["rc"],
-            "rc64": prm["rc64"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
+            "rc64": prm["rc64"], "rcmid": prm["rcmid"], "P": prm["P"], "M": prm["M"], "Mt": prm["Mt"],
             "fft": {0: "auto", 1: "cufft", 2: "df64"}.get(prm["fft"], prm["fft"]), "gpu_launches": launches,
             "stage_ms": {k: round(v, 3) for k, v in stages.items()}, "path_roofline_frac": round(path, 3),
             "stages_roofline": st_list}
@@ -622,6 +635,7 @@ def run_ours(args, rank, world, local_rank):
                check=check)
     if not args.no_plain:
         out["plain_fp64_1e-10"] = run_leg(ctx, "plain_fp64_1e-10", "plain", W, W["tol"])
+        out["df64_band_1e-10"] = run_leg(ctx, "df64_band_1e-10", "band", W, W["tol"])
     if not args.no_mixed:
         out["mixed_1e-5"] = run_leg(ctx, "mixed_1e-5", "mixed", MIXED, MIXED["tol"])
         out["fp64_1e-5"] = run_leg(ctx, "fp64_1e-5", "fp64", MIXED, MIXED["tol"])

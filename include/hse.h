@@ -109,6 +109,9 @@ typedef struct {
   size_t grid_bytes; /* device bytes held by grids and tables                      */
   int spread_tile[3];/* grid points along x, y, z that one warp of the spread owns   *
                       * (one per lane; product 32), see hse_plan_set_spread_tile   */
+  double rcmid;      /* HSE_FP64, targets = sources: pairs at distance in [rcmid,   *
+                      * min(rc64, rc)) are evaluated in double-float arithmetic    *
+                      * (hse_plan_set_rcmid); 0: none                              */
 } hse_params;
 
 /*
@@ -144,6 +147,17 @@ hse_status hse_plan_get_params(hse_plan plan, hse_params* out);
  * hse_params); rc64 >= rc evaluates everything in FP64.
  * HSE_ERR_INVALID for rc64 < 0 or an HSE_MIXED plan. */
 hse_status hse_plan_set_rc64(hse_plan plan, double rc64);
+/* Double-float band of the real-space sum (Sec. 5.1) of an HSE_FP64 plan with
+ * targets = sources: pairs at distance in [rcmid, min(rc64, rc)) are
+ * evaluated in double-float (~48-bit head/tail) arithmetic on the FP32 pipe by
+ * a second kernel instead of in FP64: relative error ~1e-11 per pair term
+ * (FP64 ~1e-15, the FP32 shell beyond rc64 ~1e-7) at a fraction of the cost,
+ * since GB300's FP64 pipe executes 2 multiply-adds per SM and clock against
+ * 128 on the FP32 pipe.  Pairs closer than rcmid, and pairs with an end point
+ * within 1/64 of their distance of the wall, stay in FP64.  rcmid = 0 (the
+ * default) or rcmid >= min(rc64, rc): no band.  HSE_ERR_INVALID for rcmid < 0
+ * or an HSE_MIXED plan. */
+hse_status hse_plan_set_rcmid(hse_plan plan, double rcmid);
 
 /* Choose the transforms of the Fourier part (HSE_FFT_AUTO, HSE_FFT_CUFFT or
  * HSE_FFT_DF64; hse_params.fft reports the choice).  Builds what the choice

@@ -12,7 +12,7 @@ void free_workspace(Workspace& w) {
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
   cudaFree(w.cell_start); cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr);
   cudaFree(w.prep); cudaFree(w.prep32); cudaFree(w.supp); cudaFree(w.flag); cudaFree(w.spos32); cudaFree(w.spos32lo);
-  cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
+  cudaFree(w.sstr32); cudaFree(w.sstr32lo); cudaFree(w.usort); cudaFree(w.usort4);
   if (w.flag_host) cudaFreeHost(w.flag_host);
   w = Workspace();
 }
@@ -39,13 +39,14 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   if (stride < w.prep_stride) stride = w.prep_stride;
   cudaFree(w.key_a); cudaFree(w.key_b); cudaFree(w.val_a); cudaFree(w.val_b);
   cudaFree(w.radix_hist); cudaFree(w.spos); cudaFree(w.sstr); cudaFree(w.prep); cudaFree(w.prep32); cudaFree(w.supp);
-  cudaFree(w.spos32); cudaFree(w.spos32lo); cudaFree(w.sstr32); cudaFree(w.usort); cudaFree(w.usort4);
+  cudaFree(w.spos32); cudaFree(w.spos32lo); cudaFree(w.sstr32); cudaFree(w.sstr32lo); cudaFree(w.usort);
+  cudaFree(w.usort4);
   w.usort = nullptr;
   w.usort4 = nullptr;
   w.key_a = w.key_b = w.val_a = w.val_b = w.radix_hist = w.supp = nullptr;
   w.spos = w.sstr = w.prep = nullptr;
   w.prep32 = nullptr;
-  w.spos32 = w.spos32lo = w.sstr32 = nullptr;
+  w.spos32 = w.spos32lo = w.sstr32 = w.sstr32lo = nullptr;
   w.cap = 0;
   int64_t ntiles = (cap + 2047) / 2048;
   HSE_CUDA(p, cudaMalloc(&w.key_a, sizeof(int32_t) * cap));
@@ -57,6 +58,7 @@ hse_status ensure_workspace(hse_plan p, int64_t n) {
   HSE_CUDA(p, cudaMalloc(&w.spos32, sizeof(float) * 3 * cap));
   HSE_CUDA(p, cudaMalloc(&w.spos32lo, sizeof(float) * 3 * cap));
   HSE_CUDA(p, cudaMalloc(&w.sstr32, sizeof(float) * 12 * cap));
+  HSE_CUDA(p, cudaMalloc(&w.sstr32lo, sizeof(float) * 12 * cap));
   HSE_CUDA(p, cudaMalloc(&w.usort, sizeof(double) * 3 * cap));
   HSE_CUDA(p, cudaMalloc(&w.usort4, sizeof(float4) * 2 * cap));  // partner sums, then their rounding errors
   HSE_CUDA(p, cudaMalloc(&w.sstr, sizeof(double) * 12 * cap));
@@ -219,7 +221,8 @@ __global__ void k_cell_start(const int32_t* __restrict__ key, int64_t n, int64_t
 
 __global__ void k_gather_sorted(int64_t n, int rows, const int32_t* __restrict__ perm, const double* __restrict__ pos,
                                 const double* __restrict__ str, double* __restrict__ spos, float* __restrict__ spos32,
-                                float* __restrict__ spos32lo, double* __restrict__ sstr, float* __restrict__ sstr32) {
+                                float* __restrict__ spos32lo, double* __restrict__ sstr, float* __restrict__ sstr32,
+                                float* __restrict__ sstr32lo) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = perm[i];
     for (int d = 0; d < 3; ++d) {
@@ -231,8 +234,10 @@ __global__ void k_gather_sorted(int64_t n, int rows, const int32_t* __restrict__
     }
     for (int r = 0; r < rows; ++r) {
       double v = str[r * n + j];
+      const float hi = (float)v;
       sstr[r * n + i] = v;
-      sstr32[r * n + i] = (float)v;
+      sstr32[r * n + i] = hi;
+      sstr32lo[r * n + i] = (float)(v - (double)hi);
     }
   }
 }
@@ -284,7 +289,8 @@ hse_status build_cell_list(hse_plan p, int64_t n, const double* pos, int32_t* ce
 hse_status gather_sorted(hse_plan p, int64_t n, const double* pos, const double* str, cudaStream_t s) {
   if (n == 0) return HSE_OK;
   k_gather_sorted<<<nblocks(n, 256), 256, 0, s>>>(n, str ? p->n_rows : 0, p->ws.val_a, pos, str, p->ws.spos,
-                                                   p->ws.spos32, p->ws.spos32lo, p->ws.sstr, p->ws.sstr32);
+                                                   p->ws.spos32, p->ws.spos32lo, p->ws.sstr, p->ws.sstr32,
+                                                   p->ws.sstr32lo);
   ++p->n_launch;
   return cuda_check(p, cudaGetLastError(), "k_gather_sorted");
 }

@@ -76,6 +76,18 @@ __device__ __forceinline__ df operator*(df a, float b) {
 __device__ __forceinline__ df operator*(float b, df a) { return a * b; }
 __device__ __forceinline__ df operator*(df a, int i) { return a * (float)i; }
 __device__ __forceinline__ df operator*(int i, df a) { return a * (float)i; }
+// a b + c (the real-space pair terms are written with fma(); for df64 they
+// take this double-float multiply-add).  The float and double overloads stay
+// visible inside the namespace.
+using ::fma;
+using ::fmaf;
+__device__ __forceinline__ df fma(df a, df b, df c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return c + df(p, e);
+}
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 __device__ __forceinline__ df& operator-=(df& a, df b) { return a = a - b; }
 

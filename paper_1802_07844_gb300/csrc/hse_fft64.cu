@@ -539,11 +539,27 @@ static unsigned grid_for(long long nlines, int lsh) {
   return (unsigned)(blocks < cap ? blocks : cap);
 }
 
+// Forward line passes run two radix-4 butterflies per thread and pass (N / 8
+// threads per line, two lines per block: half the warps wait at each barrier,
+// each with twice the independent work; measured 56.8 -> 55.2 ms for the
+// forward transforms of the 1M workload, while the inverse passes were 0.5 ms
+// slower that way and keep one butterfly per thread).
+static void line_shape(int N, bool fwd, int* tpl, int* lsh) {
+  if (fwd && N % 8 == 0) {
+    *tpl = N / 8;
+    *lsh = (*tpl << 1) <= kFftThreads ? 1 : 0;
+  } else {
+    *tpl = threads_per_line(N);
+    *lsh = lines_per_block_log2(N);
+  }
+}
+
 static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fwd, int nload, int nstore,
                             cudaStream_t s) {
   const Fft64Tables* t = tables(p);
-  const int lsh = lines_per_block_log2(t->sx.N);
-  const unsigned threads = (unsigned)(threads_per_line(t->sx.N) << lsh);
+  int tpl = 0, lsh = 0;
+  line_shape(t->sx.N, fwd, &tpl, &lsh);
+  const unsigned threads = (unsigned)(tpl << lsh);
   const size_t shm = sizeof(float4) * (3 * ((size_t)t->sx.N << lsh) + t->sx.N);  // three line buffers, twiddles
   if (geo.nlines <= 0) return HSE_OK;
   float4* c = reinterpret_cast<float4*>(buf);

@@ -115,6 +115,7 @@ struct Workspace {
   float* spos32 = nullptr;     // the same rounded to FP32 (head)
   float* spos32lo = nullptr;   // x - head, rounded to FP32 (tail)
   float* sstr32 = nullptr;     // sorted strengths in FP32 (mixed precision)
+  float* sstr32lo = nullptr;   // their tails: strength - head, in FP32 (double-float pairs)
   double* usort = nullptr;     // 3 x cap real-space sums in sorted order (symmetric kernel)
   float4* usort4 = nullptr;    // cap partner sums in FP32 (mixed-precision symmetric kernel)
   double* sstr = nullptr;      // rows x cap sorted strengths

@@ -664,6 +664,14 @@ extern "C" hse_status hse_plan_set_rc64(hse_plan p, double rc64) {
   return HSE_OK;
 }
 
+extern "C" hse_status hse_plan_set_rcmid(hse_plan p, double rcmid) {
+  if (!p) return HSE_ERR_INVALID;
+  if (!(rcmid >= 0.0) || p->prm.precision != HSE_FP64)
+    return set_err(p, HSE_ERR_INVALID, "rcmid needs an HSE_FP64 plan and rcmid >= 0");
+  p->prm.rcmid = rcmid;
+  return HSE_OK;
+}
+
 extern "C" hse_status hse_plan_set_fft(hse_plan p, int mode) {
   if (!p) return HSE_ERR_INVALID;
   if (mode != HSE_FFT_AUTO && mode != HSE_FFT_CUFFT && mode != HSE_FFT_DF64)

@@ -32,6 +32,7 @@
 //    with FP64 atomics.
 // Work split: one warp per target; passing candidates are compacted into a
 // per-warp queue and evaluated 32 at a time, so FP64 instructions run full warps.
+#include "hse_df64.cuh"
 #include "hse_internal.cuh"
 #include "special_tables.inc"
 
@@ -62,6 +63,10 @@ struct RealArgs {
   float img64_2;           // FP32 path: image pairs closer than this (squared) are evaluated in FP64
   float far2;              // FP64 symmetric kernel: pairs with FP32 distance^2 >= far2 take the
                            // FP32 evaluation (0: none)
+  float mid2;              // pairs with FP32 distance^2 in [mid2, far2) (or [mid2, r_c^2)) go to the
+                           // double-float kernel k_real_mid (0: none)
+  const float* sstr32lo;   // tails of the sorted strengths (double-float pairs with sstr32)
+  float2 dxi, dxi2, dkc, dk2, dk4;  // double-float constants xi, xi^2, 2 xi/sqrt(pi), 2 xi^2, 4 xi^4
   double inv_cell[3];
   int ncell[3];
   // batched instances: instance of each sorted particle (null: one instance)
@@ -74,7 +79,8 @@ __device__ __forceinline__ int cell_base(const RealArgs& a, int64_t sorted_idx) 
   return a.inst_of ? a.inst_of[sorted_idx] * a.ncells_inst : 0;
 }
 
-enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2, Q_FAR = 4 };  // Q_FAR: flag on FREE / IMAGE
+// Q_FAR: FP32 outer shell, Q_MID: double-float middle band (flags on FREE / IMAGE)
+enum { Q_FREE = 0, Q_IMAGE = 1, Q_SELF = 2, Q_FAR = 4, Q_MID = 8 };
 constexpr int kWarpsPerBlock = 4;
 constexpr int kQueue = 64;
 constexpr int kErfcxN = HSE_ERFCX_NINT * (HSE_ERFCX_DEG + 1);
@@ -421,7 +427,8 @@ template <> __device__ __forceinline__ const float* strengths_of<float>(const Re
 // cells below its image (image pairs), 32 candidates per step, with the
 // FP32 screen and the exact FP64 decision for the rest.  j_min bounds the
 // sorted source index from below (half list of the symmetric kernel).
-template <typename Visit>
+// MIDB: classify the double-float band (Q_MID); compiled out otherwise
+template <bool MIDB = false, typename Visit>
 __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* x, const float* xf, int64_t own,
                                                int lane, int free_min, int img_min, int base, Visit&& visit) {
   int cx = cell_coord(x[0], a.inv_cell[0], a.ncell[0]);
@@ -498,8 +505,11 @@ __device__ __forceinline__ void for_candidates(const RealArgs& a, const double* 
                 // of the wall: there the free and image contributions of a
                 // source cancel to O(height/rho), which would amplify rounding
                 const float hmin = fminf(xf[2], a.spos32[2 * n + j]);
-                const bool far = a.far2 > 0.0f && d2f >= a.far2 && 4096.0f * hmin * hmin >= d2f;
-                type = (pass == 0 ? Q_FREE : Q_IMAGE) | (far ? Q_FAR : 0);
+                const bool wall = 4096.0f * hmin * hmin < d2f;
+                const bool far = a.far2 > 0.0f && d2f >= a.far2 && !wall;
+                // double-float band [rcmid, rc64) (same FP32 decision in both kernels)
+                const bool mid = MIDB && !far && d2f >= a.mid2 && !wall;
+                type = (pass == 0 ? Q_FREE : Q_IMAGE) | (far ? Q_FAR : 0) | (mid ? Q_MID : 0);
               }
             }
           }
@@ -631,7 +641,8 @@ constexpr int real_min_blocks() {
   return sizeof(T) == 8 ? (KM != 3 && KM != 6 && KM != 7 ? 4 : 3) : 1;
 }
 
-template <typename T, int KM>
+// MID: the plan has a double-float band, whose pairs k_real_mid evaluates
+template <typename T, int KM, bool MID>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>()) k_real_sym(RealArgs a) {
   __shared__ int queue[kWarpsPerBlock][kQueue];
   __shared__ int queue_far[kWarpsPerBlock][kQueue];
@@ -750,10 +761,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>())
       }
     };
     float xf[3] = {x.h[0], x.h[1], x.h[2]};
-    for_candidates(a, x.d, xf, w, lane, (int)w + 1, (int)w, cell_base(a, w), [&](bool hit, int j, int type) {
-      const bool use = hit && type != Q_SELF;
+    for_candidates<MID>(a, x.d, xf, w, lane, (int)w + 1, (int)w, cell_base(a, w), [&](bool hit, int j, int type) {
+      // pairs of the double-float band are left to k_real_mid
+      const bool use = hit && type != Q_SELF && !(MID && (type & Q_MID));
       const bool far = use && (type & Q_FAR);
-      const int t = type & ~Q_FAR;
+      const int t = type & 1;
       unsigned m = __ballot_sync(0xffffffffu, use && !far);
       unsigned mf = __ballot_sync(0xffffffffu, far);
       const unsigned below = (1u << lane) - 1;
@@ -796,6 +808,213 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, real_min_blocks<T, KM>())
     }
   }
   if constexpr (sizeof(T) == 8) flush_pending();
+}
+
+// ------------------------------------------------------ double-float band
+// Pairs with distance in [rcmid, rc64) are evaluated in double-float (df64)
+// arithmetic on the FP32 pipe: ~1e-11 relative per term (the FP32 shell is
+// ~1e-7, FP64 ~1e-15), at a fraction of the FP64 pipe's cost.  Positions
+// enter as exact head differences plus tails (pair_vec_split), strengths as
+// FP32 heads plus tails; the radial functions are built from:
+//   1/rho   an FP32 estimate refined by one Newton step carried in df64;
+//   e^{-z}  z = xi^2 rho^2 in df64, z = m ln2/64 - r with a Cody-Waite split
+//           of ln2/64 (head of 12 bits: m ln2/64 is exact for |m| < 2^11),
+//           e^{-z} = 2^{m/64} e^{r}, 2^{j/64} from a float-pair table and
+//           e^{r} - 1 - r_head from its Taylor series in FP32 (|r| <= ln2/128);
+//   erfcx   the interval polynomials of the FP64 table: c0 + u (c1 + u c2)
+//           in df64, the higher terms (< 1e-4 of the sum) in FP32.
+constexpr float kLn2By64HeadF = 2839.0f / 262144.0f;  // ln2/64 rounded to 12 bits
+constexpr int kMidTab = 12;  // floats per erfcx interval: c0..c2 as pairs, c3..c8
+constexpr float kNegInvLn2By64 = 92.332482616893658f;  // 64 / ln2
+
+__device__ __forceinline__ df two_prod_f(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return df(p, fmaf(a, b, -p));
+}
+__device__ __forceinline__ df dfc(float2 v) { return df(v.x, v.y); }
+
+// the shared tables of k_real_mid: erfcx intervals (kMidTab floats each) and
+// 2^{j/64} as float pairs
+__device__ __forceinline__ void load_mid_tables(float* et, float2* t2) {
+  for (int i = threadIdx.x; i < HSE_ERFCX_NINT; i += blockDim.x) {
+    const double* c = d_erfcx_coef + i * (HSE_ERFCX_DEG + 1);
+    float* o = et + i * kMidTab;
+    for (int k = 0; k < 3; ++k) {
+      const float h = (float)c[k];
+      o[2 * k] = h;
+      o[2 * k + 1] = (float)(c[k] - (double)h);
+    }
+    for (int k = 3; k <= HSE_ERFCX_DEG; ++k) o[3 + k] = (float)c[k];
+  }
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    const float h = (float)d_exp2_j64[i];
+    t2[i] = make_float2(h, (float)(d_exp2_j64[i] - (double)h));
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ Radial<df> radial_mid(const df* r, const RealArgs& a, const float* et, const float2* t2,
+                                                 bool need_g3) {
+  // s = |r|^2
+  df s = r[0] * r[0];
+  s += r[1] * r[1];
+  s += r[2] * r[2];
+  // inv = 1/sqrt(s): y (1 + e/2), e = 1 - s y^2
+  const float y0 = rsqrtf(s.hi);
+  const df y2 = two_prod_f(y0, y0);
+  const float e = __fsub_rn(fmaf(-s.hi, y2.hi, 1.0f), fmaf(s.hi, y2.lo, __fmul_rn(s.lo, y2.hi)));
+  const df inv = df_fast_two_sum(y0, __fmul_rn(0.5f * y0, e));
+  // E = e^{-z}, z = xi^2 s
+  const df z = dfc(a.dxi2) * s;
+  const int m = __float2int_rn(-z.hi * kNegInvLn2By64);
+  const float rh = __fsub_rn(-z.hi, __fmul_rn((float)m, kLn2By64HeadF));  // exact
+  const float rl = __fsub_rn(-__fmul_rn((float)m, (float)(kLn2By64Head - (double)kLn2By64HeadF + kLn2By64Tail)),
+                             z.lo);
+  const float rr = __fadd_rn(rh, rl);
+  const float qt = fmaf(__fmul_rn(rr, rr), fmaf(rr, fmaf(rr, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f), rl);
+  const float2 tj = t2[m & 63];
+  const df p = two_prod_f(tj.x, rh);
+  const df eh = df_fast_two_sum(tj.x, p.hi);  // |p| <= ln2/128 of tj.x
+  df E = df_fast_two_sum(eh.hi, __fadd_rn(__fadd_rn(eh.lo, p.lo),
+                                          __fadd_rn(tj.y, fmaf(tj.x, qt, __fmul_rn(tj.y, rh)))));
+  const float sc = __int_as_float((127 + (m >> 6)) << 23);  // 2^floor(m/64), m >= -64 * 126
+  E = df(__fmul_rn(E.hi, sc), __fmul_rn(E.lo, sc));
+  // t = xi rho = xi s inv, erfcx(t)
+  const df t = dfc(a.dxi) * (s * inv);
+  int k = (int)(t.hi * (float)HSE_ERFCX_INV_WIDTH);
+  k = k < 0 ? 0 : (k > HSE_ERFCX_NINT - 1 ? HSE_ERFCX_NINT - 1 : k);
+  const float* c = et + k * kMidTab;
+  const float uh = __fmul_rn(__fsub_rn(t.hi, (float)(2 * k + 1) * (0.5f / HSE_ERFCX_INV_WIDTH)),
+                             2.0f * HSE_ERFCX_INV_WIDTH);  // exact
+  const float ul = __fmul_rn(t.lo, 2.0f * HSE_ERFCX_INV_WIDTH);
+  float tail = c[3 + HSE_ERFCX_DEG];
+#pragma unroll
+  for (int j = HSE_ERFCX_DEG - 1; j >= 3; --j) tail = fmaf(tail, uh, c[3 + j]);
+  tail = __fmul_rn(tail, __fmul_rn(__fmul_rn(uh, uh), uh));
+  tail = fmaf(ul, fmaf(2.0f * c[4], uh, c[2]), tail);  // P'(u) ul
+  const df h1 = (df(c[2], c[3]) + df(c[4], c[5]) * uh) * uh;
+  const df ex = (df(c[0], c[1]) + h1) + df(tail, 0.f);
+  Radial<df> R;
+  const df i2 = inv * inv;
+  R.c = dfc(a.dkc) * E;
+  R.er = (E * ex) * inv;
+  R.a1 = (R.er + R.c) * i2;
+  R.g2 = i2 * fma(df(3.0f, 0.f), R.a1, dfc(a.dk2) * R.c);
+  R.g3 = need_g3 ? -(i2 * fma(df(5.0f, 0.f), R.g2, dfc(a.dk4) * R.c)) : df(0.f, 0.f);
+  return R;
+}
+
+template <int KM>
+__device__ __forceinline__ void load_src_df(const RealArgs& a, int64_t j, Src<df>& s) {
+  const int64_t n = a.n_src;
+  auto ld = [&](int row) { return df(a.sstr32[row * n + j], a.sstr32lo[row * n + j]); };
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { s.f[i] = df(0.f, 0.f); s.g[i] = s.f[i]; s.q[i] = s.f[i]; s.tau[i] = s.f[i]; }
+  if (KM & HSE_STOKESLET)
+    for (int i = 0; i < 3; ++i) s.f[i] = ld(a.rowS + i);
+  if (KM & HSE_STRESSLET)
+    for (int i = 0; i < 3; ++i) { s.g[i] = ld(a.rowT + i); s.q[i] = ld(a.rowT + 3 + i); }
+  if (KM & HSE_ROTLET)
+    for (int i = 0; i < 3; ++i) s.tau[i] = ld(a.rowW + i);
+}
+
+// Symmetric kernel of the double-float band (targets = sources; the same
+// half list, cell scan and pair classification as k_real_sym, which skips
+// these pairs): the target's sums go to a.out (FP64 atomics, one per
+// component and target), the partner's share to the FP32 partner sums a.out4
+// with the exact rounding error of each atomic and the double-float tail in
+// a.out4lo.
+template <int KM>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real_mid(RealArgs a) {
+  __shared__ int queue[kWarpsPerBlock][kQueue];
+  __shared__ float et[HSE_ERFCX_NINT * kMidTab];
+  __shared__ float2 t2[64];
+  load_mid_tables(et, t2);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int* qu = queue[wib];
+  const int64_t n = a.n_src;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  const bool need_g3 = KM & HSE_STRESSLET;
+  const df xid = dfc(a.dxi);
+  float4 pend_old = make_float4(0.f, 0.f, 0.f, 0.f), pend_v = pend_old, pend_lo = pend_old;
+  int64_t pend_j = -1;
+  auto flush_pending = [&]() {
+    if (pend_j >= 0) {
+      float s0, e0, e1, e2;
+      two_sum(pend_old.x, pend_v.x, s0, e0);
+      two_sum(pend_old.y, pend_v.y, s0, e1);
+      two_sum(pend_old.z, pend_v.z, s0, e2);
+      atomicAdd(a.out4lo + pend_j,
+                make_float4(__fadd_rn(e0, pend_lo.x), __fadd_rn(e1, pend_lo.y), __fadd_rn(e2, pend_lo.z), 0.f));
+      pend_j = -1;
+    }
+  };
+  for (int64_t w = blockIdx.x * (int64_t)kWarpsPerBlock + wib; w < n; w += nwarps) {
+    TgtPos x;
+    for (int d = 0; d < 3; ++d) {
+      x.d[d] = a.spos[d * n + w];
+      x.h[d] = a.spos32[d * n + w];
+      x.l[d] = a.spos32lo[d * n + w];
+    }
+    const df x3 = df_norm(df(x.h[2], x.l[2]));
+    Src<df> sp;
+    load_src_df<KM>(a, w, sp);
+    df u[3] = {df(0.f, 0.f), df(0.f, 0.f), df(0.f, 0.f)};
+    int cnt = 0;
+    auto run = [&](int e) {
+      const int j = e & 0x1fffffff, type = e >> 29;
+      Src<df> s;
+      load_src_df<KM>(a, j, s);
+      float rf[3], dh[3], dl[3], hf;
+      pair_vec_split(a, x, j, type == Q_IMAGE, dh, dl, rf, &hf);
+      df r[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) r[d] = df_norm(df(dh[d], dl[d]));
+      const df h = df_norm(df(a.spos32[2 * n + j], a.spos32lo[2 * n + j]));
+      const Radial<df> R = radial_mid(r, a, et, t2, need_g3);
+      df v[3] = {df(0.f, 0.f), df(0.f, 0.f), df(0.f, 0.f)};
+      if (type == Q_FREE) {
+        add_free<df>(KM, R, r, s, xid, df(1.0f, 0.f), u);
+        add_free<df>(KM, R, r, sp, xid, df(-1.0f, 0.f), v);
+      } else {
+        add_image<df>(KM, R, r, h, x3, s, xid, u);
+        if (j != w) {
+          const df rp[3] = {-r[0], -r[1], r[2]};
+          add_image<df>(KM, R, rp, x3, h, sp, xid, v);
+        }
+      }
+      flush_pending();
+      if (type == Q_FREE || j != w) {
+        pend_v = make_float4(v[0].hi, v[1].hi, v[2].hi, 0.f);
+        pend_lo = make_float4(v[0].lo, v[1].lo, v[2].lo, 0.f);
+        pend_old = atomicAdd(a.out4 + j, pend_v);
+        pend_j = j;
+      }
+    };
+    float xf[3] = {x.h[0], x.h[1], x.h[2]};
+    for_candidates<true>(a, x.d, xf, w, lane, (int)w + 1, (int)w, cell_base(a, w), [&](bool hit, int j, int type) {
+      const bool use = hit && type != Q_SELF && (type & Q_MID);
+      const unsigned m = __ballot_sync(0xffffffffu, use);
+      if (use) qu[cnt + __popc(m & ((1u << lane) - 1))] = j | ((type & 1) << 29);
+      cnt += __popc(m);
+      __syncwarp();
+      if (cnt >= 32) {
+        run(qu[lane]);
+        __syncwarp();
+        if (lane < cnt - 32) qu[lane] = qu[32 + lane];
+        cnt -= 32;
+        __syncwarp();
+      }
+    });
+    if (lane < cnt) run(qu[lane]);
+    __syncwarp();
+    for (int i = 0; i < 3; ++i) {
+      double ud = (double)u[i].hi + (double)u[i].lo;
+      for (int off = 16; off > 0; off >>= 1) ud += __shfl_xor_sync(0xffffffffu, ud, off);
+      if (lane == 0) atomicAdd(a.out + i * n + w, ud);
+    }
+  }
+  flush_pending();
 }
 
 // caller order: out[orig(i)] = sorted[i] (+ the FP32 partner sums, if any)
@@ -933,21 +1152,70 @@ static RealArgs make_args(hse_plan p, int64_t n_src, int64_t n_tgt, const double
   for (int d = 0; d < 3; ++d) { a.inv_cell[d] = p->inv_cell[d]; a.ncell[d] = p->prm.ncell[d]; }
   a.inst_of = nullptr;
   a.ncells_inst = p->prm.ncell[0] * p->prm.ncell[1] * p->prm.ncell[2];
+  a.mid2 = 0.0f;
+  a.sstr32lo = p->ws.sstr32lo;
+  auto split = [](double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  };
+  const double xi = p->prm.xi;
+  a.dxi = split(xi);
+  a.dxi2 = split(xi * xi);
+  a.dkc = split(2.0 * xi / kSqrtPi);
+  a.dk2 = split(2.0 * xi * xi);
+  a.dk4 = split(4.0 * xi * xi * xi * xi);
   return a;
 }
 
-// symmetric kernel specialised on the kernel bits (1..7)
+// symmetric kernel specialised on the kernel bits (1..7) and on the
+// double-float band (FP64 plans only)
+template <typename T, bool MID>
+static void launch_real_sym_t(int mask, int blocks, const RealArgs& a, cudaStream_t s) {
+  switch (mask & 7) {
+    case 1: k_real_sym<T, 1, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 2: k_real_sym<T, 2, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 3: k_real_sym<T, 3, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 4: k_real_sym<T, 4, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 5: k_real_sym<T, 5, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    case 6: k_real_sym<T, 6, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+    default: k_real_sym<T, 7, MID><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+  }
+}
 template <typename T>
 static void launch_real_sym(int mask, int blocks, const RealArgs& a, cudaStream_t s) {
-  switch (mask & 7) {
-    case 1: k_real_sym<T, 1><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
-    case 2: k_real_sym<T, 2><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
-    case 3: k_real_sym<T, 3><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
-    case 4: k_real_sym<T, 4><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
-    case 5: k_real_sym<T, 5><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
-    case 6: k_real_sym<T, 6><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
-    default: k_real_sym<T, 7><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a); break;
+  if constexpr (sizeof(T) == 8) {
+    if (a.mid2 > 0.0f) {
+      launch_real_sym_t<T, true>(mask, blocks, a, s);
+      return;
+    }
   }
+  launch_real_sym_t<T, false>(mask, blocks, a, s);
+}
+
+template <int KM>
+static void launch_real_mid_t(int blocks, const RealArgs& a, cudaStream_t s) {
+  k_real_mid<KM><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);
+}
+static void launch_real_mid(int mask, int blocks, const RealArgs& a, cudaStream_t s) {
+  switch (mask & 7) {
+    case 1: launch_real_mid_t<1>(blocks, a, s); break;
+    case 2: launch_real_mid_t<2>(blocks, a, s); break;
+    case 3: launch_real_mid_t<3>(blocks, a, s); break;
+    case 4: launch_real_mid_t<4>(blocks, a, s); break;
+    case 5: launch_real_mid_t<5>(blocks, a, s); break;
+    case 6: launch_real_mid_t<6>(blocks, a, s); break;
+    default: launch_real_mid_t<7>(blocks, a, s); break;
+  }
+}
+
+// FP64 plans: the double-float band [rcmid, min(rc64, rc)) of the symmetric
+// kernel (k_real_mid); false when the plan has none
+static bool mid_band(hse_plan p, RealArgs& a) {
+  const double hi = std::fmin(p->prm.rc64 > 0.0 ? p->prm.rc64 : p->prm.rc, p->prm.rc);
+  const double lo = p->prm.rcmid;
+  if (p->prm.precision != HSE_FP64 || !(lo > 0.0) || lo >= hi) return false;
+  a.mid2 = (float)(lo * lo);
+  return true;
 }
 
 // FP64 plans: enable the FP32 outer shell [rc64, rc) of the symmetric kernel
@@ -992,16 +1260,28 @@ hse_status real_space(hse_plan p, int64_t n_src, int64_t n_tgt, const double* tg
       }
     } else {
       HSE_CUDA(p, cudaMemsetAsync(a.out, 0, sizeof(double) * 3 * n_tgt, s));
-      if (shell32(p, a)) {
+      const bool shell = shell32(p, a), mid = mid_band(p, a);
+      if (shell || mid) {
         a.out4lo = a.out4 + n_tgt;
         HSE_CUDA(p, cudaMemsetAsync(a.out4, 0, sizeof(float4) * 2 * n_tgt, s));
       }
       launch_real_sym<double>(a.mask, sym_blocks(p, n_tgt), a, s);
+      if (mid) {
+        // the band's kernel scans only the cells within min(rc64, rc)
+        RealArgs am = a;
+        const double hi = std::fmin(p->prm.rc64 > 0.0 ? p->prm.rc64 : p->prm.rc, p->prm.rc);
+        const double lmax = std::fmax(p->prm.box[0], std::fmax(p->prm.box[1], p->prm.box[2]));
+        const double rcull = hi + 1e-5 * lmax;
+        am.cull2 = (float)(rcull * rcull);
+        HSE_CUDA(p, cudaGetLastError());
+        launch_real_mid(a.mask, sym_blocks(p, n_tgt), am, s);
+        ++p->n_launch;
+      }
     }
     HSE_CUDA(p, cudaGetLastError());
     int64_t b = (n_tgt + 255) / 256;
     k_unsort<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(
-        n_tgt, p->ws.val_a, p->ws.usort, (mixed || a.far2 > 0.0f) ? p->ws.usort4 : nullptr, a.out4lo, out);
+        n_tgt, p->ws.val_a, p->ws.usort, (mixed || a.out4lo) ? p->ws.usort4 : nullptr, a.out4lo, out);
     ++p->n_launch;
   } else {
     if (mixed) k_real<float><<<warp_blocks(n_tgt), kWarpsPerBlock * 32, 0, s>>>(a);

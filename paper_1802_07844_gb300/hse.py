@@ -29,6 +29,7 @@ class hse_params(ctypes.Structure):
         ("M", ctypes.c_int), ("Mt", ctypes.c_int), ("h", ctypes.c_double), ("eta", ctypes.c_double),
         ("ncell", ctypes.c_int * 3), ("n_fft_in", ctypes.c_int), ("n_fft_out", ctypes.c_int),
         ("fft", ctypes.c_int), ("grid_bytes", ctypes.c_size_t), ("spread_tile", ctypes.c_int * 3),
+        ("rcmid", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -97,7 +98,7 @@ class HseError(RuntimeError):
 
 
 _lib = None
-_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_set_fft", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
+_NAMES = ("hse_plan_create", "hse_plan_set_grid", "hse_plan_set_rc64", "hse_plan_set_rcmid", "hse_plan_set_fft", "hse_plan_get_params", "hse_eval", "hse_eval_parts",
           "hse_cell_list", "hse_neighbor_counts", "hse_spread_grids", "hse_plan_destroy", "hse_status_string",
           "hse_last_error", "hse_plan_set_timing", "hse_plan_set_overlap", "hse_plan_set_real_residency", "hse_plan_set_spread_tile", "hse_get_eval_stats", "hse_cell_list_noalloc",
           "hse_server_create", "hse_server_submit", "hse_server_poll", "hse_server_wait", "hse_server_get_stats",
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
     L.hse_plan_set_grid.argtypes = [vp, ctypes.c_int]
     L.hse_plan_set_rc64.argtypes = [vp, ctypes.c_double]
+    L.hse_plan_set_rcmid.argtypes = [vp, ctypes.c_double]
     L.hse_plan_set_fft.argtypes = [vp, ctypes.c_int]
     L.hse_plan_get_params.argtypes = [vp, ctypes.POINTER(hse_params)]
     L.hse_eval.argtypes = [vp, i64, dp, dp, i64, dp, dp, vp]
@@ -191,6 +193,10 @@ def hse_plan_set_rc64(plan, rc64):
     """FP64 plans: pairs closer than rc64 in FP64, the shell [rc64, rc) in FP32
     (rc64 >= rc: FP64 throughout)."""
     _check(load().hse_plan_set_rc64(plan, float(rc64)), plan)
+
+
+def hse_plan_set_rcmid(plan, rcmid):
+    _check(load().hse_plan_set_rcmid(plan, float(rcmid)), plan)
 
 
 def hse_plan_set_fft(plan, mode):
@@ -498,6 +504,10 @@ class Plan:
 
     def set_rc64(self, rc64):
         hse_plan_set_rc64(self.handle, rc64)
+        self.params = hse_plan_get_params(self.handle)
+
+    def set_rcmid(self, rcmid):
+        hse_plan_set_rcmid(self.handle, rcmid)
         self.params = hse_plan_get_params(self.handle)
 
     def set_grid(self, M):

@@ -138,6 +138,33 @@ def test_full_eval_any_tile_equals_default(pkg, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("mask", [KERNEL_S, KERNEL_T, KERNEL_W, KERNEL_S | KERNEL_W, KERNEL_S | KERNEL_T | KERNEL_W])
+def test_double_float_band_matches_fp64_pairs(pkg, mask):
+    """Pairs in the double-float band [rcmid, min(rc64, rc)) evaluated on the
+    FP32 pipe agree with their FP64 evaluation to ~1e-13 of the velocity, with
+    and without an FP32 shell beyond rc64; the band's partners, own images and
+    near-wall pairs (kept in FP64) all go through the same sums."""
+    pr = problem(mask, 20000, 1.0, "near_wall", 39)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=30.0, rc=0.16, P=0, tol=1e-10)  # P, M from tol
+    src, st = dev(pr.src), dev(pr.strengths)
+    for rc64 in (0.16, 0.1):
+        plan.set_rc64(rc64)
+        plan.set_rcmid(0.0)
+        ref = host(plan.eval_parts(src, st, fourier=False)[0])
+        for rcmid in (0.02, 0.05):
+            plan.set_rcmid(rcmid)
+            assert plan.params["rcmid"] == rcmid
+            u = host(plan.eval_parts(src, st, fourier=False)[0])
+            assert oracle.rel_rms(u, ref) < 1e-12, (rc64, rcmid)
+    with pytest.raises(pkg.HseError):
+        plan.set_rcmid(-1.0)
+    plan.close()
+    mixed = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=30.0, rc=0.16, P=0, tol=1e-5, precision=pkg.HSE_MIXED)
+    with pytest.raises(pkg.HseError):
+        mixed.set_rcmid(0.05)
+    mixed.close()
+
+
 # ------------------------------------------------------- real space (Sec. 5.1)
 @pytest.mark.parametrize("mask", MASKS)
 @pytest.mark.parametrize("dist", ["uniform", "near_wall"])
