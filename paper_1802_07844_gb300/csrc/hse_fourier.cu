@@ -782,8 +782,10 @@ static PrepArgs<T> prep_args(hse_plan p, int64_t n, int paper, int ncomp) {
   a.stride = a.lay.stride;
   a.prep = reinterpret_cast<T*>(p->ws.prep);
   // 8-byte grids split small window weights to FP32 unless an FP64 plan asks
-  // for FP64 throughout (rc64 >= rc)
-  const bool split = sizeof(T) == 8 && !paper && (q.precision == HSE_MIXED || q.rc64 < q.rc);
+  // for FP64 throughout (rc64 >= rc and no double-float band); the split's
+  // error (a few 1e-14 relative) is far below any band's
+  const bool split = sizeof(T) == 8 && !paper &&
+                     (q.precision == HSE_MIXED || q.rc64 < q.rc || (q.rcmid > 0.0 && q.rcmid < q.rc));
   a.prep32 = split ? p->ws.prep32 : nullptr;
   a.supp = reinterpret_cast<int4*>(p->ws.supp);
   return a;
