@@ -635,10 +635,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_real(RealArgs a) {
 // Resident blocks per SM the FP64 symmetric kernel is compiled for: 4 (128
 // registers) where the pair arithmetic fits without spilling, which keeps 16
 // warps per SM issuing to the FP64 pipe; the masks with two strength tensors need
-// more registers (3 blocks, up to 170).
+// more registers (3 blocks, up to 170).  The FP32 kernel is latency-bound
+// (candidate scans and float4 atomics): 6 blocks (80 registers, 24 warps per
+// SM) where it fits without spilling, 5 for S+T and 4 for S+T+W; measured on
+// the N = 1M S+W workload at tol 1e-5, 21.7 ms at 4 blocks (109 registers)
+// against 18.9 ms at 6.
 template <typename T, int KM>
 constexpr int real_min_blocks() {
-  return sizeof(T) == 8 ? (KM != 3 && KM != 6 && KM != 7 ? 4 : 3) : 1;
+  return sizeof(T) == 8 ? (KM != 3 && KM != 6 && KM != 7 ? 4 : 3) : (KM == 7 ? 4 : (KM == 3 ? 5 : 6));
 }
 
 // MID: the plan has a double-float band, whose pairs k_real_mid evaluates
