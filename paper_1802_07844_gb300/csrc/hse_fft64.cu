@@ -17,7 +17,7 @@
 //
 // Each pass is a batched 1-D transform of lines.  A block holds LPB lines in
 // shared memory (element e of line l at e * LPB + l) and runs a mixed-radix
-// Stockham autosort transform over them (radices 4, 2, 5, 3), alternating
+// Stockham autosort transform over them (radices 8, 4, 2, 5, 3), alternating
 // between two shared buffers so that each radix pass needs one barrier; the
 // twiddle table sits in shared memory, and the line passes queue the next
 // line set's loads (cp.async) into a third buffer before transforming the
@@ -42,23 +42,26 @@ struct FftSteps {
   int Ns[kMaxPass];      // product of the earlier radices
   int step[kMaxPass];    // N / (Ns R): twiddle index step
   unsigned magic[kMaxPass];  // ceil(2^32 / Ns) (exact j / Ns for j, Ns < 2^16)
-  float kc[10];          // hi / lo of sin(2pi/3), cos(2pi/5), cos(4pi/5), sin(2pi/5), sin(4pi/5)
+  float kc[12];          // hi / lo of sin(2pi/3), cos(2pi/5), cos(4pi/5), sin(2pi/5), sin(4pi/5), cos(pi/4)
 };
 
 // two_first: the first pass has radix 2 (used for inputs whose upper half is
 // zero: that pass reduces to a copy, done while loading)
 // two_last: the last pass has radix 2 (used for inverse lines of which only
 // the first half is kept: that pass then computes one output per butterfly)
-static bool make_steps(int N, FftSteps* st, bool two_first = false, bool two_last = false) {
+// eight: radix 8 where 8 divides the rest (the line passes' schedules for
+// N / 8 threads per line; the z passes keep radix 4)
+static bool make_steps(int N, FftSteps* st, bool two_first = false, bool two_last = false, bool eight = false) {
   if (N < 2 || N >= 65536 || ((two_first || two_last) && N % 2 != 0) || (two_first && two_last && N % 4 != 0))
     return false;
   FftSteps s{};
   s.N = N;
   int rem = N, Ns = 1;
   while (rem > 1) {
-    int R = rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 5 == 0 ? 5 : rem % 3 == 0 ? 3 : 0;
+    int R = eight && rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 5 == 0 ? 5 : rem % 3 == 0 ? 3 : 0;
     if (two_first && s.npass == 0) R = 2;
     if (two_last) {  // keep one factor 2 for the end
+      if (R == 8 && (rem / 8) % 2 != 0) R = 4;  // radix 8 only while a factor 2 remains after it
       if (rem == 2) R = 2;
       else if (R == 4 && (rem / 4) % 2 != 0) R = (rem / 2) % 2 == 0 ? 2 : (rem % 5 == 0 ? 5 : (rem % 3 == 0 ? 3 : 2));
       else if (R == 2 && rem != 2 && (rem / 2) % 2 != 0) R = rem % 5 == 0 ? 5 : (rem % 3 == 0 ? 3 : 0);
@@ -72,9 +75,9 @@ static bool make_steps(int N, FftSteps* st, bool two_first = false, bool two_las
     Ns *= R;
     rem /= R;
   }
-  const double c[5] = {std::sin(2 * M_PI / 3), std::cos(2 * M_PI / 5), std::cos(4 * M_PI / 5), std::sin(2 * M_PI / 5),
-                       std::sin(4 * M_PI / 5)};
-  for (int i = 0; i < 5; ++i) {
+  const double c[6] = {std::sin(2 * M_PI / 3), std::cos(2 * M_PI / 5), std::cos(4 * M_PI / 5), std::sin(2 * M_PI / 5),
+                       std::sin(4 * M_PI / 5), std::sqrt(0.5)};
+  for (int i = 0; i < 6; ++i) {
     float h = (float)c[i];
     s.kc[2 * i] = h;
     s.kc[2 * i + 1] = (float)(c[i] - (double)h);
@@ -152,6 +155,28 @@ __device__ __forceinline__ void dft5(cdf* v, const float* kc) {
   v[3] = out<NORM>(sub_raw(a2, b2));
 }
 
+// radix 8 as two radix-4 DFTs of the even and odd inputs: X_k = E_k + w8^k O_k,
+// X_{k+4} = E_k - w8^k O_k, with w8 = (1 -+ i) / sqrt(2), w8^2 = -+i and
+// w8^3 = w8^2 w8 (upper signs forward); w8 O = (O + w8^2 O) / sqrt(2)
+template <bool FWD, bool NORM>
+__device__ __forceinline__ void dft8(cdf* v, const float* kc) {
+  const df c(kc[10], kc[11]);
+  cdf e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<FWD, false>(e);
+  dft4<FWD, false>(o);
+  const cdf p1 = scale_raw(c, add_raw(o[1], mul_mi<FWD>(o[1])));
+  const cdf p2 = mul_mi<FWD>(o[2]);
+  const cdf p3 = mul_mi<FWD>(scale_raw(c, add_raw(o[3], mul_mi<FWD>(o[3]))));
+  v[0] = out<NORM>(add_raw(e[0], o[0]));
+  v[4] = out<NORM>(sub_raw(e[0], o[0]));
+  v[1] = out<NORM>(add_raw(e[1], p1));
+  v[5] = out<NORM>(sub_raw(e[1], p1));
+  v[2] = out<NORM>(add_raw(e[2], p2));
+  v[6] = out<NORM>(sub_raw(e[2], p2));
+  v[3] = out<NORM>(add_raw(e[3], p3));
+  v[7] = out<NORM>(sub_raw(e[3], p3));
+}
+
 template <bool FWD>
 __device__ __forceinline__ cdf twiddle(const float4* __restrict__ tw, int idx) {
   const cdf w = ld_cdf(tw + idx);  // shared-memory copy of the table
@@ -181,6 +206,7 @@ __device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, in
     }
     if (R == 2) dft2<FWD, NORM>(v);
     else if (R == 4) dft4<FWD, NORM>(v);
+    else if (R == 8) dft8<FWD, NORM>(v, kc);
     else if (R == 3) dft3<FWD, NORM>(v, kc);
     else dft5<FWD, NORM>(v, kc);
     const int d = q * Ns * R + k;
@@ -193,7 +219,7 @@ __device__ __forceinline__ void stockham_pass(const float4* src, float4* dst, in
 // input); returns the buffer that holds the result, in natural order.  The
 // schedule lives in device memory (uniform loads) so the pass loop can index
 // it freely.
-template <bool FWD>
+template <bool FWD, bool R8 = false>  // R8: schedules may hold radix-8 passes
 __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const FftSteps* __restrict__ st, int lsh,
                                                    const float4* __restrict__ tw, int p0 = 0, int p_end = -1) {
   const int tpl = blockDim.x >> lsh;
@@ -207,6 +233,9 @@ __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const F
     if (p == npass - 1) {  // the last pass stores normalised values
       switch (st->R[p]) {
         case 4: stockham_pass<4, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        case 8:
+          if constexpr (R8) stockham_pass<8, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw);
+          break;
         case 2: stockham_pass<2, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
         case 5: stockham_pass<5, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
         default: stockham_pass<3, FWD, true>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
@@ -214,6 +243,9 @@ __device__ __forceinline__ float4* transform_block(float4* a, float4* b, const F
     } else {
       switch (st->R[p]) {
         case 4: stockham_pass<4, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
+        case 8:
+          if constexpr (R8) stockham_pass<8, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw);
+          break;
         case 2: stockham_pass<2, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
         case 5: stockham_pass<5, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
         default: stockham_pass<3, FWD, false>(a, b, N, Ns, step, magic, kc, tpl, lsh, l, tj, tw); break;
@@ -255,6 +287,7 @@ __device__ __forceinline__ void last_pass_store(const float4* src, float4* __res
     }
     if (R == 2) dft2<FWD, true>(v);
     else if (R == 4) dft4<FWD, true>(v);
+    else if (R == 8) dft8<FWD, true>(v, kc);
     else if (R == 3) dft3<FWD, true>(v, kc);
     else dft5<FWD, true>(v, kc);
 #pragma unroll
@@ -370,10 +403,13 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_fft_lines(float4
     // all passes but the last in shared memory; the last one stores to global
     const int p0 = half ? 1 : 0, pl = st->npass - 1;
     if (pl >= p0) {
-      const float4* res = transform_block<FWD>(sm + cur * n, sm + scr * n, st, lsh, stw, p0, pl);
+      const float4* res = transform_block<FWD, true>(sm + cur * n, sm + scr * n, st, lsh, stw, p0, pl);
       const int step = st->step[pl];
       switch (st->R[pl]) {
         case 4: last_pass_store<4, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
+        case 8:
+          last_pass_store<8, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw);
+          break;
         case 2: last_pass_store<2, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
         case 5: last_pass_store<5, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
         default: last_pass_store<3, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
@@ -491,9 +527,9 @@ hse_status fft64_prepare(hse_plan p) {
   Fft64Tables* t = new Fft64Tables();
   make_steps(g.Nx, &t->sx);
   make_steps(g.Nz / 2, &t->sz);
-  make_steps(g.Nx, &t->sxh, true);
+  make_steps(g.Nx, &t->sxh, true, false, g.Nx % 8 == 0);  // forward line passes (N / 8 threads per line)
   make_steps(g.Nz / 2, &t->szh, true);
-  if (!make_steps(g.Nx, &t->sxl, false, true)) t->sxl = t->sx;
+  if (!make_steps(g.Nx, &t->sxl, false, true, g.Nx % 8 == 0)) t->sxl = t->sx;
   const int n1 = g.Nx, nh = g.Nz / 2;
   cudaError_t e = cudaMalloc(&t->tw, sizeof(float4) * (n1 + nh + 2 * nh));
   if (e != cudaSuccess) {
@@ -539,13 +575,18 @@ static unsigned grid_for(long long nlines, int lsh) {
   return (unsigned)(blocks < cap ? blocks : cap);
 }
 
-// Forward line passes run two radix-4 butterflies per thread and pass (N / 8
-// threads per line, two lines per block: half the warps wait at each barrier,
-// each with twice the independent work; measured 56.8 -> 55.2 ms for the
-// forward transforms of the 1M workload, while the inverse passes were 0.5 ms
-// slower that way and keep one butterfly per thread).
-static void line_shape(int N, bool fwd, int* tpl, int* lsh) {
-  if (fwd && N % 8 == 0) {
+// Line passes of lengths divisible by 8 run N / 8 threads per line, two lines
+// per block, with radix-8 passes where the schedule allows (one radix-8
+// butterfly per thread and pass, one pass through shared memory and one
+// barrier where two radix-4 passes would take two): at N = 640 the forward
+// schedule is 2 (the load's copy), 8, 8, 5 and the inverse 8, 8, 5, 2 instead
+// of 2, 4, 4, 4, 5 and 4, 4, 4, 5, 2.  Measured on the 1M workload: forward
+// 55.1 -> 54.0 ms, inverse 31.9 -> 31.1 ms (with radix-4 passes the N / 8
+// shape had taken the forward transforms from 56.8 to 55.2 ms, and made the
+// inverse 0.5 ms slower).  Other lengths keep one radix-4 (or radix-2)
+// butterfly per thread.
+static void line_shape(int N, int* tpl, int* lsh) {
+  if (N % 8 == 0) {
     *tpl = N / 8;
     *lsh = (*tpl << 1) <= kFftThreads ? 1 : 0;
   } else {
@@ -558,7 +599,7 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
                             cudaStream_t s) {
   const Fft64Tables* t = tables(p);
   int tpl = 0, lsh = 0;
-  line_shape(t->sx.N, fwd, &tpl, &lsh);
+  line_shape(t->sx.N, &tpl, &lsh);
   const unsigned threads = (unsigned)(tpl << lsh);
   const size_t shm = sizeof(float4) * (3 * ((size_t)t->sx.N << lsh) + t->sx.N);  // three line buffers, twiddles
   if (geo.nlines <= 0) return HSE_OK;
