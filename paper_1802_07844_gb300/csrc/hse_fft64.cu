@@ -49,8 +49,8 @@ struct FftSteps {
 // zero: that pass reduces to a copy, done while loading)
 // two_last: the last pass has radix 2 (used for inverse lines of which only
 // the first half is kept: that pass then computes one output per butterfly)
-// eight: radix 8 where 8 divides the rest (the line passes' schedules for
-// N / 8 threads per line; the z passes keep radix 4)
+// eight: radix 8 where 8 divides the rest (the schedules of wide line passes,
+// see line_shape; the z passes keep radix 4)
 static bool make_steps(int N, FftSteps* st, bool two_first = false, bool two_last = false, bool eight = false) {
   if (N < 2 || N >= 65536 || ((two_first || two_last) && N % 2 != 0) || (two_first && two_last && N % 4 != 0))
     return false;
@@ -88,6 +88,8 @@ static bool make_steps(int N, FftSteps* st, bool two_first = false, bool two_las
 
 // threads per line: one radix-4 butterfly each when 4 | N, else one radix-2
 static int threads_per_line(int N) { return N % 4 == 0 ? N / 4 : N / 2; }
+// "wide" line passes: N / 8 threads per line and radix-8 schedules (line_shape)
+static bool wide_lines(int N) { return N % 8 == 0 && N >= 512; }
 
 // block shape: at most kFftThreads threads, kFftMinBlocks resident per SM
 // (register budget); compile-time tuning knobs
@@ -371,7 +373,7 @@ __device__ __forceinline__ void queue_set(const float4* data, const LineGeo& g, 
 // A block loops over line sets with three shared buffers: the set being
 // transformed, its scratch buffer, and the next set, whose loads are queued
 // (cp.async) before the current set's passes run.
-// WIDE: the N / 8 shape (radix-8 butterflies; blocks of N / 4 threads, whose
+// WIDE: wide lines (radix-8 butterflies; blocks of N / 4 threads, whose
 // residency the three line buffers in shared memory set): up to 128 registers
 // (measured on the 1M workload: forward 54.3 -> 52.9 ms, inverse 31.2 -> 30.8
 // ms against 64); other shapes keep the 64-register bound of their blocks of
@@ -408,12 +410,12 @@ __global__ void __launch_bounds__(kFftThreads, WIDE ? 1 : kFftMinBlocks) k_fft_l
     // all passes but the last in shared memory; the last one stores to global
     const int p0 = half ? 1 : 0, pl = st->npass - 1;
     if (pl >= p0) {
-      const float4* res = transform_block<FWD, true>(sm + cur * n, sm + scr * n, st, lsh, stw, p0, pl);
+      const float4* res = transform_block<FWD, WIDE>(sm + cur * n, sm + scr * n, st, lsh, stw, p0, pl);
       const int step = st->step[pl];
       switch (st->R[pl]) {
         case 4: last_pass_store<4, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
         case 8:
-          last_pass_store<8, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw);
+          if constexpr (WIDE) last_pass_store<8, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw);
           break;
         case 2: last_pass_store<2, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
         case 5: last_pass_store<5, FWD>(res, data, sc, g.es, N, step, st->kc, lsh, nstore, stw); break;
@@ -532,9 +534,9 @@ hse_status fft64_prepare(hse_plan p) {
   Fft64Tables* t = new Fft64Tables();
   make_steps(g.Nx, &t->sx);
   make_steps(g.Nz / 2, &t->sz);
-  make_steps(g.Nx, &t->sxh, true, false, g.Nx % 8 == 0);  // forward line passes (N / 8 threads per line)
+  make_steps(g.Nx, &t->sxh, true, false, wide_lines(g.Nx));  // forward line passes
   make_steps(g.Nz / 2, &t->szh, true);
-  if (!make_steps(g.Nx, &t->sxl, false, true, g.Nx % 8 == 0)) t->sxl = t->sx;
+  if (!make_steps(g.Nx, &t->sxl, false, true, wide_lines(g.Nx))) t->sxl = t->sx;
   const int n1 = g.Nx, nh = g.Nz / 2;
   cudaError_t e = cudaMalloc(&t->tw, sizeof(float4) * (n1 + nh + 2 * nh));
   if (e != cudaSuccess) {
@@ -582,18 +584,21 @@ static unsigned grid_for(long long nlines, int lsh) {
   return (unsigned)(blocks < cap ? blocks : cap);
 }
 
-// Line passes of lengths divisible by 8 run N / 8 threads per line, two lines
-// per block, with radix-8 passes where the schedule allows (one radix-8
-// butterfly per thread and pass, one pass through shared memory and one
-// barrier where two radix-4 passes would take two): at N = 640 the forward
-// schedule is 2 (the load's copy), 8, 8, 5 and the inverse 8, 8, 5, 2 instead
-// of 2, 4, 4, 4, 5 and 4, 4, 4, 5, 2.  Measured on the 1M workload: forward
-// 55.1 -> 54.0 ms, inverse 31.9 -> 31.1 ms (with radix-4 passes the N / 8
-// shape had taken the forward transforms from 56.8 to 55.2 ms, and made the
-// inverse 0.5 ms slower).  Other lengths keep one radix-4 (or radix-2)
-// butterfly per thread.
-static void line_shape(int N, int* tpl, int* lsh) {
-  if (N % 8 == 0) {
+// Line passes of lengths N >= 512 divisible by 8 ("wide" lines) run N / 8
+// threads per line, two lines per block, with radix-8 passes where the
+// schedule allows (one radix-8 butterfly per thread and pass, one pass through
+// shared memory and one barrier where two radix-4 passes would take two): at
+// N = 640 the forward schedule is 2 (the load's copy), 8, 8, 5 and the inverse
+// 8, 8, 5, 2 instead of 2, 4, 4, 4, 5 and 4, 4, 4, 5, 2.  Measured on the 1M
+// workload: forward 55.1 -> 54.0 ms, inverse 31.9 -> 31.1 ms.  Shorter lines
+// divisible by 8 keep radix 4 and N / 8 threads per line forward (two
+// butterflies per thread and pass: 56.8 -> 55.2 ms for the forward transforms
+// of the 1M workload when that was measured) and N / 4 inverse: at N = 288 or
+// 320 the N / 8 shape gives blocks of 72-80 threads, and the N = 1e5
+// workloads' inverse transforms were slower with it.  Other lengths run one
+// radix-4 (or radix-2) butterfly per thread.
+static void line_shape(int N, bool fwd, int* tpl, int* lsh) {
+  if (N % 8 == 0 && (fwd || wide_lines(N))) {
     *tpl = N / 8;
     *lsh = (*tpl << 1) <= kFftThreads ? 1 : 0;
   } else {
@@ -606,7 +611,7 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
                             cudaStream_t s) {
   const Fft64Tables* t = tables(p);
   int tpl = 0, lsh = 0;
-  line_shape(t->sx.N, &tpl, &lsh);
+  line_shape(t->sx.N, fwd, &tpl, &lsh);
   const unsigned threads = (unsigned)(tpl << lsh);
   const size_t shm = sizeof(float4) * (3 * ((size_t)t->sx.N << lsh) + t->sx.N);  // three line buffers, twiddles
   if (geo.nlines <= 0) return HSE_OK;
@@ -615,7 +620,7 @@ static hse_status run_lines(hse_plan p, double* buf, const LineGeo& geo, bool fw
   // forward passes read a zero upper half: the radix-2-first schedule; inverse
   // passes keeping the first half: the radix-2-last schedule
   const FftSteps* st = t->d_steps + (fwd ? 2 : (2 * nstore == t->sx.N ? 4 : 0));
-  const bool wide = t->sx.N % 8 == 0;  // line_shape's N / 8 shape
+  const bool wide = wide_lines(t->sx.N);
   if (fwd && wide) k_fft_lines<true, true><<<grid, threads, shm, s>>>(c, geo, st, lsh, t->tw, nload, nstore);
   else if (fwd) k_fft_lines<true, false><<<grid, threads, shm, s>>>(c, geo, st, lsh, t->tw, nload, nstore);
   else if (wide) k_fft_lines<false, true><<<grid, threads, shm, s>>>(c, geo, st, lsh, t->tw, nload, nstore);
