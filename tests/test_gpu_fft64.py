@@ -1,7 +1,8 @@
 """Double-float (df64) transforms of the FP64 Fourier part (Sec. 4 steps
 FFT - scale - IFFT) against cuFFT double on the same plan and inputs: every
 kernel mask, line lengths with radices 4, 2, 5 and 3 (including lengths not
-divisible by 4), the fallback to cuFFT for lengths with other prime factors,
+divisible by 4), the wide line passes with radix 8 (512, 576 and 640 points),
+the fallback to cuFFT for lengths with other prime factors,
 and the mode switch rules.  Both runs share the spread and the gather, so the
 comparison isolates the transforms and the scaling."""
 import numpy as np
@@ -70,6 +71,21 @@ def test_df64_bench_shape(pkg):
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=87.0, rc=0.0552, P=18, tol=0.0, M=302)
     u, ref = fourier_both(pkg, plan, pr)
     assert rel(u, ref) < 1e-12
+    plan.close()
+
+
+@pytest.mark.parametrize("M", [238, 270])
+def test_df64_wide_lines(pkg, M):
+    # lines of 512 and 576 points (Mt = 256, 288) take the wide line passes
+    # (N / 8 threads per line, radix 8): forward 2.8.8.4 and 2.8.4.3.3,
+    # inverse 8.8.4.2 and 8.4.3.3.2
+    mask = KERNEL_S | KERNEL_W
+    pr = problem(mask, 20000, 1.0, "near_wall", 80 + M % 7)
+    plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=87.0, rc=0.0552, P=18, tol=0.0, M=M)
+    assert plan.params["Mt"] == M + 18
+    u, ref = fourier_both(pkg, plan, pr)
+    assert rel(u, ref) < 1e-12
+    assert float(np.abs(u - ref).max() / np.abs(ref).max()) < 1e-12
     plan.close()
 
 
