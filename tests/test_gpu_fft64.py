@@ -65,7 +65,8 @@ def test_df64_matches_cufft(pkg, mask, M):
 
 
 def test_df64_bench_shape(pkg):
-    # the benchmark's line length (Mt = 320: 640 = 4.4.4.2.5) at a reduced count
+    # the benchmark's line length (Mt = 320: 640 points, wide passes forward
+    # 2.8.8.5, inverse 8.8.5.2) at a reduced count
     mask = KERNEL_S | KERNEL_W
     pr = problem(mask, 20000, 1.0, "near_wall", 79)
     plan = pkg.Plan(mask, (1.0, 1.0, 1.0), xi=87.0, rc=0.0552, P=18, tol=0.0, M=302)
