@@ -572,8 +572,12 @@ __device__ __forceinline__ void scale_point(const ScaleArgs<T>& a, int64_t e, co
   if (a.nout == 4) a.buf[3 * a.cstride + e] = cmk<CT>((T)ph.x, (T)ph.y);
 }
 
+// 4 resident blocks of 256 threads per SM (64 registers): the pass streams the
+// 7 input and 4 output spectra, and the extra warps keep more loads in flight
+// (measured on the 1M workload: 9.84 -> 8.93 ms against the 72-register build
+// at 3 blocks)
 template <typename T>
-__global__ void k_scale(ScaleArgs<T> a) {
+__global__ void __launch_bounds__(256, 4) k_scale(ScaleArgs<T> a) {
   typedef typename Cplx<T>::type C;
   const int Mt = a.Mt, Nx = 2 * Mt, Ny = 2 * Mt, Nzh = 2 * Mt + 1;
   const int64_t nh = (int64_t)Nx * Ny * Nzh;
