@@ -147,7 +147,9 @@ def fft_buffer_work(Mt: int, e: int):
 def stage_model(kind: str, prm: dict, n: int, rows: int, pairs: dict):
     """Per stage: (algorithmic HBM bytes, {pipe: flops}) of one evaluation.
     kind: 'fp64' (FP64 pairs within rc64, FP32 shell, df64 Fourier part),
-    'plain' (every pair in FP64, FP64 grids, cuFFT double), 'mixed' (FP32).
+    'plain' (every pair in FP64, FP64 grids, cuFFT double), 'band' (FP64
+    pairs within rcmid, double-float pairs beyond, df64 Fourier part),
+    'mixed' (FP32).
     pairs: flops of the FP64 and FP32 real-space pairs."""
     Mt, P, nin, nout = prm["Mt"], prm["P"], prm["n_fft_in"], prm["n_fft_out"]
     e = 4 if kind == "mixed" else 8

@@ -41,6 +41,33 @@ def test_pair_flops():
     assert bench.pair_flops(0, 2, 0) == bench.FLOPS_RADIAL + 2 * bench.FLOPS_IMAGE_DIR
 
 
+def test_pair_flops_split_by_kind():
+    # counts (ordered free, ordered image, own images) by cut-off, as the
+    # count-only plan would return them; nothing here touches a GPU
+    pc = bench.PairCounter(None, 0, None, None)
+    pc.cache = {0.05: (1000, 300, 10), 0.02: (100, 40, 6), 0.004: (8, 4, 2)}
+    total = bench.pair_flops(1000, 300, 10)
+    inner = bench.pair_flops(100, 40, 6)
+    mid = bench.pair_flops(8, 4, 2)
+    prm = {"rc": 0.05, "rc64": 0.02, "rcmid": 0.004}
+    assert pc.flops("mixed", prm) == {"fp32": total}
+    assert pc.flops("plain", prm) == {"fp64": total}
+    assert pc.flops("fp64", prm) == {"fp64": inner, "fp32": total - inner}
+    assert pc.flops("band", prm) == {"fp64": mid, "df64": total - mid}
+    # an FP64 plan without a shell (rc64 >= rc) counts every pair on the FP64 pipe
+    assert pc.flops("fp64", dict(prm, rc64=0.05)) == {"fp64": total}
+
+
+def test_stage_model_band():
+    prm = {"Mt": 16, "P": 8, "n_fft_in": 7, "n_fft_out": 4, "rc": 0.1, "rc64": 0.1}
+    m = bench.stage_model("band", prm, 1000, 6, {"fp64": 1.0, "df64": 2.0})
+    f = bench.stage_model("fp64", prm, 1000, 6, {"fp64": 1.0, "fp32": 2.0})
+    assert set(m["real"][1]) == {"fp64", "df64"} and set(m["fft"][1]) == {"df64"}
+    # the band changes only the real-space pipes: the Fourier part is the FP64 plan's
+    for st in ("spread", "fft", "scale", "ifft", "gather"):
+        assert m[st] == f[st]
+
+
 def test_stage_roofline_path_fraction():
     peaks = {"hbm_gbs": 1000.0, "fp64_tflops": 1.0, "fp32_tflops": 64.0, "df64_tflops": 8.0}
     model = {"a": (1e9, {}),                      # 1 ms of HBM
